@@ -1,0 +1,324 @@
+#!/usr/bin/env python
+"""Benchmark: explicit finite-volume sweep on GB300 (arXiv 2209.13768, Sec. 4.1).
+
+Default workload: one 512^3 grid, fp32 field, per-cell conductivity
+k ~ lognormal(0, 0.5), x faces Dirichlet 1 / 0, y and z zero-flux,
+dt = 0.9 x the stability limit; one benchmark step = one 1000-step solve
+(every time step of the sweep, fused `depth` steps per pass over the grid).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line. `value` is cell-updates/s (in GLUPS) with the inputs
+resident in HBM (device-side CUDA events, max over ranks); `e2e` is the same
+metric through the C ABI from pinned host buffers (field and conductivity in,
+result out, copies inside the timed region). Multi-GPU runs are independent
+replicas (weak scaling): the sweep of one grid is a single-GPU problem here.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s (GLUPS) and % HBM roofline on 1 GB300; serving p50/p99 latency"
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+KERNEL_SOURCES = ["paper_2209_13768_gb300/csrc/wfa_sweep.cuh", "paper_2209_13768_gb300/csrc/wfa_internal.cuh"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["lognormal", "heat64", "advdiff", "advdiff_bf16"], default="lognormal")
+    ap.add_argument("--solve-steps", type=int, default=0, help="time steps per benchmark step (0: workload default)")
+    ap.add_argument("--depth", type=int, default=0, help="fused steps per pass (0: tuned)")
+    ap.add_argument("--variant", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def workload(name, solve_steps):
+    from paper_2209_13768_gb300 import workloads as W
+    if name == "lognormal":
+        p = W.heat_lognormal()
+    elif name == "heat64":
+        p = W.heat_64()
+    else:
+        p = W.advection_diffusion()
+    if solve_steps:
+        p.steps = solve_steps
+    return p
+
+
+def bytes_per_cell(storage_bf16, kvar):
+    """Algorithmic HBM bytes per cell per pass: read + write of the field,
+    plus one read of k (Eq. A_eff = 2 D_u + D_k)."""
+    e = 2 if storage_bf16 else 4
+    return 2 * e + (4 if kvar else 0)
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_rate(p, budget_s):
+    """The oracle as it stands, on this host's cores, on a bounded sample of
+    the workload (a few time steps of the same grid)."""
+    import numpy as np
+
+    import oracle
+    k = p.k if isinstance(p.k, float) else np.asarray(p.k, dtype=np.float64)
+    dt = p.dt if p.dt else 0.9 * oracle.dt_max(shape=p.shape, h=p.h, k=k, u=p.u, bc=p.bc)
+    T = np.asarray(p.T0, dtype=np.float64)
+    cells = p.shape[0] * p.shape[1] * p.shape[2]
+    t0 = time.perf_counter()
+    T = oracle.run(T, 1, shape=p.shape, h=p.h, k=k, u=p.u, bc=p.bc, dt=dt)
+    one = time.perf_counter() - t0
+    n = max(1, min(50, int(budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.run(T, n, shape=p.shape, h=p.h, k=k, u=p.u, bc=p.bc, dt=dt)
+    el = time.perf_counter() - t0
+    return {"value": cells * n / el / 1e9, "unit": "GLUPS", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} fp64 time steps of the {p.shape[0]}x{p.shape[1]}x{p.shape[2]} grid "
+                      f"({p.name}), OpenMP over all host cores, after 1 warm-up step"}
+
+
+def reference_arm(args, rank):
+    """--impl reference: the FP64 oracle on the host cores, same metric/config."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    p = workload(args.workload, args.solve_steps)
+    k = p.k if isinstance(p.k, float) else np.asarray(p.k, dtype=np.float64)
+    dt = p.dt if p.dt else 0.9 * oracle.dt_max(shape=p.shape, h=p.h, k=k, u=p.u, bc=p.bc)
+    T = np.asarray(p.T0, dtype=np.float64)
+    cells = p.shape[0] * p.shape[1] * p.shape[2]
+    per_step = 1   # each benchmark step: one time step of the grid (bounded sample)
+    for _ in range(args.warmup):
+        T = oracle.run(T, per_step, shape=p.shape, h=p.h, k=k, u=p.u, bc=p.bc, dt=dt)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        T = oracle.run(T, per_step, shape=p.shape, h=p.h, k=k, u=p.u, bc=p.bc, dt=dt)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = cells * per_step * args.steps / total / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": p.name, "cells": cells, "sample": f"{per_step} time step per benchmark step"},
+            "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{per_step} fp64 time step of the full grid per benchmark step"},
+            "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_2209_13768_gb300 as wfa
+    from paper_2209_13768_gb300 import build as wfa_build
+    wfa_build.build()
+
+    p = workload(args.workload, args.solve_steps)
+    storage = wfa.BF16 if args.workload == "advdiff_bf16" else wfa.F32
+    kvar = not np.isscalar(p.k)
+    cells = p.shape[0] * p.shape[1] * p.shape[2]
+    stream = torch.cuda.Stream()
+    g = wfa.Grid(p.shape, h=p.h, storage=storage, stream=stream.cuda_stream)
+    g.set_bcs(p.bc)
+    g.set_coeffs(p.k, p.u)
+    g.set_field(p.T0)
+    dt = p.dt if p.dt else 0.9 * g.stability_dt()
+    g.set_dt(dt)
+    g.set_tuning(args.depth, args.variant)
+    depth = args.depth or (2 if kvar else 4)
+    launches_per_step = math.ceil(p.steps / depth)
+
+    for _ in range(args.warmup):
+        g.step(p.steps)
+    g.sync()
+
+    sampler = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        g.step(p.steps)
+        ev[i][1].record(stream)
+    g.sync()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * cells * p.steps * args.steps / total_s / 1e9
+
+    # roofline of the dominant kernel (the tiled sweep): algorithmic bytes per
+    # launch (read T, read k, write T once per pass) over its mean duration
+    launch_s = total_s / (args.steps * launches_per_step)
+    bpc = bytes_per_cell(storage == wfa.BF16, kvar)
+    achieved = bpc * cells / launch_s / 1e9
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    traffic = None
+    try:
+        with open(TRAFFIC_FILE) as f:
+            tr = json.load(f)
+        key = f"{args.workload}:{'bf16' if storage else 'f32'}:{'k' if kvar else 'u'}:d{depth}"
+        ent = tr.get(key)
+        if ent and ent.get("kernel_hash") == kernel_hash():
+            traffic = ent["bytes_per_launch"]
+    except (OSError, ValueError):
+        pass
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "bytes_per_cell_per_launch": bpc, "steps_per_launch": depth,
+                "effective_GBps_paper_Teff": bpc * depth * cells / launch_s / 1e9}
+
+    # end to end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        T0h = torch.from_numpy(np.ascontiguousarray(p.T0)).pin_memory()
+        kh = torch.from_numpy(np.ascontiguousarray(p.k)).pin_memory() if kvar else None
+        outh = torch.empty(tuple(p.T0.shape), dtype=torch.float32).pin_memory()
+        nrep = max(1, min(args.steps, 3))
+        e2e_t = []
+        for i in range(nrep + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.set_field(T0h)
+            g.set_coeffs(kh if kvar else p.k, p.u)
+            g.set_dt(dt)
+            g.step(p.steps)
+            g.read_field(outh)
+            if i:   # first one is a warm-up
+                e2e_t.append(time.perf_counter() - t0)
+        e2e_s = sum(e2e_t) / len(e2e_t)
+        if dist:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * cells * p.steps / e2e_s / 1e9, "unit": "GLUPS",
+               "h2d_bytes_per_step": cells * 4 * (2 if kvar else 1), "d2h_bytes_per_step": cells * 4,
+               "ms_per_step": 1e3 * e2e_s}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_rate(p, args.cpu_seconds)
+
+    g.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if storage else "f32", "data": "synthetic",
+                "config": {"workload": p.name, "cells": cells, "time_steps_per_step": p.steps, "depth": depth,
+                           "dt": dt, "storage": "bf16" if storage else "f32",
+                           "conductivity": "per-cell lognormal(0,0.5)" if kvar else f"uniform {p.k}",
+                           "l2": "inputs larger than L2 (%.0f MiB field)" % (cells * (2 if storage else 4) / 2**20),
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": args.steps * launches_per_step, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

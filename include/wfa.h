@@ -1,0 +1,210 @@
+/*
+ * wfa.h — C ABI of the GB300 explicit finite-volume field-equation library.
+ *
+ * The library advances a scalar field T on a 3D structured grid with the
+ * explicit (forward-time) finite-volume update of arXiv 2209.13768, Sec. 1.1.1
+ * (Eq. expl_form), written in conservative face-flux form so that it also
+ * covers per-cell conductivity (harmonic-mean face conductivity) and
+ * first-order upwind advection with a constant velocity:
+ *
+ *   T'_C = T_C + dt * [ sum_f K_f (T_D - T_C) / h_a^2  +  sum_a (F_a- - F_a+) / h_a ]
+ *   K_f  = 2 k_C k_D / (k_C + k_D)                  (interior face)
+ *   F    = max(u_a,0) T_lower + min(u_a,0) T_upper   (upwind face flux)
+ *
+ * With uniform k, no advection and the boundary cells held at a constant this
+ * is exactly the paper's T' = w sum_{D in N(C)} T_D + (1 - 6w) T_C,
+ * w = alpha dt / dl^2. Heat capacity is 1, so alpha = k.
+ *
+ * Conventions for every entry point:
+ *   - returns WFA_OK (0) or a negative wfa_status; nothing is thrown across
+ *     the ABI; wfa_last_error() gives a message for the calling thread;
+ *   - host buffers belong to the caller and are copied before the call
+ *     returns (reads) or filled before it returns (writes);
+ *   - device memory belongs to the grid handle and is freed by
+ *     wfa_destroy_grid;
+ *   - work is queued on the CUDA stream given at creation; calls that hand
+ *     data back to the host synchronise that stream;
+ *   - a handle is not thread-safe; distinct handles on distinct streams are.
+ *
+ * Host arrays are dense, x fastest: element (x, y, z) is at x + nx*(y + ny*z).
+ */
+#ifndef WFA_H
+#define WFA_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wfa_grid_s* wfa_grid;
+
+enum wfa_status {
+    WFA_OK = 0,
+    WFA_ERR_ARG = -1,      /* bad argument (null pointer, size, enum value)          */
+    WFA_ERR_OOM = -2,      /* device or pinned-host allocation failed                */
+    WFA_ERR_BC = -3,       /* inconsistent boundary conditions                       */
+    WFA_ERR_UNSTABLE = -4, /* dt above the stability (positivity) limit              */
+    WFA_ERR_CUDA = -5,     /* a CUDA call failed; the message names it               */
+    WFA_ERR_TIMEOUT = -6,  /* a device-side wait gave up after its iteration limit   */
+    WFA_ERR_STATE = -7,    /* call out of order (e.g. step before field / dt is set) */
+    WFA_ERR_BUDGET = -8    /* request larger than the server's memory budget         */
+};
+
+enum wfa_storage { WFA_F32 = 0, WFA_BF16 = 1 };
+
+enum wfa_bc_kind {
+    WFA_BC_DIRICHLET = 0,      /* value on the boundary face, half a cell from the centre */
+    WFA_BC_ZEROFLUX = 1,       /* no diffusive and no advective flux through the face     */
+    WFA_BC_PERIODIC = 2,       /* must be set on both faces of an axis                    */
+    WFA_BC_DIRICHLET_CELL = 3  /* outer cell layer held at the value (Eq. expl_form, C in bc) */
+};
+
+enum wfa_face { WFA_XLO = 0, WFA_XHI = 1, WFA_YLO = 2, WFA_YHI = 3, WFA_ZLO = 4, WFA_ZHI = 5 };
+
+/* ---------------------------------------------------------------- grids -- */
+
+/* Create a grid of nx*ny*nz cells of size hx*hy*hz (Sec. 1.1, control volumes;
+ * Sec. 2.1, uniform Cartesian grid). storage: WFA_F32 or WFA_BF16 (field stored
+ * in bf16, arithmetic in fp32, rounded to nearest-even after every step).
+ * cuda_stream: a cudaStream_t (NULL = the legacy default stream).
+ * Each edge must be >= 2 and the cell count <= 2^40. Boundary faces start as
+ * zero-flux; the field starts at 0. Errors: WFA_ERR_ARG, WFA_ERR_OOM, WFA_ERR_CUDA. */
+int wfa_create_grid(int nx, int ny, int nz, double hx, double hy, double hz, int storage,
+                    void* cuda_stream, wfa_grid* out);
+
+/* Free the handle and its device memory (synchronises its stream). NULL is a no-op. */
+int wfa_destroy_grid(wfa_grid g);
+
+/* Copy a dense host field (nx*ny*nz floats) in (Sec. 2.1: T_init -> WSE_Array).
+ * bf16 grids round each value to nearest-even. Held boundary layers
+ * (WFA_BC_DIRICHLET_CELL) are overwritten with their value at the next step. */
+int wfa_set_field(wfa_grid g, const float* host_dense);
+
+/* Conductivity and velocity (Eq. diff_eq with alpha = k; constant advection).
+ * k_host: nx*ny*nz floats, >= 0 and finite, or NULL to use k_uniform (>= 0).
+ * u: constant velocity in length units per time unit.
+ * Errors: WFA_ERR_ARG for a negative or non-finite value. */
+int wfa_set_coeffs(wfa_grid g, const float* k_host, double k_uniform, double ux, double uy,
+                   double uz);
+
+/* Boundary condition of one face (enum wfa_face). value: the face value for
+ * WFA_BC_DIRICHLET, the held cell value for WFA_BC_DIRICHLET_CELL (which needs
+ * an edge >= 3 on that axis), ignored otherwise. A periodic face whose
+ * opposite face is not periodic makes the next wfa_step fail with WFA_ERR_BC. */
+int wfa_set_bc(wfa_grid g, int face, int kind, double value);
+
+/* Largest stable time step, computed on the device in fp64:
+ * dt_max = 1 / max_C D_C over the cells that are not held, where D_C sums the
+ * face conductances / h^2 (2 k_C / h^2 on a Dirichlet face, 0 on a zero-flux
+ * face) and |u_a| / h_a for each outflow face that carries flux; every weight
+ * of the update is then >= 0 (Sec. 1.1.1: stable for omega < 1/6).
+ * Writes +inf when nothing couples. Synchronises the stream. Needs the
+ * coefficients (WFA_ERR_STATE otherwise). */
+int wfa_stability_dt(wfa_grid g, double* dt_max);
+
+/* Set the time step. dt must be > 0 and <= dt_max (WFA_ERR_UNSTABLE otherwise). */
+int wfa_set_dt(wfa_grid g, double dt);
+
+/* Force a kernel configuration instead of the tuned one.
+ * depth: time steps fused per pass over the grid (1..8; 0 = automatic).
+ * variant: 0 = automatic, 1..2 = one of the compiled tile shapes of the
+ * tiled TMA kernel, -1 = the one-thread-per-column kernel (one step per
+ * pass; a second, independent realisation of the same per-cell arithmetic).
+ * Results do not depend on the choice: every kernel evaluates the same fixed
+ * per-cell expression, so fields are bit-identical. */
+int wfa_set_tuning(wfa_grid g, int depth, int variant);
+
+/* Advance n >= 0 time steps (asynchronous on the grid's stream).
+ * Errors: WFA_ERR_STATE before the field, coefficients and dt are set,
+ * WFA_ERR_BC for an unpaired periodic face, WFA_ERR_CUDA. */
+int wfa_step(wfa_grid g, long long n);
+
+/* Number of steps taken since the last wfa_set_field. */
+int wfa_steps_done(wfa_grid g, long long* n);
+
+/* Copy the field out as dense fp32 (nx*ny*nz floats). Synchronises the stream. */
+int wfa_read_field(wfa_grid g, float* host_dense);
+
+/* Total heat E = sum_C T_C hx hy hz, summed on the device in fp64 in a fixed
+ * order (bit-reproducible for a given grid). Synchronises the stream.
+ * Sec. 3, reduction of a field to one value. */
+int wfa_total_heat(wfa_grid g, double* e);
+
+/* Wait for the grid's queued work; reports a device-side error. */
+int wfa_sync(wfa_grid g);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* wfa_last_error(void);
+
+/* ----------------------------------------------------------- batching -- */
+
+/* Advance many grids in one go (Sec. 4.1.2: iteration rate at small
+ * workloads per processor). gs[i] advances steps[i] >= 0 steps. All grids must
+ * share the stream of gs[0] and have their field, coefficients and dt set.
+ * The steps run as one CUDA-graph launch of a persistent multi-grid kernel
+ * whose blocks take (grid, tile, round) work items in dependency order.
+ * Results are bitwise identical to calling wfa_step on each grid. */
+int wfa_batch_run(wfa_grid* gs, const long long* steps, int count);
+
+/* ------------------------------------------------------------- serving -- */
+
+typedef struct wfa_server_s* wfa_server;
+
+/* A transient solve submitted to the server. The server copies every input
+ * before wfa_server_submit returns; out_host must stay valid until the
+ * ticket is done. dt <= 0 selects 0.9 * dt_max. */
+typedef struct {
+    int nx, ny, nz;
+    double hx, hy, hz;
+    int storage;              /* WFA_F32 / WFA_BF16 */
+    const float* T0_host;     /* nx*ny*nz */
+    const float* k_host;      /* nx*ny*nz, or NULL for k_uniform */
+    double k_uniform;
+    double ux, uy, uz;
+    int bc_kind[6];
+    double bc_value[6];
+    double dt;
+    long long steps;
+    float* out_host;          /* nx*ny*nz, written when the ticket is done */
+} wfa_request;
+
+typedef struct {
+    long long submitted, admitted, completed, rejected;
+    long long ticks;           /* scheduler iterations that launched work */
+    double cell_updates;       /* total cell-updates performed */
+    double busy_seconds;       /* wall time with work on the device */
+    double p50_latency_s, p99_latency_s, mean_latency_s;  /* submit -> result on host */
+    size_t resident_bytes, peak_resident_bytes;
+} wfa_server_stats;
+
+/* Start a continuous-batching server on its own scheduler thread.
+ * hbm_budget_bytes: admission limit on the device memory of resident
+ * requests; max_resident: most requests on the device at once (0 = 1024);
+ * quantum: steps each resident request advances per scheduler tick (0 = 64).
+ * Requests that arrive while others run are admitted at the next tick as
+ * memory and slots free up; all resident requests advance together in one
+ * batched launch per tick. */
+int wfa_server_create(size_t hbm_budget_bytes, int max_resident, long long quantum,
+                      wfa_server* out);
+
+/* Queue a request; *ticket identifies it. WFA_ERR_BUDGET if it can never fit. */
+int wfa_server_submit(wfa_server s, const wfa_request* r, long long* ticket);
+
+/* *done = 1 once out_host holds the result (0 while queued or running;
+ * -1 if the request failed, with the reason in wfa_last_error()). */
+int wfa_server_poll(wfa_server s, long long ticket, int* done);
+
+/* Block until the ticket is done or timeout_s passes (WFA_ERR_TIMEOUT). */
+int wfa_server_wait(wfa_server s, long long ticket, double timeout_s);
+
+int wfa_server_stats_get(wfa_server s, wfa_server_stats* st);
+
+/* Stop the scheduler (finishing resident work first) and free everything. */
+int wfa_server_destroy(wfa_server s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WFA_H */

@@ -1,0 +1,676 @@
+// Grid handles, field transfer (pack / unpack), halo maintenance and the fp64
+// reductions (total heat, stability limit) behind the C ABI in include/wfa.h.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <cmath>
+#include <new>
+
+#include "wfa_internal.cuh"
+
+namespace wfa {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    set_error("%s failed: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? WFA_ERR_OOM : WFA_ERR_CUDA;
+}
+
+static int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+// ------------------------------------------------------------ coefficients --
+int build_coef(const wfa_grid_s* g, SweepCoef* c) {
+    memset(c, 0, sizeof *c);
+    for (int a = 0; a < 3; ++a) c->n[a] = g->n[a];
+    c->sy = g->px;
+    c->sz = g->px * g->py;
+    const double dt = g->dt;
+    for (int a = 0; a < 3; ++a) {
+        const int lo = g->bc_kind[2 * a], hi = g->bc_kind[2 * a + 1];
+        if ((lo == WFA_BC_PERIODIC) != (hi == WFA_BC_PERIODIC))
+            return fail(WFA_ERR_BC, "axis %d: a periodic face needs a periodic opposite face", a);
+        if ((lo == WFA_BC_DIRICHLET_CELL || hi == WFA_BC_DIRICHLET_CELL) && g->n[a] < 3)
+            return fail(WFA_ERR_BC, "axis %d: held boundary cells need an edge >= 3", a);
+        c->periodic[a] = lo == WFA_BC_PERIODIC;
+        const double h = g->h[a];
+        const double cd = dt / (h * h);
+        const double ap = dt * (g->u[a] > 0 ? g->u[a] : 0.0) / h;   // -face inflow weight
+        const double am = dt * (g->u[a] < 0 ? -g->u[a] : 0.0) / h;  // +face inflow weight
+        c->cd[a] = (float)cd;
+        c->adv[2 * a] = (float)ap;
+        c->adv[2 * a + 1] = (float)am;
+        c->w_in[2 * a] = (float)(g->k_uniform * cd + ap);
+        c->w_in[2 * a + 1] = (float)(g->k_uniform * cd + am);
+        for (int side = 0; side < 2; ++side) {
+            const int f = 2 * a + side;
+            const double A = side == 0 ? ap : am;
+            c->bkind[f] = g->bc_kind[f];
+            c->tb[f] = (float)g->bc_value[f];
+            c->held[f] = g->bc_kind[f] == WFA_BC_DIRICHLET_CELL;
+            if (g->bc_kind[f] == WFA_BC_DIRICHLET) c->w_bd[f] = (float)(2.0 * g->k_uniform * cd + A);
+            else if (g->bc_kind[f] == WFA_BC_PERIODIC) c->w_bd[f] = c->w_in[f];
+            else c->w_bd[f] = 0.0f;
+        }
+        // a zero-flux face stops the advective flux: the cell keeps (or loses)
+        // the upwind transport that its interior-face weights assume
+        if (lo == WFA_BC_ZEROFLUX) c->s_lo[a] = (float)(am - ap);
+        if (hi == WFA_BC_ZEROFLUX) c->s_hi[a] = (float)(ap - am);
+        if (c->s_lo[a] != 0.0f || c->s_hi[a] != 0.0f) c->any_self = 1;
+    }
+    return WFA_OK;
+}
+
+// ------------------------------------------------------------ pack/unpack --
+struct Geo {
+    int n[3];
+    long long px, py;
+};
+
+template <typename S>
+__global__ void pack_kernel(const float* __restrict__ dense, S* __restrict__ origin, Geo geo) {
+    const long long N = (long long)geo.n[0] * geo.n[1] * geo.n[2];
+    const long long sz = geo.px * geo.py;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % geo.n[0]);
+        const long long r = i / geo.n[0];
+        const int y = (int)(r % geo.n[1]);
+        const int z = (int)(r / geo.n[1]);
+        origin[z * sz + y * geo.px + x] = from_f32<S>(dense[i]);
+    }
+}
+
+template <typename S>
+__global__ void unpack_kernel(const S* __restrict__ origin, float* __restrict__ dense, Geo geo) {
+    const long long N = (long long)geo.n[0] * geo.n[1] * geo.n[2];
+    const long long sz = geo.px * geo.py;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % geo.n[0]);
+        const long long r = i / geo.n[0];
+        const int y = (int)(r % geo.n[1]);
+        const int z = (int)(r / geo.n[1]);
+        dense[i] = to_f32<S>(origin[z * sz + y * geo.px + x]);
+    }
+}
+
+struct HaloSpec {
+    int n[3];
+    long long px, py;
+    int periodic[3];
+    int held[6];
+    float gam[6];
+};
+
+// Value a domain cell must hold if a held layer covers it (last face wins).
+__device__ __forceinline__ bool held_value(const HaloSpec& h, int x, int y, int z, float* v) {
+    bool any = false;
+    const int c[3] = {x, y, z};
+    for (int f = 0; f < 6; ++f) {
+        if (!h.held[f]) continue;
+        const int a = f >> 1;
+        if (c[a] == ((f & 1) ? h.n[a] - 1 : 0)) {
+            *v = h.gam[f];
+            any = true;
+        }
+    }
+    return any;
+}
+
+// Write the held layers and the halo (periodic twins; 0 elsewhere) of one
+// padded buffer. Every cell of the padded box is visited once.
+template <typename S>
+__global__ void halo_kernel(S* __restrict__ base, HaloSpec h, long long total) {
+    const long long ex = h.n[0] + 2 * HALO, ey = h.n[1] + 2 * HALO;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % ex) - HALO;
+        const long long r = i / ex;
+        const int y = (int)(r % ey) - HALO;
+        const int z = (int)(r / ey) - HALO;
+        const int c[3] = {x, y, z};
+        bool outside = false, fill_zero = false;
+        int w[3];
+        for (int a = 0; a < 3; ++a) {
+            w[a] = c[a];
+            if (c[a] < 0 || c[a] >= h.n[a]) {
+                outside = true;
+                if (h.periodic[a]) w[a] = ((c[a] % h.n[a]) + h.n[a]) % h.n[a];
+                else fill_zero = true;
+            }
+        }
+        S* dst = base + ((long long)(z + HALO) * h.py + (y + HALO)) * h.px + (x + HALO);
+        float v;
+        if (!outside) {
+            if (held_value(h, x, y, z, &v)) *dst = from_f32<S>(v);
+            continue;
+        }
+        if (fill_zero) {
+            *dst = from_f32<S>(0.0f);
+            continue;
+        }
+        if (held_value(h, w[0], w[1], w[2], &v)) {
+            *dst = from_f32<S>(v);
+        } else {
+            const S* src = base + ((long long)(w[2] + HALO) * h.py + (w[1] + HALO)) * h.px + (w[0] + HALO);
+            *dst = *src;
+        }
+    }
+}
+
+static int grid_blocks(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    if (b > 152 * 16) b = 152 * 16;
+    return (int)(b < 1 ? 1 : b);
+}
+
+static HaloSpec halo_spec(const wfa_grid_s* g) {
+    HaloSpec h;
+    memset(&h, 0, sizeof h);
+    for (int a = 0; a < 3; ++a) {
+        h.n[a] = g->n[a];
+        h.periodic[a] = g->bc_kind[2 * a] == WFA_BC_PERIODIC && g->bc_kind[2 * a + 1] == WFA_BC_PERIODIC;
+    }
+    h.px = g->px;
+    h.py = g->py;
+    for (int f = 0; f < 6; ++f) {
+        h.held[f] = g->bc_kind[f] == WFA_BC_DIRICHLET_CELL;
+        h.gam[f] = (float)g->bc_value[f];
+    }
+    return h;
+}
+
+int refresh_halo(wfa_grid_s* g, int buf) {
+    HaloSpec h = halo_spec(g);
+    const long long total = (long long)(g->n[0] + 2 * HALO) * (g->n[1] + 2 * HALO) * (g->n[2] + 2 * HALO);
+    const int thr = 256;
+    if (g->storage == WFA_BF16)
+        halo_kernel<__nv_bfloat16><<<grid_blocks(total, thr), thr, 0, g->stream>>>(
+            (__nv_bfloat16*)g->T[buf], h, total);
+    else
+        halo_kernel<float><<<grid_blocks(total, thr), thr, 0, g->stream>>>((float*)g->T[buf], h, total);
+    WFA_CUDA(cudaGetLastError());
+    return WFA_OK;
+}
+
+// --------------------------------------------------------------- reductions --
+constexpr int RED_BLOCKS = 304;
+constexpr int RED_THREADS = 256;
+
+template <typename S>
+__global__ void __launch_bounds__(RED_THREADS) heat_partial_kernel(const S* __restrict__ origin, Geo geo,
+                                                                   double* __restrict__ partials) {
+    __shared__ double sh[RED_THREADS];
+    const long long N = (long long)geo.n[0] * geo.n[1] * geo.n[2];
+    const long long sz = geo.px * geo.py;
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)RED_THREADS + threadIdx.x; i < N;
+         i += (long long)RED_BLOCKS * RED_THREADS) {
+        const int x = (int)(i % geo.n[0]);
+        const long long r = i / geo.n[0];
+        const int y = (int)(r % geo.n[1]);
+        const int z = (int)(r / geo.n[1]);
+        acc += (double)to_f32<S>(origin[z * sz + y * geo.px + x]);
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+// Fixed-order finish: one block, a tree over RED_BLOCKS partials.
+__global__ void __launch_bounds__(512) finish_sum_kernel(const double* __restrict__ partials, int n,
+                                                         double scale, double* __restrict__ out) {
+    __shared__ double sh[512];
+    sh[threadIdx.x] = threadIdx.x < n ? partials[threadIdx.x] : 0.0;
+    __syncthreads();
+    for (int s = 256; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0] * scale;
+}
+
+struct RateSpec {
+    int n[3];
+    long long px, py;
+    int kind[6];
+    int held[6];
+    double inv_h2[3], up[3], um[3];  // 1/h^2, max(u,0)/h, max(-u,0)/h
+    double k_uniform;
+};
+
+__device__ __forceinline__ double harm64(double a, double b) {
+    const double s = a + b;
+    return s > 0.0 ? 2.0 * a * b / s : 0.0;
+}
+
+// D_C of one cell in fp64 (see wfa_stability_dt), 0 for held cells.
+__global__ void __launch_bounds__(RED_THREADS) rate_partial_kernel(const float* __restrict__ korigin, RateSpec r,
+                                                                   double* __restrict__ partials) {
+    __shared__ double sh[RED_THREADS];
+    const long long N = (long long)r.n[0] * r.n[1] * r.n[2];
+    const long long sz = r.px * r.py;
+    double best = 0.0;
+    for (long long i = blockIdx.x * (long long)RED_THREADS + threadIdx.x; i < N;
+         i += (long long)RED_BLOCKS * RED_THREADS) {
+        int c[3];
+        c[0] = (int)(i % r.n[0]);
+        const long long q = i / r.n[0];
+        c[1] = (int)(q % r.n[1]);
+        c[2] = (int)(q / r.n[1]);
+        bool held = false;
+        for (int f = 0; f < 6; ++f)
+            if (r.held[f] && c[f >> 1] == ((f & 1) ? r.n[f >> 1] - 1 : 0)) held = true;
+        if (held) continue;
+        const long long idx = c[2] * sz + c[1] * r.px + c[0];
+        const long long st[3] = {1, r.px, sz};
+        const double kC = korigin ? (double)korigin[idx] : r.k_uniform;
+        double D = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            for (int side = 0; side < 2; ++side) {
+                const int f = 2 * a + side;
+                const bool edge = side == 0 ? c[a] == 0 : c[a] == r.n[a] - 1;
+                bool active = true;
+                if (r.kind[f] == WFA_BC_PERIODIC && r.n[a] == 1) {
+                    continue;
+                } else if (edge && r.kind[f] != WFA_BC_PERIODIC) {
+                    if (r.kind[f] == WFA_BC_DIRICHLET) D += 2.0 * kC * r.inv_h2[a];
+                    else active = false;
+                } else {
+                    // interior or periodic neighbour (periodic twins live in the halo)
+                    const double kD = korigin ? (double)korigin[idx + (side ? st[a] : -st[a])] : r.k_uniform;
+                    D += harm64(kC, kD) * r.inv_h2[a];
+                }
+                if (active) D += side ? r.up[a] : r.um[a];
+            }
+        }
+        best = fmax(best, D);
+    }
+    sh[threadIdx.x] = best;
+    __syncthreads();
+    for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(512) finish_max_kernel(const double* __restrict__ partials, int n,
+                                                         double* __restrict__ out) {
+    __shared__ double sh[512];
+    sh[threadIdx.x] = threadIdx.x < n ? partials[threadIdx.x] : 0.0;
+    __syncthreads();
+    for (int s = 256; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+// k halo: periodic twins (the harmonic mean across a wrap face reads them), 0 elsewhere.
+__global__ void k_halo_kernel(float* __restrict__ base, HaloSpec h, long long total) {
+    const long long ex = h.n[0] + 2 * HALO, ey = h.n[1] + 2 * HALO;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c[3] = {(int)(i % ex) - HALO, (int)((i / ex) % ey) - HALO, (int)(i / (ex * ey)) - HALO};
+        bool outside = false, zero = false;
+        int w[3];
+        for (int a = 0; a < 3; ++a) {
+            w[a] = c[a];
+            if (c[a] < 0 || c[a] >= h.n[a]) {
+                outside = true;
+                if (h.periodic[a]) w[a] = ((c[a] % h.n[a]) + h.n[a]) % h.n[a];
+                else zero = true;
+            }
+        }
+        if (!outside) continue;
+        float* dst = base + ((long long)(c[2] + HALO) * h.py + (c[1] + HALO)) * h.px + (c[0] + HALO);
+        *dst = zero ? 0.0f : base[((long long)(w[2] + HALO) * h.py + (w[1] + HALO)) * h.px + (w[0] + HALO)];
+    }
+}
+
+int check_status(wfa_grid_s* g) {
+    WFA_CUDA(cudaMemcpyAsync(g->h_status, g->d_status, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    WFA_CUDA(cudaStreamSynchronize(g->stream));
+    if (*g->h_status != 0) {
+        const int code = *g->h_status;
+        *g->h_status = 0;
+        cudaMemsetAsync(g->d_status, 0, sizeof(int), g->stream);
+        cudaStreamSynchronize(g->stream);
+        return fail(WFA_ERR_TIMEOUT, "a device-side wait gave up after its time limit (code %d)", code);
+    }
+    return WFA_OK;
+}
+
+}  // namespace wfa
+
+using namespace wfa;
+
+// =============================================================== C ABI ====
+extern "C" {
+
+const char* wfa_last_error(void) { return g_last_error.c_str(); }
+
+int wfa_create_grid(int nx, int ny, int nz, double hx, double hy, double hz, int storage,
+                    void* cuda_stream, wfa_grid* out) {
+    if (!out) return fail(WFA_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (nx < 2 || ny < 2 || nz < 2) return fail(WFA_ERR_ARG, "every edge must be >= 2 (got %d %d %d)", nx, ny, nz);
+    if (!(hx > 0 && hy > 0 && hz > 0) || !std::isfinite(hx) || !std::isfinite(hy) || !std::isfinite(hz))
+        return fail(WFA_ERR_ARG, "cell sizes must be finite and > 0");
+    if (storage != WFA_F32 && storage != WFA_BF16) return fail(WFA_ERR_ARG, "storage must be WFA_F32 or WFA_BF16");
+    if ((double)nx * ny * nz > (double)(1LL << 40)) return fail(WFA_ERR_ARG, "grid too large");
+    wfa_grid_s* g = new (std::nothrow) wfa_grid_s();
+    if (!g) return fail(WFA_ERR_OOM, "host allocation failed");
+    g->n[0] = nx; g->n[1] = ny; g->n[2] = nz;
+    g->h[0] = hx; g->h[1] = hy; g->h[2] = hz;
+    g->storage = storage;
+    g->esize = storage == WFA_BF16 ? 2 : 4;
+    g->stream = (cudaStream_t)cuda_stream;
+    const long long align = 128 / g->esize;
+    g->px = ((nx + 2LL * HALO + align - 1) / align) * align;
+    g->py = ny + 2LL * HALO;
+    g->pz = nz + 2LL * HALO;
+    for (int f = 0; f < 6; ++f) { g->bc_kind[f] = WFA_BC_ZEROFLUX; g->bc_value[f] = 0.0; }
+    const size_t bytes = field_elems(g) * g->esize;
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&g->T[b], bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_partials, 4096 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&g->h_result, 64);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&g->h_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_status, 0, sizeof(int), g->stream);
+    if (e == cudaSuccess) {
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMemsetAsync(g->T[b], 0, bytes, g->stream);
+    }
+    if (e != cudaSuccess) {
+        int rc = cuda_fail(e, "wfa_create_grid allocation");
+        wfa_destroy_grid(g);
+        return rc;
+    }
+    *out = g;
+    return WFA_OK;
+}
+
+int wfa_destroy_grid(wfa_grid g) {
+    if (!g) return WFA_OK;
+    cudaStreamSynchronize(g->stream);
+    for (int b = 0; b < 2; ++b) if (g->T[b]) cudaFree(g->T[b]);
+    if (g->k) cudaFree(g->k);
+    if (g->d_partials) cudaFree(g->d_partials);
+    if (g->d_stage) cudaFree(g->d_stage);
+    if (g->h_result) cudaFreeHost(g->h_result);
+    if (g->d_status) cudaFree(g->d_status);
+    if (g->h_status) cudaFreeHost(g->h_status);
+    free_tmaps(g);
+    delete g;
+    return WFA_OK;
+}
+
+static int ensure_stage(wfa_grid g) {
+    if (g->d_stage) return WFA_OK;
+    const size_t N = (size_t)g->n[0] * g->n[1] * g->n[2];
+    WFA_CUDA(cudaMalloc(&g->d_stage, N * sizeof(float)));
+    return WFA_OK;
+}
+
+static Geo geo_of(const wfa_grid_s* g) {
+    Geo geo;
+    for (int a = 0; a < 3; ++a) geo.n[a] = g->n[a];
+    geo.px = g->px;
+    geo.py = g->py;
+    return geo;
+}
+
+int wfa_set_field(wfa_grid g, const float* host_dense) {
+    if (!g || !host_dense) return fail(WFA_ERR_ARG, "NULL argument");
+    int rc = ensure_stage(g);
+    if (rc) return rc;
+    const long long N = (long long)g->n[0] * g->n[1] * g->n[2];
+    WFA_CUDA(cudaMemcpyAsync(g->d_stage, host_dense, N * sizeof(float), cudaMemcpyHostToDevice, g->stream));
+    const int thr = 256;
+    const Geo geo = geo_of(g);
+    if (g->storage == WFA_BF16)
+        pack_kernel<__nv_bfloat16><<<grid_blocks(N, thr), thr, 0, g->stream>>>(
+            g->d_stage, (__nv_bfloat16*)g->T[g->cur] + domain_offset(g), geo);
+    else
+        pack_kernel<float><<<grid_blocks(N, thr), thr, 0, g->stream>>>(
+            g->d_stage, (float*)g->T[g->cur] + domain_offset(g), geo);
+    WFA_CUDA(cudaGetLastError());
+    // the host buffer may be reused as soon as we return
+    WFA_CUDA(cudaStreamSynchronize(g->stream));
+    g->field_set = true;
+    g->halo_dirty = true;
+    g->steps_done = 0;
+    return WFA_OK;
+}
+
+int wfa_set_coeffs(wfa_grid g, const float* k_host, double k_uniform, double ux, double uy, double uz) {
+    if (!g) return fail(WFA_ERR_ARG, "NULL grid");
+    if (!std::isfinite(ux) || !std::isfinite(uy) || !std::isfinite(uz))
+        return fail(WFA_ERR_ARG, "velocity must be finite");
+    if (!k_host && (!(k_uniform >= 0) || !std::isfinite(k_uniform)))
+        return fail(WFA_ERR_ARG, "k_uniform must be finite and >= 0");
+    const long long N = (long long)g->n[0] * g->n[1] * g->n[2];
+    if (k_host) {
+        for (long long i = 0; i < N; ++i)
+            if (!(k_host[i] >= 0.0f) || !std::isfinite(k_host[i]))
+                return fail(WFA_ERR_ARG, "k[%lld] = %g is negative or not finite", i, (double)k_host[i]);
+        if (!g->k) {
+            WFA_CUDA(cudaMalloc(&g->k, field_elems(g) * sizeof(float)));
+            WFA_CUDA(cudaMemsetAsync(g->k, 0, field_elems(g) * sizeof(float), g->stream));
+        }
+        int rc = ensure_stage(g);
+        if (rc) return rc;
+        WFA_CUDA(cudaMemcpyAsync(g->d_stage, k_host, N * sizeof(float), cudaMemcpyHostToDevice, g->stream));
+        const int thr = 256;
+        pack_kernel<float><<<grid_blocks(N, thr), thr, 0, g->stream>>>(g->d_stage, g->k + domain_offset(g),
+                                                                         geo_of(g));
+        WFA_CUDA(cudaGetLastError());
+        WFA_CUDA(cudaStreamSynchronize(g->stream));
+        g->k_uniform = 0.0;
+    } else {
+        if (g->k) {
+            cudaStreamSynchronize(g->stream);
+            cudaFree(g->k);
+            g->k = nullptr;
+            free_tmaps(g);
+        }
+        g->k_uniform = k_uniform;
+    }
+    g->u[0] = ux; g->u[1] = uy; g->u[2] = uz;
+    g->coeffs_set = true;
+    g->dt_set = false;   // the limit may have moved
+    g->halo_dirty = true;
+    return WFA_OK;
+}
+
+int wfa_set_bc(wfa_grid g, int face, int kind, double value) {
+    if (!g) return fail(WFA_ERR_ARG, "NULL grid");
+    if (face < 0 || face > 5) return fail(WFA_ERR_ARG, "face %d out of range", face);
+    if (kind < 0 || kind > 3) return fail(WFA_ERR_ARG, "boundary kind %d out of range", kind);
+    if (!std::isfinite(value)) return fail(WFA_ERR_ARG, "boundary value must be finite");
+    if (kind == WFA_BC_DIRICHLET_CELL && g->n[face / 2] < 3)
+        return fail(WFA_ERR_BC, "held boundary cells need an edge >= 3");
+    g->bc_kind[face] = kind;
+    g->bc_value[face] = value;
+    g->halo_dirty = true;
+    g->dt_set = false;
+    return WFA_OK;
+}
+
+static RateSpec rate_spec(const wfa_grid_s* g) {
+    RateSpec r;
+    memset(&r, 0, sizeof r);
+    for (int a = 0; a < 3; ++a) {
+        r.n[a] = g->n[a];
+        r.inv_h2[a] = 1.0 / (g->h[a] * g->h[a]);
+        r.up[a] = (g->u[a] > 0 ? g->u[a] : 0.0) / g->h[a];
+        r.um[a] = (g->u[a] < 0 ? -g->u[a] : 0.0) / g->h[a];
+    }
+    for (int f = 0; f < 6; ++f) {
+        r.kind[f] = g->bc_kind[f];
+        r.held[f] = g->bc_kind[f] == WFA_BC_DIRICHLET_CELL;
+    }
+    r.px = g->px;
+    r.py = g->py;
+    r.k_uniform = g->k_uniform;
+    return r;
+}
+
+static int prepare_k_halo(wfa_grid g) {
+    if (!g->k) return WFA_OK;
+    HaloSpec h = halo_spec(g);
+    const long long total = (long long)(g->n[0] + 2 * HALO) * (g->n[1] + 2 * HALO) * (g->n[2] + 2 * HALO);
+    k_halo_kernel<<<grid_blocks(total, 256), 256, 0, g->stream>>>(g->k, h, total);
+    WFA_CUDA(cudaGetLastError());
+    return WFA_OK;
+}
+
+int wfa_stability_dt(wfa_grid g, double* dt_max) {
+    if (!g || !dt_max) return fail(WFA_ERR_ARG, "NULL argument");
+    if (!g->coeffs_set) return fail(WFA_ERR_STATE, "set the coefficients first");
+    for (int a = 0; a < 3; ++a)
+        if ((g->bc_kind[2 * a] == WFA_BC_PERIODIC) != (g->bc_kind[2 * a + 1] == WFA_BC_PERIODIC))
+            return fail(WFA_ERR_BC, "axis %d: a periodic face needs a periodic opposite face", a);
+    int rc = prepare_k_halo(g);
+    if (rc) return rc;
+    RateSpec r = rate_spec(g);
+    rate_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, g->stream>>>(g->k ? g->k + domain_offset(g) : nullptr, r,
+                                                                   g->d_partials);
+    finish_max_kernel<<<1, 512, 0, g->stream>>>(g->d_partials, RED_BLOCKS, g->d_partials + RED_BLOCKS);
+    WFA_CUDA(cudaGetLastError());
+    WFA_CUDA(cudaMemcpyAsync(g->h_result, g->d_partials + RED_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost,
+                             g->stream));
+    WFA_CUDA(cudaStreamSynchronize(g->stream));
+    const double dmax = g->h_result[0];
+    *dt_max = dmax > 0.0 ? 1.0 / dmax : INFINITY;
+    return WFA_OK;
+}
+
+int wfa_set_dt(wfa_grid g, double dt) {
+    if (!g) return fail(WFA_ERR_ARG, "NULL grid");
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(WFA_ERR_ARG, "dt must be finite and > 0");
+    double lim;
+    int rc = wfa_stability_dt(g, &lim);
+    if (rc) return rc;
+    if (dt > lim) return fail(WFA_ERR_UNSTABLE, "dt = %.17g exceeds the stability limit %.17g", dt, lim);
+    g->dt = dt;
+    g->dt_set = true;
+    return WFA_OK;
+}
+
+int wfa_set_tuning(wfa_grid g, int depth, int variant) {
+    if (!g) return fail(WFA_ERR_ARG, "NULL grid");
+    if (depth < 0 || depth > MAX_DEPTH) return fail(WFA_ERR_ARG, "depth must be 0..%d", MAX_DEPTH);
+    if (variant < -1 || variant > NUM_TILE_VARIANTS) return fail(WFA_ERR_ARG, "variant must be -1..%d", NUM_TILE_VARIANTS);
+    g->force_depth = depth;
+    g->force_variant = variant;
+    return WFA_OK;
+}
+
+int wfa_step(wfa_grid g, long long n) {
+    if (!g) return fail(WFA_ERR_ARG, "NULL grid");
+    if (n < 0) return fail(WFA_ERR_ARG, "negative step count");
+    if (!g->field_set || !g->coeffs_set || !g->dt_set)
+        return fail(WFA_ERR_STATE, "set the field, the coefficients and dt before stepping");
+    SweepCoef c;
+    int rc = build_coef(g, &c);
+    if (rc) return rc;
+    if (n == 0) return WFA_OK;
+    if (g->halo_dirty) {
+        rc = refresh_halo(g, g->cur);
+        if (rc) return rc;
+        rc = prepare_k_halo(g);
+        if (rc) return rc;
+        g->halo_dirty = false;
+    }
+    rc = launch_sweep(g, n);
+    if (rc) return rc;
+    g->steps_done += n;
+    return WFA_OK;
+}
+
+int wfa_steps_done(wfa_grid g, long long* n) {
+    if (!g || !n) return fail(WFA_ERR_ARG, "NULL argument");
+    *n = g->steps_done;
+    return WFA_OK;
+}
+
+int wfa_read_field(wfa_grid g, float* host_dense) {
+    if (!g || !host_dense) return fail(WFA_ERR_ARG, "NULL argument");
+    if (!g->field_set) return fail(WFA_ERR_STATE, "no field set");
+    int rc = ensure_stage(g);
+    if (rc) return rc;
+    if (g->halo_dirty) {   // held layers show their value even before the first step
+        rc = refresh_halo(g, g->cur);
+        if (rc) return rc;
+    }
+    const long long N = (long long)g->n[0] * g->n[1] * g->n[2];
+    const int thr = 256;
+    const Geo geo = geo_of(g);
+    if (g->storage == WFA_BF16)
+        unpack_kernel<__nv_bfloat16><<<grid_blocks(N, thr), thr, 0, g->stream>>>(
+            (const __nv_bfloat16*)g->T[g->cur] + domain_offset(g), g->d_stage, geo);
+    else
+        unpack_kernel<float><<<grid_blocks(N, thr), thr, 0, g->stream>>>(
+            (const float*)g->T[g->cur] + domain_offset(g), g->d_stage, geo);
+    WFA_CUDA(cudaGetLastError());
+    WFA_CUDA(cudaMemcpyAsync(host_dense, g->d_stage, N * sizeof(float), cudaMemcpyDeviceToHost, g->stream));
+    return check_status(g);
+}
+
+int wfa_total_heat(wfa_grid g, double* e) {
+    int rc_;
+    if (!g || !e) return fail(WFA_ERR_ARG, "NULL argument");
+    if (!g->field_set) return fail(WFA_ERR_STATE, "no field set");
+    if (g->halo_dirty) {
+        int rc = refresh_halo(g, g->cur);
+        if (rc) return rc;
+    }
+    const Geo geo = geo_of(g);
+    if (g->storage == WFA_BF16)
+        heat_partial_kernel<__nv_bfloat16><<<RED_BLOCKS, RED_THREADS, 0, g->stream>>>(
+            (const __nv_bfloat16*)g->T[g->cur] + domain_offset(g), geo, g->d_partials);
+    else
+        heat_partial_kernel<float><<<RED_BLOCKS, RED_THREADS, 0, g->stream>>>(
+            (const float*)g->T[g->cur] + domain_offset(g), geo, g->d_partials);
+    finish_sum_kernel<<<1, 512, 0, g->stream>>>(g->d_partials, RED_BLOCKS, g->h[0] * g->h[1] * g->h[2],
+                                                g->d_partials + RED_BLOCKS);
+    WFA_CUDA(cudaGetLastError());
+    WFA_CUDA(cudaMemcpyAsync(g->h_result, g->d_partials + RED_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost,
+                             g->stream));
+    rc_ = check_status(g);
+    *e = g->h_result[0];
+    return rc_;
+}
+
+int wfa_sync(wfa_grid g) {
+    if (!g) return fail(WFA_ERR_ARG, "NULL grid");
+    return check_status(g);
+}
+
+}  // extern "C"

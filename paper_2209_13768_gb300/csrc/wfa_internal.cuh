@@ -1,0 +1,194 @@
+// Internal declarations of the GB300 finite-volume sweep library.
+//
+// Device layout of a field (one "padded" array per ping-pong buffer):
+//   every axis carries HALO = 8 extra cells on each side; x is padded further
+//   so that a row is a multiple of 128 bytes:
+//     px = round_up(nx + 2*HALO, 128 / element_size), py = ny + 2*HALO, pz = nz + 2*HALO
+//   domain cell (x, y, z), -HALO <= x < nx + HALO, is element
+//     ((z + HALO) * py + (y + HALO)) * px + (x + HALO)
+//   Halo cells of a periodic axis hold copies of the cells one period away
+//   ("twins"), kept current by every kernel that writes the field, so a tile
+//   near the edge reads its wrapped neighbours as ordinary memory. Halo cells
+//   of other axes are never read by an updated cell: a boundary cell takes its
+//   outside neighbour from the boundary condition.
+//   Per-cell conductivity k (fp32) uses the same layout (its periodic twins are
+//   written once by wfa_set_coeffs).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/wfa.h"
+
+namespace wfa {
+
+constexpr int HALO = 8;       // halo width on every side (>= the deepest temporal block)
+constexpr int MAX_DEPTH = 8;  // steps fused per pass over the grid
+constexpr int NUM_TILE_VARIANTS = 2;  // tile shapes compiled per (storage, k mode, depth)
+
+// ---------------------------------------------------------------- errors --
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+#define WFA_CUDA(call)                                                  \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return ::wfa::cuda_fail(e_, #call);      \
+    } while (0)
+
+// ------------------------------------------------------- kernel parameters --
+// Everything a sweep needs, by value (coefficients already rounded to fp32 on
+// the host from fp64, in a fixed way, so every kernel sees the same bits).
+struct SweepCoef {
+    int n[3];              // nx, ny, nz
+    long long sy, sz;      // element strides of y and z in the padded layout
+    int periodic[3];       // axis periodic (both faces)
+    int bkind[6];          // face kind (enum wfa_bc_kind)
+    float tb[6];           // Dirichlet face value (fp32)
+    float w_in[6];         // uniform k: coefficient of an interior face, k dt/h^2 + A_f
+    float w_bd[6];         // uniform k: coefficient of the boundary face (Dirichlet: 2k dt/h^2 + A_f; else 0)
+    float cd[3];           // dt / h_a^2 (per-cell k: face coefficient = harmonic mean * cd + A_f)
+    float adv[6];          // A_f: upwind coefficient of face f: -face dt*max(u,0)/h, +face dt*max(-u,0)/h
+    float s_lo[3], s_hi[3];  // self term of a cell on a zero-flux face with advection
+    int held[6];           // face holds its outer cell layer (Dirichlet cell)
+    int any_self;          // some zero-flux face carries a self term
+};
+
+}  // namespace wfa
+
+struct wfa_grid_s {
+    int n[3];
+    double h[3];
+    int storage;          // WFA_F32 / WFA_BF16
+    int esize;            // bytes per stored element
+    cudaStream_t stream;
+    long long px, py, pz; // padded extents (elements)
+    void* T[2];           // ping-pong padded fields (allocation bases)
+    float* k;             // padded per-cell conductivity or nullptr
+    int cur;              // buffer holding the current field
+    double k_uniform;
+    double u[3];
+    int bc_kind[6];
+    double bc_value[6];
+    double dt;
+    bool field_set, coeffs_set, dt_set, halo_dirty;
+    long long steps_done;
+    int force_depth, force_variant;   // wfa_set_tuning (0 = automatic)
+    double* d_partials;   // fp64 reduction partials (scratch)
+    double* h_result;     // pinned host word for reduction results
+    float* d_stage;       // dense fp32 staging buffer for set/read (scratch)
+    int* d_status;        // device error word (a bounded wait that gave up)
+    int* h_status;        // pinned host copy
+    void* tmaps;          // wfa::TmapCache (TMA descriptors for the current tile box)
+    int tuned_depth, tuned_variant;   // configuration picked by the autotuner (0 = none)
+};
+
+namespace wfa {
+
+inline long long domain_offset(const wfa_grid_s* g) {
+    return ((long long)HALO * g->py + HALO) * g->px + HALO;
+}
+inline size_t field_elems(const wfa_grid_s* g) { return (size_t)g->px * g->py * g->pz; }
+
+int build_coef(const wfa_grid_s* g, SweepCoef* c);       // host: fp64 -> fp32 coefficients
+int refresh_halo(wfa_grid_s* g, int buf);                 // twins + held layers of one buffer
+int launch_sweep(wfa_grid_s* g, long long nsteps);        // advance nsteps on g->stream
+int check_status(wfa_grid_s* g);                          // sync + report a device-side timeout
+void free_tmaps(wfa_grid_s* g);
+
+// ----------------------------------------------------------- device math --
+// The fixed per-cell arithmetic. Every kernel that updates a cell calls these
+// with the same operands, so any two kernels (any tile shape, temporal depth
+// or batching) produce bit-identical fields. The *_rn intrinsics are never
+// contracted into other operations by the compiler.
+
+// Face coefficient from the harmonic mean of two conductivities:
+// 2 a b / (a + b) * cd, 0 when a + b == 0. Symmetric in (a, b) bit for bit.
+__device__ __forceinline__ float harm_face(float a, float b, float cd) {
+    const float s = __fadd_rn(a, b);
+    const float p = __fmul_rn(__fmul_rn(2.0f, a), b);
+    const float hm = (s > 0.0f) ? __fdividef(p, s) : 0.0f;
+    return __fmul_rn(hm, cd);
+}
+
+// Boundary (Dirichlet) face coefficient for per-cell k: 2 k_C dt / h^2.
+__device__ __forceinline__ float dirichlet_face(float kc, float cd) {
+    return __fmul_rn(__fmul_rn(2.0f, kc), cd);
+}
+
+// T' = T_C + sum_f w_f (T_f - T_C) + s T_C, faces in the order -x,+x,-y,+y,-z,+z.
+__device__ __forceinline__ float cell_update(float tc, float txm, float txp, float tym, float typ,
+                                             float tzm, float tzp, float wxm, float wxp, float wym,
+                                             float wyp, float wzm, float wzp, float s) {
+    float acc = __fmul_rn(wxm, __fsub_rn(txm, tc));
+    acc = __fmaf_rn(wxp, __fsub_rn(txp, tc), acc);
+    acc = __fmaf_rn(wym, __fsub_rn(tym, tc), acc);
+    acc = __fmaf_rn(wyp, __fsub_rn(typ, tc), acc);
+    acc = __fmaf_rn(wzm, __fsub_rn(tzm, tc), acc);
+    acc = __fmaf_rn(wzp, __fsub_rn(tzp, tc), acc);
+    acc = __fmaf_rn(s, tc, acc);
+    return __fadd_rn(tc, acc);
+}
+
+// Self term of a cell from the zero-flux faces it touches (fixed order).
+__device__ __forceinline__ float self_term(const SweepCoef& c, int x, int y, int z) {
+    float s = 0.0f;
+    if (!c.any_self) return s;
+    if (x == 0) s = __fadd_rn(s, c.s_lo[0]);
+    if (x == c.n[0] - 1) s = __fadd_rn(s, c.s_hi[0]);
+    if (y == 0) s = __fadd_rn(s, c.s_lo[1]);
+    if (y == c.n[1] - 1) s = __fadd_rn(s, c.s_hi[1]);
+    if (z == 0) s = __fadd_rn(s, c.s_lo[2]);
+    if (z == c.n[2] - 1) s = __fadd_rn(s, c.s_hi[2]);
+    return s;
+}
+
+// Cell held by a Dirichlet-cell layer.
+__device__ __forceinline__ bool is_held(const SweepCoef& c, int x, int y, int z) {
+    return (c.held[0] && x == 0) || (c.held[1] && x == c.n[0] - 1) || (c.held[2] && y == 0) ||
+           (c.held[3] && y == c.n[1] - 1) || (c.held[4] && z == 0) || (c.held[5] && z == c.n[2] - 1);
+}
+
+// Storage conversions.
+template <typename S> __device__ __forceinline__ float to_f32(S v);
+template <> __device__ __forceinline__ float to_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) {
+    return __bfloat162float(v);
+}
+template <typename S> __device__ __forceinline__ S from_f32(float v);
+template <> __device__ __forceinline__ float from_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float v) {
+    return __float2bfloat16_rn(v);
+}
+// Value as stored (bf16 fields round after every step, also inside a fused block).
+template <typename S> __device__ __forceinline__ float storage_round(float v) {
+    return to_f32<S>(from_f32<S>(v));
+}
+
+// Write v at (x, y, z) and at every periodic twin of that cell inside the halo.
+template <typename S>
+__device__ __forceinline__ void store_with_twins(S* origin, const SweepCoef& c, int x, int y, int z,
+                                                 S v) {
+    origin[(long long)z * c.sz + (long long)y * c.sy + x] = v;
+    const bool nearx = c.periodic[0] && (x < HALO || x >= c.n[0] - HALO);
+    const bool neary = c.periodic[1] && (y < HALO || y >= c.n[1] - HALO);
+    const bool nearz = c.periodic[2] && (z < HALO || z >= c.n[2] - HALO);
+    if (!(nearx || neary || nearz)) return;
+    // twins: coordinate + m * n inside [-HALO, n + HALO)
+    for (int zz = nearz ? z - ((z + HALO) / c.n[2]) * c.n[2] : z; zz < c.n[2] + HALO;
+         zz += nearz ? c.n[2] : (1 << 30)) {
+        for (int yy = neary ? y - ((y + HALO) / c.n[1]) * c.n[1] : y; yy < c.n[1] + HALO;
+             yy += neary ? c.n[1] : (1 << 30)) {
+            for (int xx = nearx ? x - ((x + HALO) / c.n[0]) * c.n[0] : x; xx < c.n[0] + HALO;
+                 xx += nearx ? c.n[0] : (1 << 30)) {
+                if (xx == x && yy == y && zz == z) continue;
+                origin[(long long)zz * c.sz + (long long)yy * c.sy + xx] = v;
+            }
+        }
+    }
+}
+
+}  // namespace wfa

@@ -1,0 +1,332 @@
+// Continuous-batching request server: transient solves of different sizes
+// and step counts are admitted by device-memory budget, kept resident, and
+// advanced together — every scheduler tick moves each resident request by up
+// to `quantum` steps in one batched launch (wfa_batch_run). Requests that
+// arrive while others run join at the next tick; finished requests are
+// copied to their host buffers and their memory is released at once.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/wfa.h"
+
+namespace wfa {
+void set_error(const char* fmt, ...);
+}
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+
+struct Req {
+    long long ticket = 0;
+    wfa_request spec{};
+    std::vector<float> T0, k;
+    wfa_grid g = nullptr;
+    long long remaining = 0;
+    size_t bytes = 0;
+    int state = 0;   // 0 queued, 1 resident, 2 done, -1 failed
+    std::string err;
+    clk::time_point t_submit, t_done;
+};
+
+// Device bytes a request holds while resident (two field buffers with their
+// halo, per-cell k, the dense staging buffer).
+size_t device_bytes(const wfa_request& r) {
+    const long long halo = 8;
+    const long long es = r.storage == WFA_BF16 ? 2 : 4;
+    const long long align = 128 / es;
+    const long long px = ((r.nx + 2 * halo + align - 1) / align) * align;
+    const long long padded = px * (r.ny + 2 * halo) * (r.nz + 2 * halo);
+    const long long dense = (long long)r.nx * r.ny * r.nz;
+    size_t b = (size_t)(2 * padded * es + dense * 4 + 64 * 1024);
+    if (r.k_host) b += (size_t)padded * 4;
+    return b;
+}
+
+}  // namespace
+
+struct wfa_server_s {
+    size_t budget = 0;
+    int max_resident = 1024;
+    long long quantum = 64;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Req*> pending;
+    std::vector<Req*> resident;
+    std::unordered_map<long long, Req*> all;
+    long long next_ticket = 1;
+    bool stop = false;
+    std::thread th;
+
+    // stats
+    long long submitted = 0, admitted = 0, completed = 0, rejected = 0, ticks = 0;
+    double cell_updates = 0.0, busy_s = 0.0;
+    size_t used = 0, peak_used = 0;
+    std::vector<double> latencies;
+
+    void run();
+    int setup(Req* r);
+    void finish(Req* r, bool ok, const std::string& why);
+};
+
+int wfa_server_s::setup(Req* r) {
+    const wfa_request& s = r->spec;
+    int rc = wfa_create_grid(s.nx, s.ny, s.nz, s.hx, s.hy, s.hz, s.storage, stream, &r->g);
+    if (rc) return rc;
+    for (int f = 0; f < 6 && !rc; ++f) rc = wfa_set_bc(r->g, f, s.bc_kind[f], s.bc_value[f]);
+    if (!rc) rc = wfa_set_coeffs(r->g, r->k.empty() ? nullptr : r->k.data(), s.k_uniform, s.ux, s.uy, s.uz);
+    if (!rc) rc = wfa_set_field(r->g, r->T0.data());
+    double dt = s.dt;
+    if (!rc && !(dt > 0)) {
+        double lim = 0;
+        rc = wfa_stability_dt(r->g, &lim);
+        dt = std::isfinite(lim) ? 0.9 * lim : 1.0;
+    }
+    if (!rc) rc = wfa_set_dt(r->g, dt);
+    // the host copies are no longer needed once the device holds them
+    std::vector<float>().swap(r->T0);
+    std::vector<float>().swap(r->k);
+    return rc;
+}
+
+void wfa_server_s::finish(Req* r, bool ok, const std::string& why) {
+    if (r->g) {
+        wfa_destroy_grid(r->g);
+        r->g = nullptr;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    r->state = ok ? 2 : -1;
+    r->err = why;
+    r->t_done = clk::now();
+    used -= r->bytes;
+    if (ok) {
+        ++completed;
+        latencies.push_back(std::chrono::duration<double>(r->t_done - r->t_submit).count());
+    }
+    cv_done.notify_all();
+}
+
+void wfa_server_s::run() {
+    cudaSetDevice(device);
+    std::vector<Req*> fresh;
+    std::vector<wfa_grid> gs;
+    std::vector<long long> steps;
+    for (;;) {
+        fresh.clear();
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv_work.wait(lk, [&] { return stop || !pending.empty() || !resident.empty(); });
+            if (stop && pending.empty() && resident.empty()) break;
+            // admission: first come, first served, while memory and slots allow
+            while (!pending.empty() && (int)resident.size() < max_resident) {
+                Req* r = pending.front();
+                if (used + r->bytes > budget) break;
+                pending.pop_front();
+                used += r->bytes;
+                peak_used = std::max(peak_used, used);
+                r->state = 1;
+                ++admitted;
+                resident.push_back(r);
+                fresh.push_back(r);
+            }
+        }
+        for (Req* r : fresh) {
+            int rc = setup(r);
+            if (rc) {
+                std::string why = wfa_last_error();
+                {
+                    std::lock_guard<std::mutex> lk(mu);
+                    resident.erase(std::find(resident.begin(), resident.end(), r));
+                }
+                finish(r, false, why);
+            }
+        }
+        std::vector<Req*> work;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            work = resident;
+        }
+        if (work.empty()) continue;
+        gs.clear();
+        steps.clear();
+        double upd = 0.0;
+        for (Req* r : work) {
+            const long long q = std::min(r->remaining, quantum);
+            gs.push_back(r->g);
+            steps.push_back(q);
+            upd += (double)q * r->spec.nx * r->spec.ny * r->spec.nz;
+        }
+        const auto t0 = clk::now();
+        int rc = wfa_batch_run(gs.data(), steps.data(), (int)gs.size());
+        if (!rc) rc = cudaStreamSynchronize(stream) == cudaSuccess ? 0 : WFA_ERR_CUDA;
+        const auto t1 = clk::now();
+        std::vector<Req*> done;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            ++ticks;
+            busy_s += std::chrono::duration<double>(t1 - t0).count();
+            if (!rc) cell_updates += upd;
+            for (size_t i = 0; i < work.size(); ++i) {
+                if (rc || (work[i]->remaining -= steps[i]) <= 0) done.push_back(work[i]);
+            }
+            for (Req* r : done) resident.erase(std::find(resident.begin(), resident.end(), r));
+        }
+        std::string why = rc ? std::string(wfa_last_error()) : std::string();
+        for (Req* r : done) {
+            int rr = rc ? rc : wfa_read_field(r->g, r->spec.out_host);
+            finish(r, rr == 0, rr ? (rc ? why : std::string(wfa_last_error())) : std::string());
+        }
+    }
+}
+
+extern "C" {
+
+int wfa_server_create(size_t hbm_budget_bytes, int max_resident, long long quantum, wfa_server* out) {
+    if (!out || hbm_budget_bytes == 0 || max_resident < 0 || quantum < 0) {
+        wfa::set_error("wfa_server_create: bad arguments");
+        return WFA_ERR_ARG;
+    }
+    wfa_server_s* s = new wfa_server_s();
+    s->budget = hbm_budget_bytes;
+    s->max_resident = max_resident ? max_resident : 1024;
+    s->quantum = quantum ? quantum : 64;
+    cudaGetDevice(&s->device);
+    cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        wfa::set_error("cudaStreamCreate failed: %s", cudaGetErrorString(e));
+        delete s;
+        return WFA_ERR_CUDA;
+    }
+    s->th = std::thread([s] { s->run(); });
+    *out = s;
+    return WFA_OK;
+}
+
+int wfa_server_submit(wfa_server s, const wfa_request* r, long long* ticket) {
+    if (!s || !r || !ticket || !r->T0_host || !r->out_host || r->steps < 0 || r->nx < 2 || r->ny < 2 ||
+        r->nz < 2) {
+        wfa::set_error("wfa_server_submit: bad arguments");
+        return WFA_ERR_ARG;
+    }
+    Req* q = new Req();
+    q->spec = *r;
+    q->bytes = device_bytes(*r);
+    q->remaining = r->steps;
+    const size_t n = (size_t)r->nx * r->ny * r->nz;
+    q->T0.assign(r->T0_host, r->T0_host + n);
+    if (r->k_host) q->k.assign(r->k_host, r->k_host + n);
+    q->t_submit = clk::now();
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (q->bytes > s->budget) {
+        ++s->rejected;
+        delete q;
+        wfa::set_error("request needs %zu bytes, above the server budget %zu", device_bytes(*r), s->budget);
+        return WFA_ERR_BUDGET;
+    }
+    q->ticket = s->next_ticket++;
+    s->all[q->ticket] = q;
+    s->pending.push_back(q);
+    ++s->submitted;
+    *ticket = q->ticket;
+    s->cv_work.notify_one();
+    return WFA_OK;
+}
+
+int wfa_server_poll(wfa_server s, long long ticket, int* done) {
+    if (!s || !done) return WFA_ERR_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) {
+        wfa::set_error("unknown ticket %lld", ticket);
+        return WFA_ERR_ARG;
+    }
+    const Req* r = it->second;
+    *done = r->state == 2 ? 1 : (r->state < 0 ? -1 : 0);
+    if (r->state < 0) wfa::set_error("%s", r->err.c_str());
+    return WFA_OK;
+}
+
+int wfa_server_wait(wfa_server s, long long ticket, double timeout_s) {
+    if (!s) return WFA_ERR_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) {
+        wfa::set_error("unknown ticket %lld", ticket);
+        return WFA_ERR_ARG;
+    }
+    Req* r = it->second;
+    const auto deadline = clk::now() + std::chrono::duration_cast<clk::duration>(
+                                           std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 1e9));
+    if (!s->cv_done.wait_until(lk, deadline, [&] { return r->state == 2 || r->state < 0; })) {
+        wfa::set_error("ticket %lld not done within %.3f s", ticket, timeout_s);
+        return WFA_ERR_TIMEOUT;
+    }
+    if (r->state < 0) {
+        wfa::set_error("%s", r->err.c_str());
+        return WFA_ERR_STATE;
+    }
+    return WFA_OK;
+}
+
+int wfa_server_stats_get(wfa_server s, wfa_server_stats* st) {
+    if (!s || !st) return WFA_ERR_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    memset(st, 0, sizeof *st);
+    st->submitted = s->submitted;
+    st->admitted = s->admitted;
+    st->completed = s->completed;
+    st->rejected = s->rejected;
+    st->ticks = s->ticks;
+    st->cell_updates = s->cell_updates;
+    st->busy_seconds = s->busy_s;
+    st->resident_bytes = s->used;
+    st->peak_resident_bytes = s->peak_used;
+    if (!s->latencies.empty()) {
+        std::vector<double> v = s->latencies;
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double p) {
+            const double pos = p * (v.size() - 1);
+            const size_t lo = (size_t)pos;
+            const size_t hi = std::min(lo + 1, v.size() - 1);
+            return v[lo] + (pos - lo) * (v[hi] - v[lo]);
+        };
+        st->p50_latency_s = pct(0.50);
+        st->p99_latency_s = pct(0.99);
+        double sum = 0;
+        for (double x : v) sum += x;
+        st->mean_latency_s = sum / v.size();
+    }
+    return WFA_OK;
+}
+
+int wfa_server_destroy(wfa_server s) {
+    if (!s) return WFA_OK;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+        s->cv_work.notify_all();
+    }
+    if (s->th.joinable()) s->th.join();
+    for (auto& kv : s->all) delete kv.second;
+    cudaStreamDestroy(s->stream);
+    delete s;
+    return WFA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,467 @@
+// Sweep kernels: D explicit finite-volume steps per pass over the grid
+// (arXiv 2209.13768, Sec. 1.1.1, Eq. expl_form in face-flux form).
+//
+// sweep_tb<S, KVAR, D, EX, EY, R> — the hot path.
+//   * One thread block owns an extended EX x EY tile of (x, y) columns and
+//     marches along z. Output is the inner (EX - 2 PX) x (EY - 2 D) tile; the
+//     ring of PX >= D columns and D rows around it is recomputed redundantly
+//     (overlapped tiling), so the D fused steps need no exchange with other
+//     blocks.
+//   * Input planes (and, for per-cell conductivity, k planes) arrive by TMA
+//     (cp.async.bulk.tensor.3d) into a ring of shared-memory slots, P planes
+//     ahead of use, each slot completing on its own mbarrier.
+//   * Stage s (1..D) at iteration j updates plane j - s (a wavefront in z):
+//     z-neighbours come from a per-thread register queue, x/y neighbours from
+//     one shared-memory plane per stage written at the end of the previous
+//     iteration.
+//   * Every thread owns 4 consecutive x cells in R consecutive rows (128-bit
+//     shared loads); face conductances between its own cells are computed
+//     once and used by both cells, the z face is carried to the next plane.
+//   * The last stage writes its plane straight to global memory (and to the
+//     periodic twins in the halo).
+// Bounded waits: a TMA that does not land within ~2 s sets the grid's status
+// word, the block drains its copies (bounded again) and exits.
+#pragma once
+
+#include "wfa_internal.cuh"
+
+namespace wfa {
+
+struct SweepArgs {
+    SweepCoef c;
+    const void* tin;    // input field, domain origin
+    void* tout;         // output field, domain origin
+    const float* k;     // conductivity, domain origin (nullptr for uniform k)
+    int tiles_x, tiles_y, zchunk, nzchunk, items;
+    int* status;
+};
+
+// --------------------------------------------------------------- PTX helpers --
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for one phase of an mbarrier; false after ~2 s without completion.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > 2000000000ull) return false;
+    }
+    return true;
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
+                                            int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// 4 consecutive stored values <-> 4 floats.
+template <typename S> struct Vec4;
+template <> struct Vec4<float> {
+    __device__ __forceinline__ static void load(const float* p, float v[4]) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
+    __device__ __forceinline__ static void store(float* p, const float v[4]) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <> struct Vec4<__nv_bfloat16> {
+    __device__ __forceinline__ static void load(const __nv_bfloat16* p, float v[4]) {
+        const uint2 q = *reinterpret_cast<const uint2*>(p);
+        const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&q.x);
+        const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&q.y);
+        v[0] = __low2float(a); v[1] = __high2float(a); v[2] = __low2float(b); v[3] = __high2float(b);
+    }
+    __device__ __forceinline__ static void store(__nv_bfloat16* p, const float v[4]) {
+        __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+        __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
+        uint2 q;
+        q.x = *reinterpret_cast<uint32_t*>(&a);
+        q.y = *reinterpret_cast<uint32_t*>(&b);
+        *reinterpret_cast<uint2*>(p) = q;
+    }
+};
+
+// ------------------------------------------------------------ simple kernel --
+// One thread per (x, y) column, neighbours read from global memory. One step.
+// Used for grids too small for the tiled kernel's box and as a second,
+// independent realisation of the same per-cell arithmetic.
+template <typename S, bool KVAR>
+__global__ void __launch_bounds__(256) sweep_simple(SweepArgs a) {
+    const SweepCoef& c = a.c;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= c.n[0] || y >= c.n[1]) return;
+    const S* __restrict__ in = (const S*)a.tin;
+    S* __restrict__ out = (S*)a.tout;
+    const long long st[3] = {1, c.sy, c.sz};
+    for (int z = 0; z < c.n[2]; ++z) {
+        const long long i = z * c.sz + y * c.sy + x;
+        const float tc = to_f32<S>(in[i]);
+        float v = tc;
+        if (!is_held(c, x, y, z)) {
+            const float kc = KVAR ? a.k[i] : 0.0f;
+            const int pos[3] = {x, y, z};
+            float tn[6], w[6];
+#pragma unroll
+            for (int f = 0; f < 6; ++f) {
+                const int ax = f >> 1, side = f & 1;
+                const bool edge = side ? pos[ax] == c.n[ax] - 1 : pos[ax] == 0;
+                if (edge && !c.periodic[ax]) {
+                    const bool dir = c.bkind[f] == WFA_BC_DIRICHLET;
+                    tn[f] = dir ? c.tb[f] : 0.0f;
+                    if (KVAR) w[f] = dir ? __fadd_rn(dirichlet_face(kc, c.cd[ax]), c.adv[f]) : 0.0f;
+                    else w[f] = c.w_bd[f];
+                } else {
+                    const long long j = i + (side ? st[ax] : -st[ax]);
+                    tn[f] = to_f32<S>(in[j]);
+                    w[f] = KVAR ? __fadd_rn(harm_face(kc, a.k[j], c.cd[ax]), c.adv[f]) : c.w_in[f];
+                }
+            }
+            v = cell_update(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], w[0], w[1], w[2], w[3], w[4], w[5],
+                            self_term(c, x, y, z));
+        }
+        store_with_twins<S>(out, c, x, y, z, from_f32<S>(v));
+    }
+}
+
+// --------------------------------------------------------- tiled kernel ----
+template <typename S, bool KVAR, int D, int EX, int EY, int R>
+struct TbCfg {
+    static constexpr int VA = 16 / (int)sizeof(S);          // elements per 16 bytes (TMA x alignment)
+    static constexpr int PX = ((D + VA - 1) / VA) * VA;     // x halo, a multiple of VA
+    static constexpr int TX = EX - 2 * PX;                  // output tile
+    static constexpr int TY = EY - 2 * D;
+    static constexpr int NTX = EX / 4, NTY = EY / R, NT = NTX * NTY;
+    static constexpr int MINB = (NT <= 256 && D <= 2) ? 2 : 1;   // blocks per SM the register budget targets
+    static constexpr int P = 2;                             // planes in flight ahead of use
+    static constexpr int NS = P + 2;                        // input ring slots (= mbarriers)
+    static constexpr int NK = KVAR ? D + P + 2 : 0;         // k ring slots
+    static constexpr int PLANE = EX * EY;
+    static constexpr size_t BAR_BYTES = 1024;   // mbarriers; keeps the ring 1024-byte aligned
+    static constexpr size_t RING_BYTES = (size_t)NS * PLANE * sizeof(S);
+    static constexpr size_t K_BYTES = (size_t)NK * PLANE * sizeof(float);
+    static constexpr size_t SBUF_BYTES = (size_t)(D > 1 ? D - 1 : 0) * PLANE * sizeof(float);
+    static constexpr size_t SMEM = 1024 + BAR_BYTES + RING_BYTES + K_BYTES + SBUF_BYTES;
+    static constexpr uint32_t TX_BYTES = (uint32_t)(PLANE * sizeof(S) + (KVAR ? PLANE * sizeof(float) : 0));
+    static_assert(EX % 4 == 0 && EX % VA == 0 && EX <= 256 && EY <= 256, "TMA box");
+    static_assert(EY % R == 0, "rows per thread");
+    static_assert(TX > 0 && TY > 0, "tile too small for this depth");
+    static_assert(NT <= 1024, "too many threads");
+    static_assert(D >= 1 && D <= MAX_DEPTH && PX <= HALO, "depth");
+    static_assert(SMEM <= 232448, "shared memory above the 227 KB a block may use");
+};
+
+template <typename S, bool KVAR, int D, int EX, int EY, int R>
+__global__ void __launch_bounds__(TbCfg<S, KVAR, D, EX, EY, R>::NT, TbCfg<S, KVAR, D, EX, EY, R>::MINB)
+    sweep_tb(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmK, SweepArgs a) {
+    using Cfg = TbCfg<S, KVAR, D, EX, EY, R>;
+    constexpr int PX = Cfg::PX, TX = Cfg::TX, TY = Cfg::TY, NTX = Cfg::NTX, NS = Cfg::NS, NK = Cfg::NK,
+                  P = Cfg::P, PLANE = Cfg::PLANE;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // TMA destinations: keep every slot 1024-byte aligned (SMEM reserves the slack)
+    unsigned char* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+    S* ring = reinterpret_cast<S*>(smem + Cfg::BAR_BYTES);
+    float* kring = reinterpret_cast<float*>(smem + Cfg::BAR_BYTES + Cfg::RING_BYTES);
+    float* sbuf = reinterpret_cast<float*>(smem + Cfg::BAR_BYTES + Cfg::RING_BYTES + Cfg::K_BYTES);
+
+    const SweepCoef& c = a.c;
+    const int tid = threadIdx.x;
+    const int xl = 4 * (tid % NTX);   // first local x of this thread's cells
+    const int yl = R * (tid / NTX);   // first local row
+    const bool perx = c.periodic[0], pery = c.periodic[1], perz = c.periodic[2];
+
+    if (tid == 0) {
+        for (int b = 0; b < NS; ++b) mbar_init(&bars[b], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    uint32_t cnt = 0;        // planes this block has consumed (ring slot / barrier phase)
+    uint32_t issued_hi = 0;  // thread 0: counter one past the last plane issued
+    uint32_t fail_idx = 0;
+    bool failed = false;
+
+    for (int item = blockIdx.x; item < a.items && !failed; item += gridDim.x) {
+        const int tix = item % a.tiles_x;
+        const int rest = item / a.tiles_x;
+        const int tiy = rest % a.tiles_y;
+        const int zci = rest / a.tiles_y;
+        const int x0 = tix * TX, y0 = tiy * TY;
+        const int z0 = zci * a.zchunk;
+        const int z1 = min(z0 + a.zchunk, c.n[2]);
+        const int jstart = z0 - D, jend = z1 + D;   // stage-0 planes streamed through
+        const int gx0 = x0 - PX + xl, gy0 = y0 - D + yl;
+
+        auto issue = [&](uint32_t idx, int plane) {
+            uint64_t* bar = &bars[idx % NS];
+            mbar_expect_tx(bar, Cfg::TX_BYTES);
+            tma_load_3d(ring + (idx % NS) * PLANE, &tmT, bar, x0 - PX + HALO, y0 - D + HALO, plane + HALO);
+            if (KVAR)
+                tma_load_3d(kring + (idx % (NK > 0 ? NK : 1)) * PLANE, &tmK, bar, x0 - PX + HALO,
+                            y0 - D + HALO, plane + HALO);
+        };
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            for (int p = 0; p <= P && jstart + p < jend; ++p) {
+                issue(cnt + p, jstart + p);
+                issued_hi = cnt + p + 1;
+            }
+        }
+
+        // per-cell constants over the march
+        bool bxm[4], bxp[4], bym[R], byp[R];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            bxm[i] = !perx && gx0 + i == 0;
+            bxp[i] = !perx && gx0 + i == c.n[0] - 1;
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            bym[r] = !pery && gy0 + r == 0;
+            byp[r] = !pery && gy0 + r == c.n[1] - 1;
+        }
+        const float tbxm = c.bkind[0] == WFA_BC_DIRICHLET ? c.tb[0] : 0.0f;
+        const float tbxp = c.bkind[1] == WFA_BC_DIRICHLET ? c.tb[1] : 0.0f;
+        const float tbym = c.bkind[2] == WFA_BC_DIRICHLET ? c.tb[2] : 0.0f;
+        const float tbyp = c.bkind[3] == WFA_BC_DIRICHLET ? c.tb[3] : 0.0f;
+        const float tbzm = c.bkind[4] == WFA_BC_DIRICHLET ? c.tb[4] : 0.0f;
+        const float tbzp = c.bkind[5] == WFA_BC_DIRICHLET ? c.tb[5] : 0.0f;
+
+        float zm[D][R][4], zc[D][R][4];   // stage s-1 outputs at planes q-1, q (s = 1..D)
+        float gz[D][R][4];                // per-cell k: conductance of the z face above the last plane
+#pragma unroll
+        for (int s = 0; s < D; ++s)
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) zm[s][r][i] = zc[s][r][i] = gz[s][r][i] = 0.0f;
+
+        for (int j = jstart; j < jend; ++j) {
+            const uint32_t idx = cnt + (uint32_t)(j - jstart);
+            // a copy that never lands leaves garbage in the slot; the block
+            // agrees to stop at the barrier below before issuing anything new
+            const bool late = !mbar_wait_bounded(&bars[idx % NS], (idx / NS) & 1u);
+            const S* cur0 = ring + (idx % NS) * PLANE;        // stage-0 plane j
+            const S* prev0 = ring + ((idx + NS - 1) % NS) * PLANE;  // stage-0 plane j-1
+
+            float nw[D + 1][R][4];
+#pragma unroll
+            for (int r = 0; r < R; ++r) Vec4<S>::load(cur0 + (yl + r) * EX + xl, nw[0][r]);
+
+#pragma unroll
+            for (int s = 1; s <= D; ++s) {
+                const int q = j - s;   // plane this stage updates
+                // only the columns later stages (or the output) depend on
+                const int lo_x = PX - (D - s), hi_x = EX - PX + (D - s);
+                const int lo_y = s, hi_y = EY - s;
+                const bool need = xl + 4 > lo_x && xl < hi_x && yl + R > lo_y && yl < hi_y;
+                if (!need) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) nw[s][r][i] = 0.0f;
+                    continue;
+                }
+                // x/y neighbours of stage s-1 at plane q
+                auto nb = [&](int xx, int yy) -> float {
+                    xx = min(max(xx, 0), EX - 1);
+                    yy = min(max(yy, 0), EY - 1);
+                    if (s == 1) return to_f32<S>(prev0[yy * EX + xx]);
+                    return sbuf[(s - 2) * PLANE + yy * EX + xx];
+                };
+                float below[4], above[4];
+                {
+                    const int yb = max(yl - 1, 0), ya = min(yl + R, EY - 1);
+                    if (s == 1) {
+                        Vec4<S>::load(prev0 + yb * EX + xl, below);
+                        Vec4<S>::load(prev0 + ya * EX + xl, above);
+                    } else {
+                        Vec4<float>::load(sbuf + (s - 2) * PLANE + yb * EX + xl, below);
+                        Vec4<float>::load(sbuf + (s - 2) * PLANE + ya * EX + xl, above);
+                    }
+                }
+                const bool bzm = !perz && q == 0, bzp = !perz && q == c.n[2] - 1;
+
+                // per-cell k: this stage's k plane (q) and the one above (q + 1)
+                constexpr uint32_t NKS = NK > 0 ? NK : 1;
+                const float* kq = kring + ((idx + 2u * NKS - (uint32_t)s) % NKS) * PLANE;
+                const float* kqp = kring + ((idx + 2u * NKS - (uint32_t)s + 1u) % NKS) * PLANE;
+                float kc[R][4], kb[4], ka[4];
+                if (KVAR) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) Vec4<float>::load(kq + (yl + r) * EX + xl, kc[r]);
+                    Vec4<float>::load(kq + max(yl - 1, 0) * EX + xl, kb);
+                    Vec4<float>::load(kq + min(yl + R, EY - 1) * EX + xl, ka);
+                }
+
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float left = nb(xl - 1, yl + r);
+                    const float right = nb(xl + 4, yl + r);
+                    const int gy = gy0 + r;
+                    float gx[5], kzp[4];
+                    if (KVAR) {
+                        const float kl = kq[(yl + r) * EX + max(xl - 1, 0)];
+                        const float kr = kq[(yl + r) * EX + min(xl + 4, EX - 1)];
+                        gx[0] = harm_face(kl, kc[r][0], c.cd[0]);
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) gx[i + 1] = harm_face(kc[r][i], kc[r][i + 1], c.cd[0]);
+                        gx[4] = harm_face(kc[r][3], kr, c.cd[0]);
+                        Vec4<float>::load(kqp + (yl + r) * EX + xl, kzp);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float tc = zc[s - 1][r][i];
+                        float txm = i == 0 ? left : zc[s - 1][r][i - 1];
+                        float txp = i == 3 ? right : zc[s - 1][r][i + 1];
+                        float tym = r == 0 ? below[i] : zc[s - 1][r - 1][i];
+                        float typ = r == R - 1 ? above[i] : zc[s - 1][r + 1][i];
+                        float tzm = zm[s - 1][r][i];
+                        float tzp = nw[s - 1][r][i];
+                        if (bxm[i]) txm = tbxm;
+                        if (bxp[i]) txp = tbxp;
+                        if (bym[r]) tym = tbym;
+                        if (byp[r]) typ = tbyp;
+                        if (bzm) tzm = tbzm;
+                        if (bzp) tzp = tbzp;
+                        float wxm, wxp, wym, wyp, wzm, wzp;
+                        if (KVAR) {
+                            const float kk = kc[r][i];
+                            const float gym = harm_face(r == 0 ? kb[i] : kc[r - 1][i], kk, c.cd[1]);
+                            const float gyp = harm_face(kk, r == R - 1 ? ka[i] : kc[r + 1][i], c.cd[1]);
+                            const float gzm_ = gz[s - 1][r][i];
+                            const float gzp_ = harm_face(kk, kzp[i], c.cd[2]);
+                            gz[s - 1][r][i] = gzp_;
+                            const float dx = dirichlet_face(kk, c.cd[0]);
+                            const float dy = dirichlet_face(kk, c.cd[1]);
+                            const float dz = dirichlet_face(kk, c.cd[2]);
+                            wxm = bxm[i] ? (c.bkind[0] == WFA_BC_DIRICHLET ? __fadd_rn(dx, c.adv[0]) : 0.0f)
+                                         : __fadd_rn(gx[i], c.adv[0]);
+                            wxp = bxp[i] ? (c.bkind[1] == WFA_BC_DIRICHLET ? __fadd_rn(dx, c.adv[1]) : 0.0f)
+                                         : __fadd_rn(gx[i + 1], c.adv[1]);
+                            wym = bym[r] ? (c.bkind[2] == WFA_BC_DIRICHLET ? __fadd_rn(dy, c.adv[2]) : 0.0f)
+                                         : __fadd_rn(gym, c.adv[2]);
+                            wyp = byp[r] ? (c.bkind[3] == WFA_BC_DIRICHLET ? __fadd_rn(dy, c.adv[3]) : 0.0f)
+                                         : __fadd_rn(gyp, c.adv[3]);
+                            wzm = bzm ? (c.bkind[4] == WFA_BC_DIRICHLET ? __fadd_rn(dz, c.adv[4]) : 0.0f)
+                                      : __fadd_rn(gzm_, c.adv[4]);
+                            wzp = bzp ? (c.bkind[5] == WFA_BC_DIRICHLET ? __fadd_rn(dz, c.adv[5]) : 0.0f)
+                                      : __fadd_rn(gzp_, c.adv[5]);
+                        } else {
+                            wxm = bxm[i] ? c.w_bd[0] : c.w_in[0];
+                            wxp = bxp[i] ? c.w_bd[1] : c.w_in[1];
+                            wym = bym[r] ? c.w_bd[2] : c.w_in[2];
+                            wyp = byp[r] ? c.w_bd[3] : c.w_in[3];
+                            wzm = bzm ? c.w_bd[4] : c.w_in[4];
+                            wzp = bzp ? c.w_bd[5] : c.w_in[5];
+                        }
+                        const int gx_ = gx0 + i;
+                        float v;
+                        if (is_held(c, gx_, gy, q)) {
+                            v = tc;
+                        } else {
+                            v = cell_update(tc, txm, txp, tym, typ, tzm, tzp, wxm, wxp, wym, wyp, wzm, wzp,
+                                            self_term(c, gx_, gy, q));
+                        }
+                        nw[s][r][i] = storage_round<S>(v);
+                    }
+                }
+            }
+
+            // every read of prev0 and of the stage planes is done
+            if (__syncthreads_or(late)) {
+                failed = true;
+                fail_idx = idx;
+                break;
+            }
+#pragma unroll
+            for (int s = 1; s < D; ++s)
+#pragma unroll
+                for (int r = 0; r < R; ++r) Vec4<float>::store(sbuf + (s - 1) * PLANE + (yl + r) * EX + xl, nw[s][r]);
+#pragma unroll
+            for (int s = 0; s < D; ++s)
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        zm[s][r][i] = zc[s][r][i];
+                        zc[s][r][i] = nw[s][r][i];
+                    }
+
+            // output: stage D at plane j - D
+            {
+                const int q = j - D;
+                if (q >= z0 && q < z1 && xl >= PX && xl < PX + TX) {
+                    S* out = (S*)a.tout;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const int ly = yl + r, gy = gy0 + r;
+                        if (ly < D || ly >= D + TY || gy >= c.n[1]) continue;
+                        const int gx = gx0;
+                        const bool plain = gx + 3 < c.n[0] && !(perx && (gx < HALO || gx + 3 >= c.n[0] - HALO)) &&
+                                           !(pery && (gy < HALO || gy >= c.n[1] - HALO)) &&
+                                           !(perz && (q < HALO || q >= c.n[2] - HALO));
+                        if (plain) {
+                            Vec4<S>::store(out + (long long)q * c.sz + (long long)gy * c.sy + gx, nw[D][r]);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                if (gx + i < c.n[0]) store_with_twins<S>(out, c, gx + i, gy, q, from_f32<S>(nw[D][r][i]));
+                        }
+                    }
+                }
+            }
+            __syncthreads();   // stage planes written; the ring slot of plane j-1 is free
+            if (tid == 0 && j + P + 1 < jend) {
+                fence_proxy_async_smem();
+                issue(idx + P + 1, j + P + 1);
+                issued_hi = idx + P + 2;
+            }
+        }
+        if (failed) break;
+        cnt += (uint32_t)(jend - jstart);
+    }
+
+    if (failed) {
+        // drain: wait (bounded) for the copies this block issued and has not consumed
+        if (tid == 0) {
+            atomicExch(a.status, 1);
+            for (uint32_t u = fail_idx; u < issued_hi; ++u) (void)mbar_wait_bounded(&bars[u % NS], (u / NS) & 1u);
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace wfa

@@ -1,0 +1,72 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry
+point that include/wfa.h declares; the product path never touches the oracle."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
+
+
+def declared_functions():
+    names = set()
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(wfa_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2209_13768_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("wfa_create_grid", "wfa_set_coeffs", "wfa_set_bc", "wfa_step", "wfa_read_field",
+              "wfa_stability_dt", "wfa_total_heat", "wfa_batch_run", "wfa_server_submit"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = declared_functions() - exported
+    assert not missing, f"declared but not exported: {sorted(missing)}"
+
+
+def test_binding_loads_without_gpu_and_types_every_symbol(libpath):
+    import paper_2209_13768_gb300 as wfa
+    L = wfa.lib()
+    assert set(wfa.SIGNATURES) == declared_functions()
+    for name in declared_functions():
+        assert getattr(L, name) is not None
+    assert wfa.last_error() == ""
+
+
+def test_argument_errors_need_no_gpu(libpath):
+    import ctypes
+    import paper_2209_13768_gb300 as wfa
+    L = wfa.lib()
+    out = ctypes.c_void_p()
+    assert L.wfa_create_grid(1, 4, 4, 1.0, 1.0, 1.0, 0, None, ctypes.byref(out)) == -1
+    assert "edge" in wfa.last_error()
+    assert L.wfa_create_grid(4, 4, 4, -1.0, 1.0, 1.0, 0, None, ctypes.byref(out)) == -1
+    assert L.wfa_create_grid(4, 4, 4, 1.0, 1.0, 1.0, 7, None, ctypes.byref(out)) == -1
+    assert L.wfa_step(None, 1) == -1
+    assert L.wfa_destroy_grid(None) == 0
+
+
+def test_product_path_does_not_use_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2209_13768_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "wfa_oracle" not in text, f

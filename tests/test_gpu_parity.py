@@ -1,0 +1,226 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances. FP32 fields: L-infinity error relative to max |T| <= 1e-5 after
+100 steps (the update is a convex combination for dt <= dt_max, so per-step
+fp32 rounding, ~6e-8 relative, adds up at most linearly: 100 steps stay well
+below 1e-5). BF16 storage: <= (n + 1) * 2^-9 relative (initial rounding plus
+one nearest-even rounding per step, propagated without growth by the same
+non-expansive update), and against the oracle run with the same per-step
+bf16 rounding, within a few bf16 ulps where fp32 vs fp64 arithmetic tips a
+rounding. Across kernels (tile shapes, temporal depths, the one-column
+kernel) the per-cell expression is fixed, so fields must be bit-identical.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2209_13768_gb300 as wfa
+from paper_2209_13768_gb300 import workloads as W
+from helpers import make_grid, oracle_dt, rel_linf, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+D, ZF, P, DC = W.D, W.ZF, W.P, W.DC
+F32_TOL = 1e-5
+
+
+def bf16_bound(steps):
+    return (steps + 1) * 2.0**-9
+
+
+# ---------------------------------------------------------------- config 1 --
+@pytest.mark.parametrize("held", [False, True])
+def test_heat64_matches_oracle(held):
+    p = W.heat_64(held_cells=held)
+    ref = run_oracle(p)
+    assert abs(oracle_dt(p) - (0.9 / 6 if held else 0.1)) < 1e-15
+    outs = {}
+    for variant, depth in [(-1, 1), (1, 1), (1, 2), (1, 4), (2, 3), (1, 8), (2, 8), (0, 0)]:
+        T = run_gpu(p, depth=depth, variant=variant)
+        err = rel_linf(T, ref)
+        assert err <= F32_TOL, (variant, depth, err)
+        outs[(variant, depth)] = T
+    base = outs[(-1, 1)]
+    for key, T in outs.items():
+        np.testing.assert_array_equal(T, base, err_msg=str(key))
+
+
+def test_heat64_dt_limit_on_gpu():
+    p = W.heat_64()
+    with make_grid(p) as g:
+        assert abs(g.stability_dt() - 1.0 / 9.0) < 1e-15
+    p = W.heat_64(held_cells=True)
+    with make_grid(p) as g:
+        assert abs(g.stability_dt() - 1.0 / 6.0) < 1e-15
+
+
+# ----------------------------------------------------- every boundary mix --
+MIXES = [
+    [(D, 0.3), (D, -0.7), (D, 1.0), (D, 0.0), (D, 0.5), (D, 2.0)],
+    [(ZF, 0)] * 6,
+    [(P, 0)] * 6,
+    [(DC, 0.25), (DC, 0.75), (DC, -0.5), (DC, 1.0), (DC, 0.1), (DC, 0.2)],
+    [(D, 1.0), (ZF, 0), (P, 0), (P, 0), (DC, 0.5), (D, 0.0)],
+    [(DC, 1.0), (D, 0.0), (ZF, 0), (DC, 0.3), (P, 0), (P, 0)],
+    [(P, 0), (P, 0), (D, 0.2), (ZF, 0), (ZF, 0), (D, 0.8)],
+]
+
+
+def _mixed_problem(mix, shape=(37, 29, 23), kvar=True, adv=True, seed=0):
+    rng = np.random.default_rng(1000 + seed)
+    nx, ny, nz = shape
+    k = np.exp(0.5 * rng.standard_normal((nz, ny, nx))).astype(np.float32) if kvar else 0.8
+    u = tuple(rng.uniform(-0.4, 0.4, 3)) if adv else (0.0, 0.0, 0.0)
+    h = tuple(rng.uniform(0.8, 1.25, 3))
+    T0 = rng.uniform(0, 1, (nz, ny, nx)).astype(np.float32)
+    return W.Problem(shape=shape, T0=T0, k=k, u=u, bc=MIXES[mix], h=h, steps=20)
+
+
+@pytest.mark.parametrize("kvar,adv", [(True, True), (False, True), (True, False), (False, False)])
+@pytest.mark.parametrize("mix", range(len(MIXES)))
+def test_boundary_mixes_all_kernels(mix, kvar, adv):
+    p = _mixed_problem(mix, kvar=kvar, adv=adv, seed=mix)
+    ref = run_oracle(p)
+    base = run_gpu(p, variant=-1)
+    assert rel_linf(base, ref) <= F32_TOL
+    for variant in (1, 2):
+        for depth in range(1, 9):
+            T = run_gpu(p, depth=depth, variant=variant)
+            np.testing.assert_array_equal(T, base, err_msg=f"variant {variant} depth {depth}")
+
+
+@pytest.mark.parametrize("shape", [(2, 2, 2), (3, 2, 5), (5, 7, 3), (64, 3, 9), (131, 67, 4)])
+def test_small_and_ragged_shapes(shape):
+    for mix in (0, 2, 4):
+        if any(k == DC for k, _ in MIXES[mix]) and min(shape) < 3:
+            continue
+        p = _mixed_problem(mix, shape=shape, seed=7)
+        p.steps = 9
+        ref = run_oracle(p)
+        base = run_gpu(p, variant=-1)
+        assert rel_linf(base, ref) <= F32_TOL
+        for depth in (1, 3, 8):
+            np.testing.assert_array_equal(run_gpu(p, depth=depth, variant=1), base)
+
+
+def test_zero_steps_and_step_accounting():
+    p = _mixed_problem(4)
+    with make_grid(p) as g:
+        g.step(0)
+        T = g.read_field()
+        held = oracle.run(p.T0, 0, shape=p.shape, h=p.h, k=np.asarray(p.k, np.float64), u=p.u, bc=p.bc, dt=0.1)
+        np.testing.assert_array_equal(T, held.astype(np.float32))
+        g.step(5)
+        g.step(6)
+        assert g.steps_done() == 11
+        np.testing.assert_array_equal(g.read_field(), run_gpu(p, steps=11))
+
+
+# -------------------------------------------------------------- bf16 ------
+@pytest.mark.parametrize("mix", [0, 2, 4])
+def test_bf16_storage(mix):
+    p = _mixed_problem(mix, seed=3)
+    p.steps = 30
+    ref = run_oracle(p)
+    ref_rounded = run_oracle(p, round_to="bf16", T0=oracle.round_to(p.T0, "bf16"))
+    base = run_gpu(p, storage=wfa.BF16, variant=-1)
+    assert rel_linf(base, ref) <= bf16_bound(p.steps)
+    # same per-step rounding as the oracle diagnostic: at most a few bf16 ulps apart
+    ulp = 2.0**-7 * np.maximum(np.abs(ref_rounded), 2.0**-126)
+    assert np.max(np.abs(base - ref_rounded) / ulp) <= 4.0
+    for depth in (1, 2, 5, 8):
+        for variant in (1, 2):
+            np.testing.assert_array_equal(run_gpu(p, storage=wfa.BF16, depth=depth, variant=variant), base)
+
+
+# ------------------------------------------------------ reductions (fp64) --
+def test_stability_dt_matches_oracle():
+    for mix in range(len(MIXES)):
+        p = _mixed_problem(mix, seed=11)
+        ref = oracle.dt_max(shape=p.shape, h=p.h, k=np.asarray(p.k, np.float64), u=p.u, bc=p.bc)
+        with make_grid(p) as g:
+            got = g.stability_dt()
+        assert abs(got - ref) <= 1e-13 * ref, (mix, got, ref)
+
+
+def test_unstable_dt_rejected():
+    p = _mixed_problem(0)
+    with make_grid(p) as g:
+        lim = g.stability_dt()
+        g.set_dt(lim)   # the limit itself is allowed
+        with pytest.raises(wfa.WfaError) as e:
+            g.set_dt(lim * 1.001)
+        assert e.value.code == -4
+
+
+def test_total_heat_matches_oracle():
+    for storage in (wfa.F32, wfa.BF16):
+        p = _mixed_problem(1, seed=5)
+        with make_grid(p, storage=storage) as g:
+            g.step(7)
+            T = g.read_field()
+            e = g.total_heat()
+        ref = oracle.total_heat(T.astype(np.float64), p.h)
+        assert abs(e - ref) <= 1e-12 * abs(ref)
+
+
+@pytest.mark.parametrize("mix", [1, 2])
+def test_conservation_on_gpu(mix):
+    # zero-flux / periodic faces: total heat changes only by fp32 rounding
+    p = _mixed_problem(mix, shape=(48, 40, 36), seed=2)
+    with make_grid(p) as g:
+        e0 = g.total_heat()
+        g.step(200)
+        e1 = g.total_heat()
+    assert abs(e1 - e0) <= 1e-5 * abs(e0)
+
+
+# ------------------------------------------------------- state & errors --
+def test_call_order_errors():
+    g = wfa.Grid((8, 8, 8))
+    with pytest.raises(wfa.WfaError) as e:
+        g.step(1)
+    assert e.value.code == -7
+    g.set_bcs([(P, 0), (D, 0)] + [(ZF, 0)] * 4)
+    g.set_coeffs(1.0)
+    with pytest.raises(wfa.WfaError) as e:
+        g.stability_dt()
+    assert e.value.code == -3
+    g.close()
+
+
+def test_checkpoint_resume_is_bitwise():
+    p = _mixed_problem(4, seed=9)
+    full = run_gpu(p, steps=23, depth=3, variant=1)
+    with make_grid(p, depth=2, variant=2) as g:
+        g.step(10)
+        mid = g.read_field()
+    q = W.Problem(shape=p.shape, T0=mid, k=p.k, u=p.u, bc=p.bc, h=p.h)
+    with make_grid(q, dt=None) as g2:
+        g2.set_dt(run_dt(p))
+        g2.step(13)
+        np.testing.assert_array_equal(g2.read_field(), full)
+
+
+def run_dt(p):
+    with make_grid(p) as g:
+        return p.dt if p.dt else p.dt_factor * g.stability_dt()
+
+
+# ------------------------------------------ reduced copies of the configs --
+def test_lognormal_reduced():
+    p = W.heat_lognormal(shape=(96, 80, 72), steps=100)
+    ref = run_oracle(p)
+    for depth in (1, 2, 4):
+        T = run_gpu(p, depth=depth)
+        assert rel_linf(T, ref) <= F32_TOL
+        assert T.min() >= -1e-6 and T.max() <= 1 + 1e-6   # maximum principle
+
+
+@pytest.mark.parametrize("storage", [wfa.F32, wfa.BF16])
+def test_advection_diffusion_reduced(storage):
+    p = W.advection_diffusion(shape=(128, 96, 64), steps=100)
+    ref = run_oracle(p)
+    T = run_gpu(p, storage=storage)
+    err = rel_linf(T, ref)
+    assert err <= (F32_TOL if storage == wfa.F32 else bf16_bound(p.steps)), err
