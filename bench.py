@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["lognormal", "heat64", "advdiff", "advdiff_bf16"], default="lognormal")
     ap.add_argument("--solve-steps", type=int, default=0, help="time steps per benchmark step (0: workload default)")
+    ap.add_argument("--shape", type=str, default="", help="NX,NY,NZ: same physics on another grid (profiling)")
     ap.add_argument("--depth", type=int, default=0, help="fused steps per pass (0: tuned)")
     ap.add_argument("--variant", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
@@ -60,14 +61,15 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def workload(name, solve_steps):
+def workload(name, solve_steps, shape=""):
     from paper_2209_13768_gb300 import workloads as W
+    kw = {"shape": tuple(int(v) for v in shape.split(","))} if shape else {}
     if name == "lognormal":
-        p = W.heat_lognormal()
+        p = W.heat_lognormal(**kw)
     elif name == "heat64":
         p = W.heat_64()
     else:
-        p = W.advection_diffusion()
+        p = W.advection_diffusion(**kw)
     if solve_steps:
         p.steps = solve_steps
     return p
@@ -156,7 +158,7 @@ def reference_arm(args, rank):
     import numpy as np
 
     import oracle
-    p = workload(args.workload, args.solve_steps)
+    p = workload(args.workload, args.solve_steps, args.shape)
     k = p.k if isinstance(p.k, float) else np.asarray(p.k, dtype=np.float64)
     dt = p.dt if p.dt else 0.9 * oracle.dt_max(shape=p.shape, h=p.h, k=k, u=p.u, bc=p.bc)
     T = np.asarray(p.T0, dtype=np.float64)
@@ -203,7 +205,7 @@ def main():
     from paper_2209_13768_gb300 import build as wfa_build
     wfa_build.build()
 
-    p = workload(args.workload, args.solve_steps)
+    p = workload(args.workload, args.solve_steps, args.shape)
     storage = wfa.BF16 if args.workload == "advdiff_bf16" else wfa.F32
     kvar = not np.isscalar(p.k)
     cells = p.shape[0] * p.shape[1] * p.shape[2]

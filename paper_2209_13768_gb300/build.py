@@ -50,14 +50,20 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
+    """WFA_CHECKED=1 in the environment builds the self-checking variant
+    (bounds-checked global stores and TMA coordinates, -DWFA_CHECKED)."""
+    checked = os.environ.get("WFA_CHECKED", "") not in ("", "0")
+    stamp = LIB + ".flags"
+    want = "checked" if checked else "release"
+    have = open(stamp).read() if os.path.exists(stamp) else "release"
+    if not force and up_to_date() and have == want:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [cc] + ARCH + FLAGS + ["-c", src, "-o", obj]
+        cmd = [cc] + ARCH + FLAGS + (["-DWFA_CHECKED"] if checked else []) + ["-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -77,6 +83,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr[-6000:]}")
     os.replace(tmp, LIB)
+    with open(stamp, "w") as f:
+        f.write(want)
     return LIB
 
 

@@ -43,6 +43,11 @@ int build_coef(const wfa_grid_s* g, SweepCoef* c) {
     for (int a = 0; a < 3; ++a) c->n[a] = g->n[a];
     c->sy = g->px;
     c->sz = g->px * g->py;
+    c->px = g->px;
+    c->py = g->py;
+    c->pz = g->pz;
+    c->lo = -domain_offset(g);
+    c->hi = (long long)field_elems(g) - domain_offset(g);
     const double dt = g->dt;
     for (int a = 0; a < 3; ++a) {
         const int lo = g->bc_kind[2 * a], hi = g->bc_kind[2 * a + 1];
@@ -86,7 +91,7 @@ struct Geo {
 };
 
 template <typename S>
-__global__ void pack_kernel(const float* __restrict__ dense, S* __restrict__ origin, Geo geo) {
+__global__ void pack_kernel(const float* __restrict__ dense, S* __restrict__ origin, const __grid_constant__ Geo geo) {
     const long long N = (long long)geo.n[0] * geo.n[1] * geo.n[2];
     const long long sz = geo.px * geo.py;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
@@ -100,7 +105,7 @@ __global__ void pack_kernel(const float* __restrict__ dense, S* __restrict__ ori
 }
 
 template <typename S>
-__global__ void unpack_kernel(const S* __restrict__ origin, float* __restrict__ dense, Geo geo) {
+__global__ void unpack_kernel(const S* __restrict__ origin, float* __restrict__ dense, const __grid_constant__ Geo geo) {
     const long long N = (long long)geo.n[0] * geo.n[1] * geo.n[2];
     const long long sz = geo.px * geo.py;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
@@ -139,7 +144,7 @@ __device__ __forceinline__ bool held_value(const HaloSpec& h, int x, int y, int 
 // Write the held layers and the halo (periodic twins; 0 elsewhere) of one
 // padded buffer. Every cell of the padded box is visited once.
 template <typename S>
-__global__ void halo_kernel(S* __restrict__ base, HaloSpec h, long long total) {
+__global__ void halo_kernel(S* __restrict__ base, const __grid_constant__ HaloSpec h, long long total) {
     const long long ex = h.n[0] + 2 * HALO, ey = h.n[1] + 2 * HALO;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
@@ -217,7 +222,7 @@ constexpr int RED_BLOCKS = 304;
 constexpr int RED_THREADS = 256;
 
 template <typename S>
-__global__ void __launch_bounds__(RED_THREADS) heat_partial_kernel(const S* __restrict__ origin, Geo geo,
+__global__ void __launch_bounds__(RED_THREADS) heat_partial_kernel(const S* __restrict__ origin, const __grid_constant__ Geo geo,
                                                                    double* __restrict__ partials) {
     __shared__ double sh[RED_THREADS];
     const long long N = (long long)geo.n[0] * geo.n[1] * geo.n[2];
@@ -268,7 +273,7 @@ __device__ __forceinline__ double harm64(double a, double b) {
 }
 
 // D_C of one cell in fp64 (see wfa_stability_dt), 0 for held cells.
-__global__ void __launch_bounds__(RED_THREADS) rate_partial_kernel(const float* __restrict__ korigin, RateSpec r,
+__global__ void __launch_bounds__(RED_THREADS) rate_partial_kernel(const float* __restrict__ korigin, const __grid_constant__ RateSpec r,
                                                                    double* __restrict__ partials) {
     __shared__ double sh[RED_THREADS];
     const long long N = (long long)r.n[0] * r.n[1] * r.n[2];
@@ -331,7 +336,7 @@ __global__ void __launch_bounds__(512) finish_max_kernel(const double* __restric
 }
 
 // k halo: periodic twins (the harmonic mean across a wrap face reads them), 0 elsewhere.
-__global__ void k_halo_kernel(float* __restrict__ base, HaloSpec h, long long total) {
+__global__ void k_halo_kernel(float* __restrict__ base, const __grid_constant__ HaloSpec h, long long total) {
     const long long ex = h.n[0] + 2 * HALO, ey = h.n[1] + 2 * HALO;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
@@ -353,13 +358,16 @@ __global__ void k_halo_kernel(float* __restrict__ base, HaloSpec h, long long to
 }
 
 int check_status(wfa_grid_s* g) {
-    WFA_CUDA(cudaMemcpyAsync(g->h_status, g->d_status, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    WFA_CUDA(cudaMemcpyAsync(g->h_status, g->d_status, 8 * sizeof(int), cudaMemcpyDeviceToHost, g->stream));
     WFA_CUDA(cudaStreamSynchronize(g->stream));
-    if (*g->h_status != 0) {
-        const int code = *g->h_status;
-        *g->h_status = 0;
-        cudaMemsetAsync(g->d_status, 0, sizeof(int), g->stream);
+    if (g->h_status[0] != 0) {
+        const int* st = g->h_status;
+        const int code = st[0];
+        cudaMemsetAsync(g->d_status, 0, 8 * sizeof(int), g->stream);
         cudaStreamSynchronize(g->stream);
+        if (code >= 10)
+            return fail(WFA_ERR_CUDA, "checked build: bad access, code %d at (%d, %d, %d) extra %d", code, st[1],
+                        st[2], st[3], st[4]);
         return fail(WFA_ERR_TIMEOUT, "a device-side wait gave up after its time limit (code %d)", code);
     }
     return WFA_OK;
@@ -400,9 +408,9 @@ int wfa_create_grid(int nx, int ny, int nz, double hx, double hy, double hz, int
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&g->T[b], bytes);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_partials, 4096 * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost(&g->h_result, 64);
-    if (e == cudaSuccess) e = cudaMalloc(&g->d_status, sizeof(int));
-    if (e == cudaSuccess) e = cudaMallocHost(&g->h_status, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_status, 0, sizeof(int), g->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_status, 8 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&g->h_status, 8 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_status, 0, 8 * sizeof(int), g->stream);
     if (e == cudaSuccess) {
         for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMemsetAsync(g->T[b], 0, bytes, g->stream);
     }

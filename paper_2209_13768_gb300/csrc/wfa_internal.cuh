@@ -33,10 +33,12 @@ constexpr int NUM_TILE_VARIANTS = 2;  // tile shapes compiled per (storage, k mo
 // ---------------------------------------------------------------- errors --
 void set_error(const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
-#define WFA_CUDA(call)                                                  \
-    do {                                                                \
-        cudaError_t e_ = (call);                                        \
-        if (e_ != cudaSuccess) return ::wfa::cuda_fail(e_, #call);      \
+#define WFA_STR2(x) #x
+#define WFA_STR(x) WFA_STR2(x)
+#define WFA_CUDA(call)                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) return ::wfa::cuda_fail(e_, #call " (" __FILE__ ":" WFA_STR(__LINE__) ")"); \
     } while (0)
 
 // ------------------------------------------------------- kernel parameters --
@@ -55,7 +57,26 @@ struct SweepCoef {
     float s_lo[3], s_hi[3];  // self term of a cell on a zero-flux face with advection
     int held[6];           // face holds its outer cell layer (Dirichlet cell)
     int any_self;          // some zero-flux face carries a self term
+    long long px, py, pz;  // padded extents (TMA coordinates live in [0, p*))
+    long long lo, hi;      // valid element offsets relative to the domain origin
 };
+
+// Self-checking build (-DWFA_CHECKED): global stores and TMA coordinates are
+// checked against their allocation; a bad one is recorded in the grid's
+// status words (code, x, y, z, extra) and skipped instead of performed.
+#ifdef WFA_CHECKED
+__device__ __forceinline__ bool wfa_chk(bool ok, int* st, int code, int x, int y, int z, int e) {
+    if (!ok && st) {
+        if (atomicCAS(st, 0, code) == 0) {
+            st[1] = x; st[2] = y; st[3] = z; st[4] = e;
+        }
+    }
+    return ok;
+}
+#define WFA_CHK(ok, st, code, x, y, z, e) ::wfa::wfa_chk((ok), (st), (code), (x), (y), (z), (e))
+#else
+#define WFA_CHK(ok, st, code, x, y, z, e) true
+#endif
 
 }  // namespace wfa
 
@@ -168,24 +189,36 @@ template <typename S> __device__ __forceinline__ float storage_round(float v) {
     return to_f32<S>(from_f32<S>(v));
 }
 
+// Twins of coordinate x along an axis of n cells inside [-HALO, n + HALO):
+// the first one and how many there are (1 when the axis is not periodic or x
+// is far from both ends).
+__device__ __forceinline__ void twin_range(int x, int n, bool periodic, int* first, int* count) {
+    if (periodic && (x < HALO || x >= n - HALO)) {
+        const int lo = x - ((x + HALO) / n) * n;           // smallest twin >= -HALO
+        *first = lo;
+        *count = (n + HALO - 1 - lo) / n + 1;              // twins below n + HALO
+    } else {
+        *first = x;
+        *count = 1;
+    }
+}
+
 // Write v at (x, y, z) and at every periodic twin of that cell inside the halo.
 template <typename S>
 __device__ __forceinline__ void store_with_twins(S* origin, const SweepCoef& c, int x, int y, int z,
-                                                 S v) {
-    origin[(long long)z * c.sz + (long long)y * c.sy + x] = v;
-    const bool nearx = c.periodic[0] && (x < HALO || x >= c.n[0] - HALO);
-    const bool neary = c.periodic[1] && (y < HALO || y >= c.n[1] - HALO);
-    const bool nearz = c.periodic[2] && (z < HALO || z >= c.n[2] - HALO);
-    if (!(nearx || neary || nearz)) return;
-    // twins: coordinate + m * n inside [-HALO, n + HALO)
-    for (int zz = nearz ? z - ((z + HALO) / c.n[2]) * c.n[2] : z; zz < c.n[2] + HALO;
-         zz += nearz ? c.n[2] : (1 << 30)) {
-        for (int yy = neary ? y - ((y + HALO) / c.n[1]) * c.n[1] : y; yy < c.n[1] + HALO;
-             yy += neary ? c.n[1] : (1 << 30)) {
-            for (int xx = nearx ? x - ((x + HALO) / c.n[0]) * c.n[0] : x; xx < c.n[0] + HALO;
-                 xx += nearx ? c.n[0] : (1 << 30)) {
-                if (xx == x && yy == y && zz == z) continue;
-                origin[(long long)zz * c.sz + (long long)yy * c.sy + xx] = v;
+                                                 S v, int* st = nullptr) {
+    int x0, nxt, y0, nyt, z0, nzt;
+    twin_range(x, c.n[0], c.periodic[0] != 0, &x0, &nxt);
+    twin_range(y, c.n[1], c.periodic[1] != 0, &y0, &nyt);
+    twin_range(z, c.n[2], c.periodic[2] != 0, &z0, &nzt);
+    for (int iz = 0; iz < nzt; ++iz) {
+        const int zz = z0 + iz * c.n[2];
+        for (int iy = 0; iy < nyt; ++iy) {
+            const int yy = y0 + iy * c.n[1];
+            for (int ix = 0; ix < nxt; ++ix) {
+                const int xx = x0 + ix * c.n[0];
+                const long long off = (long long)zz * c.sz + (long long)yy * c.sy + xx;
+                if (WFA_CHK(off >= c.lo && off < c.hi, st, 11, xx, yy, zz, 0)) origin[off] = v;
             }
         }
     }

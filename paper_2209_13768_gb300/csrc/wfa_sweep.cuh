@@ -117,7 +117,7 @@ template <> struct Vec4<__nv_bfloat16> {
 // Used for grids too small for the tiled kernel's box and as a second,
 // independent realisation of the same per-cell arithmetic.
 template <typename S, bool KVAR>
-__global__ void __launch_bounds__(256) sweep_simple(SweepArgs a) {
+__global__ void __launch_bounds__(256) sweep_simple(const __grid_constant__ SweepArgs a) {
     const SweepCoef& c = a.c;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -144,6 +144,7 @@ __global__ void __launch_bounds__(256) sweep_simple(SweepArgs a) {
                     else w[f] = c.w_bd[f];
                 } else {
                     const long long j = i + (side ? st[ax] : -st[ax]);
+                    if (!WFA_CHK(j >= c.lo && j < c.hi, a.status, 20, x, y, z, f)) continue;
                     tn[f] = to_f32<S>(in[j]);
                     w[f] = KVAR ? __fadd_rn(harm_face(kc, a.k[j], c.cd[ax]), c.adv[f]) : c.w_in[f];
                 }
@@ -151,7 +152,7 @@ __global__ void __launch_bounds__(256) sweep_simple(SweepArgs a) {
             v = cell_update(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], w[0], w[1], w[2], w[3], w[4], w[5],
                             self_term(c, x, y, z));
         }
-        store_with_twins<S>(out, c, x, y, z, from_f32<S>(v));
+        store_with_twins<S>(out, c, x, y, z, from_f32<S>(v), a.status);
     }
 }
 
@@ -159,6 +160,7 @@ __global__ void __launch_bounds__(256) sweep_simple(SweepArgs a) {
 template <typename S, bool KVAR, int D, int EX, int EY, int R>
 struct TbCfg {
     static constexpr int VA = 16 / (int)sizeof(S);          // elements per 16 bytes (TMA x alignment)
+    static constexpr int DEPTH = D;
     static constexpr int PX = ((D + VA - 1) / VA) * VA;     // x halo, a multiple of VA
     static constexpr int TX = EX - 2 * PX;                  // output tile
     static constexpr int TY = EY - 2 * D;
@@ -182,9 +184,26 @@ struct TbCfg {
     static_assert(SMEM <= 232448, "shared memory above the 227 KB a block may use");
 };
 
+// Issue the TMA copies of input plane `plane` (and its k plane) into the ring
+// slot of counter idx; both complete on the slot's mbarrier.
+template <typename Cfg, bool KVAR, typename S>
+__device__ __forceinline__ void issue_plane(const CUtensorMap* mT, const CUtensorMap* mK, S* ring, float* kring,
+                                            uint64_t* bars, uint32_t idx, int x0, int y0, int plane,
+                                            const SweepArgs& a) {
+    const int tx = x0 - Cfg::PX + HALO, ty = y0 - Cfg::DEPTH + HALO, tz = plane + HALO;
+    if (!WFA_CHK(tx >= 0 && tx % Cfg::VA == 0 && tx < a.c.px && ty >= 0 && ty < a.c.py && tz >= 0 && tz < a.c.pz,
+                 a.status, 13, tx, ty, tz, (int)idx))
+        return;
+    uint64_t* bar = &bars[idx % Cfg::NS];
+    mbar_expect_tx(bar, Cfg::TX_BYTES);
+    tma_load_3d(ring + (idx % Cfg::NS) * Cfg::PLANE, mT, bar, tx, ty, tz);
+    if (KVAR) tma_load_3d(kring + (idx % (Cfg::NK > 0 ? Cfg::NK : 1)) * Cfg::PLANE, mK, bar, tx, ty, tz);
+}
+
 template <typename S, bool KVAR, int D, int EX, int EY, int R>
 __global__ void __launch_bounds__(TbCfg<S, KVAR, D, EX, EY, R>::NT, TbCfg<S, KVAR, D, EX, EY, R>::MINB)
-    sweep_tb(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmK, SweepArgs a) {
+    sweep_tb(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmK,
+             const __grid_constant__ SweepArgs a) {
     using Cfg = TbCfg<S, KVAR, D, EX, EY, R>;
     constexpr int PX = Cfg::PX, TX = Cfg::TX, TY = Cfg::TY, NTX = Cfg::NTX, NS = Cfg::NS, NK = Cfg::NK,
                   P = Cfg::P, PLANE = Cfg::PLANE;
@@ -202,6 +221,16 @@ __global__ void __launch_bounds__(TbCfg<S, KVAR, D, EX, EY, R>::NT, TbCfg<S, KVA
     const int yl = R * (tid / NTX);   // first local row
     const bool perx = c.periodic[0], pery = c.periodic[1], perz = c.periodic[2];
 
+#ifdef WFA_CHECKED
+    // the TMA descriptor operands must be the kernel's grid-constant parameters
+    if (tid == 0) {
+        WFA_CHK(__isGridConstant(&tmT) && __isGridConstant(&tmK), a.status, 14, 0, 0, 0, 0);
+        WFA_CHK(__isShared(smem_raw), a.status, 15, 0, 0, 0, 0);
+    }
+#define SIDX(i, lim) (WFA_CHK((i) >= 0 && (i) < (lim), a.status, 16, (int)(i), (int)(lim), __LINE__, 0) ? (i) : 0)
+#else
+#define SIDX(i, lim) (i)
+#endif
     if (tid == 0) {
         for (int b = 0; b < NS; ++b) mbar_init(&bars[b], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -224,18 +253,10 @@ __global__ void __launch_bounds__(TbCfg<S, KVAR, D, EX, EY, R>::NT, TbCfg<S, KVA
         const int jstart = z0 - D, jend = z1 + D;   // stage-0 planes streamed through
         const int gx0 = x0 - PX + xl, gy0 = y0 - D + yl;
 
-        auto issue = [&](uint32_t idx, int plane) {
-            uint64_t* bar = &bars[idx % NS];
-            mbar_expect_tx(bar, Cfg::TX_BYTES);
-            tma_load_3d(ring + (idx % NS) * PLANE, &tmT, bar, x0 - PX + HALO, y0 - D + HALO, plane + HALO);
-            if (KVAR)
-                tma_load_3d(kring + (idx % (NK > 0 ? NK : 1)) * PLANE, &tmK, bar, x0 - PX + HALO,
-                            y0 - D + HALO, plane + HALO);
-        };
         if (tid == 0) {
             fence_proxy_async_smem();
             for (int p = 0; p <= P && jstart + p < jend; ++p) {
-                issue(cnt + p, jstart + p);
+                issue_plane<Cfg, KVAR>(&tmT, &tmK, ring, kring, bars, cnt + p, x0, y0, jstart + p, a);
                 issued_hi = cnt + p + 1;
             }
         }
@@ -278,7 +299,7 @@ __global__ void __launch_bounds__(TbCfg<S, KVAR, D, EX, EY, R>::NT, TbCfg<S, KVA
 
             float nw[D + 1][R][4];
 #pragma unroll
-            for (int r = 0; r < R; ++r) Vec4<S>::load(cur0 + (yl + r) * EX + xl, nw[0][r]);
+            for (int r = 0; r < R; ++r) Vec4<S>::load(cur0 + SIDX((yl + r) * EX + xl, PLANE - 3), nw[0][r]);
 
 #pragma unroll
             for (int s = 1; s <= D; ++s) {
@@ -295,21 +316,15 @@ __global__ void __launch_bounds__(TbCfg<S, KVAR, D, EX, EY, R>::NT, TbCfg<S, KVA
                     continue;
                 }
                 // x/y neighbours of stage s-1 at plane q
-                auto nb = [&](int xx, int yy) -> float {
-                    xx = min(max(xx, 0), EX - 1);
-                    yy = min(max(yy, 0), EY - 1);
-                    if (s == 1) return to_f32<S>(prev0[yy * EX + xx]);
-                    return sbuf[(s - 2) * PLANE + yy * EX + xx];
-                };
                 float below[4], above[4];
                 {
                     const int yb = max(yl - 1, 0), ya = min(yl + R, EY - 1);
                     if (s == 1) {
-                        Vec4<S>::load(prev0 + yb * EX + xl, below);
-                        Vec4<S>::load(prev0 + ya * EX + xl, above);
+                        Vec4<S>::load(prev0 + SIDX(yb * EX + xl, PLANE - 3), below);
+                        Vec4<S>::load(prev0 + SIDX(ya * EX + xl, PLANE - 3), above);
                     } else {
-                        Vec4<float>::load(sbuf + (s - 2) * PLANE + yb * EX + xl, below);
-                        Vec4<float>::load(sbuf + (s - 2) * PLANE + ya * EX + xl, above);
+                        Vec4<float>::load(sbuf + SIDX((s - 2) * PLANE + yb * EX + xl, (D - 1) * PLANE - 3), below);
+                        Vec4<float>::load(sbuf + SIDX((s - 2) * PLANE + ya * EX + xl, (D - 1) * PLANE - 3), above);
                     }
                 }
                 const bool bzm = !perz && q == 0, bzp = !perz && q == c.n[2] - 1;
@@ -321,25 +336,28 @@ __global__ void __launch_bounds__(TbCfg<S, KVAR, D, EX, EY, R>::NT, TbCfg<S, KVA
                 float kc[R][4], kb[4], ka[4];
                 if (KVAR) {
 #pragma unroll
-                    for (int r = 0; r < R; ++r) Vec4<float>::load(kq + (yl + r) * EX + xl, kc[r]);
-                    Vec4<float>::load(kq + max(yl - 1, 0) * EX + xl, kb);
-                    Vec4<float>::load(kq + min(yl + R, EY - 1) * EX + xl, ka);
+                    for (int r = 0; r < R; ++r) Vec4<float>::load(kq + SIDX((yl + r) * EX + xl, PLANE - 3), kc[r]);
+                    Vec4<float>::load(kq + SIDX(max(yl - 1, 0) * EX + xl, PLANE - 3), kb);
+                    Vec4<float>::load(kq + SIDX(min(yl + R, EY - 1) * EX + xl, PLANE - 3), ka);
                 }
 
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const float left = nb(xl - 1, yl + r);
-                    const float right = nb(xl + 4, yl + r);
+                    // x neighbours of the row ends (clamped: only out-of-tile cells read a clamped value)
+                    const int il = SIDX((yl + r) * EX + max(xl - 1, 0), PLANE);
+                    const int ir = SIDX((yl + r) * EX + min(xl + 4, EX - 1), PLANE);
+                    const float left = s == 1 ? to_f32<S>(prev0[il]) : sbuf[SIDX((s - 2) * PLANE + il, (D - 1) * PLANE)];
+                    const float right = s == 1 ? to_f32<S>(prev0[ir]) : sbuf[SIDX((s - 2) * PLANE + ir, (D - 1) * PLANE)];
                     const int gy = gy0 + r;
                     float gx[5], kzp[4];
                     if (KVAR) {
-                        const float kl = kq[(yl + r) * EX + max(xl - 1, 0)];
-                        const float kr = kq[(yl + r) * EX + min(xl + 4, EX - 1)];
+                        const float kl = kq[SIDX((yl + r) * EX + max(xl - 1, 0), PLANE)];
+                        const float kr = kq[SIDX((yl + r) * EX + min(xl + 4, EX - 1), PLANE)];
                         gx[0] = harm_face(kl, kc[r][0], c.cd[0]);
 #pragma unroll
                         for (int i = 0; i < 3; ++i) gx[i + 1] = harm_face(kc[r][i], kc[r][i + 1], c.cd[0]);
                         gx[4] = harm_face(kc[r][3], kr, c.cd[0]);
-                        Vec4<float>::load(kqp + (yl + r) * EX + xl, kzp);
+                        Vec4<float>::load(kqp + SIDX((yl + r) * EX + xl, PLANE - 3), kzp);
                     }
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
@@ -409,7 +427,7 @@ __global__ void __launch_bounds__(TbCfg<S, KVAR, D, EX, EY, R>::NT, TbCfg<S, KVA
 #pragma unroll
             for (int s = 1; s < D; ++s)
 #pragma unroll
-                for (int r = 0; r < R; ++r) Vec4<float>::store(sbuf + (s - 1) * PLANE + (yl + r) * EX + xl, nw[s][r]);
+                for (int r = 0; r < R; ++r) Vec4<float>::store(sbuf + SIDX((s - 1) * PLANE + (yl + r) * EX + xl, (D - 1) * PLANE - 3), nw[s][r]);
 #pragma unroll
             for (int s = 0; s < D; ++s)
 #pragma unroll
@@ -434,11 +452,14 @@ __global__ void __launch_bounds__(TbCfg<S, KVAR, D, EX, EY, R>::NT, TbCfg<S, KVA
                                            !(pery && (gy < HALO || gy >= c.n[1] - HALO)) &&
                                            !(perz && (q < HALO || q >= c.n[2] - HALO));
                         if (plain) {
-                            Vec4<S>::store(out + (long long)q * c.sz + (long long)gy * c.sy + gx, nw[D][r]);
+                            const long long off = (long long)q * c.sz + (long long)gy * c.sy + gx;
+                            if (WFA_CHK(off >= c.lo && off + 3 < c.hi && (off & 3) == 0, a.status, 10, gx, gy, q, r))
+                                Vec4<S>::store(out + off, nw[D][r]);
                         } else {
 #pragma unroll
                             for (int i = 0; i < 4; ++i)
-                                if (gx + i < c.n[0]) store_with_twins<S>(out, c, gx + i, gy, q, from_f32<S>(nw[D][r][i]));
+                                if (gx + i < c.n[0])
+                                    store_with_twins<S>(out, c, gx + i, gy, q, from_f32<S>(nw[D][r][i]), a.status);
                         }
                     }
                 }
@@ -446,13 +467,14 @@ __global__ void __launch_bounds__(TbCfg<S, KVAR, D, EX, EY, R>::NT, TbCfg<S, KVA
             __syncthreads();   // stage planes written; the ring slot of plane j-1 is free
             if (tid == 0 && j + P + 1 < jend) {
                 fence_proxy_async_smem();
-                issue(idx + P + 1, j + P + 1);
+                issue_plane<Cfg, KVAR>(&tmT, &tmK, ring, kring, bars, idx + P + 1, x0, y0, j + P + 1, a);
                 issued_hi = idx + P + 2;
             }
         }
         if (failed) break;
         cnt += (uint32_t)(jend - jstart);
     }
+#undef SIDX
 
     if (failed) {
         // drain: wait (bounded) for the copies this block issued and has not consumed
