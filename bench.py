@@ -217,7 +217,11 @@ def main():
     dt = p.dt if p.dt else 0.9 * g.stability_dt()
     g.set_dt(dt)
     g.set_tuning(args.depth, args.variant)
-    depth = args.depth or (2 if kvar else 4)
+    if args.depth or args.variant:
+        depth = args.depth or (1 if args.variant in (-1, 3) else 2)
+        variant = args.variant or (3 if depth == 1 else 1)
+    else:   # autotune: time the compiled configurations on this grid, keep the fastest
+        depth, variant = g.autotune()
     launches_per_step = math.ceil(p.steps / depth)
 
     for _ in range(args.warmup):
@@ -311,6 +315,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if storage else "f32", "data": "synthetic",
                 "config": {"workload": p.name, "cells": cells, "time_steps_per_step": p.steps, "depth": depth,
+                           "kernel": {3: "sweep_col", -1: "sweep_simple"}.get(variant, f"sweep_tb variant {variant}"),
                            "dt": dt, "storage": "bf16" if storage else "f32",
                            "conductivity": "per-cell lognormal(0,0.5)" if kvar else f"uniform {p.k}",
                            "l2": "inputs larger than L2 (%.0f MiB field)" % (cells * (2 if storage else 4) / 2**20),

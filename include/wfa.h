@@ -108,12 +108,25 @@ int wfa_set_dt(wfa_grid g, double dt);
 
 /* Force a kernel configuration instead of the tuned one.
  * depth: time steps fused per pass over the grid (1..8; 0 = automatic).
- * variant: 0 = automatic, 1..2 = one of the compiled tile shapes of the
- * tiled TMA kernel, -1 = the one-thread-per-column kernel (one step per
- * pass; a second, independent realisation of the same per-cell arithmetic).
+ * variant: 0 = automatic; 1..2 = one of the compiled tile shapes of the
+ * tiled TMA kernel (depth steps per pass); 3 = the column-march kernel (one
+ * step per pass, register queue along z, no shared memory); -1 = the plain
+ * one-thread-per-column kernel (one step per pass; a second, independent
+ * realisation of the same per-cell arithmetic).
  * Results do not depend on the choice: every kernel evaluates the same fixed
  * per-cell expression, so fields are bit-identical. */
 int wfa_set_tuning(wfa_grid g, int depth, int variant);
+
+/* Time the compiled kernel configurations (column march; tiled TMA kernel at
+ * depths 1..8 and two tile shapes) on this grid and use the fastest from now
+ * on. The trials run on a scratch copy of the field: the field and the step
+ * count are left as they were, and results never depend on the choice. The
+ * choice is also remembered for later grids of the same size class (storage,
+ * conductivity mode, advection, log2 of each edge) in this process, and in
+ * the file named by the environment variable WFA_TUNE_CACHE if it is set.
+ * Synchronises the stream; needs one extra field of device memory while it
+ * runs. *depth / *variant (may be NULL) receive the choice. */
+int wfa_autotune(wfa_grid g, int* depth, int* variant);
 
 /* Advance n >= 0 time steps (asynchronous on the grid's stream).
  * Errors: WFA_ERR_STATE before the field, coefficients and dt are set,

@@ -59,6 +59,7 @@ SIGNATURES = {
     "wfa_stability_dt": (_i, [_vp, _dp]),
     "wfa_set_dt": (_i, [_vp, _d]),
     "wfa_set_tuning": (_i, [_vp, _i, _i]),
+    "wfa_autotune": (_i, [_vp, _ip, _ip]),
     "wfa_step": (_i, [_vp, _ll]),
     "wfa_steps_done": (_i, [_vp, _llp]),
     "wfa_read_field": (_i, [_vp, _fp]),
@@ -183,6 +184,12 @@ class Grid:
 
     def set_tuning(self, depth=0, variant=0):
         check(lib().wfa_set_tuning(self.handle, int(depth), int(variant)), "wfa_set_tuning")
+
+    def autotune(self):
+        """Pick the fastest kernel configuration for this grid; returns (depth, variant)."""
+        d, v = ctypes.c_int(), ctypes.c_int()
+        check(lib().wfa_autotune(self.handle, ctypes.byref(d), ctypes.byref(v)), "wfa_autotune")
+        return d.value, v.value
 
     def step(self, n):
         check(lib().wfa_step(self.handle, int(n)), "wfa_step")

@@ -60,7 +60,7 @@ int build_coef(const wfa_grid_s* g, SweepCoef* c) {
         const double cd = dt / (h * h);
         const double ap = dt * (g->u[a] > 0 ? g->u[a] : 0.0) / h;   // -face inflow weight
         const double am = dt * (g->u[a] < 0 ? -g->u[a] : 0.0) / h;  // +face inflow weight
-        c->cd[a] = (float)cd;
+        c->tcd[a] = (float)(2.0 * cd);
         c->adv[2 * a] = (float)ap;
         c->adv[2 * a + 1] = (float)am;
         c->w_in[2 * a] = (float)(g->k_uniform * cd + ap);
@@ -83,6 +83,8 @@ int build_coef(const wfa_grid_s* g, SweepCoef* c) {
     }
     return WFA_OK;
 }
+
+__global__ void recip_kernel(const float* __restrict__ k, float* __restrict__ r, long long n);
 
 // ------------------------------------------------------------ pack/unpack --
 struct Geo {
@@ -373,6 +375,12 @@ int check_status(wfa_grid_s* g) {
     return WFA_OK;
 }
 
+// r = 1/k (IEEE division; 1/0 = inf makes every face of that cell insulating).
+__global__ void recip_kernel(const float* __restrict__ k, float* __restrict__ r, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        r[i] = __fdiv_rn(1.0f, k[i]);
+}
+
 }  // namespace wfa
 
 using namespace wfa;
@@ -428,6 +436,7 @@ int wfa_destroy_grid(wfa_grid g) {
     cudaStreamSynchronize(g->stream);
     for (int b = 0; b < 2; ++b) if (g->T[b]) cudaFree(g->T[b]);
     if (g->k) cudaFree(g->k);
+    if (g->r) cudaFree(g->r);
     if (g->d_partials) cudaFree(g->d_partials);
     if (g->d_stage) cudaFree(g->d_stage);
     if (g->h_result) cudaFreeHost(g->h_result);
@@ -476,6 +485,8 @@ int wfa_set_field(wfa_grid g, const float* host_dense) {
     return WFA_OK;
 }
 
+static int prepare_k_halo(wfa_grid g);
+
 int wfa_set_coeffs(wfa_grid g, const float* k_host, double k_uniform, double ux, double uy, double uz) {
     if (!g) return fail(WFA_ERR_ARG, "NULL grid");
     if (!std::isfinite(ux) || !std::isfinite(uy) || !std::isfinite(uz))
@@ -490,6 +501,7 @@ int wfa_set_coeffs(wfa_grid g, const float* k_host, double k_uniform, double ux,
         if (!g->k) {
             WFA_CUDA(cudaMalloc(&g->k, field_elems(g) * sizeof(float)));
             WFA_CUDA(cudaMemsetAsync(g->k, 0, field_elems(g) * sizeof(float), g->stream));
+            WFA_CUDA(cudaMalloc(&g->r, field_elems(g) * sizeof(float)));
         }
         int rc = ensure_stage(g);
         if (rc) return rc;
@@ -498,13 +510,17 @@ int wfa_set_coeffs(wfa_grid g, const float* k_host, double k_uniform, double ux,
         pack_kernel<float><<<grid_blocks(N, thr), thr, 0, g->stream>>>(g->d_stage, g->k + domain_offset(g),
                                                                          geo_of(g));
         WFA_CUDA(cudaGetLastError());
+        int rc2 = prepare_k_halo(g);
+        if (rc2) return rc2;
         WFA_CUDA(cudaStreamSynchronize(g->stream));
         g->k_uniform = 0.0;
     } else {
         if (g->k) {
             cudaStreamSynchronize(g->stream);
             cudaFree(g->k);
+            cudaFree(g->r);
             g->k = nullptr;
+            g->r = nullptr;
             free_tmaps(g);
         }
         g->k_uniform = k_uniform;
@@ -549,11 +565,15 @@ static RateSpec rate_spec(const wfa_grid_s* g) {
     return r;
 }
 
+// k halo (periodic twins), then r = 1/k over the whole padded buffer.
 static int prepare_k_halo(wfa_grid g) {
     if (!g->k) return WFA_OK;
     HaloSpec h = halo_spec(g);
     const long long total = (long long)(g->n[0] + 2 * HALO) * (g->n[1] + 2 * HALO) * (g->n[2] + 2 * HALO);
     k_halo_kernel<<<grid_blocks(total, 256), 256, 0, g->stream>>>(g->k, h, total);
+    WFA_CUDA(cudaGetLastError());
+    const long long all = (long long)field_elems(g);
+    recip_kernel<<<grid_blocks(all, 256), 256, 0, g->stream>>>(g->k, g->r, all);
     WFA_CUDA(cudaGetLastError());
     return WFA_OK;
 }
@@ -594,7 +614,7 @@ int wfa_set_dt(wfa_grid g, double dt) {
 int wfa_set_tuning(wfa_grid g, int depth, int variant) {
     if (!g) return fail(WFA_ERR_ARG, "NULL grid");
     if (depth < 0 || depth > MAX_DEPTH) return fail(WFA_ERR_ARG, "depth must be 0..%d", MAX_DEPTH);
-    if (variant < -1 || variant > NUM_TILE_VARIANTS) return fail(WFA_ERR_ARG, "variant must be -1..%d", NUM_TILE_VARIANTS);
+    if (variant < -1 || variant > COL_VARIANT) return fail(WFA_ERR_ARG, "variant must be -1..%d", COL_VARIANT);
     g->force_depth = depth;
     g->force_variant = variant;
     return WFA_OK;
@@ -620,6 +640,20 @@ int wfa_step(wfa_grid g, long long n) {
     if (rc) return rc;
     g->steps_done += n;
     return WFA_OK;
+}
+
+int wfa_autotune(wfa_grid g, int* depth, int* variant) {
+    if (!g) return fail(WFA_ERR_ARG, "NULL grid");
+    if (!g->field_set || !g->coeffs_set || !g->dt_set)
+        return fail(WFA_ERR_STATE, "set the field, the coefficients and dt before tuning");
+    if (g->halo_dirty) {
+        int rc = refresh_halo(g, g->cur);
+        if (rc) return rc;
+        rc = prepare_k_halo(g);
+        if (rc) return rc;
+        g->halo_dirty = false;
+    }
+    return autotune(g, depth, variant);
 }
 
 int wfa_steps_done(wfa_grid g, long long* n) {

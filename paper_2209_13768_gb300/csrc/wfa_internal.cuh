@@ -29,6 +29,7 @@ namespace wfa {
 constexpr int HALO = 8;       // halo width on every side (>= the deepest temporal block)
 constexpr int MAX_DEPTH = 8;  // steps fused per pass over the grid
 constexpr int NUM_TILE_VARIANTS = 2;  // tile shapes compiled per (storage, k mode, depth)
+constexpr int COL_VARIANT = 3;        // the one-step column-march kernel
 
 // ---------------------------------------------------------------- errors --
 void set_error(const char* fmt, ...);
@@ -52,7 +53,7 @@ struct SweepCoef {
     float tb[6];           // Dirichlet face value (fp32)
     float w_in[6];         // uniform k: coefficient of an interior face, k dt/h^2 + A_f
     float w_bd[6];         // uniform k: coefficient of the boundary face (Dirichlet: 2k dt/h^2 + A_f; else 0)
-    float cd[3];           // dt / h_a^2 (per-cell k: face coefficient = harmonic mean * cd + A_f)
+    float tcd[3];          // 2 dt / h_a^2 (per-cell k: face coefficient = tcd / (1/k_C + 1/k_D) + A_f)
     float adv[6];          // A_f: upwind coefficient of face f: -face dt*max(u,0)/h, +face dt*max(-u,0)/h
     float s_lo[3], s_hi[3];  // self term of a cell on a zero-flux face with advection
     int held[6];           // face holds its outer cell layer (Dirichlet cell)
@@ -88,7 +89,8 @@ struct wfa_grid_s {
     cudaStream_t stream;
     long long px, py, pz; // padded extents (elements)
     void* T[2];           // ping-pong padded fields (allocation bases)
-    float* k;             // padded per-cell conductivity or nullptr
+    float* k;             // padded per-cell conductivity or nullptr (fp64 stability limit)
+    float* r;             // padded reciprocal conductivity 1/k (the sweeps' operand)
     int cur;              // buffer holding the current field
     double k_uniform;
     double u[3];
@@ -118,6 +120,7 @@ int build_coef(const wfa_grid_s* g, SweepCoef* c);       // host: fp64 -> fp32 c
 int refresh_halo(wfa_grid_s* g, int buf);                 // twins + held layers of one buffer
 int launch_sweep(wfa_grid_s* g, long long nsteps);        // advance nsteps on g->stream
 int check_status(wfa_grid_s* g);                          // sync + report a device-side timeout
+int autotune(wfa_grid_s* g, int* depth, int* variant);    // pick the fastest kernel configuration
 void free_tmaps(wfa_grid_s* g);
 
 // ----------------------------------------------------------- device math --
@@ -126,31 +129,40 @@ void free_tmaps(wfa_grid_s* g);
 // or batching) produce bit-identical fields. The *_rn intrinsics are never
 // contracted into other operations by the compiler.
 
-// Face coefficient from the harmonic mean of two conductivities:
-// 2 a b / (a + b) * cd, 0 when a + b == 0. Symmetric in (a, b) bit for bit.
-__device__ __forceinline__ float harm_face(float a, float b, float cd) {
-    const float s = __fadd_rn(a, b);
-    const float p = __fmul_rn(__fmul_rn(2.0f, a), b);
-    const float hm = (s > 0.0f) ? __fdividef(p, s) : 0.0f;
-    return __fmul_rn(hm, cd);
+// Face coefficient between two cells from their reciprocal conductivities
+// ra = 1/k_C, rb = 1/k_D: the harmonic mean 2 k_C k_D / (k_C + k_D) equals
+// 2 / (ra + rb); tcd = 2 dt / h^2. A zero conductivity (r = inf) gives 0,
+// the harmonic mean's limit. Symmetric in (ra, rb) bit for bit.
+// The reciprocal is the hardware approximation (PTX rcp.approx.ftz.f32,
+// about 1 ulp; 1/inf = 0), one instruction.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float face_r(float ra, float rb, float tcd) {
+    return __fmul_rn(tcd, rcp_approx(__fadd_rn(ra, rb)));
 }
 
-// Boundary (Dirichlet) face coefficient for per-cell k: 2 k_C dt / h^2.
-__device__ __forceinline__ float dirichlet_face(float kc, float cd) {
-    return __fmul_rn(__fmul_rn(2.0f, kc), cd);
-}
+// Dirichlet face: conductance 2 k_C / h^2 (value on the face, half a cell
+// away) = tcd / r_C.
+__device__ __forceinline__ float dirichlet_r(float rc, float tcd) { return __fmul_rn(tcd, rcp_approx(rc)); }
 
-// T' = T_C + sum_f w_f (T_f - T_C) + s T_C, faces in the order -x,+x,-y,+y,-z,+z.
-__device__ __forceinline__ float cell_update(float tc, float txm, float txp, float tym, float typ,
-                                             float tzm, float tzp, float wxm, float wxp, float wym,
-                                             float wyp, float wzm, float wzp, float s) {
+// Sum of the face terms of one cell: sum_f w_f (T_f - T_C), faces in the
+// order -x, +x, -y, +y, -z, +z. The update is T' = T_C + acc (plus s T_C
+// first when the cell has a nonzero zero-flux self term).
+__device__ __forceinline__ float flux_sum(float tc, float txm, float txp, float tym, float typ, float tzm,
+                                          float tzp, float wxm, float wxp, float wym, float wyp, float wzm,
+                                          float wzp) {
     float acc = __fmul_rn(wxm, __fsub_rn(txm, tc));
     acc = __fmaf_rn(wxp, __fsub_rn(txp, tc), acc);
     acc = __fmaf_rn(wym, __fsub_rn(tym, tc), acc);
     acc = __fmaf_rn(wyp, __fsub_rn(typ, tc), acc);
     acc = __fmaf_rn(wzm, __fsub_rn(tzm, tc), acc);
-    acc = __fmaf_rn(wzp, __fsub_rn(tzp, tc), acc);
-    acc = __fmaf_rn(s, tc, acc);
+    return __fmaf_rn(wzp, __fsub_rn(tzp, tc), acc);
+}
+__device__ __forceinline__ float finish_update(float tc, float acc, float s) {
+    if (s != 0.0f) acc = __fmaf_rn(s, tc, acc);
     return __fadd_rn(tc, acc);
 }
 

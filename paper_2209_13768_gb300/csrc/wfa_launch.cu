@@ -4,8 +4,12 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <stdio.h>
+
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <string>
 
 #include "wfa_sweep_impl.cuh"
 
@@ -63,7 +67,7 @@ static int encode_map(CUtensorMap* m, const void* base, CUtensorMapDataType dt, 
 static int get_tmaps(wfa_grid_s* g, int ex, int ey, TmapCache** out) {
     TmapCache* tc = (TmapCache*)g->tmaps;
     if (tc && tc->ex == ex && tc->ey == ey && tc->tbase[0] == g->T[0] && tc->tbase[1] == g->T[1] &&
-        tc->kbase == g->k) {
+        tc->kbase == g->r) {
         *out = tc;
         return WFA_OK;
     }
@@ -84,13 +88,13 @@ static int get_tmaps(wfa_grid_s* g, int ex, int ey, TmapCache** out) {
         if (rc) return rc;
         tc->tbase[b] = g->T[b];
     }
-    if (g->k) {
-        int rc = encode_map(&tc->k, g->k, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, ex, ey);
+    if (g->r) {
+        int rc = encode_map(&tc->k, g->r, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, ex, ey);
         if (rc) return rc;
     } else {
         tc->k = tc->t[0];   // never read
     }
-    tc->kbase = g->k;
+    tc->kbase = g->r;
     tc->ex = ex;
     tc->ey = ey;
     *out = tc;
@@ -108,10 +112,73 @@ static int num_sms() {
     return n;
 }
 
-// Depth used when nobody forced one and the autotuner has no entry.
-static int default_depth(const wfa_grid_s* g) {
-    if (g->tuned_depth) return g->tuned_depth;
-    return g->k ? 2 : 4;
+// ------------------------------------------------------------ tuning ------
+// Kernel configuration of a pass: variant (COL_VARIANT = column march, one
+// step; 1..NUM_TILE_VARIANTS = tiled TMA kernel, `depth` fused steps; -1 = the
+// plain one-column kernel) and depth.
+struct Choice {
+    int variant, depth;
+};
+
+// Autotuned choices, per size class, shared by every grid of the process and
+// optionally persisted (WFA_TUNE_CACHE = path of a small text file).
+static std::mutex g_tune_mu;
+static std::map<std::string, Choice> g_tune;
+static bool g_tune_loaded = false;
+
+static int ceil_log2(int v) {
+    int k = 0;
+    while ((1 << k) < v) ++k;
+    return k;
+}
+
+static std::string tune_key(const wfa_grid_s* g) {
+    char buf[128];
+    const bool adv = g->u[0] != 0.0 || g->u[1] != 0.0 || g->u[2] != 0.0;
+    snprintf(buf, sizeof buf, "%s.%s.%s.%d.%d.%d", g->storage == WFA_BF16 ? "bf16" : "f32", g->r ? "k" : "u",
+             adv ? "adv" : "noadv", ceil_log2(g->n[0]), ceil_log2(g->n[1]), ceil_log2(g->n[2]));
+    return buf;
+}
+
+static void tune_load_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char* path = getenv("WFA_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    char key[128];
+    int v, d;
+    while (fscanf(f, "%127s %d %d", key, &v, &d) == 3) g_tune[key] = Choice{v, d};
+    fclose(f);
+}
+
+static void tune_save_locked() {
+    const char* path = getenv("WFA_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = fopen(path, "w");
+    if (!f) return;
+    for (const auto& kv : g_tune) fprintf(f, "%s %d %d\n", kv.first.c_str(), kv.second.variant, kv.second.depth);
+    fclose(f);
+}
+
+static Choice choose(const wfa_grid_s* g) {
+    Choice ch{COL_VARIANT, 1};   // untuned default: the column-march kernel, one step per pass
+    if (g->tuned_variant) {
+        ch = Choice{g->tuned_variant, g->tuned_depth};
+    } else {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load_locked();
+        auto it = g_tune.find(tune_key(g));
+        if (it != g_tune.end()) ch = it->second;
+    }
+    if (g->force_variant || g->force_depth) {
+        const int v = g->force_variant ? g->force_variant : (g->force_depth > 1 ? 1 : COL_VARIANT);
+        int d = g->force_depth ? g->force_depth : (v == COL_VARIANT || v < 0 ? 1 : 2);
+        ch = Choice{v, d};
+    }
+    if (ch.variant < 0 || ch.variant == COL_VARIANT) ch.depth = 1;
+    return ch;
 }
 
 static TbEntry entry_for(const wfa_grid_s* g, int depth, int variant) {
@@ -149,7 +216,7 @@ static SweepArgs base_args(wfa_grid_s* g, const SweepCoef& c, int in_buf) {
     const long long off = domain_offset(g);
     a.tin = (const char*)g->T[in_buf] + off * g->esize;
     a.tout = (char*)g->T[1 - in_buf] + off * g->esize;
-    a.k = g->k ? g->k + off : nullptr;
+    a.rk = g->r ? g->r + off : nullptr;
     a.status = g->d_status;
     return a;
 }
@@ -164,6 +231,16 @@ static int one_pass(wfa_grid_s* g, const SweepCoef& c, int depth, int variant) {
         else
             e = g->k ? launch_simple_f32_k(a, g->stream) : launch_simple_f32_u(a, g->stream);
         if (e != cudaSuccess) return cuda_fail(e, "sweep_simple launch");
+        g->cur = 1 - g->cur;
+        return WFA_OK;
+    }
+    if (variant == COL_VARIANT) {   // column-march kernel, one step
+        cudaError_t e;
+        if (g->storage == WFA_BF16)
+            e = g->r ? launch_col_bf16_k(a, g->stream, num_sms()) : launch_col_bf16_u(a, g->stream, num_sms());
+        else
+            e = g->r ? launch_col_f32_k(a, g->stream, num_sms()) : launch_col_f32_u(a, g->stream, num_sms());
+        if (e != cudaSuccess) return cuda_fail(e, "sweep_col launch");
         g->cur = 1 - g->cur;
         return WFA_OK;
     }
@@ -193,15 +270,73 @@ int launch_sweep(wfa_grid_s* g, long long nsteps) {
     SweepCoef c;
     int rc = build_coef(g, &c);
     if (rc) return rc;
-    const int variant = g->force_variant ? g->force_variant : (g->tuned_variant ? g->tuned_variant : 1);
-    int depth = g->force_depth ? g->force_depth : default_depth(g);
-    if (variant < 0) depth = 1;
+    const Choice ch = choose(g);
     while (nsteps > 0) {
-        const int d = (int)std::min<long long>(depth, nsteps);
-        rc = one_pass(g, c, d, variant);
+        const int d = (int)std::min<long long>(ch.depth, nsteps);
+        rc = one_pass(g, c, d, ch.variant);
         if (rc) return rc;
         nsteps -= d;
     }
+    return WFA_OK;
+}
+
+// Time every compiled configuration on a scratch copy of the grid's field
+// and keep the fastest (results do not depend on the choice).
+int autotune(wfa_grid_s* g, int* depth_out, int* variant_out) {
+    SweepCoef c;
+    int rc = build_coef(g, &c);
+    if (rc) return rc;
+    static const Choice cands[] = {{COL_VARIANT, 1}, {1, 1}, {2, 1}, {1, 2}, {2, 2}, {1, 3}, {2, 3},
+                                   {1, 4}, {2, 4}, {1, 6}, {1, 8}};
+    const size_t bytes = field_elems(g) * g->esize;
+    void* save = nullptr;
+    WFA_CUDA(cudaMalloc(&save, bytes));
+    const int cur0 = g->cur;
+    cudaError_t e = cudaMemcpyAsync(save, g->T[cur0], bytes, cudaMemcpyDeviceToDevice, g->stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const long long cells = (long long)g->n[0] * g->n[1] * g->n[2];
+    const int steps = cells > (1LL << 22) ? 24 : 96;   // divisible by every depth tried
+    Choice best{COL_VARIANT, 1};
+    float best_ms = 1e30f;
+    for (const Choice& ch : cands) {
+        if (e != cudaSuccess) break;
+        // one warm-up pass, then the timed passes
+        rc = one_pass(g, c, ch.depth, ch.variant);
+        if (rc) break;
+        cudaEventRecord(e0, g->stream);
+        for (int s = 0; s < steps && !rc; s += ch.depth) rc = one_pass(g, c, ch.depth, ch.variant);
+        cudaEventRecord(e1, g->stream);
+        if (rc) break;
+        e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best = ch;
+        }
+    }
+    // put the field back exactly as it was
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->T[cur0], save, bytes, cudaMemcpyDeviceToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    g->cur = cur0;
+    g->halo_dirty = true;   // the other buffer's halo was rewritten by the trials
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(save);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    g->tuned_variant = best.variant;
+    g->tuned_depth = best.depth;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load_locked();
+        g_tune[tune_key(g)] = best;
+        tune_save_locked();
+    }
+    if (depth_out) *depth_out = best.depth;
+    if (variant_out) *variant_out = best.variant;
     return WFA_OK;
 }
 

@@ -31,7 +31,7 @@ struct SweepArgs {
     SweepCoef c;
     const void* tin;    // input field, domain origin
     void* tout;         // output field, domain origin
-    const float* k;     // conductivity, domain origin (nullptr for uniform k)
+    const float* rk;    // reciprocal conductivity 1/k, domain origin (nullptr for uniform k)
     int tiles_x, tiles_y, zchunk, nzchunk, items;
     int* status;
 };
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256) sweep_simple(const __grid_constant__ Swee
         const float tc = to_f32<S>(in[i]);
         float v = tc;
         if (!is_held(c, x, y, z)) {
-            const float kc = KVAR ? a.k[i] : 0.0f;
+            const float rc = KVAR ? a.rk[i] : 0.0f;
             const int pos[3] = {x, y, z};
             float tn[6], w[6];
 #pragma unroll
@@ -140,49 +140,92 @@ __global__ void __launch_bounds__(256) sweep_simple(const __grid_constant__ Swee
                 if (edge && !c.periodic[ax]) {
                     const bool dir = c.bkind[f] == WFA_BC_DIRICHLET;
                     tn[f] = dir ? c.tb[f] : 0.0f;
-                    if (KVAR) w[f] = dir ? __fadd_rn(dirichlet_face(kc, c.cd[ax]), c.adv[f]) : 0.0f;
+                    if (KVAR) w[f] = dir ? __fadd_rn(dirichlet_r(rc, c.tcd[ax]), c.adv[f]) : 0.0f;
                     else w[f] = c.w_bd[f];
                 } else {
                     const long long j = i + (side ? st[ax] : -st[ax]);
                     if (!WFA_CHK(j >= c.lo && j < c.hi, a.status, 20, x, y, z, f)) continue;
                     tn[f] = to_f32<S>(in[j]);
-                    w[f] = KVAR ? __fadd_rn(harm_face(kc, a.k[j], c.cd[ax]), c.adv[f]) : c.w_in[f];
+                    w[f] = KVAR ? __fadd_rn(face_r(rc, a.rk[j], c.tcd[ax]), c.adv[f]) : c.w_in[f];
                 }
             }
-            v = cell_update(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], w[0], w[1], w[2], w[3], w[4], w[5],
-                            self_term(c, x, y, z));
+            v = finish_update(tc, flux_sum(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], w[0], w[1], w[2], w[3], w[4], w[5]),
+                              self_term(c, x, y, z));
         }
         store_with_twins<S>(out, c, x, y, z, from_f32<S>(v), a.status);
     }
 }
 
 // --------------------------------------------------------- tiled kernel ----
-template <typename S, bool KVAR, int D, int EX, int EY, int R>
+template <typename S, bool KVAR, int D, int EX, int EY, int R, int PF = 2>
 struct TbCfg {
     static constexpr int VA = 16 / (int)sizeof(S);          // elements per 16 bytes (TMA x alignment)
     static constexpr int DEPTH = D;
-    static constexpr int PX = ((D + VA - 1) / VA) * VA;     // x halo, a multiple of VA
+    // x halo = the allocation's halo, so a box starts at allocated column x0;
+    // with TX a multiple of 128 bytes every box row is line-aligned
+    static constexpr int PX = HALO;
     static constexpr int TX = EX - 2 * PX;                  // output tile
     static constexpr int TY = EY - 2 * D;
     static constexpr int NTX = EX / 4, NTY = EY / R, NT = NTX * NTY;
     static constexpr int MINB = (NT <= 256 && D <= 2) ? 2 : 1;   // blocks per SM the register budget targets
-    static constexpr int P = 2;                             // planes in flight ahead of use
+    static constexpr int P = PF;                            // planes in flight ahead of use
     static constexpr int NS = P + 2;                        // input ring slots (= mbarriers)
     static constexpr int NK = KVAR ? D + P + 2 : 0;         // k ring slots
     static constexpr int PLANE = EX * EY;
     static constexpr size_t BAR_BYTES = 1024;   // mbarriers; keeps the ring 1024-byte aligned
-    static constexpr size_t RING_BYTES = (size_t)NS * PLANE * sizeof(S);
-    static constexpr size_t K_BYTES = (size_t)NK * PLANE * sizeof(float);
+    // slot strides padded to 128 bytes: every TMA destination stays 128-byte aligned
+    static constexpr size_t SLOT_T = ((size_t)PLANE * sizeof(S) + 127) / 128 * 128;
+    static constexpr size_t SLOT_K = ((size_t)PLANE * sizeof(float) + 127) / 128 * 128;
+    static constexpr size_t RING_BYTES = (size_t)NS * SLOT_T;
+    static constexpr size_t K_BYTES = (size_t)NK * SLOT_K;
     static constexpr size_t SBUF_BYTES = (size_t)(D > 1 ? D - 1 : 0) * PLANE * sizeof(float);
     static constexpr size_t SMEM = 1024 + BAR_BYTES + RING_BYTES + K_BYTES + SBUF_BYTES;
     static constexpr uint32_t TX_BYTES = (uint32_t)(PLANE * sizeof(S) + (KVAR ? PLANE * sizeof(float) : 0));
     static_assert(EX % 4 == 0 && EX % VA == 0 && EX <= 256 && EY <= 256, "TMA box");
     static_assert(EY % R == 0, "rows per thread");
     static_assert(TX > 0 && TY > 0, "tile too small for this depth");
+    static_assert((TX * (int)sizeof(S)) % 128 == 0, "output tile width must be a multiple of 128 bytes");
     static_assert(NT <= 1024, "too many threads");
     static_assert(D >= 1 && D <= MAX_DEPTH && PX <= HALO, "depth");
     static_assert(SMEM <= 232448, "shared memory above the 227 KB a block may use");
+    static_assert(SLOT_T % 128 == 0 && SLOT_K % 128 == 0 && BAR_BYTES % 1024 == 0 && RING_BYTES % 128 == 0,
+                  "TMA destinations must be 128-byte aligned");
 };
+
+// Update of a cell that touches the domain boundary: the face values and
+// coefficients computed for an interior face are replaced by the boundary
+// condition's (Dirichlet: the face value with 2 k_C dt / h^2; zero-flux: no
+// flux), held cells keep their value, and zero-flux faces with advection add
+// the self term. Called only for boundary cells, so it stays out of line.
+template <bool KVAR>
+__device__ __noinline__ float boundary_update(const SweepCoef* cp, float tc, float txm, float txp, float tym,
+                                              float typ, float tzm, float tzp, float wxm, float wxp, float wym,
+                                              float wyp, float wzm, float wzp, float rc, int x, int y, int z) {
+    const SweepCoef& c = *cp;
+    if (is_held(c, x, y, z)) return tc;
+    float t[6] = {txm, txp, tym, typ, tzm, tzp};
+    float w[6] = {wxm, wxp, wym, wyp, wzm, wzp};
+    const int pos[3] = {x, y, z};
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        const int ax = f >> 1;
+        const bool edge = (f & 1) ? pos[ax] == c.n[ax] - 1 : pos[ax] == 0;
+        if (edge && !c.periodic[ax]) {
+            const bool dir = c.bkind[f] == WFA_BC_DIRICHLET;
+            t[f] = dir ? c.tb[f] : 0.0f;
+            if (KVAR) w[f] = dir ? __fadd_rn(dirichlet_r(rc, c.tcd[ax]), c.adv[f]) : 0.0f;
+            else w[f] = c.w_bd[f];
+        }
+    }
+    return finish_update(tc, flux_sum(tc, t[0], t[1], t[2], t[3], t[4], t[5], w[0], w[1], w[2], w[3], w[4], w[5]),
+                         self_term(c, x, y, z));
+}
+
+template <typename S>
+__device__ __noinline__ void store_twins_out_of_line(S* out, const SweepCoef* c, int x, int y, int z, float v,
+                                                     int* st) {
+    store_with_twins<S>(out, *c, x, y, z, from_f32<S>(v), st);
+}
 
 // Issue the TMA copies of input plane `plane` (and its k plane) into the ring
 // slot of counter idx; both complete on the slot's mbarrier.
@@ -196,15 +239,16 @@ __device__ __forceinline__ void issue_plane(const CUtensorMap* mT, const CUtenso
         return;
     uint64_t* bar = &bars[idx % Cfg::NS];
     mbar_expect_tx(bar, Cfg::TX_BYTES);
-    tma_load_3d(ring + (idx % Cfg::NS) * Cfg::PLANE, mT, bar, tx, ty, tz);
-    if (KVAR) tma_load_3d(kring + (idx % (Cfg::NK > 0 ? Cfg::NK : 1)) * Cfg::PLANE, mK, bar, tx, ty, tz);
+    tma_load_3d(reinterpret_cast<char*>(ring) + (idx % Cfg::NS) * Cfg::SLOT_T, mT, bar, tx, ty, tz);
+    if (KVAR)
+        tma_load_3d(reinterpret_cast<char*>(kring) + (idx % (Cfg::NK > 0 ? Cfg::NK : 1)) * Cfg::SLOT_K, mK, bar, tx, ty, tz);
 }
 
-template <typename S, bool KVAR, int D, int EX, int EY, int R>
-__global__ void __launch_bounds__(TbCfg<S, KVAR, D, EX, EY, R>::NT, TbCfg<S, KVAR, D, EX, EY, R>::MINB)
+template <typename S, bool KVAR, int D, int EX, int EY, int R, int PF>
+__global__ void __launch_bounds__(TbCfg<S, KVAR, D, EX, EY, R, PF>::NT, TbCfg<S, KVAR, D, EX, EY, R, PF>::MINB)
     sweep_tb(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmK,
              const __grid_constant__ SweepArgs a) {
-    using Cfg = TbCfg<S, KVAR, D, EX, EY, R>;
+    using Cfg = TbCfg<S, KVAR, D, EX, EY, R, PF>;
     constexpr int PX = Cfg::PX, TX = Cfg::TX, TY = Cfg::TY, NTX = Cfg::NTX, NS = Cfg::NS, NK = Cfg::NK,
                   P = Cfg::P, PLANE = Cfg::PLANE;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -273,15 +317,26 @@ __global__ void __launch_bounds__(TbCfg<S, KVAR, D, EX, EY, R>::NT, TbCfg<S, KVA
             bym[r] = !pery && gy0 + r == 0;
             byp[r] = !pery && gy0 + r == c.n[1] - 1;
         }
-        const float tbxm = c.bkind[0] == WFA_BC_DIRICHLET ? c.tb[0] : 0.0f;
-        const float tbxp = c.bkind[1] == WFA_BC_DIRICHLET ? c.tb[1] : 0.0f;
-        const float tbym = c.bkind[2] == WFA_BC_DIRICHLET ? c.tb[2] : 0.0f;
-        const float tbyp = c.bkind[3] == WFA_BC_DIRICHLET ? c.tb[3] : 0.0f;
-        const float tbzm = c.bkind[4] == WFA_BC_DIRICHLET ? c.tb[4] : 0.0f;
-        const float tbzp = c.bkind[5] == WFA_BC_DIRICHLET ? c.tb[5] : 0.0f;
+        // output rows / columns of this thread and whether they need no periodic twins
+        const bool out_cols = xl >= PX && xl < PX + TX;
+        bool out_row[R], plain_row[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int ly = yl + r, gy = gy0 + r;
+            out_row[r] = ly >= D && ly < D + TY && gy < c.n[1];
+            plain_row[r] = gx0 + 3 < c.n[0] && !(perx && (gx0 < HALO || gx0 + 3 >= c.n[0] - HALO)) &&
+                           !(pery && (gy < HALO || gy >= c.n[1] - HALO));
+        }
+        bool thread_inner = true;   // no own cell has an x or y boundary face
+#pragma unroll
+        for (int i = 0; i < 4; ++i) thread_inner = thread_inner && !bxm[i] && !bxp[i];
+#pragma unroll
+        for (int r = 0; r < R; ++r) thread_inner = thread_inner && !bym[r] && !byp[r];
+        const bool has_adv = c.adv[0] != 0.0f || c.adv[1] != 0.0f || c.adv[2] != 0.0f || c.adv[3] != 0.0f ||
+                             c.adv[4] != 0.0f || c.adv[5] != 0.0f;
 
         float zm[D][R][4], zc[D][R][4];   // stage s-1 outputs at planes q-1, q (s = 1..D)
-        float gz[D][R][4];                // per-cell k: conductance of the z face above the last plane
+        float gz[D][R][4];                // per-cell k: coefficient of the z face below the next plane
 #pragma unroll
         for (int s = 0; s < D; ++s)
 #pragma unroll
@@ -294,8 +349,8 @@ __global__ void __launch_bounds__(TbCfg<S, KVAR, D, EX, EY, R>::NT, TbCfg<S, KVA
             // a copy that never lands leaves garbage in the slot; the block
             // agrees to stop at the barrier below before issuing anything new
             const bool late = !mbar_wait_bounded(&bars[idx % NS], (idx / NS) & 1u);
-            const S* cur0 = ring + (idx % NS) * PLANE;        // stage-0 plane j
-            const S* prev0 = ring + ((idx + NS - 1) % NS) * PLANE;  // stage-0 plane j-1
+            const S* cur0 = reinterpret_cast<const S*>(reinterpret_cast<const char*>(ring) + (idx % NS) * Cfg::SLOT_T);  // stage-0 plane j
+            const S* prev0 = reinterpret_cast<const S*>(reinterpret_cast<const char*>(ring) + ((idx + NS - 1) % NS) * Cfg::SLOT_T);  // j-1
 
             float nw[D + 1][R][4];
 #pragma unroll
@@ -329,18 +384,44 @@ __global__ void __launch_bounds__(TbCfg<S, KVAR, D, EX, EY, R>::NT, TbCfg<S, KVA
                 }
                 const bool bzm = !perz && q == 0, bzp = !perz && q == c.n[2] - 1;
 
-                // per-cell k: this stage's k plane (q) and the one above (q + 1)
+                // per-cell k: this stage's 1/k plane (q) and the one above (q + 1)
                 constexpr uint32_t NKS = NK > 0 ? NK : 1;
-                const float* kq = kring + ((idx + 2u * NKS - (uint32_t)s) % NKS) * PLANE;
-                const float* kqp = kring + ((idx + 2u * NKS - (uint32_t)s + 1u) % NKS) * PLANE;
-                float kc[R][4], kb[4], ka[4];
+                const float* kq = reinterpret_cast<const float*>(reinterpret_cast<const char*>(kring) + ((idx + 2u * NKS - (uint32_t)s) % NKS) * Cfg::SLOT_K);
+                const float* kqp = reinterpret_cast<const float*>(reinterpret_cast<const char*>(kring) + ((idx + 2u * NKS - (uint32_t)s + 1u) % NKS) * Cfg::SLOT_K);
+                float kc[R][4];          // 1/k of the own cells
+                float gxf[R][5];         // x faces: left of cell i is gxf[r][i], right is gxf[r][i+1]
+                float gyf[R + 1][4];     // y faces: below row r is gyf[r], above is gyf[r+1]
+                float gzp[R][4];         // z face above plane q (carried to the next plane)
                 if (KVAR) {
+                    float kb[4], ka[4];
 #pragma unroll
                     for (int r = 0; r < R; ++r) Vec4<float>::load(kq + SIDX((yl + r) * EX + xl, PLANE - 3), kc[r]);
                     Vec4<float>::load(kq + SIDX(max(yl - 1, 0) * EX + xl, PLANE - 3), kb);
                     Vec4<float>::load(kq + SIDX(min(yl + R, EY - 1) * EX + xl, PLANE - 3), ka);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const float kl = kq[SIDX((yl + r) * EX + max(xl - 1, 0), PLANE)];
+                        const float kr = kq[SIDX((yl + r) * EX + min(xl + 4, EX - 1), PLANE)];
+                        gxf[r][0] = face_r(kl, kc[r][0], c.tcd[0]);
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) gxf[r][i + 1] = face_r(kc[r][i], kc[r][i + 1], c.tcd[0]);
+                        gxf[r][4] = face_r(kc[r][3], kr, c.tcd[0]);
+                        float kzp[4];
+                        Vec4<float>::load(kqp + SIDX((yl + r) * EX + xl, PLANE - 3), kzp);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) gzp[r][i] = face_r(kc[r][i], kzp[i], c.tcd[2]);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        gyf[0][i] = face_r(kb[i], kc[0][i], c.tcd[1]);
+                        gyf[R][i] = face_r(kc[R - 1][i], ka[i], c.tcd[1]);
+#pragma unroll
+                        for (int r = 1; r < R; ++r) gyf[r][i] = face_r(kc[r - 1][i], kc[r][i], c.tcd[1]);
+                    }
                 }
 
+                // fast path: no cell of this thread touches a boundary at this plane
+                const bool fast = thread_inner && !bzm && !bzp;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     // x neighbours of the row ends (clamped: only out-of-tile cells read a clamped value)
@@ -349,16 +430,6 @@ __global__ void __launch_bounds__(TbCfg<S, KVAR, D, EX, EY, R>::NT, TbCfg<S, KVA
                     const float left = s == 1 ? to_f32<S>(prev0[il]) : sbuf[SIDX((s - 2) * PLANE + il, (D - 1) * PLANE)];
                     const float right = s == 1 ? to_f32<S>(prev0[ir]) : sbuf[SIDX((s - 2) * PLANE + ir, (D - 1) * PLANE)];
                     const int gy = gy0 + r;
-                    float gx[5], kzp[4];
-                    if (KVAR) {
-                        const float kl = kq[SIDX((yl + r) * EX + max(xl - 1, 0), PLANE)];
-                        const float kr = kq[SIDX((yl + r) * EX + min(xl + 4, EX - 1), PLANE)];
-                        gx[0] = harm_face(kl, kc[r][0], c.cd[0]);
-#pragma unroll
-                        for (int i = 0; i < 3; ++i) gx[i + 1] = harm_face(kc[r][i], kc[r][i + 1], c.cd[0]);
-                        gx[4] = harm_face(kc[r][3], kr, c.cd[0]);
-                        Vec4<float>::load(kqp + SIDX((yl + r) * EX + xl, PLANE - 3), kzp);
-                    }
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const float tc = zc[s - 1][r][i];
@@ -368,53 +439,36 @@ __global__ void __launch_bounds__(TbCfg<S, KVAR, D, EX, EY, R>::NT, TbCfg<S, KVA
                         float typ = r == R - 1 ? above[i] : zc[s - 1][r + 1][i];
                         float tzm = zm[s - 1][r][i];
                         float tzp = nw[s - 1][r][i];
-                        if (bxm[i]) txm = tbxm;
-                        if (bxp[i]) txp = tbxp;
-                        if (bym[r]) tym = tbym;
-                        if (byp[r]) typ = tbyp;
-                        if (bzm) tzm = tbzm;
-                        if (bzp) tzp = tbzp;
                         float wxm, wxp, wym, wyp, wzm, wzp;
                         if (KVAR) {
-                            const float kk = kc[r][i];
-                            const float gym = harm_face(r == 0 ? kb[i] : kc[r - 1][i], kk, c.cd[1]);
-                            const float gyp = harm_face(kk, r == R - 1 ? ka[i] : kc[r + 1][i], c.cd[1]);
-                            const float gzm_ = gz[s - 1][r][i];
-                            const float gzp_ = harm_face(kk, kzp[i], c.cd[2]);
-                            gz[s - 1][r][i] = gzp_;
-                            const float dx = dirichlet_face(kk, c.cd[0]);
-                            const float dy = dirichlet_face(kk, c.cd[1]);
-                            const float dz = dirichlet_face(kk, c.cd[2]);
-                            wxm = bxm[i] ? (c.bkind[0] == WFA_BC_DIRICHLET ? __fadd_rn(dx, c.adv[0]) : 0.0f)
-                                         : __fadd_rn(gx[i], c.adv[0]);
-                            wxp = bxp[i] ? (c.bkind[1] == WFA_BC_DIRICHLET ? __fadd_rn(dx, c.adv[1]) : 0.0f)
-                                         : __fadd_rn(gx[i + 1], c.adv[1]);
-                            wym = bym[r] ? (c.bkind[2] == WFA_BC_DIRICHLET ? __fadd_rn(dy, c.adv[2]) : 0.0f)
-                                         : __fadd_rn(gym, c.adv[2]);
-                            wyp = byp[r] ? (c.bkind[3] == WFA_BC_DIRICHLET ? __fadd_rn(dy, c.adv[3]) : 0.0f)
-                                         : __fadd_rn(gyp, c.adv[3]);
-                            wzm = bzm ? (c.bkind[4] == WFA_BC_DIRICHLET ? __fadd_rn(dz, c.adv[4]) : 0.0f)
-                                      : __fadd_rn(gzm_, c.adv[4]);
-                            wzp = bzp ? (c.bkind[5] == WFA_BC_DIRICHLET ? __fadd_rn(dz, c.adv[5]) : 0.0f)
-                                      : __fadd_rn(gzp_, c.adv[5]);
+                            wxm = gxf[r][i]; wxp = gxf[r][i + 1];
+                            wym = gyf[r][i]; wyp = gyf[r + 1][i];
+                            wzm = gz[s - 1][r][i]; wzp = gzp[r][i];
+                            if (has_adv) {
+                                wxm = __fadd_rn(wxm, c.adv[0]); wxp = __fadd_rn(wxp, c.adv[1]);
+                                wym = __fadd_rn(wym, c.adv[2]); wyp = __fadd_rn(wyp, c.adv[3]);
+                                wzm = __fadd_rn(wzm, c.adv[4]); wzp = __fadd_rn(wzp, c.adv[5]);
+                            }
                         } else {
-                            wxm = bxm[i] ? c.w_bd[0] : c.w_in[0];
-                            wxp = bxp[i] ? c.w_bd[1] : c.w_in[1];
-                            wym = bym[r] ? c.w_bd[2] : c.w_in[2];
-                            wyp = byp[r] ? c.w_bd[3] : c.w_in[3];
-                            wzm = bzm ? c.w_bd[4] : c.w_in[4];
-                            wzp = bzp ? c.w_bd[5] : c.w_in[5];
+                            wxm = c.w_in[0]; wxp = c.w_in[1]; wym = c.w_in[2];
+                            wyp = c.w_in[3]; wzm = c.w_in[4]; wzp = c.w_in[5];
                         }
-                        const int gx_ = gx0 + i;
                         float v;
-                        if (is_held(c, gx_, gy, q)) {
-                            v = tc;
+                        const bool edge_cell = !fast && (bxm[i] || bxp[i] || bym[r] || byp[r] || bzm || bzp);
+                        if (!edge_cell) {
+                            v = __fadd_rn(tc, flux_sum(tc, txm, txp, tym, typ, tzm, tzp, wxm, wxp, wym, wyp, wzm, wzp));
                         } else {
-                            v = cell_update(tc, txm, txp, tym, typ, tzm, tzp, wxm, wxp, wym, wyp, wzm, wzp,
-                                            self_term(c, gx_, gy, q));
+                            v = boundary_update<KVAR>(&c, tc, txm, txp, tym, typ, tzm, tzp, wxm, wxp, wym, wyp, wzm,
+                                                      wzp, KVAR ? kc[r][i] : 0.0f, gx0 + i, gy, q);
                         }
                         nw[s][r][i] = storage_round<S>(v);
                     }
+                }
+                if (KVAR) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) gz[s - 1][r][i] = gzp[r][i];
                 }
             }
 
@@ -441,16 +495,15 @@ __global__ void __launch_bounds__(TbCfg<S, KVAR, D, EX, EY, R>::NT, TbCfg<S, KVA
             // output: stage D at plane j - D
             {
                 const int q = j - D;
-                if (q >= z0 && q < z1 && xl >= PX && xl < PX + TX) {
+                if (q >= z0 && q < z1 && out_cols) {
                     S* out = (S*)a.tout;
+                    const bool zplain = !(perz && (q < HALO || q >= c.n[2] - HALO));
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
-                        const int ly = yl + r, gy = gy0 + r;
-                        if (ly < D || ly >= D + TY || gy >= c.n[1]) continue;
+                        if (!out_row[r]) continue;
+                        const int gy = gy0 + r;
                         const int gx = gx0;
-                        const bool plain = gx + 3 < c.n[0] && !(perx && (gx < HALO || gx + 3 >= c.n[0] - HALO)) &&
-                                           !(pery && (gy < HALO || gy >= c.n[1] - HALO)) &&
-                                           !(perz && (q < HALO || q >= c.n[2] - HALO));
+                        const bool plain = plain_row[r] && zplain;
                         if (plain) {
                             const long long off = (long long)q * c.sz + (long long)gy * c.sy + gx;
                             if (WFA_CHK(off >= c.lo && off + 3 < c.hi && (off & 3) == 0, a.status, 10, gx, gy, q, r))
@@ -458,8 +511,7 @@ __global__ void __launch_bounds__(TbCfg<S, KVAR, D, EX, EY, R>::NT, TbCfg<S, KVA
                         } else {
 #pragma unroll
                             for (int i = 0; i < 4; ++i)
-                                if (gx + i < c.n[0])
-                                    store_with_twins<S>(out, c, gx + i, gy, q, from_f32<S>(nw[D][r][i]), a.status);
+                                if (gx + i < c.n[0]) store_twins_out_of_line<S>(out, &c, gx + i, gy, q, nw[D][r][i], a.status);
                         }
                     }
                 }

@@ -1,0 +1,198 @@
+// sweep_col<S, KVAR>: one explicit step per pass (Sec. 1.1.1,
+// Eq. expl_form in face-flux form) without shared memory or barriers.
+//
+// Every thread owns 4 consecutive x cells of one row and marches along z over
+// a chunk of planes. Its own values at planes z-1, z, z+1 live in a register
+// queue; the loads for the next plane (own cells and their x / y
+// neighbours, 128-bit along x) are issued one plane ahead so their latency
+// overlaps the current plane's arithmetic. x / y neighbours of a thread are
+// other threads' cells of the same plane, so they come from L1; every value
+// is read from DRAM about once per pass. The per-cell arithmetic is the same
+// fixed expression as the tiled kernels (bit-identical results).
+#pragma once
+
+#include <algorithm>
+
+#include "wfa_sweep.cuh"
+
+namespace wfa {
+
+template <typename S>
+__device__ __forceinline__ void ldg4(const S* p, float v[4]);
+template <>
+__device__ __forceinline__ void ldg4<float>(const float* p, float v[4]) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+template <>
+__device__ __forceinline__ void ldg4<__nv_bfloat16>(const __nv_bfloat16* p, float v[4]) {
+    const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
+    const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&q.x);
+    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&q.y);
+    v[0] = __low2float(a); v[1] = __high2float(a); v[2] = __low2float(b); v[3] = __high2float(b);
+}
+template <typename S>
+__device__ __forceinline__ float ldg1(const S* p) {
+    return to_f32<S>(*p);
+}
+template <>
+__device__ __forceinline__ float ldg1<float>(const float* p) {
+    return __ldg(p);
+}
+
+// x / y neighbours of one plane for one thread: the 4 cells below and above in
+// y and the x neighbours of the row ends; same for 1/k. They belong to other
+// threads' columns, so they come from L1 (or L2).
+template <typename S, bool KVAR>
+struct ColNb {
+    float ty_m[4], ty_p[4], tx_m, tx_p;
+    float ry_m[4], ry_p[4], rx_m, rx_p;
+    __device__ __forceinline__ void load(const S* tp, const float* rp, long long sy) {
+        ldg4<S>(tp - sy, ty_m);
+        ldg4<S>(tp + sy, ty_p);
+        tx_m = ldg1<S>(tp - 1);
+        tx_p = ldg1<S>(tp + 4);
+        if (KVAR) {
+            ldg4<float>(rp - sy, ry_m);
+            ldg4<float>(rp + sy, ry_p);
+            rx_m = __ldg(rp - 1);
+            rx_p = __ldg(rp + 4);
+        }
+    }
+};
+
+// Occupancy, not register-level prefetch, hides the DRAM latency here: the
+// kernel keeps few live values (64-85 registers) so three or four blocks fit
+// on an SM, and the z extent is cut into short chunks so that tens of
+// thousands of blocks stream the grid at once.
+// blocks per SM the register budget targets: per-cell k needs a few more live
+// values (no spills at three blocks); uniform k fits four
+template <bool KVAR> struct ColOcc { static constexpr int blocks = KVAR ? 3 : 4, unroll = KVAR ? 2 : 1; };
+
+template <typename S, bool KVAR>
+__global__ void __launch_bounds__(256, ColOcc<KVAR>::blocks) sweep_col(const __grid_constant__ SweepArgs a) {
+    const SweepCoef& c = a.c;
+    const int gx = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    const int gy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (gx >= c.n[0] || gy >= c.n[1]) return;
+    const int z0 = blockIdx.z * a.zchunk;
+    const int z1 = min(z0 + a.zchunk, c.n[2]);
+    const long long sy = c.sy, sz = c.sz;
+    const long long col = (long long)gy * sy + gx;
+    // plane p of T is tcol + p * sz (-1 <= p <= nz, inside the halo)
+    const S* __restrict__ tcol = (const S*)a.tin + col;
+    const float* __restrict__ rcol = KVAR ? a.rk + col : nullptr;
+    S* __restrict__ tout = (S*)a.tout;
+
+    const bool perx = c.periodic[0], pery = c.periodic[1], perz = c.periodic[2];
+    const bool bym = !pery && gy == 0, byp = !pery && gy == c.n[1] - 1;
+    const bool edge_x = !perx && (gx == 0 || gx + 3 >= c.n[0] - 1);
+    const bool inner_xy = !edge_x && !bym && !byp && gx + 3 < c.n[0];
+    const bool has_adv = c.adv[0] != 0.0f || c.adv[1] != 0.0f || c.adv[2] != 0.0f || c.adv[3] != 0.0f ||
+                         c.adv[4] != 0.0f || c.adv[5] != 0.0f;
+    const bool plain_xy = gx + 3 < c.n[0] && !(perx && (gx < HALO || gx + 3 >= c.n[0] - HALO)) &&
+                          !(pery && (gy < HALO || gy >= c.n[1] - HALO));
+
+    float tm[4], tc[4], rc[4], gzm[4];
+    ldg4<S>(tcol + (long long)(z0 - 1) * sz, tm);
+    ldg4<S>(tcol + (long long)z0 * sz, tc);
+    if (KVAR) {
+        float rb[4];
+        ldg4<float>(rcol + (long long)(z0 - 1) * sz, rb);
+        ldg4<float>(rcol + (long long)z0 * sz, rc);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) gzm[i] = face_r(rb[i], rc[i], c.tcd[2]);
+    }
+
+#pragma unroll(ColOcc<KVAR>::unroll)
+    for (int z = z0; z < z1; ++z) {
+        const S* tp = tcol + (long long)z * sz;
+        const float* rp = KVAR ? rcol + (long long)z * sz : nullptr;
+        float tz[4], rz[4];
+        ldg4<S>(tp + sz, tz);                       // own cells, plane z + 1
+        if (KVAR) ldg4<float>(rp + sz, rz);
+        ColNb<S, KVAR> nb;                          // x / y neighbours, plane z
+        nb.load(tp, rp, sy);
+
+        const bool bzm = !perz && z == 0, bzp = !perz && z == c.n[2] - 1;
+        const bool fast = inner_xy && !bzm && !bzp;
+        float xf[5], gzp[4];
+        if (KVAR) {
+            xf[0] = face_r(nb.rx_m, rc[0], c.tcd[0]);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) xf[i + 1] = face_r(rc[i], rc[i + 1], c.tcd[0]);
+            xf[4] = face_r(rc[3], nb.rx_p, c.tcd[0]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) gzp[i] = face_r(rc[i], rz[i], c.tcd[2]);
+        }
+        float out[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float txm = i == 0 ? nb.tx_m : tc[i - 1];
+            const float txp = i == 3 ? nb.tx_p : tc[i + 1];
+            float wxm, wxp, wym, wyp, wzm, wzp;
+            if (KVAR) {
+                wxm = xf[i];
+                wxp = xf[i + 1];
+                wym = face_r(nb.ry_m[i], rc[i], c.tcd[1]);
+                wyp = face_r(rc[i], nb.ry_p[i], c.tcd[1]);
+                wzm = gzm[i];
+                wzp = gzp[i];
+                if (has_adv) {
+                    wxm = __fadd_rn(wxm, c.adv[0]); wxp = __fadd_rn(wxp, c.adv[1]);
+                    wym = __fadd_rn(wym, c.adv[2]); wyp = __fadd_rn(wyp, c.adv[3]);
+                    wzm = __fadd_rn(wzm, c.adv[4]); wzp = __fadd_rn(wzp, c.adv[5]);
+                }
+            } else {
+                wxm = c.w_in[0]; wxp = c.w_in[1]; wym = c.w_in[2];
+                wyp = c.w_in[3]; wzm = c.w_in[4]; wzp = c.w_in[5];
+            }
+            const bool edge_cell = !fast && (bym || byp || bzm || bzp ||
+                                             (!perx && (gx + i == 0 || gx + i == c.n[0] - 1)));
+            float v;
+            if (!edge_cell) {
+                v = __fadd_rn(tc[i], flux_sum(tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i], tm[i], tz[i], wxm, wxp,
+                                              wym, wyp, wzm, wzp));
+            } else {
+                v = boundary_update<KVAR>(&c, tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i], tm[i], tz[i], wxm, wxp,
+                                          wym, wyp, wzm, wzp, KVAR ? rc[i] : 0.0f, gx + i, gy, z);
+            }
+            out[i] = storage_round<S>(v);
+        }
+        const bool plain = plain_xy && !(perz && (z < HALO || z >= c.n[2] - HALO));
+        if (plain) {
+            Vec4<S>::store(tout + (long long)z * sz + col, out);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (gx + i < c.n[0]) store_twins_out_of_line<S>(tout, &c, gx + i, gy, z, out[i], a.status);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            tm[i] = tc[i];
+            tc[i] = tz[i];
+            if (KVAR) {
+                rc[i] = rz[i];
+                gzm[i] = gzp[i];
+            }
+        }
+    }
+}
+
+template <typename S, bool KVAR>
+cudaError_t col_launch(const SweepArgs& a_in, cudaStream_t st, int nsm) {
+    SweepArgs a = a_in;
+    dim3 block(16, 16);
+    const int gxb = (a.c.n[0] + 63) / 64, gyb = (a.c.n[1] + 15) / 16;
+    // z chunks of about 16 planes: many short columns stream the grid at once
+    long long want = (long long)nsm * ColOcc<KVAR>::blocks * 16;
+    int nch = (int)std::max<long long>(1, want / std::max(1, gxb * gyb));
+    nch = std::min(nch, std::max(1, a.c.n[2] / 16));
+    a.zchunk = (a.c.n[2] + nch - 1) / nch;
+    nch = (a.c.n[2] + a.zchunk - 1) / a.zchunk;
+    dim3 grid(gxb, gyb, nch);
+    sweep_col<S, KVAR><<<grid, block, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace wfa

@@ -1,4 +1,5 @@
 // Compiled sweep kernels: f32 storage, per-cell conductivity, depths 1..8.
+#include "wfa_sweep_col.cuh"
 #include "wfa_sweep_impl.cuh"
 
 namespace wfa {
@@ -9,15 +10,34 @@ constexpr bool KVAR = true;
 
 // tile shape (EX, EY, R) per variant and depth, sized to the 227 KB of
 // shared memory a block may hold (per-cell k keeps D + 4 k planes on chip)
+// Shared-memory bytes per (x, y) column of the box: input ring (4 slots),
+// k ring (D + 4 slots), one float plane per inner stage.
+constexpr int col_bytes(int D) {
+    return 4 * (int)sizeof(S) + (KVAR ? 4 * (D + 4) : 0) + 4 * (D - 1);
+}
+// Rows of the box: as many as fit the budget (two blocks per SM for depth
+// <= 2, one block beyond), even, at most 64 and 512 threads, at least 2 D + 2.
+constexpr int rows_for(int D, int EX) {
+    const int budget = (D <= 2 ? 110 : 218) * 1024;
+    int ey = budget / (col_bytes(D) * EX);
+    const int ey_threads = ((D <= 2 ? 256 : 512) / (EX / 4)) * 2;   // threads: 2 blocks/SM for D <= 2
+    ey = ey > 64 ? 64 : ey;
+    ey = ey > ey_threads ? ey_threads : ey;
+    ey -= ey % 2;
+    return ey < 2 * D + 2 ? 2 * D + 2 : ey;
+}
+
+template <int D> struct variant_is_wide { static constexpr bool value = true; };
+
+// Tile shapes: the output width TX = EX - 16 is a multiple of 128 bytes.
 template <int D>
 TbEntry pick(int variant) {
-    if (variant == 2) {
-        constexpr int EX = (KVAR && D > 4) ? 96 : 128;
-        constexpr int EY = D <= 2 ? 16 : (D <= 4 ? 24 : (KVAR ? 24 : 32));
-        return make_entry<S, KVAR, D, EX, EY, 2>();
-    }
-    constexpr int EY = D <= 2 ? 32 : (D <= 4 ? 48 : (KVAR ? 32 : 64));
-    return make_entry<S, KVAR, D, 64, EY, 2>();
+    // variant 2: TX = 128 where its smallest box still fits, else as variant 1
+    constexpr bool wide_fits = col_bytes(D) * 144 * (2 * D + 2) <= 218 * 1024;
+    constexpr int EX = (variant_is_wide<D>::value && wide_fits) ? 144 : 80;
+    if (variant == 2) return make_entry<S, KVAR, D, (wide_fits ? 144 : 80), rows_for(D, wide_fits ? 144 : 80), 2, 2>();
+    (void)EX;
+    return make_entry<S, KVAR, D, 80, rows_for(D, 80), 2, 2>();   // TX = 64
 }
 }  // namespace
 
@@ -36,6 +56,10 @@ TbEntry tb_entry_f32_k(int depth, int variant) {
 
 cudaError_t launch_simple_f32_k(const SweepArgs& a, cudaStream_t st) {
     return simple_launch<S, KVAR>(a, st);
+}
+
+cudaError_t launch_col_f32_k(const SweepArgs& a, cudaStream_t st, int nsm) {
+    return col_launch<S, KVAR>(a, st, nsm);
 }
 
 }  // namespace wfa

@@ -30,31 +30,36 @@ cudaError_t launch_simple_f32_u(const SweepArgs& a, cudaStream_t st);
 cudaError_t launch_simple_f32_k(const SweepArgs& a, cudaStream_t st);
 cudaError_t launch_simple_bf16_u(const SweepArgs& a, cudaStream_t st);
 cudaError_t launch_simple_bf16_k(const SweepArgs& a, cudaStream_t st);
+// one-step column-march kernel (variant 3)
+cudaError_t launch_col_f32_u(const SweepArgs& a, cudaStream_t st, int nsm);
+cudaError_t launch_col_f32_k(const SweepArgs& a, cudaStream_t st, int nsm);
+cudaError_t launch_col_bf16_u(const SweepArgs& a, cudaStream_t st, int nsm);
+cudaError_t launch_col_bf16_k(const SweepArgs& a, cudaStream_t st, int nsm);
 
-template <typename S, bool KVAR, int D, int EX, int EY, int R>
+template <typename S, bool KVAR, int D, int EX, int EY, int R, int PF>
 cudaError_t tb_launch(const CUtensorMap* tmT, const CUtensorMap* tmK, const SweepArgs& a, int blocks,
                       cudaStream_t st) {
-    using Cfg = TbCfg<S, KVAR, D, EX, EY, R>;
+    using Cfg = TbCfg<S, KVAR, D, EX, EY, R, PF>;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_tb<S, KVAR, D, EX, EY, R>,
+        cudaError_t e = cudaFuncSetAttribute(sweep_tb<S, KVAR, D, EX, EY, R, PF>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    sweep_tb<S, KVAR, D, EX, EY, R><<<blocks, Cfg::NT, Cfg::SMEM, st>>>(*tmT, *tmK, a);
+    sweep_tb<S, KVAR, D, EX, EY, R, PF><<<blocks, Cfg::NT, Cfg::SMEM, st>>>(*tmT, *tmK, a);
     return cudaGetLastError();
 }
 
-template <typename S, bool KVAR, int D, int EX, int EY, int R>
+template <typename S, bool KVAR, int D, int EX, int EY, int R, int PF>
 int tb_occupancy() {
-    using Cfg = TbCfg<S, KVAR, D, EX, EY, R>;
+    using Cfg = TbCfg<S, KVAR, D, EX, EY, R, PF>;
     static int occ = -1;
     if (occ < 0) {
-        cudaFuncSetAttribute(sweep_tb<S, KVAR, D, EX, EY, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(sweep_tb<S, KVAR, D, EX, EY, R, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Cfg::SMEM);
         int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_tb<S, KVAR, D, EX, EY, R>, Cfg::NT,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_tb<S, KVAR, D, EX, EY, R, PF>, Cfg::NT,
                                                           Cfg::SMEM) != cudaSuccess)
             n = 1;
         occ = n > 0 ? n : 1;
@@ -62,12 +67,12 @@ int tb_occupancy() {
     return occ;
 }
 
-template <typename S, bool KVAR, int D, int EX, int EY, int R>
+template <typename S, bool KVAR, int D, int EX, int EY, int R, int PF>
 TbEntry make_entry() {
-    using Cfg = TbCfg<S, KVAR, D, EX, EY, R>;
+    using Cfg = TbCfg<S, KVAR, D, EX, EY, R, PF>;
     TbEntry e;
-    e.launch = &tb_launch<S, KVAR, D, EX, EY, R>;
-    e.occupancy = &tb_occupancy<S, KVAR, D, EX, EY, R>;
+    e.launch = &tb_launch<S, KVAR, D, EX, EY, R, PF>;
+    e.occupancy = &tb_occupancy<S, KVAR, D, EX, EY, R, PF>;
     e.ex = EX; e.ey = EY; e.r = R;
     e.px = Cfg::PX; e.tx = Cfg::TX; e.ty = Cfg::TY;
     e.depth = D;

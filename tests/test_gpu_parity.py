@@ -35,7 +35,7 @@ def test_heat64_matches_oracle(held):
     ref = run_oracle(p)
     assert abs(oracle_dt(p) - (0.9 / 6 if held else 0.1)) < 1e-15
     outs = {}
-    for variant, depth in [(-1, 1), (1, 1), (1, 2), (1, 4), (2, 3), (1, 8), (2, 8), (0, 0)]:
+    for variant, depth in [(-1, 1), (1, 1), (1, 2), (1, 4), (2, 3), (1, 8), (2, 8), (3, 1), (0, 0)]:
         T = run_gpu(p, depth=depth, variant=variant)
         err = rel_linf(T, ref)
         assert err <= F32_TOL, (variant, depth, err)
@@ -87,6 +87,7 @@ def test_boundary_mixes_all_kernels(mix, kvar, adv):
         for depth in range(1, 9):
             T = run_gpu(p, depth=depth, variant=variant)
             np.testing.assert_array_equal(T, base, err_msg=f"variant {variant} depth {depth}")
+    np.testing.assert_array_equal(run_gpu(p, variant=3), base, err_msg="column kernel")
 
 
 @pytest.mark.parametrize("shape", [(2, 2, 2), (3, 2, 5), (5, 7, 3), (64, 3, 9), (131, 67, 4)])
@@ -101,6 +102,7 @@ def test_small_and_ragged_shapes(shape):
         assert rel_linf(base, ref) <= F32_TOL
         for depth in (1, 3, 8):
             np.testing.assert_array_equal(run_gpu(p, depth=depth, variant=1), base)
+        np.testing.assert_array_equal(run_gpu(p, variant=3), base)
 
 
 def test_zero_steps_and_step_accounting():
@@ -131,6 +133,7 @@ def test_bf16_storage(mix):
     for depth in (1, 2, 5, 8):
         for variant in (1, 2):
             np.testing.assert_array_equal(run_gpu(p, storage=wfa.BF16, depth=depth, variant=variant), base)
+    np.testing.assert_array_equal(run_gpu(p, storage=wfa.BF16, variant=3), base)
 
 
 # ------------------------------------------------------ reductions (fp64) --
@@ -224,3 +227,17 @@ def test_advection_diffusion_reduced(storage):
     T = run_gpu(p, storage=storage)
     err = rel_linf(T, ref)
     assert err <= (F32_TOL if storage == wfa.F32 else bf16_bound(p.steps)), err
+
+
+def test_autotune_keeps_state_and_results():
+    p = _mixed_problem(4, shape=(70, 45, 33), seed=21)
+    ref = run_gpu(p, steps=17, variant=-1)
+    with make_grid(p) as g:
+        g.step(5)
+        before = g.read_field()
+        d, v = g.autotune()
+        assert 1 <= d <= 8 and v in (1, 2, 3)
+        np.testing.assert_array_equal(g.read_field(), before)
+        assert g.steps_done() == 5
+        g.step(12)
+        np.testing.assert_array_equal(g.read_field(), ref)
