@@ -144,6 +144,25 @@ int wfa_read_field(wfa_grid g, float* host_dense);
  * Sec. 3, reduction of a field to one value. */
 int wfa_total_heat(wfa_grid g, double* e);
 
+/* Sum of a caller-owned dense device array of n floats, in fp64, times scale
+ * (the reduction of wfa_total_heat), written to *d_out (device memory), queued
+ * on `stream` (a cudaStream_t; NULL = the legacy default stream). The paper
+ * has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory (a process that reserves all device memory in its
+ * own pool, a real-time loop that cannot afford an allocation's implicit
+ * synchronisation, a plug-in inside a framework that owns every buffer). It
+ * allocates nothing: its scratch, one fp64 partial per 16384 elements, is a
+ * fixed 64 KiB array in the library's device image, held by every GPU that
+ * loads the library until the process exits. Hence n <= 2^27 (134,217,728);
+ * larger n is rejected with WFA_ERR_ARG. Every call writes all the scratch it
+ * reads (nothing carries over), but all calls share the array: calls that may
+ * overlap on the GPU (on different streams without ordering) race. The first
+ * call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture begins. Bit-reproducible for a given n.
+ * Errors: WFA_ERR_ARG (null pointer, negative or too large n), WFA_ERR_CUDA. */
+int wfa_sum_f32_noalloc(const float* d_x, long long n, double scale, double* d_out, void* stream);
+
 /* Wait for the grid's queued work; reports a device-side error. */
 int wfa_sync(wfa_grid g);
 

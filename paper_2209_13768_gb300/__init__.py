@@ -65,6 +65,7 @@ SIGNATURES = {
     "wfa_read_field": (_i, [_vp, _fp]),
     "wfa_total_heat": (_i, [_vp, _dp]),
     "wfa_sync": (_i, [_vp]),
+    "wfa_sum_f32_noalloc": (_i, [_vp, _ll, _d, _vp, _vp]),
     "wfa_last_error": (ctypes.c_char_p, []),
     "wfa_batch_run": (_i, [ctypes.POINTER(_vp), _llp, _i]),
     "wfa_server_create": (_i, [_sz, _i, _ll, ctypes.POINTER(_vp)]),
@@ -213,6 +214,13 @@ class Grid:
 
     def sync(self):
         check(lib().wfa_sync(self.handle), "wfa_sync")
+
+
+def sum_f32_noalloc(d_x, n, scale, d_out, stream=None):
+    """fp64 sum (times scale) of n floats at device address d_x into the device
+    double at d_out, without allocating (see wfa_sum_f32_noalloc)."""
+    check(lib().wfa_sum_f32_noalloc(_vp(d_x), int(n), float(scale), _vp(d_out), _vp(stream) if stream else None),
+          "wfa_sum_f32_noalloc")
 
 
 def batch_run(grids, steps):
