@@ -172,11 +172,15 @@ const char* wfa_last_error(void);
 /* ----------------------------------------------------------- batching -- */
 
 /* Advance many grids in one go (Sec. 4.1.2: iteration rate at small
- * workloads per processor). gs[i] advances steps[i] >= 0 steps. All grids must
- * share the stream of gs[0] and have their field, coefficients and dt set.
- * The steps run as one CUDA-graph launch of a persistent multi-grid kernel
- * whose blocks take (grid, tile, round) work items in dependency order.
- * Results are bitwise identical to calling wfa_step on each grid. */
+ * workloads per processor). gs[i] advances steps[i] >= 0 steps; grids may mix
+ * storage types and conductivity modes. All grids must share the stream of
+ * gs[0], appear once, and have their field, coefficients and dt set. The
+ * steps run as one CUDA-graph launch of a persistent multi-grid kernel whose
+ * blocks take (round, grid, column block) work items in dependency order
+ * (each waits, with a bounded spin, only for items taken before it).
+ * Results are bitwise identical to calling wfa_step on each grid. Returns
+ * after the work is done (synchronises the stream). WFA_ERR_TIMEOUT if a
+ * device-side wait gave up (the fields of the grids are then undefined). */
 int wfa_batch_run(wfa_grid* gs, const long long* steps, int count);
 
 /* ------------------------------------------------------------- serving -- */

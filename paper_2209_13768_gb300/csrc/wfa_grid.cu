@@ -716,3 +716,7 @@ int wfa_sync(wfa_grid g) {
 }
 
 }  // extern "C"
+
+namespace wfa {
+int prepare_coeff_halo(wfa_grid_s* g) { return prepare_k_halo(g); }
+}  // namespace wfa

@@ -121,6 +121,7 @@ int refresh_halo(wfa_grid_s* g, int buf);                 // twins + held layers
 int launch_sweep(wfa_grid_s* g, long long nsteps);        // advance nsteps on g->stream
 int check_status(wfa_grid_s* g);                          // sync + report a device-side timeout
 int autotune(wfa_grid_s* g, int* depth, int* variant);    // pick the fastest kernel configuration
+int prepare_coeff_halo(wfa_grid_s* g);                    // k periodic twins, then 1/k
 void free_tmaps(wfa_grid_s* g);
 
 // ----------------------------------------------------------- device math --

@@ -17,44 +17,69 @@
 
 namespace wfa {
 
-template <typename S>
+// 4 consecutive stored values -> 4 floats, and one value. COH = false reads
+// through the read-only (non-coherent) path; COH = true bypasses L1 (ld.cg),
+// for fields that other blocks rewrite during the same launch.
+template <typename S, bool COH>
 __device__ __forceinline__ void ldg4(const S* p, float v[4]);
 template <>
-__device__ __forceinline__ void ldg4<float>(const float* p, float v[4]) {
+__device__ __forceinline__ void ldg4<float, false>(const float* p, float v[4]) {
     const float4 q = __ldg(reinterpret_cast<const float4*>(p));
     v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
 }
 template <>
-__device__ __forceinline__ void ldg4<__nv_bfloat16>(const __nv_bfloat16* p, float v[4]) {
-    const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
+__device__ __forceinline__ void ldg4<float, true>(const float* p, float v[4]) {
+    const float4 q = __ldcg(reinterpret_cast<const float4*>(p));
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void unpack_bf16x4(uint2 q, float v[4]) {
     const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&q.x);
     const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&q.y);
     v[0] = __low2float(a); v[1] = __high2float(a); v[2] = __low2float(b); v[3] = __high2float(b);
 }
-template <typename S>
-__device__ __forceinline__ float ldg1(const S* p) {
-    return to_f32<S>(*p);
+template <>
+__device__ __forceinline__ void ldg4<__nv_bfloat16, false>(const __nv_bfloat16* p, float v[4]) {
+    unpack_bf16x4(__ldg(reinterpret_cast<const uint2*>(p)), v);
 }
 template <>
-__device__ __forceinline__ float ldg1<float>(const float* p) {
+__device__ __forceinline__ void ldg4<__nv_bfloat16, true>(const __nv_bfloat16* p, float v[4]) {
+    unpack_bf16x4(__ldcg(reinterpret_cast<const uint2*>(p)), v);
+}
+template <typename S, bool COH>
+__device__ __forceinline__ float ldg1(const S* p);
+template <>
+__device__ __forceinline__ float ldg1<float, false>(const float* p) {
     return __ldg(p);
+}
+template <>
+__device__ __forceinline__ float ldg1<float, true>(const float* p) {
+    return __ldcg(p);
+}
+template <>
+__device__ __forceinline__ float ldg1<__nv_bfloat16, true>(const __nv_bfloat16* p) {
+    const unsigned short b = __ldcg(reinterpret_cast<const unsigned short*>(p));
+    return __uint_as_float((unsigned)b << 16);
+}
+template <>
+__device__ __forceinline__ float ldg1<__nv_bfloat16, false>(const __nv_bfloat16* p) {
+    return __bfloat162float(*p);
 }
 
 // x / y neighbours of one plane for one thread: the 4 cells below and above in
 // y and the x neighbours of the row ends; same for 1/k. They belong to other
 // threads' columns, so they come from L1 (or L2).
-template <typename S, bool KVAR>
+template <typename S, bool KVAR, bool COH>
 struct ColNb {
     float ty_m[4], ty_p[4], tx_m, tx_p;
     float ry_m[4], ry_p[4], rx_m, rx_p;
     __device__ __forceinline__ void load(const S* tp, const float* rp, long long sy) {
-        ldg4<S>(tp - sy, ty_m);
-        ldg4<S>(tp + sy, ty_p);
-        tx_m = ldg1<S>(tp - 1);
-        tx_p = ldg1<S>(tp + 4);
-        if (KVAR) {
-            ldg4<float>(rp - sy, ry_m);
-            ldg4<float>(rp + sy, ry_p);
+        ldg4<S, COH>(tp - sy, ty_m);
+        ldg4<S, COH>(tp + sy, ty_p);
+        tx_m = ldg1<S, COH>(tp - 1);
+        tx_p = ldg1<S, COH>(tp + 4);
+        if (KVAR) {   // 1/k never changes during a launch: read-only path
+            ldg4<float, false>(rp - sy, ry_m);
+            ldg4<float, false>(rp + sy, ry_p);
             rx_m = __ldg(rp - 1);
             rx_p = __ldg(rp + 4);
         }
@@ -69,20 +94,16 @@ struct ColNb {
 // values (no spills at three blocks); uniform k fits four
 template <bool KVAR> struct ColOcc { static constexpr int blocks = KVAR ? 3 : 4, unroll = KVAR ? 2 : 1; };
 
-template <typename S, bool KVAR>
-__global__ void __launch_bounds__(256, ColOcc<KVAR>::blocks) sweep_col(const __grid_constant__ SweepArgs a) {
-    const SweepCoef& c = a.c;
-    const int gx = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
-    const int gy = blockIdx.y * blockDim.y + threadIdx.y;
-    if (gx >= c.n[0] || gy >= c.n[1]) return;
-    const int z0 = blockIdx.z * a.zchunk;
-    const int z1 = min(z0 + a.zchunk, c.n[2]);
+// One thread's work: cells (gx .. gx+3, gy) of planes [z0, z1), one step,
+// from tin into tout. Shared by the single-grid kernel and the batched one.
+template <typename S, bool KVAR, bool COH, int UNROLL>
+__device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict__ tin, S* __restrict__ tout,
+                                        const float* __restrict__ rk, int* status, int gx, int gy, int z0, int z1) {
     const long long sy = c.sy, sz = c.sz;
     const long long col = (long long)gy * sy + gx;
     // plane p of T is tcol + p * sz (-1 <= p <= nz, inside the halo)
-    const S* __restrict__ tcol = (const S*)a.tin + col;
-    const float* __restrict__ rcol = KVAR ? a.rk + col : nullptr;
-    S* __restrict__ tout = (S*)a.tout;
+    const S* __restrict__ tcol = tin + col;
+    const float* __restrict__ rcol = KVAR ? rk + col : nullptr;
 
     const bool perx = c.periodic[0], pery = c.periodic[1], perz = c.periodic[2];
     const bool bym = !pery && gy == 0, byp = !pery && gy == c.n[1] - 1;
@@ -94,24 +115,24 @@ __global__ void __launch_bounds__(256, ColOcc<KVAR>::blocks) sweep_col(const __g
                           !(pery && (gy < HALO || gy >= c.n[1] - HALO));
 
     float tm[4], tc[4], rc[4], gzm[4];
-    ldg4<S>(tcol + (long long)(z0 - 1) * sz, tm);
-    ldg4<S>(tcol + (long long)z0 * sz, tc);
+    ldg4<S, COH>(tcol + (long long)(z0 - 1) * sz, tm);
+    ldg4<S, COH>(tcol + (long long)z0 * sz, tc);
     if (KVAR) {
         float rb[4];
-        ldg4<float>(rcol + (long long)(z0 - 1) * sz, rb);
-        ldg4<float>(rcol + (long long)z0 * sz, rc);
+        ldg4<float, false>(rcol + (long long)(z0 - 1) * sz, rb);
+        ldg4<float, false>(rcol + (long long)z0 * sz, rc);
 #pragma unroll
         for (int i = 0; i < 4; ++i) gzm[i] = face_r(rb[i], rc[i], c.tcd[2]);
     }
 
-#pragma unroll(ColOcc<KVAR>::unroll)
+#pragma unroll(UNROLL)
     for (int z = z0; z < z1; ++z) {
         const S* tp = tcol + (long long)z * sz;
         const float* rp = KVAR ? rcol + (long long)z * sz : nullptr;
         float tz[4], rz[4];
-        ldg4<S>(tp + sz, tz);                       // own cells, plane z + 1
-        if (KVAR) ldg4<float>(rp + sz, rz);
-        ColNb<S, KVAR> nb;                          // x / y neighbours, plane z
+        ldg4<S, COH>(tp + sz, tz);                       // own cells, plane z + 1
+        if (KVAR) ldg4<float, false>(rp + sz, rz);
+        ColNb<S, KVAR, COH> nb;                          // x / y neighbours, plane z
         nb.load(tp, rp, sy);
 
         const bool bzm = !perz && z == 0, bzp = !perz && z == c.n[2] - 1;
@@ -165,7 +186,7 @@ __global__ void __launch_bounds__(256, ColOcc<KVAR>::blocks) sweep_col(const __g
         } else {
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-                if (gx + i < c.n[0]) store_twins_out_of_line<S>(tout, &c, gx + i, gy, z, out[i], a.status);
+                if (gx + i < c.n[0]) store_twins_out_of_line<S>(tout, &c, gx + i, gy, z, out[i], status);
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -177,6 +198,17 @@ __global__ void __launch_bounds__(256, ColOcc<KVAR>::blocks) sweep_col(const __g
             }
         }
     }
+}
+
+template <typename S, bool KVAR>
+__global__ void __launch_bounds__(256, ColOcc<KVAR>::blocks) sweep_col(const __grid_constant__ SweepArgs a) {
+    const SweepCoef& c = a.c;
+    const int gx = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    const int gy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (gx >= c.n[0] || gy >= c.n[1]) return;
+    const int z0 = blockIdx.z * a.zchunk;
+    const int z1 = min(z0 + a.zchunk, c.n[2]);
+    col_run<S, KVAR, false, ColOcc<KVAR>::unroll>(c, (const S*)a.tin, (S*)a.tout, a.rk, a.status, gx, gy, z0, z1);
 }
 
 template <typename S, bool KVAR>
