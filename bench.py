@@ -42,7 +42,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["lognormal", "heat64", "advdiff", "advdiff_bf16"], default="lognormal")
+    ap.add_argument("--workload", choices=["lognormal", "heat64", "advdiff", "advdiff_bf16", "batch", "serve"],
+                    default="lognormal")
+    ap.add_argument("--serve-requests", type=int, default=400,
+                    help="requests in the serving sample added to the line (0: none)")
     ap.add_argument("--solve-steps", type=int, default=0, help="time steps per benchmark step (0: workload default)")
     ap.add_argument("--shape", type=str, default="", help="NX,NY,NZ: same physics on another grid (profiling)")
     ap.add_argument("--depth", type=int, default=0, help="fused steps per pass (0: tuned)")
@@ -183,6 +186,112 @@ def reference_arm(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def serving_sample(n_requests, rate=200.0, seed=5, pool=24):
+    """Poisson arrivals (rate per second) of heat / advection-diffusion solves,
+    edges log-uniform in [32, 256], steps U{50..2000}, fp32 or bf16 (config 5).
+    Inputs come from a pool of `pool` request shapes (generated once); each
+    arrival keeps its own time, step count and storage. Runs the stream through
+    the continuous-batching server and through the plain form (one grid at a
+    time, first come first served, wfa_step), and reports both."""
+    import numpy as np
+
+    import paper_2209_13768_gb300 as wfa
+    from paper_2209_13768_gb300 import workloads as W
+    arrivals = W.request_stream(rate=rate, count=n_requests, seed=seed, pool=pool)
+    reqs = [(a.t, a.problem, a.problem.steps, a.storage) for a in arrivals]
+    updates = sum(p.shape[0] * p.shape[1] * p.shape[2] * n for _, p, n, _ in reqs)
+
+    def run_server():
+        lat = []
+        with wfa.Server(budget_bytes=120 << 30, quantum=64) as srv:
+            t0 = time.perf_counter()
+            tickets = []
+            for t, p, n, st in reqs:
+                dt = t - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                tickets.append((srv.submit(p.shape, p.T0, n, h=p.h, storage=st, k=p.k, u=p.u, bc=p.bc, dt=p.dt), t))
+            for tk, t in tickets:
+                srv.wait(tk, timeout=600)
+            wall = time.perf_counter() - t0
+            stats = srv.stats()
+        return wall, stats
+
+    def run_fifo():
+        lat = []
+        t0 = time.perf_counter()
+        for t, p, n, st in reqs:
+            dt = t - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            with wfa.Grid(p.shape, h=p.h, storage=st) as g:
+                g.set_bcs(p.bc)
+                g.set_coeffs(p.k, p.u)
+                g.set_field(p.T0)
+                g.set_dt(p.dt if p.dt else 0.9 * g.stability_dt())
+                g.step(n)
+                g.read_field()
+            lat.append(time.perf_counter() - t0 - t)
+        wall = time.perf_counter() - t0
+        lat.sort()
+        return wall, lat
+
+    wall_s, st = run_server()
+    wall_f, lat_f = run_fifo()
+    pct = lambda v, q: v[min(len(v) - 1, int(q * (len(v) - 1) + 0.5))]
+    return {"requests": len(reqs), "rate_per_s": rate, "offered_GLUPS": updates / reqs[-1][0] / 1e9,
+            "continuous_batching": {"GLUPS": updates / wall_s / 1e9, "p50_s": st["p50_latency_s"],
+                                    "p99_s": st["p99_latency_s"], "wall_s": wall_s, "ticks": st["ticks"]},
+            "one_grid_per_launch_fifo": {"GLUPS": updates / wall_f / 1e9, "p50_s": pct(lat_f, 0.5),
+                                         "p99_s": pct(lat_f, 0.99), "wall_s": wall_f},
+            "inputs": f"pool of {pool} request shapes from the config-5 stream"}
+
+
+def batch_bench(args):
+    """256 grids, edges log-uniform in [16,128], k lognormal(0,0.5), steps
+    U{50..500} (config 4): one persistent CUDA-graph launch vs one grid at a
+    time through wfa_step."""
+    import numpy as np
+    import torch
+
+    import paper_2209_13768_gb300 as wfa
+    from paper_2209_13768_gb300 import workloads as W
+    probs = W.batch_grids()
+    grids = []
+    for p in probs:
+        g = wfa.Grid(p.shape)
+        g.set_bcs(p.bc)
+        g.set_coeffs(p.k, p.u)
+        g.set_field(p.T0)
+        g.set_dt(0.9 * g.stability_dt())
+        grids.append(g)
+    steps = [p.steps for p in probs]
+    updates = sum(p.shape[0] * p.shape[1] * p.shape[2] * n for p, n in zip(probs, steps))
+    wfa.batch_run(grids, [1] * len(grids))   # builds the graph
+    times = []
+    for _ in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        wfa.batch_run(grids, steps)
+        times.append(time.perf_counter() - t0)
+    t_batch = sum(times[args.warmup:]) / args.steps
+    t0 = time.perf_counter()
+    for g, n in zip(grids, steps):
+        g.step(n)
+    for g in grids:
+        g.sync()
+    t_solo = time.perf_counter() - t0
+    for g in grids:
+        g.close()
+    line = {"metric": METRIC, "value": updates / t_batch / 1e9, "unit": "GLUPS", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_batch, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "256 grids, edges log-uniform [16,128], k lognormal(0,0.5), steps U{50..500}",
+                       "cell_updates_per_step": updates},
+            "one_grid_per_launch": {"value": updates / t_solo / 1e9, "unit": "GLUPS", "ms_per_step": 1e3 * t_solo}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -204,6 +313,12 @@ def main():
     import paper_2209_13768_gb300 as wfa
     from paper_2209_13768_gb300 import build as wfa_build
     wfa_build.build()
+    if args.workload == "batch":
+        batch_bench(args)
+        return
+    if args.workload == "serve":
+        print(json.dumps({"metric": METRIC, "serving": serving_sample(args.serve_requests or 400)}), flush=True)
+        return
 
     p = workload(args.workload, args.solve_steps, args.shape)
     storage = wfa.BF16 if args.workload == "advdiff_bf16" else wfa.F32
@@ -308,6 +423,9 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_rate(p, args.cpu_seconds)
+    serving = None
+    if rank == 0 and world == 1 and args.serve_requests and args.workload == "lognormal" and not args.shape:
+        serving = serving_sample(args.serve_requests)
 
     g.close()
     if rank == 0:
@@ -320,7 +438,7 @@ def main():
                            "conductivity": "per-cell lognormal(0,0.5)" if kvar else f"uniform {p.k}",
                            "l2": "inputs larger than L2 (%.0f MiB field)" % (cells * (2 if storage else 4) / 2**20),
                            "parallelism": f"replicas x{world}"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serving": serving,
                 "gpu_launches": args.steps * launches_per_step, "clocks": clocks}
         print(json.dumps(line), flush=True)
     if dist:

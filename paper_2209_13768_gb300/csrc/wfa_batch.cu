@@ -34,7 +34,7 @@ struct BatchGrid {
     SweepCoef c;
     const void* tb[2];    // domain origins of the field buffers; round r reads tb[r & 1]
     const float* rk;      // 1/k (nullptr for uniform k)
-    int bf16, kvar;
+    int bf16, kvar, adv;
     int nbx, nby, nch;    // column blocks per round
     int items;            // nbx * nby * nch
     long long steps;
@@ -79,7 +79,7 @@ __device__ __forceinline__ int load_acquire(const int* p) {
     return v;
 }
 
-template <typename S, bool KVAR>
+template <typename S, bool KVAR, bool ADV>
 __device__ __forceinline__ void batch_item(const BatchGrid& bg, int r, int blk, int* status) {
     const int bx = blk % bg.nbx;
     const int rest = blk / bg.nbx;
@@ -90,7 +90,7 @@ __device__ __forceinline__ void batch_item(const BatchGrid& bg, int r, int blk, 
     if (gx >= bg.c.n[0] || gy >= bg.c.n[1]) return;
     const int z0 = ch * ZCHUNK;
     const int z1 = min(z0 + ZCHUNK, bg.c.n[2]);
-    col_run<S, KVAR, true, 1>(bg.c, (const S*)bg.tb[r & 1], (S*)bg.tb[(r + 1) & 1], bg.rk, status, gx, gy, z0,
+    col_run<S, KVAR, ADV, true, 1, false>(bg.c, (const S*)bg.tb[r & 1], (S*)bg.tb[(r + 1) & 1], bg.rk, status, gx, gy, z0,
                               z1);
 }
 
@@ -134,11 +134,13 @@ __global__ void __launch_bounds__(BATCH_THREADS, 2)
         __syncthreads();
         if (!s_ok) break;
         if (bg.bf16) {
-            if (bg.kvar) batch_item<__nv_bfloat16, true>(bg, r, blk, status);
-            else batch_item<__nv_bfloat16, false>(bg, r, blk, status);
+            if (!bg.kvar) batch_item<__nv_bfloat16, false, false>(bg, r, blk, status);
+            else if (bg.adv) batch_item<__nv_bfloat16, true, true>(bg, r, blk, status);
+            else batch_item<__nv_bfloat16, true, false>(bg, r, blk, status);
         } else {
-            if (bg.kvar) batch_item<float, true>(bg, r, blk, status);
-            else batch_item<float, false>(bg, r, blk, status);
+            if (!bg.kvar) batch_item<float, false, false>(bg, r, blk, status);
+            else if (bg.adv) batch_item<float, true, true>(bg, r, blk, status);
+            else batch_item<float, true, false>(bg, r, blk, status);
         }
         __threadfence();   // this thread's stores before the count below
         __syncthreads();
@@ -314,6 +316,7 @@ extern "C" int wfa_batch_run(wfa_grid* gs, const long long* steps, int count) {
         b.rk = g->r ? g->r + off : nullptr;
         b.bf16 = g->storage == WFA_BF16;
         b.kvar = g->r != nullptr;
+        for (int f = 0; f < 6; ++f) b.adv |= b.c.adv[f] != 0.0f;
         b.nbx = (g->n[0] + 4 * BX - 1) / (4 * BX);
         b.nby = (g->n[1] + BY - 1) / BY;
         b.nch = (g->n[2] + ZCHUNK - 1) / ZCHUNK;

@@ -112,6 +112,41 @@ template <> struct Vec4<__nv_bfloat16> {
     }
 };
 
+// ------------------------------------------------------------ one cell ------
+// One cell with every boundary rule applied, neighbours read from the field
+// (periodic neighbours from the halo twins). i is the cell's element offset.
+template <typename S, bool KVAR>
+__device__ __forceinline__ float general_cell(const SweepCoef& c, const S* __restrict__ in,
+                                              const float* __restrict__ rk, long long i, int x, int y, int z,
+                                              int* status) {
+    const float tc = to_f32<S>(in[i]);
+    if (is_held(c, x, y, z)) return tc;
+    const float rc = KVAR ? rk[i] : 0.0f;
+    const int pos[3] = {x, y, z};
+    const long long st[3] = {1, c.sy, c.sz};
+    float tn[6], w[6];
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        const int ax = f >> 1, side = f & 1;
+        const bool edge = side ? pos[ax] == c.n[ax] - 1 : pos[ax] == 0;
+        tn[f] = 0.0f;
+        w[f] = 0.0f;
+        if (edge && !c.periodic[ax]) {
+            const bool dir = c.bkind[f] == WFA_BC_DIRICHLET;
+            tn[f] = dir ? c.tb[f] : 0.0f;
+            if (KVAR) w[f] = dir ? __fadd_rn(dirichlet_r(rc, c.tcd[ax]), c.adv[f]) : 0.0f;
+            else w[f] = c.w_bd[f];
+        } else {
+            const long long j = i + (side ? st[ax] : -st[ax]);
+            if (!WFA_CHK(j >= c.lo && j < c.hi, status, 20, x, y, z, f)) continue;
+            tn[f] = to_f32<S>(in[j]);
+            w[f] = KVAR ? __fadd_rn(face_r(rc, rk[j], c.tcd[ax]), c.adv[f]) : c.w_in[f];
+        }
+    }
+    return finish_update(tc, flux_sum(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], w[0], w[1], w[2], w[3], w[4], w[5]),
+                         self_term(c, x, y, z));
+}
+
 // ------------------------------------------------------------ simple kernel --
 // One thread per (x, y) column, neighbours read from global memory. One step.
 // Used for grids too small for the tiled kernel's box and as a second,
@@ -127,31 +162,7 @@ __global__ void __launch_bounds__(256) sweep_simple(const __grid_constant__ Swee
     const long long st[3] = {1, c.sy, c.sz};
     for (int z = 0; z < c.n[2]; ++z) {
         const long long i = z * c.sz + y * c.sy + x;
-        const float tc = to_f32<S>(in[i]);
-        float v = tc;
-        if (!is_held(c, x, y, z)) {
-            const float rc = KVAR ? a.rk[i] : 0.0f;
-            const int pos[3] = {x, y, z};
-            float tn[6], w[6];
-#pragma unroll
-            for (int f = 0; f < 6; ++f) {
-                const int ax = f >> 1, side = f & 1;
-                const bool edge = side ? pos[ax] == c.n[ax] - 1 : pos[ax] == 0;
-                if (edge && !c.periodic[ax]) {
-                    const bool dir = c.bkind[f] == WFA_BC_DIRICHLET;
-                    tn[f] = dir ? c.tb[f] : 0.0f;
-                    if (KVAR) w[f] = dir ? __fadd_rn(dirichlet_r(rc, c.tcd[ax]), c.adv[f]) : 0.0f;
-                    else w[f] = c.w_bd[f];
-                } else {
-                    const long long j = i + (side ? st[ax] : -st[ax]);
-                    if (!WFA_CHK(j >= c.lo && j < c.hi, a.status, 20, x, y, z, f)) continue;
-                    tn[f] = to_f32<S>(in[j]);
-                    w[f] = KVAR ? __fadd_rn(face_r(rc, a.rk[j], c.tcd[ax]), c.adv[f]) : c.w_in[f];
-                }
-            }
-            v = finish_update(tc, flux_sum(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], w[0], w[1], w[2], w[3], w[4], w[5]),
-                              self_term(c, x, y, z));
-        }
+        const float v = general_cell<S, KVAR>(c, in, a.rk, i, x, y, z, a.status);
         store_with_twins<S>(out, c, x, y, z, from_f32<S>(v), a.status);
     }
 }

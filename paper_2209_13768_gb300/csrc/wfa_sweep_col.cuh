@@ -96,7 +96,11 @@ template <bool KVAR> struct ColOcc { static constexpr int blocks = KVAR ? 3 : 4,
 
 // One thread's work: cells (gx .. gx+3, gy) of planes [z0, z1), one step,
 // from tin into tout. Shared by the single-grid kernel and the batched one.
-template <typename S, bool KVAR, bool COH, int UNROLL>
+// FIX = true: every cell takes the interior formula and full 4-cell vectors
+// are stored without conditions; boundary cells and periodic halo copies are
+// rewritten afterwards by boundary_fix and twin_copy (single-grid passes).
+// FIX = false: boundary cells and halo copies are handled in place.
+template <typename S, bool KVAR, bool ADV, bool COH, int UNROLL, bool FIX>
 __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict__ tin, S* __restrict__ tout,
                                         const float* __restrict__ rk, int* status, int gx, int gy, int z0, int z1) {
     const long long sy = c.sy, sz = c.sz;
@@ -109,8 +113,6 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
     const bool bym = !pery && gy == 0, byp = !pery && gy == c.n[1] - 1;
     const bool edge_x = !perx && (gx == 0 || gx + 3 >= c.n[0] - 1);
     const bool inner_xy = !edge_x && !bym && !byp && gx + 3 < c.n[0];
-    const bool has_adv = c.adv[0] != 0.0f || c.adv[1] != 0.0f || c.adv[2] != 0.0f || c.adv[3] != 0.0f ||
-                         c.adv[4] != 0.0f || c.adv[5] != 0.0f;
     const bool plain_xy = gx + 3 < c.n[0] && !(perx && (gx < HALO || gx + 3 >= c.n[0] - HALO)) &&
                           !(pery && (gy < HALO || gy >= c.n[1] - HALO));
 
@@ -146,42 +148,56 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
 #pragma unroll
             for (int i = 0; i < 4; ++i) gzp[i] = face_r(rc[i], rz[i], c.tcd[2]);
         }
-        float out[4];
+        // face weights of the 4 cells (same values on both paths below)
+        float w[4][6];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const float txm = i == 0 ? nb.tx_m : tc[i - 1];
-            const float txp = i == 3 ? nb.tx_p : tc[i + 1];
-            float wxm, wxp, wym, wyp, wzm, wzp;
             if (KVAR) {
-                wxm = xf[i];
-                wxp = xf[i + 1];
-                wym = face_r(nb.ry_m[i], rc[i], c.tcd[1]);
-                wyp = face_r(rc[i], nb.ry_p[i], c.tcd[1]);
-                wzm = gzm[i];
-                wzp = gzp[i];
-                if (has_adv) {
-                    wxm = __fadd_rn(wxm, c.adv[0]); wxp = __fadd_rn(wxp, c.adv[1]);
-                    wym = __fadd_rn(wym, c.adv[2]); wyp = __fadd_rn(wyp, c.adv[3]);
-                    wzm = __fadd_rn(wzm, c.adv[4]); wzp = __fadd_rn(wzp, c.adv[5]);
+                w[i][0] = xf[i];
+                w[i][1] = xf[i + 1];
+                w[i][2] = face_r(nb.ry_m[i], rc[i], c.tcd[1]);
+                w[i][3] = face_r(rc[i], nb.ry_p[i], c.tcd[1]);
+                w[i][4] = gzm[i];
+                w[i][5] = gzp[i];
+                if (ADV) {
+#pragma unroll
+                    for (int f = 0; f < 6; ++f) w[i][f] = __fadd_rn(w[i][f], c.adv[f]);
                 }
             } else {
-                wxm = c.w_in[0]; wxp = c.w_in[1]; wym = c.w_in[2];
-                wyp = c.w_in[3]; wzm = c.w_in[4]; wzp = c.w_in[5];
+#pragma unroll
+                for (int f = 0; f < 6; ++f) w[i][f] = c.w_in[f];
             }
-            const bool edge_cell = !fast && (bym || byp || bzm || bzp ||
-                                             (!perx && (gx + i == 0 || gx + i == c.n[0] - 1)));
-            float v;
-            if (!edge_cell) {
-                v = __fadd_rn(tc[i], flux_sum(tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i], tm[i], tz[i], wxm, wxp,
-                                              wym, wyp, wzm, wzp));
-            } else {
-                v = boundary_update<KVAR>(&c, tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i], tm[i], tz[i], wxm, wxp,
-                                          wym, wyp, wzm, wzp, KVAR ? rc[i] : 0.0f, gx + i, gy, z);
+        }
+        float out[4];
+        if (FIX || fast) {   // no cell of this thread touches a boundary at this plane
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float txm = i == 0 ? nb.tx_m : tc[i - 1];
+                const float txp = i == 3 ? nb.tx_p : tc[i + 1];
+                out[i] = storage_round<S>(__fadd_rn(tc[i], flux_sum(tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i], tm[i],
+                                                                    tz[i], w[i][0], w[i][1], w[i][2], w[i][3],
+                                                                    w[i][4], w[i][5])));
             }
-            out[i] = storage_round<S>(v);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float txm = i == 0 ? nb.tx_m : tc[i - 1];
+                const float txp = i == 3 ? nb.tx_p : tc[i + 1];
+                const bool edge_cell = bym || byp || bzm || bzp || (!perx && (gx + i == 0 || gx + i == c.n[0] - 1));
+                float v;
+                if (!edge_cell) {
+                    v = __fadd_rn(tc[i], flux_sum(tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i], tm[i], tz[i], w[i][0],
+                                                  w[i][1], w[i][2], w[i][3], w[i][4], w[i][5]));
+                } else {
+                    v = boundary_update<KVAR>(&c, tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i], tm[i], tz[i], w[i][0],
+                                              w[i][1], w[i][2], w[i][3], w[i][4], w[i][5], KVAR ? rc[i] : 0.0f,
+                                              gx + i, gy, z);
+                }
+                out[i] = storage_round<S>(v);
+            }
         }
         const bool plain = plain_xy && !(perz && (z < HALO || z >= c.n[2] - HALO));
-        if (plain) {
+        if (FIX || plain) {   // FIX: a partial vector at the x end writes into the halo (rewritten later)
             Vec4<S>::store(tout + (long long)z * sz + col, out);
         } else {
 #pragma unroll
@@ -200,7 +216,9 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
     }
 }
 
-template <typename S, bool KVAR>
+// ADV: per-cell k with a nonzero upwind weight on some face (uniform k folds
+// the upwind weights into its constants and never needs it)
+template <typename S, bool KVAR, bool ADV>
 __global__ void __launch_bounds__(256, ColOcc<KVAR>::blocks) sweep_col(const __grid_constant__ SweepArgs a) {
     const SweepCoef& c = a.c;
     const int gx = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
@@ -208,7 +226,60 @@ __global__ void __launch_bounds__(256, ColOcc<KVAR>::blocks) sweep_col(const __g
     if (gx >= c.n[0] || gy >= c.n[1]) return;
     const int z0 = blockIdx.z * a.zchunk;
     const int z1 = min(z0 + a.zchunk, c.n[2]);
-    col_run<S, KVAR, false, ColOcc<KVAR>::unroll>(c, (const S*)a.tin, (S*)a.tout, a.rk, a.status, gx, gy, z0, z1);
+    col_run<S, KVAR, ADV, false, ColOcc<KVAR>::unroll, true>(c, (const S*)a.tin, (S*)a.tout, a.rk, a.status, gx, gy,
+                                                              z0, z1);
+}
+
+// Boundary cells (the outer layer on every non-periodic face): recomputed
+// from the input field with the boundary conditions, one thread per cell
+// (cells on an edge are visited once per face; they get the same value).
+template <typename S, bool KVAR>
+__global__ void __launch_bounds__(256) boundary_fix(const __grid_constant__ SweepArgs a, long long total) {
+    const SweepCoef& c = a.c;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        long long u = t;
+        int pos[3] = {0, 0, 0};
+        for (int ax = 0; ax < 3; ++ax) {
+            if (c.periodic[ax]) continue;
+            const int b = ax == 0 ? 1 : 0, d = ax == 2 ? 1 : 2;
+            const long long face = 2LL * c.n[b] * c.n[d];
+            if (u >= face) {
+                u -= face;
+                continue;
+            }
+            const long long plane = (long long)c.n[b] * c.n[d];
+            pos[ax] = u >= plane ? c.n[ax] - 1 : 0;
+            u %= plane;
+            pos[b] = (int)(u % c.n[b]);
+            pos[d] = (int)(u / c.n[b]);
+            break;
+        }
+        const long long i = (long long)pos[2] * c.sz + (long long)pos[1] * c.sy + pos[0];
+        const float v = general_cell<S, KVAR>(c, (const S*)a.tin, a.rk, i, pos[0], pos[1], pos[2], a.status);
+        ((S*)a.tout)[i] = from_f32<S>(v);
+    }
+}
+
+// Periodic halo copies of one axis, over the full extent of the other two
+// (their halos included, so corners are right when the axes go x, y, z).
+template <typename S>
+__global__ void __launch_bounds__(256) twin_copy(const __grid_constant__ SweepCoef c, S* origin, int ax) {
+    const int b = ax == 0 ? 1 : 0, d = ax == 2 ? 1 : 2;
+    const long long eb = c.n[b] + 2 * HALO, ed = c.n[d] + 2 * HALO;
+    const long long total = 2LL * HALO * eb * ed;
+    const long long st[3] = {1, c.sy, c.sz};
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(t % (2 * HALO));   // halo layer: 0..HALO-1 below, HALO..2 HALO-1 above
+        const long long rest = t / (2 * HALO);
+        const int pb = (int)(rest % eb) - HALO, pd = (int)(rest / eb) - HALO;
+        const int dst = k < HALO ? k - HALO : c.n[ax] + (k - HALO);
+        int src = dst % c.n[ax];
+        if (src < 0) src += c.n[ax];
+        const long long other = pb * st[b] + pd * st[d];
+        origin[other + dst * st[ax]] = origin[other + src * st[ax]];
+    }
 }
 
 template <typename S, bool KVAR>
@@ -223,8 +294,34 @@ cudaError_t col_launch(const SweepArgs& a_in, cudaStream_t st, int nsm) {
     a.zchunk = (a.c.n[2] + nch - 1) / nch;
     nch = (a.c.n[2] + a.zchunk - 1) / a.zchunk;
     dim3 grid(gxb, gyb, nch);
-    sweep_col<S, KVAR><<<grid, block, 0, st>>>(a);
-    return cudaGetLastError();
+    const bool adv = KVAR && (a.c.adv[0] != 0.0f || a.c.adv[1] != 0.0f || a.c.adv[2] != 0.0f ||
+                              a.c.adv[3] != 0.0f || a.c.adv[4] != 0.0f || a.c.adv[5] != 0.0f);
+    if (adv) sweep_col<S, KVAR, true><<<grid, block, 0, st>>>(a);
+    else sweep_col<S, KVAR, false><<<grid, block, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    long long bcells = 0;
+    for (int ax = 0; ax < 3; ++ax) {
+        if (a.c.periodic[ax]) continue;
+        const int b = ax == 0 ? 1 : 0, d = ax == 2 ? 1 : 2;
+        bcells += 2LL * a.c.n[b] * a.c.n[d];
+    }
+    if (bcells > 0) {
+        const int nb = (int)std::min<long long>((bcells + 255) / 256, (long long)nsm * 8);
+        boundary_fix<S, KVAR><<<nb, 256, 0, st>>>(a, bcells);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    for (int ax = 0; ax < 3; ++ax) {
+        if (!a.c.periodic[ax]) continue;
+        const int b = ax == 0 ? 1 : 0, d = ax == 2 ? 1 : 2;
+        const long long total = 2LL * HALO * (a.c.n[b] + 2 * HALO) * (a.c.n[d] + 2 * HALO);
+        const int nb = (int)std::min<long long>((total + 255) / 256, (long long)nsm * 8);
+        twin_copy<S><<<nb, 256, 0, st>>>(a.c, (S*)a.tout, ax);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace wfa

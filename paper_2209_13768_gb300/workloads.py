@@ -102,10 +102,15 @@ class Arrival:
     storage: int       # 0 fp32, 1 bf16
 
 
-def request_stream(rate=200.0, count=10000, lo=32, hi=256, steps=(50, 2000), seed=5, duration=None):
+def request_stream(rate=200.0, count=10000, lo=32, hi=256, steps=(50, 2000), seed=5, duration=None, pool=None):
     """Poisson arrivals (mean `rate` per second) of heat or advection-diffusion
     solves (probability 1/2 each), edges log-uniform in [lo, hi], steps uniform
-    in [steps[0], steps[1]], fp32 or bf16 storage (probability 1/2 each)."""
+    in [steps[0], steps[1]], fp32 or bf16 storage (probability 1/2 each).
+    pool: only the first `pool` arrivals get their own fields; arrival i
+    reuses the shape and fields of arrival i % pool (its time, step count and
+    storage stay its own), so long streams need little host memory."""
+    from dataclasses import replace
+
     rng = np.random.default_rng(seed)
     t = 0.0
     out = []
@@ -117,7 +122,11 @@ def request_stream(rate=200.0, count=10000, lo=32, hi=256, steps=(50, 2000), see
         shape = tuple(int(e) for e in edges)
         n = int(rng.integers(steps[0], steps[1] + 1))
         s = int(rng.integers(0, 2**31))
-        if rng.random() < 0.5:
+        heat = rng.random() < 0.5
+        storage = int(rng.random() < 0.5)
+        if pool is not None and len(out) >= pool:
+            prob = replace(out[len(out) % pool].problem, steps=n)
+        elif heat:
             prob = Problem(shape=shape, T0=uniform01(shape, s), k=lognormal_k(shape, s + 1),
                            bc=[(D, 0.0)] * 6, steps=n, name="heat")
         else:
@@ -125,5 +134,5 @@ def request_stream(rate=200.0, count=10000, lo=32, hi=256, steps=(50, 2000), see
             prob = Problem(shape=shape, T0=gaussian_blob(shape, (nx / 2, ny / 2, nz / 2), max(2.0, min(shape) / 16)),
                            k=0.05, u=(0.3, 0.1, 0.05), bc=[(P, 0.0)] * 2 + [(ZF, 0.0)] * 4, dt=1.0,
                            steps=n, name="advection-diffusion")
-        out.append(Arrival(t=t, problem=prob, storage=int(rng.random() < 0.5)))
+        out.append(Arrival(t=t, problem=prob, storage=storage))
     return out
