@@ -33,7 +33,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell-updates/s (GLUPS) and % HBM roofline on 1 GB300; serving p50/p99 latency"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
-KERNEL_SOURCES = ["paper_2209_13768_gb300/csrc/wfa_sweep.cuh", "paper_2209_13768_gb300/csrc/wfa_internal.cuh"]
+KERNEL_SOURCES = ["paper_2209_13768_gb300/csrc/wfa_sweep_col.cuh", "paper_2209_13768_gb300/csrc/wfa_sweep.cuh",
+                  "paper_2209_13768_gb300/csrc/wfa_internal.cuh"]
 
 
 def parse():
@@ -337,7 +338,11 @@ def main():
         variant = args.variant or (3 if depth == 1 else 1)
     else:   # autotune: time the compiled configurations on this grid, keep the fastest
         depth, variant = g.autotune()
-    launches_per_step = math.ceil(p.steps / depth)
+    passes_per_step = math.ceil(p.steps / depth)
+    # kernels per pass: the column-march pass adds a boundary fix-up kernel
+    # (when some axis is not periodic) and one twin copy per periodic axis
+    periodic = [p.bc[2 * a][0] == "periodic" for a in range(3)]
+    kernels_per_pass = 1 + (not all(periodic)) + sum(periodic) if variant == 3 else 1
 
     for _ in range(args.warmup):
         g.step(p.steps)
@@ -345,6 +350,9 @@ def main():
 
     sampler = ClockSampler(local)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    # the dominant kernel's own launches are bracketed by events inside the
+    # library, on the grid's stream; sample at most about 4000 of them
+    g.set_kernel_timing(max(1, math.ceil(args.steps * passes_per_step / 4000)))
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -356,6 +364,8 @@ def main():
     g.sync()
     torch.cuda.synchronize()
     clocks = sampler.stop()
+    kernel_ms, kernel_launches = g.kernel_time()
+    g.set_kernel_timing(0)
     if dist:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -366,9 +376,11 @@ def main():
         total_s = float(t.item())
     value = world * cells * p.steps * args.steps / total_s / 1e9
 
-    # roofline of the dominant kernel (the tiled sweep): algorithmic bytes per
-    # launch (read T, read k, write T once per pass) over its mean duration
-    launch_s = total_s / (args.steps * launches_per_step)
+    # roofline of the dominant kernel (the main sweep): algorithmic bytes per
+    # launch (read T, read k, write T once per pass) over its mean duration,
+    # from the event pairs the library recorded around its sampled launches
+    pass_s = total_s / (args.steps * passes_per_step)
+    launch_s = kernel_ms / 1e3 / kernel_launches if kernel_launches else pass_s
     bpc = bytes_per_cell(storage == wfa.BF16, kvar)
     achieved = bpc * cells / launch_s / 1e9
     peaks = {}
@@ -382,7 +394,7 @@ def main():
     try:
         with open(TRAFFIC_FILE) as f:
             tr = json.load(f)
-        key = f"{args.workload}:{'bf16' if storage else 'f32'}:{'k' if kvar else 'u'}:d{depth}"
+        key = f"{'bf16' if storage else 'f32'}:{'k' if kvar else 'u'}:{'adv' if any(p.u) else 'noadv'}:v{variant}:d{depth}"
         ent = tr.get(key)
         if ent and ent.get("kernel_hash") == kernel_hash():
             traffic = ent["bytes_per_launch"]
@@ -391,7 +403,9 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "bytes_per_cell_per_launch": bpc, "steps_per_launch": depth,
-                "effective_GBps_paper_Teff": bpc * depth * cells / launch_s / 1e9}
+                "kernel_ms_mean": launch_s * 1e3, "kernel_launches_timed": kernel_launches,
+                "pass_ms_mean": pass_s * 1e3, "pass_GBps": bpc * cells / pass_s / 1e9,
+                "effective_GBps_paper_Teff": bpc * depth * cells / pass_s / 1e9}
 
     # end to end through the C ABI from pinned host buffers
     e2e = None
@@ -431,7 +445,7 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if storage else "f32", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": p.name, "cells": cells, "time_steps_per_step": p.steps, "depth": depth,
                            "kernel": {3: "sweep_col", -1: "sweep_simple"}.get(variant, f"sweep_tb variant {variant}"),
                            "dt": dt, "storage": "bf16" if storage else "f32",
@@ -439,7 +453,7 @@ def main():
                            "l2": "inputs larger than L2 (%.0f MiB field)" % (cells * (2 if storage else 4) / 2**20),
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serving": serving,
-                "gpu_launches": args.steps * launches_per_step, "clocks": clocks}
+                "gpu_launches": args.steps * passes_per_step * kernels_per_pass, "clocks": clocks}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -166,6 +166,21 @@ int wfa_sum_f32_noalloc(const float* d_x, long long n, double scale, double* d_o
 /* Wait for the grid's queued work; reports a device-side error. */
 int wfa_sync(wfa_grid g);
 
+/* Kernel timing, a profiling aid with no counterpart in the paper.
+ * wfa_set_kernel_timing(g, every): every > 0 records a CUDA event pair on the
+ * grid's stream just before and just after the main sweep kernel of every
+ * every-th pass that wfa_step launches from now on (a pass's boundary fix-up
+ * and periodic-copy kernels fall outside the pair; autotuning trials are not
+ * sampled); 0 turns timing off and frees the events. At most 4096 pairs are
+ * held; later passes go unsampled until wfa_kernel_time reads them.
+ * Errors: WFA_ERR_ARG for a NULL grid or every < 0. */
+int wfa_set_kernel_timing(wfa_grid g, int every);
+
+/* Synchronise the stream, then give the summed duration in milliseconds and
+ * the number of the sampled kernel launches since the last call (0 and 0 when
+ * timing is off), and start counting afresh. */
+int wfa_kernel_time(wfa_grid g, double* ms, long long* launches);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* wfa_last_error(void);
 

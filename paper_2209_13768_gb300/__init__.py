@@ -65,6 +65,8 @@ SIGNATURES = {
     "wfa_read_field": (_i, [_vp, _fp]),
     "wfa_total_heat": (_i, [_vp, _dp]),
     "wfa_sync": (_i, [_vp]),
+    "wfa_set_kernel_timing": (_i, [_vp, _i]),
+    "wfa_kernel_time": (_i, [_vp, _dp, _llp]),
     "wfa_sum_f32_noalloc": (_i, [_vp, _ll, _d, _vp, _vp]),
     "wfa_last_error": (ctypes.c_char_p, []),
     "wfa_batch_run": (_i, [ctypes.POINTER(_vp), _llp, _i]),
@@ -214,6 +216,16 @@ class Grid:
 
     def sync(self):
         check(lib().wfa_sync(self.handle), "wfa_sync")
+
+    def set_kernel_timing(self, every):
+        """Time the main sweep kernel of every every-th pass with CUDA events (0: off)."""
+        check(lib().wfa_set_kernel_timing(self.handle, int(every)), "wfa_set_kernel_timing")
+
+    def kernel_time(self):
+        """(summed milliseconds, launches) of the sampled kernels since the last call."""
+        ms, n = ctypes.c_double(), ctypes.c_longlong()
+        check(lib().wfa_kernel_time(self.handle, ctypes.byref(ms), ctypes.byref(n)), "wfa_kernel_time")
+        return ms.value, n.value
 
 
 def sum_f32_noalloc(d_x, n, scale, d_out, stream=None):

@@ -443,6 +443,7 @@ int wfa_destroy_grid(wfa_grid g) {
     if (g->d_status) cudaFree(g->d_status);
     if (g->h_status) cudaFreeHost(g->h_status);
     free_tmaps(g);
+    free_timing(g);
     delete g;
     return WFA_OK;
 }

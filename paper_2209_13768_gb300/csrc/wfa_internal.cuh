@@ -107,6 +107,9 @@ struct wfa_grid_s {
     int* h_status;        // pinned host copy
     void* tmaps;          // wfa::TmapCache (TMA descriptors for the current tile box)
     int tuned_depth, tuned_variant;   // configuration picked by the autotuner (0 = none)
+    int timing_every;     // wfa_set_kernel_timing: sample every n-th pass (0 = off)
+    long long timing_pass;
+    void* timing;         // wfa::KernelTiming (recorded event pairs)
 };
 
 namespace wfa {
@@ -123,6 +126,7 @@ int check_status(wfa_grid_s* g);                          // sync + report a dev
 int autotune(wfa_grid_s* g, int* depth, int* variant);    // pick the fastest kernel configuration
 int prepare_coeff_halo(wfa_grid_s* g);                    // k periodic twins, then 1/k
 void free_tmaps(wfa_grid_s* g);
+void free_timing(wfa_grid_s* g);
 
 // ----------------------------------------------------------- device math --
 // The fixed per-cell arithmetic. Every kernel that updates a cell calls these

@@ -10,6 +10,8 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <new>
+#include <vector>
 
 #include "wfa_sweep_impl.cuh"
 
@@ -26,6 +28,41 @@ struct TmapCache {
 void free_tmaps(wfa_grid_s* g) {
     free(g->tmaps);
     g->tmaps = nullptr;
+}
+
+// Event pairs bracketing the main sweep kernel of sampled passes.
+constexpr int TIMING_MAX_PAIRS = 4096;
+struct KernelTiming {
+    std::vector<cudaEvent_t> ev;   // pair i: ev[2i] before, ev[2i + 1] after
+    int used = 0;
+};
+
+void free_timing(wfa_grid_s* g) {
+    auto* t = static_cast<KernelTiming*>(g->timing);
+    if (!t) return;
+    for (cudaEvent_t e : t->ev) cudaEventDestroy(e);
+    delete t;
+    g->timing = nullptr;
+}
+
+// The pair for this pass, or null when the pass is not sampled (timing off,
+// not an every-th pass, or every pair in use until the next read).
+static const cudaEvent_t* timing_slot(wfa_grid_s* g) {
+    if (g->timing_every <= 0) return nullptr;
+    if (g->timing_pass++ % g->timing_every) return nullptr;
+    auto* t = static_cast<KernelTiming*>(g->timing);
+    if (!t || t->used >= TIMING_MAX_PAIRS) return nullptr;
+    if (2 * t->used == (int)t->ev.size()) {
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess) return nullptr;
+        if (cudaEventCreate(&b) != cudaSuccess) {
+            cudaEventDestroy(a);
+            return nullptr;
+        }
+        t->ev.push_back(a);
+        t->ev.push_back(b);
+    }
+    return &t->ev[2 * t->used++];
 }
 
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -224,12 +261,15 @@ static SweepArgs base_args(wfa_grid_s* g, const SweepCoef& c, int in_buf) {
 // One pass of `depth` fused steps from buffer g->cur into the other buffer.
 static int one_pass(wfa_grid_s* g, const SweepCoef& c, int depth, int variant) {
     SweepArgs a = base_args(g, c, g->cur);
+    const cudaEvent_t* ev = timing_slot(g);
     if (variant < 0) {   // one-column reference kernel, one step
         cudaError_t e;
+        if (ev) cudaEventRecord(ev[0], g->stream);
         if (g->storage == WFA_BF16)
             e = g->k ? launch_simple_bf16_k(a, g->stream) : launch_simple_bf16_u(a, g->stream);
         else
             e = g->k ? launch_simple_f32_k(a, g->stream) : launch_simple_f32_u(a, g->stream);
+        if (ev) cudaEventRecord(ev[1], g->stream);
         if (e != cudaSuccess) return cuda_fail(e, "sweep_simple launch");
         g->cur = 1 - g->cur;
         return WFA_OK;
@@ -237,9 +277,9 @@ static int one_pass(wfa_grid_s* g, const SweepCoef& c, int depth, int variant) {
     if (variant == COL_VARIANT) {   // column-march kernel, one step
         cudaError_t e;
         if (g->storage == WFA_BF16)
-            e = g->r ? launch_col_bf16_k(a, g->stream, num_sms()) : launch_col_bf16_u(a, g->stream, num_sms());
+            e = g->r ? launch_col_bf16_k(a, g->stream, num_sms(), ev) : launch_col_bf16_u(a, g->stream, num_sms(), ev);
         else
-            e = g->r ? launch_col_f32_k(a, g->stream, num_sms()) : launch_col_f32_u(a, g->stream, num_sms());
+            e = g->r ? launch_col_f32_k(a, g->stream, num_sms(), ev) : launch_col_f32_u(a, g->stream, num_sms(), ev);
         if (e != cudaSuccess) return cuda_fail(e, "sweep_col launch");
         g->cur = 1 - g->cur;
         return WFA_OK;
@@ -260,7 +300,9 @@ static int one_pass(wfa_grid_s* g, const SweepCoef& c, int depth, int variant) {
     }
     a.items = (int)items;
     const int blocks = (int)std::min<long long>(items, resident);
+    if (ev) cudaEventRecord(ev[0], g->stream);
     cudaError_t e = en.launch(&tm->t[g->cur], &tm->k, a, blocks, g->stream);
+    if (ev) cudaEventRecord(ev[1], g->stream);
     if (e != cudaSuccess) return cuda_fail(e, "sweep_tb launch");
     g->cur = 1 - g->cur;
     return WFA_OK;
@@ -286,6 +328,13 @@ int autotune(wfa_grid_s* g, int* depth_out, int* variant_out) {
     SweepCoef c;
     int rc = build_coef(g, &c);
     if (rc) return rc;
+    // trial passes are not the caller's steps: keep them out of kernel timing
+    struct Pause {
+        wfa_grid_s* g;
+        int every;
+        ~Pause() { g->timing_every = every; }
+    } pause{g, g->timing_every};
+    g->timing_every = 0;
     static const Choice cands[] = {{COL_VARIANT, 1}, {1, 1}, {2, 1}, {1, 2}, {2, 2}, {1, 3}, {2, 3},
                                    {1, 4}, {2, 4}, {1, 6}, {1, 8}};
     const size_t bytes = field_elems(g) * g->esize;
@@ -341,3 +390,45 @@ int autotune(wfa_grid_s* g, int* depth_out, int* variant_out) {
 }
 
 }  // namespace wfa
+
+extern "C" {
+
+int wfa_set_kernel_timing(wfa_grid g, int every) {
+    if (!g) { wfa::set_error("NULL grid"); return WFA_ERR_ARG; }
+    if (every < 0) { wfa::set_error("every must be >= 0"); return WFA_ERR_ARG; }
+    wfa::free_timing(g);
+    g->timing_every = every;
+    g->timing_pass = 0;
+    if (every > 0) {
+        g->timing = new (std::nothrow) wfa::KernelTiming();
+        if (!g->timing) {
+            g->timing_every = 0;
+            wfa::set_error("host allocation failed");
+            return WFA_ERR_OOM;
+        }
+    }
+    return WFA_OK;
+}
+
+int wfa_kernel_time(wfa_grid g, double* ms, long long* launches) {
+    if (!g || !ms || !launches) { wfa::set_error("NULL argument"); return WFA_ERR_ARG; }
+    *ms = 0.0;
+    *launches = 0;
+    auto* t = static_cast<wfa::KernelTiming*>(g->timing);
+    if (!t) return WFA_OK;
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    double sum = 0.0;
+    for (int i = 0; i < t->used && e == cudaSuccess; ++i) {
+        float m = 0.0f;
+        e = cudaEventElapsedTime(&m, t->ev[2 * i], t->ev[2 * i + 1]);
+        sum += m;
+    }
+    const int n = t->used;
+    t->used = 0;
+    if (e != cudaSuccess) return wfa::cuda_fail(e, "wfa_kernel_time");
+    *ms = sum;
+    *launches = n;
+    return WFA_OK;
+}
+
+}  // extern "C"

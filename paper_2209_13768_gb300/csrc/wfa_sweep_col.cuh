@@ -90,9 +90,9 @@ struct ColNb {
 // kernel keeps few live values (64-85 registers) so three or four blocks fit
 // on an SM, and the z extent is cut into short chunks so that tens of
 // thousands of blocks stream the grid at once.
-// blocks per SM the register budget targets: per-cell k needs a few more live
-// values (no spills at three blocks); uniform k fits four
-template <bool KVAR> struct ColOcc { static constexpr int blocks = KVAR ? 3 : 4, unroll = KVAR ? 2 : 1; };
+// blocks per SM the register budget targets (measured: per-cell k is fastest
+// at four blocks of 64 registers, uniform k at six with the z loop unrolled)
+template <bool KVAR> struct ColOcc { static constexpr int blocks = KVAR ? 4 : 6, unroll = KVAR ? 1 : 2; };
 
 // One thread's work: cells (gx .. gx+3, gy) of planes [z0, z1), one step,
 // from tin into tout. Shared by the single-grid kernel and the batched one.
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(256) twin_copy(const __grid_constant__ SweepCo
 }
 
 template <typename S, bool KVAR>
-cudaError_t col_launch(const SweepArgs& a_in, cudaStream_t st, int nsm) {
+cudaError_t col_launch(const SweepArgs& a_in, cudaStream_t st, int nsm, const cudaEvent_t* ev) {
     SweepArgs a = a_in;
     dim3 block(16, 16);
     const int gxb = (a.c.n[0] + 63) / 64, gyb = (a.c.n[1] + 15) / 16;
@@ -296,8 +296,10 @@ cudaError_t col_launch(const SweepArgs& a_in, cudaStream_t st, int nsm) {
     dim3 grid(gxb, gyb, nch);
     const bool adv = KVAR && (a.c.adv[0] != 0.0f || a.c.adv[1] != 0.0f || a.c.adv[2] != 0.0f ||
                               a.c.adv[3] != 0.0f || a.c.adv[4] != 0.0f || a.c.adv[5] != 0.0f);
+    if (ev) cudaEventRecord(ev[0], st);
     if (adv) sweep_col<S, KVAR, true><<<grid, block, 0, st>>>(a);
     else sweep_col<S, KVAR, false><<<grid, block, 0, st>>>(a);
+    if (ev) cudaEventRecord(ev[1], st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     long long bcells = 0;

@@ -27,17 +27,15 @@ constexpr int rows_for(int D, int EX) {
     return ey < 2 * D + 2 ? 2 * D + 2 : ey;
 }
 
-template <int D> struct variant_is_wide { static constexpr bool value = true; };
-
-// Tile shapes: the output width TX = EX - 16 is a multiple of 128 bytes.
+// Tile shapes; the output width TX = EX - 16 is a multiple of 128 bytes.
+// Variant 1: EX = 80. Variant 2: EX = 144 where its smallest box fits the
+// shared memory, else as variant 1.
 template <int D>
 TbEntry pick(int variant) {
-    // variant 2: TX = 128 where its smallest box still fits, else as variant 1
     constexpr bool wide_fits = col_bytes(D) * 144 * (2 * D + 2) <= 218 * 1024;
-    constexpr int EX = (variant_is_wide<D>::value && wide_fits) ? 144 : 80;
-    if (variant == 2) return make_entry<S, KVAR, D, (wide_fits ? 144 : 80), rows_for(D, wide_fits ? 144 : 80), 2, 2>();
-    (void)EX;
-    return make_entry<S, KVAR, D, 80, rows_for(D, 80), 2, 2>();   // TX = 64
+    constexpr int WIDE = wide_fits ? 144 : 80;
+    if (variant == 2) return make_entry<S, KVAR, D, WIDE, rows_for(D, WIDE), 2, 2>();
+    return make_entry<S, KVAR, D, 80, rows_for(D, 80), 2, 2>();
 }
 }  // namespace
 
@@ -58,8 +56,8 @@ cudaError_t launch_simple_f32_k(const SweepArgs& a, cudaStream_t st) {
     return simple_launch<S, KVAR>(a, st);
 }
 
-cudaError_t launch_col_f32_k(const SweepArgs& a, cudaStream_t st, int nsm) {
-    return col_launch<S, KVAR>(a, st, nsm);
+cudaError_t launch_col_f32_k(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev) {
+    return col_launch<S, KVAR>(a, st, nsm, ev);
 }
 
 }  // namespace wfa

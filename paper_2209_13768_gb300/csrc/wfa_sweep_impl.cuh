@@ -30,11 +30,12 @@ cudaError_t launch_simple_f32_u(const SweepArgs& a, cudaStream_t st);
 cudaError_t launch_simple_f32_k(const SweepArgs& a, cudaStream_t st);
 cudaError_t launch_simple_bf16_u(const SweepArgs& a, cudaStream_t st);
 cudaError_t launch_simple_bf16_k(const SweepArgs& a, cudaStream_t st);
-// one-step column-march kernel (variant 3)
-cudaError_t launch_col_f32_u(const SweepArgs& a, cudaStream_t st, int nsm);
-cudaError_t launch_col_f32_k(const SweepArgs& a, cudaStream_t st, int nsm);
-cudaError_t launch_col_bf16_u(const SweepArgs& a, cudaStream_t st, int nsm);
-cudaError_t launch_col_bf16_k(const SweepArgs& a, cudaStream_t st, int nsm);
+// one-step column-march kernel (variant 3); ev (may be null): events recorded
+// just before and just after the main kernel, outside its fix-up kernels
+cudaError_t launch_col_f32_u(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev);
+cudaError_t launch_col_f32_k(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev);
+cudaError_t launch_col_bf16_u(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev);
+cudaError_t launch_col_bf16_k(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev);
 
 template <typename S, bool KVAR, int D, int EX, int EY, int R, int PF>
 cudaError_t tb_launch(const CUtensorMap* tmT, const CUtensorMap* tmK, const SweepArgs& a, int blocks,

@@ -241,3 +241,20 @@ def test_autotune_keeps_state_and_results():
         assert g.steps_done() == 5
         g.step(12)
         np.testing.assert_array_equal(g.read_field(), ref)
+
+
+@pytest.mark.parametrize("depth,variant", [(1, 3), (2, 1), (1, -1)])
+def test_kernel_timing_samples_and_leaves_results_alone(depth, variant):
+    p = W.heat_lognormal(shape=(40, 33, 27), steps=12)
+    ref = run_gpu(p, depth=depth, variant=variant)
+    with make_grid(p, depth=depth, variant=variant) as g:
+        assert g.kernel_time() == (0.0, 0)          # off: nothing recorded
+        g.set_kernel_timing(2)                       # passes 0, 2, 4, ... are sampled
+        g.step(p.steps)
+        ms, n = g.kernel_time()
+        assert n == (p.steps // depth + 1) // 2 and ms > 0
+        assert g.kernel_time() == (0.0, 0)           # a read starts a new count
+        g.set_kernel_timing(0)
+        np.testing.assert_array_equal(g.read_field(), ref)
+        with pytest.raises(wfa.WfaError):
+            g.set_kernel_timing(-1)
