@@ -189,7 +189,7 @@ def reference_arm(args, rank):
 
 def serving_sample(n_requests, rate=200.0, seed=5, pool=24):
     """Poisson arrivals (rate per second) of heat / advection-diffusion solves,
-    edges log-uniform in [32, 256], steps U{50..2000}, fp32 or bf16 (config 5).
+    edges log-uniform in [32, 256], steps U{50..2000}, fp32 or bf16.
     Inputs come from a pool of `pool` request shapes (generated once); each
     arrival keeps its own time, step count and storage. Runs the stream through
     the continuous-batching server and through the plain form (one grid at a
@@ -245,12 +245,12 @@ def serving_sample(n_requests, rate=200.0, seed=5, pool=24):
                                     "p99_s": st["p99_latency_s"], "wall_s": wall_s, "ticks": st["ticks"]},
             "one_grid_per_launch_fifo": {"GLUPS": updates / wall_f / 1e9, "p50_s": pct(lat_f, 0.5),
                                          "p99_s": pct(lat_f, 0.99), "wall_s": wall_f},
-            "inputs": f"pool of {pool} request shapes from the config-5 stream"}
+            "inputs": f"pool of {pool} request shapes from the serving request stream"}
 
 
 def batch_bench(args):
     """256 grids, edges log-uniform in [16,128], k lognormal(0,0.5), steps
-    U{50..500} (config 4): one persistent CUDA-graph launch vs one grid at a
+    U{50..500}: one persistent CUDA-graph launch vs one grid at a
     time through wfa_step."""
     import numpy as np
     import torch

@@ -81,6 +81,27 @@ int build_coef(const wfa_grid_s* g, SweepCoef* c) {
         if (hi == WFA_BC_ZEROFLUX) c->s_hi[a] = (float)(ap - am);
         if (c->s_lo[a] != 0.0f || c->s_hi[a] != 0.0f) c->any_self = 1;
     }
+    // Boundary faces as ghost cells. With per-cell k the halo layer next to a
+    // Dirichlet face holds the face value with k = inf (1/k = 0), so the
+    // harmonic-mean face coefficient tcd / (1/k_C + 0) is the Dirichlet one,
+    // tcd / (1/k_C), bit for bit; next to a zero-flux face it holds k = 0
+    // (1/k = inf), so the coefficient is 0. The interior formula is then exact
+    // on boundary cells, unless a cell is held, a zero-flux face meets
+    // advection (no ghost value gives the self term), or a bf16 halo cannot
+    // hold a Dirichlet value exactly.
+    bool any_adv = false;
+    for (int f = 0; f < 6; ++f) any_adv = any_adv || c->adv[f] != 0.0f;
+    c->halo_bc = g->r != nullptr;
+    for (int f = 0; f < 6; ++f) {
+        const int kind = g->bc_kind[f];
+        if (kind == WFA_BC_DIRICHLET_CELL) c->halo_bc = 0;
+        if (kind == WFA_BC_ZEROFLUX && any_adv) c->halo_bc = 0;
+        if (kind == WFA_BC_DIRICHLET && g->storage == WFA_BF16) {
+            uint32_t bits;
+            memcpy(&bits, &c->tb[f], sizeof bits);
+            if (bits & 0xFFFFu) c->halo_bc = 0;   // low 16 bits set: not a bf16 value
+        }
+    }
     return WFA_OK;
 }
 
@@ -125,8 +146,23 @@ struct HaloSpec {
     long long px, py;
     int periodic[3];
     int held[6];
-    float gam[6];
+    int dirichlet[6];   // face value on the face (ghost cells hold it)
+    float gam[6];       // held-layer or Dirichlet value
 };
+
+// Dirichlet face whose ghost layer holds the halo cell c (outside the domain
+// on exactly one axis, and that axis not periodic), or -1.
+__device__ __forceinline__ int ghost_face(const HaloSpec& h, const int c[3]) {
+    int face = -1, outside = 0;
+    for (int a = 0; a < 3; ++a) {
+        if (c[a] < 0 || c[a] >= h.n[a]) {
+            ++outside;
+            face = 2 * a + (c[a] >= h.n[a]);
+            if (h.periodic[a]) face = -1;
+        }
+    }
+    return outside == 1 && face >= 0 && h.dirichlet[face] ? face : -1;
+}
 
 // Value a domain cell must hold if a held layer covers it (last face wins).
 __device__ __forceinline__ bool held_value(const HaloSpec& h, int x, int y, int z, float* v) {
@@ -143,8 +179,9 @@ __device__ __forceinline__ bool held_value(const HaloSpec& h, int x, int y, int 
     return any;
 }
 
-// Write the held layers and the halo (periodic twins; 0 elsewhere) of one
-// padded buffer. Every cell of the padded box is visited once.
+// Write the held layers and the halo of one padded buffer: periodic twins,
+// the face value in the ghost layers of Dirichlet faces, 0 elsewhere. Every
+// cell of the padded box is visited once.
 template <typename S>
 __global__ void halo_kernel(S* __restrict__ base, const __grid_constant__ HaloSpec h, long long total) {
     const long long ex = h.n[0] + 2 * HALO, ey = h.n[1] + 2 * HALO;
@@ -172,7 +209,8 @@ __global__ void halo_kernel(S* __restrict__ base, const __grid_constant__ HaloSp
             continue;
         }
         if (fill_zero) {
-            *dst = from_f32<S>(0.0f);
+            const int f = ghost_face(h, c);
+            *dst = from_f32<S>(f >= 0 ? h.gam[f] : 0.0f);
             continue;
         }
         if (held_value(h, w[0], w[1], w[2], &v)) {
@@ -201,21 +239,27 @@ static HaloSpec halo_spec(const wfa_grid_s* g) {
     h.py = g->py;
     for (int f = 0; f < 6; ++f) {
         h.held[f] = g->bc_kind[f] == WFA_BC_DIRICHLET_CELL;
+        h.dirichlet[f] = g->bc_kind[f] == WFA_BC_DIRICHLET;
         h.gam[f] = (float)g->bc_value[f];
     }
     return h;
 }
 
+// Halo of buffer buf, then of the other one: a pass writes only domain cells
+// and periodic twins, so the ghost layers of both must be in place. (The
+// other buffer's twins and held cells are rewritten by the next pass.)
 int refresh_halo(wfa_grid_s* g, int buf) {
     HaloSpec h = halo_spec(g);
     const long long total = (long long)(g->n[0] + 2 * HALO) * (g->n[1] + 2 * HALO) * (g->n[2] + 2 * HALO);
     const int thr = 256;
-    if (g->storage == WFA_BF16)
-        halo_kernel<__nv_bfloat16><<<grid_blocks(total, thr), thr, 0, g->stream>>>(
-            (__nv_bfloat16*)g->T[buf], h, total);
-    else
-        halo_kernel<float><<<grid_blocks(total, thr), thr, 0, g->stream>>>((float*)g->T[buf], h, total);
-    WFA_CUDA(cudaGetLastError());
+    for (int b : {buf, 1 - buf}) {
+        if (g->storage == WFA_BF16)
+            halo_kernel<__nv_bfloat16><<<grid_blocks(total, thr), thr, 0, g->stream>>>(
+                (__nv_bfloat16*)g->T[b], h, total);
+        else
+            halo_kernel<float><<<grid_blocks(total, thr), thr, 0, g->stream>>>((float*)g->T[b], h, total);
+        WFA_CUDA(cudaGetLastError());
+    }
     return WFA_OK;
 }
 
@@ -337,7 +381,8 @@ __global__ void __launch_bounds__(512) finish_max_kernel(const double* __restric
     if (threadIdx.x == 0) *out = sh[0];
 }
 
-// k halo: periodic twins (the harmonic mean across a wrap face reads them), 0 elsewhere.
+// k halo: periodic twins (the harmonic mean across a wrap face reads them),
+// inf in the ghost layers of Dirichlet faces, 0 elsewhere (see build_coef).
 __global__ void k_halo_kernel(float* __restrict__ base, const __grid_constant__ HaloSpec h, long long total) {
     const long long ex = h.n[0] + 2 * HALO, ey = h.n[1] + 2 * HALO;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -355,7 +400,8 @@ __global__ void k_halo_kernel(float* __restrict__ base, const __grid_constant__ 
         }
         if (!outside) continue;
         float* dst = base + ((long long)(c[2] + HALO) * h.py + (c[1] + HALO)) * h.px + (c[0] + HALO);
-        *dst = zero ? 0.0f : base[((long long)(w[2] + HALO) * h.py + (w[1] + HALO)) * h.px + (w[0] + HALO)];
+        *dst = zero ? (ghost_face(h, c) >= 0 ? INFINITY : 0.0f)
+                    : base[((long long)(w[2] + HALO) * h.py + (w[1] + HALO)) * h.px + (w[0] + HALO)];
     }
 }
 

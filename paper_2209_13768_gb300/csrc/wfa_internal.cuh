@@ -58,6 +58,8 @@ struct SweepCoef {
     float s_lo[3], s_hi[3];  // self term of a cell on a zero-flux face with advection
     int held[6];           // face holds its outer cell layer (Dirichlet cell)
     int any_self;          // some zero-flux face carries a self term
+    int halo_bc;           // the halo encodes every boundary face (see build_coef): the
+                           // interior formula is exact on boundary cells too
     long long px, py, pz;  // padded extents (TMA coordinates live in [0, p*))
     long long lo, hi;      // valid element offsets relative to the domain origin
 };

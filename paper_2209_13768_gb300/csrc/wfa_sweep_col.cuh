@@ -96,9 +96,10 @@ template <bool KVAR> struct ColOcc { static constexpr int blocks = KVAR ? 4 : 6,
 
 // One thread's work: cells (gx .. gx+3, gy) of planes [z0, z1), one step,
 // from tin into tout. Shared by the single-grid kernel and the batched one.
-// FIX = true: every cell takes the interior formula and full 4-cell vectors
-// are stored without conditions; boundary cells and periodic halo copies are
-// rewritten afterwards by boundary_fix and twin_copy (single-grid passes).
+// FIX = true: every cell takes the interior formula and stores go out as
+// 4-cell vectors (masked at the x end only); boundary cells and periodic halo
+// copies are rewritten afterwards by boundary_fix (unless the halo encodes
+// the boundary conditions) and twin_copy (single-grid passes).
 // FIX = false: boundary cells and halo copies are handled in place.
 template <typename S, bool KVAR, bool ADV, bool COH, int UNROLL, bool FIX>
 __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict__ tin, S* __restrict__ tout,
@@ -197,7 +198,11 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
             }
         }
         const bool plain = plain_xy && !(perz && (z < HALO || z >= c.n[2] - HALO));
-        if (FIX || plain) {   // FIX: a partial vector at the x end writes into the halo (rewritten later)
+        if (FIX && gx + 3 >= c.n[0]) {   // partial vector at the x end: the halo keeps its ghost values
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (gx + i < c.n[0]) tout[(long long)z * sz + col + i] = from_f32<S>(out[i]);
+        } else if (FIX || plain) {
             Vec4<S>::store(tout + (long long)z * sz + col, out);
         } else {
 #pragma unroll
@@ -308,7 +313,7 @@ cudaError_t col_launch(const SweepArgs& a_in, cudaStream_t st, int nsm, const cu
         const int b = ax == 0 ? 1 : 0, d = ax == 2 ? 1 : 2;
         bcells += 2LL * a.c.n[b] * a.c.n[d];
     }
-    if (bcells > 0) {
+    if (bcells > 0 && !a.c.halo_bc) {
         const int nb = (int)std::min<long long>((bcells + 255) / 256, (long long)nsm * 8);
         boundary_fix<S, KVAR><<<nb, 256, 0, st>>>(a, bcells);
         e = cudaGetLastError();

@@ -28,7 +28,7 @@ def bf16_bound(steps):
     return (steps + 1) * 2.0**-9
 
 
-# ---------------------------------------------------------------- config 1 --
+# ------------------------------------------------------------ heat 64^3 --
 @pytest.mark.parametrize("held", [False, True])
 def test_heat64_matches_oracle(held):
     p = W.heat_64(held_cells=held)
@@ -103,6 +103,43 @@ def test_small_and_ragged_shapes(shape):
         for depth in (1, 3, 8):
             np.testing.assert_array_equal(run_gpu(p, depth=depth, variant=1), base)
         np.testing.assert_array_equal(run_gpu(p, variant=3), base)
+
+
+
+GHOST_MIX = [(D, 0.5), (D, -0.75), (ZF, 0), (D, 1.0), (D, 0.0), (ZF, 0)]   # values exact in bf16
+
+
+@pytest.mark.parametrize("storage", [wfa.F32, wfa.BF16])
+def test_ghost_layer_boundaries(storage):
+    # per-cell k without advection and Dirichlet values a bf16 halo holds
+    # exactly: the column kernel reads the boundary conditions from ghost
+    # layers (k = inf beside a Dirichlet face, k = 0 beside a zero-flux one)
+    for shape in [(37, 29, 23), (6, 5, 9), (64, 16, 16), (2, 3, 2)]:
+        p = _mixed_problem(0, shape=shape, kvar=True, adv=False, seed=11)
+        p.bc = GHOST_MIX
+        base = run_gpu(p, storage=storage, variant=-1)
+        np.testing.assert_array_equal(run_gpu(p, storage=storage, variant=3), base, err_msg=str(shape))
+        if storage == wfa.F32:
+            assert rel_linf(base, run_oracle(p)) <= F32_TOL
+    # boundary conditions changed between steps (odd counts leave the field in
+    # either buffer): both buffers' ghost layers follow every change
+    p = _mixed_problem(0, kvar=True, adv=False, seed=12)
+    p.bc = GHOST_MIX
+    changes = [[], [(0, ZF, 0.0)], [(2, D, 0.25)], [(0, P, 0.0), (1, P, 0.0)], [(5, D, -1.0)], [(3, DC, 0.5)],
+               [(3, D, 0.5), (0, D, 2.0), (1, ZF, 0.0)]]
+    grids = [make_grid(p, storage=storage, variant=v) for v in (3, -1)]
+    try:
+        for change in changes:
+            for g in grids:
+                for face, kind, value in change:
+                    g.set_bc(face, kind, value)
+                if change:
+                    g.set_dt(0.5 * g.stability_dt())
+                g.step(3)
+            np.testing.assert_array_equal(grids[0].read_field(), grids[1].read_field(), err_msg=f"after {change}")
+    finally:
+        for g in grids:
+            g.close()
 
 
 def test_zero_steps_and_step_accounting():
