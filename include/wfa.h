@@ -189,13 +189,14 @@ const char* wfa_last_error(void);
 /* Advance many grids in one go (Sec. 4.1.2: iteration rate at small
  * workloads per processor). gs[i] advances steps[i] >= 0 steps; grids may mix
  * storage types and conductivity modes. All grids must share the stream of
- * gs[0], appear once, and have their field, coefficients and dt set. The
- * steps run as one CUDA-graph launch of a persistent multi-grid kernel whose
- * blocks take (round, grid, column block) work items in dependency order
- * (each waits, with a bounded spin, only for items taken before it).
- * Results are bitwise identical to calling wfa_step on each grid. Returns
- * after the work is done (synchronises the stream). WFA_ERR_TIMEOUT if a
- * device-side wait gave up (the fields of the grids are then undefined). */
+ * gs[0], appear once, and have their field, coefficients and dt set. Step s
+ * of every grid with more than s steps runs in one multi-grid launch per
+ * class of grids (storage type, conductivity mode, advection, boundary
+ * faces in ghost layers or not); nothing inside a launch waits on another
+ * block. Results are bitwise identical to calling wfa_step on each grid.
+ * Returns after the work is done (synchronises the stream).
+ * Errors: WFA_ERR_ARG (NULL or repeated grid, negative steps, different
+ * streams), WFA_ERR_STATE (a grid not ready to step), WFA_ERR_CUDA. */
 int wfa_batch_run(wfa_grid* gs, const long long* steps, int count);
 
 /* ------------------------------------------------------------- serving -- */

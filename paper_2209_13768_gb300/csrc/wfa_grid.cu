@@ -4,6 +4,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cmath>
 #include <new>
 
@@ -310,6 +311,7 @@ struct RateSpec {
     int kind[6];
     int held[6];
     double inv_h2[3], up[3], um[3];  // 1/h^2, max(u,0)/h, max(-u,0)/h
+    float inv_h2f[3], upf[3], umf[3];
     double k_uniform;
 };
 
@@ -318,55 +320,152 @@ __device__ __forceinline__ double harm64(double a, double b) {
     return s > 0.0 ? 2.0 * a * b / s : 0.0;
 }
 
-// D_C of one cell in fp64 (see wfa_stability_dt), 0 for held cells.
-__global__ void __launch_bounds__(RED_THREADS) rate_partial_kernel(const float* __restrict__ korigin, const __grid_constant__ RateSpec r,
-                                                                   double* __restrict__ partials) {
-    __shared__ double sh[RED_THREADS];
-    const long long N = (long long)r.n[0] * r.n[1] * r.n[2];
-    const long long sz = r.px * r.py;
-    double best = 0.0;
-    for (long long i = blockIdx.x * (long long)RED_THREADS + threadIdx.x; i < N;
-         i += (long long)RED_BLOCKS * RED_THREADS) {
-        int c[3];
-        c[0] = (int)(i % r.n[0]);
-        const long long q = i / r.n[0];
-        c[1] = (int)(q % r.n[1]);
-        c[2] = (int)(q / r.n[1]);
-        bool held = false;
-        for (int f = 0; f < 6; ++f)
-            if (r.held[f] && c[f >> 1] == ((f & 1) ? r.n[f >> 1] - 1 : 0)) held = true;
-        if (held) continue;
-        const long long idx = c[2] * sz + c[1] * r.px + c[0];
-        const long long st[3] = {1, r.px, sz};
-        const double kC = korigin ? (double)korigin[idx] : r.k_uniform;
-        double D = 0.0;
-        for (int a = 0; a < 3; ++a) {
-            for (int side = 0; side < 2; ++side) {
-                const int f = 2 * a + side;
-                const bool edge = side == 0 ? c[a] == 0 : c[a] == r.n[a] - 1;
-                bool active = true;
-                if (r.kind[f] == WFA_BC_PERIODIC && r.n[a] == 1) {
-                    continue;
-                } else if (edge && r.kind[f] != WFA_BC_PERIODIC) {
-                    if (r.kind[f] == WFA_BC_DIRICHLET) D += 2.0 * kC * r.inv_h2[a];
-                    else active = false;
-                } else {
-                    // interior or periodic neighbour (periodic twins live in the halo)
-                    const double kD = korigin ? (double)korigin[idx + (side ? st[a] : -st[a])] : r.k_uniform;
-                    D += harm64(kC, kD) * r.inv_h2[a];
-                }
-                if (active) D += side ? r.up[a] : r.um[a];
+__device__ __forceinline__ bool rate_held(const RateSpec& r, const int c[3]) {
+    bool held = false;
+    for (int f = 0; f < 6; ++f)
+        if (r.held[f] && c[f >> 1] == ((f & 1) ? r.n[f >> 1] - 1 : 0)) held = true;
+    return held;
+}
+
+// D_C of one cell in fp64 (see wfa_stability_dt): the sum of the cell's
+// outflow coefficients per unit dt, faces in the order -x, +x, -y, +y, -z, +z.
+__device__ __forceinline__ double rate64(const float* __restrict__ korigin, const RateSpec& r, const int c[3],
+                                         long long idx) {
+    const long long st[3] = {1, r.px, r.px * r.py};
+    const double kC = korigin ? (double)korigin[idx] : r.k_uniform;
+    double D = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        for (int side = 0; side < 2; ++side) {
+            const int f = 2 * a + side;
+            const bool edge = side == 0 ? c[a] == 0 : c[a] == r.n[a] - 1;
+            bool active = true;
+            if (edge && r.kind[f] != WFA_BC_PERIODIC) {
+                if (r.kind[f] == WFA_BC_DIRICHLET) D += 2.0 * kC * r.inv_h2[a];
+                else active = false;
+            } else {
+                // interior or periodic neighbour (periodic twins live in the halo)
+                const double kD = korigin ? (double)korigin[idx + (side ? st[a] : -st[a])] : r.k_uniform;
+                D += harm64(kC, kD) * r.inv_h2[a];
             }
+            if (active) D += side ? r.up[a] : r.um[a];
         }
-        best = fmax(best, D);
     }
+    return D;
+}
+
+// The same sum in fp32 with the harmonic mean as 2 / (1/a + 1/b): every
+// operation is correctly rounded and every term is >= 0, so for a cell whose
+// k values lie in [1e-15, 1e15] (or are 0) the result is within 18 units of
+// 2^-24, relative, of the fp64 one. A cell with other k values is `risky`.
+__device__ __forceinline__ float rate32(const float* __restrict__ korigin, const RateSpec& r, const int c[3],
+                                        long long idx, bool* risky) {
+    const long long st[3] = {1, r.px, r.px * r.py};
+    const float kC = korigin[idx];
+    bool bad = kC != 0.0f && !(kC >= 1e-15f && kC <= 1e15f);
+    float D = 0.0f;
+    for (int a = 0; a < 3; ++a) {
+        for (int side = 0; side < 2; ++side) {
+            const int f = 2 * a + side;
+            const bool edge = side == 0 ? c[a] == 0 : c[a] == r.n[a] - 1;
+            bool active = true;
+            if (edge && r.kind[f] != WFA_BC_PERIODIC) {
+                if (r.kind[f] == WFA_BC_DIRICHLET) D = __fadd_rn(D, __fmul_rn(__fmul_rn(2.0f, kC), r.inv_h2f[a]));
+                else active = false;
+            } else {
+                const float kD = korigin[idx + (side ? st[a] : -st[a])];
+                bad = bad || (kD != 0.0f && !(kD >= 1e-15f && kD <= 1e15f));
+                const float h = (kC > 0.0f && kD > 0.0f)
+                                    ? __fdiv_rn(2.0f, __fadd_rn(__fdiv_rn(1.0f, kC), __fdiv_rn(1.0f, kD)))
+                                    : 0.0f;
+                D = __fadd_rn(D, __fmul_rn(h, r.inv_h2f[a]));
+            }
+            if (active) D = __fadd_rn(D, side ? r.upf[a] : r.umf[a]);
+        }
+    }
+    *risky = bad;
+    return D;
+}
+
+__device__ __forceinline__ void cell_of(const RateSpec& r, long long i, int c[3], long long* idx) {
+    c[0] = (int)(i % r.n[0]);
+    const long long q = i / r.n[0];
+    c[1] = (int)(q % r.n[1]);
+    c[2] = (int)(q / r.n[1]);
+    *idx = (long long)c[2] * r.px * r.py + (long long)c[1] * r.px + c[0];
+}
+
+__device__ __forceinline__ void block_max_out(double best, double* __restrict__ out) {
+    __shared__ double sh[RED_THREADS];
     sh[threadIdx.x] = best;
     __syncthreads();
     for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + s]);
         __syncthreads();
     }
-    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+// Block maxima of D_C in fp64 over every cell that is not held.
+__global__ void __launch_bounds__(RED_THREADS) rate_partial_kernel(const float* __restrict__ korigin,
+                                                                   const __grid_constant__ RateSpec r,
+                                                                   double* __restrict__ partials) {
+    const long long N = (long long)r.n[0] * r.n[1] * r.n[2];
+    double best = 0.0;
+    for (long long i = blockIdx.x * (long long)RED_THREADS + threadIdx.x; i < N;
+         i += (long long)RED_BLOCKS * RED_THREADS) {
+        int c[3];
+        long long idx;
+        cell_of(r, i, c, &idx);
+        if (!rate_held(r, c)) best = fmax(best, rate64(korigin, r, c, idx));
+    }
+    block_max_out(best, &partials[blockIdx.x]);
+}
+
+// Per-cell k, pass 1: block maxima of the fp32 D_C over the cells that are
+// neither held nor risky.
+__global__ void __launch_bounds__(RED_THREADS) rate32_partial_kernel(const float* __restrict__ korigin,
+                                                                     const __grid_constant__ RateSpec r,
+                                                                     double* __restrict__ partials) {
+    const long long N = (long long)r.n[0] * r.n[1] * r.n[2];
+    float best = 0.0f;
+    for (long long i = blockIdx.x * (long long)RED_THREADS + threadIdx.x; i < N;
+         i += (long long)RED_BLOCKS * RED_THREADS) {
+        int c[3];
+        long long idx;
+        cell_of(r, i, c, &idx);
+        if (rate_held(r, c)) continue;
+        bool risky;
+        const float d = rate32(korigin, r, c, idx, &risky);
+        if (!risky) best = fmaxf(best, d);
+    }
+    block_max_out((double)best, &partials[blockIdx.x]);
+}
+
+// Per-cell k, pass 2: fp64 D_C of the candidates only, the cells whose fp32
+// value reaches M (1 - 2^-12), M the pass-1 maximum, and the risky cells. The
+// cell with the largest fp64 value is always a candidate: its fp32 value is
+// at least M (1 - 2 * 18 * 2^-24) > M (1 - 2^-12). So the maximum over the
+// candidates is the fp64 maximum over all cells, the same number as the
+// one-pass reduction gives.
+__global__ void __launch_bounds__(RED_THREADS) rate_cand_kernel(const float* __restrict__ korigin,
+                                                                const __grid_constant__ RateSpec r,
+                                                                const double* __restrict__ m32,
+                                                                double* __restrict__ partials) {
+    const long long N = (long long)r.n[0] * r.n[1] * r.n[2];
+    const float m = (float)*m32;
+    const float thr = __fsub_rn(m, __fmul_rn(m, 0x1p-12f));
+    double best = 0.0;
+    for (long long i = blockIdx.x * (long long)RED_THREADS + threadIdx.x; i < N;
+         i += (long long)RED_BLOCKS * RED_THREADS) {
+        int c[3];
+        long long idx;
+        cell_of(r, i, c, &idx);
+        if (rate_held(r, c)) continue;
+        bool risky;
+        const float d = rate32(korigin, r, c, idx, &risky);
+        if (risky || d >= thr) best = fmax(best, rate64(korigin, r, c, idx));
+    }
+    block_max_out(best, &partials[blockIdx.x]);
 }
 
 __global__ void __launch_bounds__(512) finish_max_kernel(const double* __restrict__ partials, int n,
@@ -575,6 +674,7 @@ int wfa_set_coeffs(wfa_grid g, const float* k_host, double k_uniform, double ux,
     g->u[0] = ux; g->u[1] = uy; g->u[2] = uz;
     g->coeffs_set = true;
     g->dt_set = false;   // the limit may have moved
+    g->limit_valid = false;
     g->halo_dirty = true;
     return WFA_OK;
 }
@@ -590,6 +690,7 @@ int wfa_set_bc(wfa_grid g, int face, int kind, double value) {
     g->bc_value[face] = value;
     g->halo_dirty = true;
     g->dt_set = false;
+    g->limit_valid = false;
     return WFA_OK;
 }
 
@@ -606,10 +707,68 @@ static RateSpec rate_spec(const wfa_grid_s* g) {
         r.kind[f] = g->bc_kind[f];
         r.held[f] = g->bc_kind[f] == WFA_BC_DIRICHLET_CELL;
     }
+    for (int a = 0; a < 3; ++a) {
+        r.inv_h2f[a] = (float)r.inv_h2[a];
+        r.upf[a] = (float)r.up[a];
+        r.umf[a] = (float)r.um[a];
+    }
     r.px = g->px;
     r.py = g->py;
     r.k_uniform = g->k_uniform;
     return r;
+}
+
+// The fp32 first pass keeps every product of a k in [1e-15, 1e15] with these
+// factors inside the normal fp32 range.
+static bool rate32_applies(const RateSpec& r) {
+    for (int a = 0; a < 3; ++a) {
+        if (!(r.inv_h2[a] >= 1e-15 && r.inv_h2[a] <= 1e15)) return false;
+        for (double v : {r.up[a], r.um[a]})
+            if (v != 0.0 && !(v >= 1e-30 && v <= 1e30)) return false;
+    }
+    return true;
+}
+
+// Uniform k: D_C depends only on which faces of the cell are boundary faces,
+// so the maximum is taken over the (at most 27) cell classes on the host:
+// per axis the low end, an interior position (when the edge is >= 3) and the
+// high end. The expression is the device's (rate64) term for term.
+static double uniform_rate_max(const RateSpec& r) {
+    double best = 0.0;
+    int pos[3][3], npos[3];
+    for (int a = 0; a < 3; ++a) {
+        npos[a] = 0;
+        pos[a][npos[a]++] = 0;
+        if (r.n[a] >= 3) pos[a][npos[a]++] = 1;
+        pos[a][npos[a]++] = r.n[a] - 1;
+    }
+    for (int i = 0; i < npos[0]; ++i)
+        for (int j = 0; j < npos[1]; ++j)
+            for (int l = 0; l < npos[2]; ++l) {
+                const int c[3] = {pos[0][i], pos[1][j], pos[2][l]};
+                bool held = false;
+                for (int f = 0; f < 6; ++f)
+                    if (r.held[f] && c[f >> 1] == ((f & 1) ? r.n[f >> 1] - 1 : 0)) held = true;
+                if (held) continue;
+                const double kC = r.k_uniform;
+                double D = 0.0;
+                for (int a = 0; a < 3; ++a)
+                    for (int side = 0; side < 2; ++side) {
+                        const int f = 2 * a + side;
+                        const bool edge = side == 0 ? c[a] == 0 : c[a] == r.n[a] - 1;
+                        bool active = true;
+                        if (edge && r.kind[f] != WFA_BC_PERIODIC) {
+                            if (r.kind[f] == WFA_BC_DIRICHLET) D += 2.0 * kC * r.inv_h2[a];
+                            else active = false;
+                        } else {
+                            const double s2 = kC + kC;
+                            D += (s2 > 0.0 ? 2.0 * kC * kC / s2 : 0.0) * r.inv_h2[a];
+                        }
+                        if (active) D += side ? r.up[a] : r.um[a];
+                    }
+                best = std::max(best, D);
+            }
+    return best;
 }
 
 // k halo (periodic twins), then r = 1/k over the whole padded buffer.
@@ -631,18 +790,36 @@ int wfa_stability_dt(wfa_grid g, double* dt_max) {
     for (int a = 0; a < 3; ++a)
         if ((g->bc_kind[2 * a] == WFA_BC_PERIODIC) != (g->bc_kind[2 * a + 1] == WFA_BC_PERIODIC))
             return fail(WFA_ERR_BC, "axis %d: a periodic face needs a periodic opposite face", a);
-    int rc = prepare_k_halo(g);
-    if (rc) return rc;
-    RateSpec r = rate_spec(g);
-    rate_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, g->stream>>>(g->k ? g->k + domain_offset(g) : nullptr, r,
-                                                                   g->d_partials);
-    finish_max_kernel<<<1, 512, 0, g->stream>>>(g->d_partials, RED_BLOCKS, g->d_partials + RED_BLOCKS);
-    WFA_CUDA(cudaGetLastError());
-    WFA_CUDA(cudaMemcpyAsync(g->h_result, g->d_partials + RED_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost,
-                             g->stream));
-    WFA_CUDA(cudaStreamSynchronize(g->stream));
-    const double dmax = g->h_result[0];
-    *dt_max = dmax > 0.0 ? 1.0 / dmax : INFINITY;
+    if (!g->limit_valid) {
+        RateSpec r = rate_spec(g);
+        double dmax;
+        if (!g->k) {
+            dmax = uniform_rate_max(r);
+        } else {
+            int rc = prepare_k_halo(g);
+            if (rc) return rc;
+            const float* ko = g->k + domain_offset(g);
+            double* part = g->d_partials;
+            if (rate32_applies(r)) {
+                rate32_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, g->stream>>>(ko, r, part);
+                finish_max_kernel<<<1, 512, 0, g->stream>>>(part, RED_BLOCKS, part + RED_BLOCKS);
+                rate_cand_kernel<<<RED_BLOCKS, RED_THREADS, 0, g->stream>>>(ko, r, part + RED_BLOCKS,
+                                                                            part + 2 * RED_BLOCKS);
+                finish_max_kernel<<<1, 512, 0, g->stream>>>(part + 2 * RED_BLOCKS, RED_BLOCKS, part + RED_BLOCKS + 1);
+            } else {
+                rate_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, g->stream>>>(ko, r, part + 2 * RED_BLOCKS);
+                finish_max_kernel<<<1, 512, 0, g->stream>>>(part + 2 * RED_BLOCKS, RED_BLOCKS, part + RED_BLOCKS + 1);
+            }
+            WFA_CUDA(cudaGetLastError());
+            WFA_CUDA(cudaMemcpyAsync(g->h_result, part + RED_BLOCKS + 1, sizeof(double), cudaMemcpyDeviceToHost,
+                                     g->stream));
+            WFA_CUDA(cudaStreamSynchronize(g->stream));
+            dmax = g->h_result[0];
+        }
+        g->limit = dmax > 0.0 ? 1.0 / dmax : INFINITY;
+        g->limit_valid = true;
+    }
+    *dt_max = g->limit;
     return WFA_OK;
 }
 

@@ -99,6 +99,8 @@ struct wfa_grid_s {
     int bc_kind[6];
     double bc_value[6];
     double dt;
+    double limit;         // stability limit dt_max of the current coefficients and faces
+    bool limit_valid;
     bool field_set, coeffs_set, dt_set, halo_dirty;
     long long steps_done;
     int force_depth, force_variant;   // wfa_set_tuning (0 = automatic)

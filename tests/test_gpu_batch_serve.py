@@ -2,7 +2,6 @@
 
 Both run the same per-cell arithmetic as wfa_step, so every result must be
 bit-identical to the grid advanced alone."""
-import os
 import time
 
 import numpy as np
@@ -61,27 +60,36 @@ def test_batch_matches_oracle():
             g.close()
 
 
-def test_batch_wait_times_out_cleanly():
-    # a dependency that nothing ever satisfies (host-side test hook): the
-    # bounded device wait gives up, the call reports it, the context lives on
-    p = _problem(0, np.random.default_rng(3))
-    p.steps = 4
-    g = make_grid(p)
+def test_batch_sizes_steps_and_classes():
+    # tiny and large grids, zero and single steps, every class of the batched
+    # sweep (f32 / bf16, uniform / per-cell k, advection, ghost-layer faces)
+    rng = np.random.default_rng(17)
+    shapes = [(2, 2, 2), (3, 5, 2), (130, 67, 40), (16, 16, 16), (9, 70, 5), (64, 8, 33)]
+    mixes = [[(D, 0.5)] * 6, [(D, 0.25), (ZF, 0), (ZF, 0), (D, -0.5), (ZF, 0), (D, 1.0)],
+             [(P, 0)] * 2 + [(ZF, 0)] * 4, [(DC, 1.0)] + [(D, 0.0)] * 5]
+    probs, storages = [], []
+    for i in range(24):
+        shape = shapes[i % len(shapes)]
+        nx, ny, nz = shape
+        mix = mixes[(i // 2) % len(mixes)]
+        if any(k == DC for k, _ in mix) and min(shape) < 3:
+            mix = mixes[0]
+        kvar = i % 3 != 0
+        k = np.exp(0.5 * rng.standard_normal((nz, ny, nx))).astype(np.float32) if kvar else 0.6
+        u = tuple(rng.uniform(-0.3, 0.3, 3)) if i % 4 == 1 else (0.0, 0.0, 0.0)
+        T0 = rng.uniform(0, 1, (nz, ny, nx)).astype(np.float32)
+        probs.append(W.Problem(shape=shape, T0=T0, k=k, u=u, bc=mix, steps=[0, 1, 2, 7, 23, 40][i % 6]))
+        storages.append(wfa.BF16 if i % 5 == 2 else wfa.F32)
+    grids = [make_grid(p, storage=s) for p, s in zip(probs, storages)]
     try:
-        os.environ["WFA_TEST_BATCH_STALL"] = "1"
-        t0 = time.time()
-        with pytest.raises(wfa.WfaError) as e:
-            wfa.batch_run([g], [4])
-        assert e.value.code == -6
-        assert time.time() - t0 < 30
+        wfa.batch_run(grids, [p.steps for p in probs])
+        for p, s, g in zip(probs, storages, grids):
+            assert g.steps_done() == p.steps
+            np.testing.assert_array_equal(g.read_field(), run_gpu(p, storage=s, variant=-1),
+                                          err_msg=f"{p.shape} steps {p.steps} storage {s}")
     finally:
-        os.environ.pop("WFA_TEST_BATCH_STALL", None)
-        g.close()
-    q = _problem(1, np.random.default_rng(4))
-    q.steps = 5
-    with make_grid(q) as g2:
-        wfa.batch_run([g2], [5])
-        np.testing.assert_array_equal(g2.read_field(), run_gpu(q, variant=-1))
+        for g in grids:
+            g.close()
 
 
 def test_server_results_equal_alone_and_in_a_mix():

@@ -183,6 +183,39 @@ def test_stability_dt_matches_oracle():
         assert abs(got - ref) <= 1e-13 * ref, (mix, got, ref)
 
 
+
+@pytest.mark.parametrize("case", ["layered", "extreme", "zeros", "tiny_h", "uniform"])
+def test_stability_dt_two_pass_cases(case):
+    # per-cell k takes an fp32 pass, then fp64 on the near-maximal cells only;
+    # ties, k values outside the fp32 pass's range, zero k and cell sizes that
+    # send it to the one-pass fp64 reduction must all give the fp64 maximum
+    rng = np.random.default_rng(21)
+    shape = (23, 17, 12)
+    nx, ny, nz = shape
+    for mix in range(len(MIXES)):
+        p = _mixed_problem(mix, shape=shape, seed=mix)
+        if case == "layered":
+            p.k = np.broadcast_to(rng.uniform(0.5, 2.0, nx).astype(np.float32), (nz, ny, nx)).copy()
+        elif case == "extreme":
+            k = np.asarray(p.k).copy()
+            k[3, 4, 5], k[7, 2, 9], k[0, 0, 0] = 1e20, 1e-20, 3e16
+            p.k = k
+        elif case == "zeros":
+            k = np.asarray(p.k).copy()
+            k[rng.random(k.shape) < 0.3] = 0.0
+            p.k = k
+        elif case == "tiny_h":
+            p.h = (1e-9, 2e-9, 1.5e-9)
+        else:
+            p.k = 0.7
+        k = p.k if np.isscalar(p.k) else np.asarray(p.k, np.float64)
+        ref = oracle.dt_max(shape=p.shape, h=p.h, k=k, u=p.u, bc=p.bc)
+        with make_grid(p, dt=1e-30) as g:
+            got = g.stability_dt()
+            assert g.stability_dt() == got     # cached until the coefficients or faces change
+        assert abs(got - ref) <= 1e-13 * ref, (case, mix, got, ref)
+
+
 def test_unstable_dt_rejected():
     p = _mixed_problem(0)
     with make_grid(p) as g:
