@@ -57,6 +57,21 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x, dist, device):
+    """Largest x over all ranks: the slowest replica sets the job's time."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, updates_per_rank, seconds):
+    """Whole-job GLUPS: every rank advances its own replica (weak scaling)."""
+    return world * updates_per_rank / seconds / 1e9
+
+
 def kernel_hash():
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES:
@@ -370,11 +385,8 @@ def main():
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([total_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * cells * p.steps * args.steps / total_s / 1e9
+    total_s = max_over_ranks(total_s, dist, "cuda")
+    value = job_rate(world, cells * p.steps * args.steps, total_s)
 
     # roofline of the dominant kernel (the main sweep): algorithmic bytes per
     # launch (read T, read k, write T once per pass) over its mean duration,
@@ -426,11 +438,8 @@ def main():
             if i:   # first one is a warm-up
                 e2e_t.append(time.perf_counter() - t0)
         e2e_s = sum(e2e_t) / len(e2e_t)
-        if dist:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * cells * p.steps / e2e_s / 1e9, "unit": "GLUPS",
+        e2e_s = max_over_ranks(e2e_s, dist, "cuda")
+        e2e = {"value": job_rate(world, cells * p.steps, e2e_s), "unit": "GLUPS",
                "h2d_bytes_per_step": cells * 4 * (2 if kvar else 1), "d2h_bytes_per_step": cells * 4,
                "ms_per_step": 1e3 * e2e_s}
 

@@ -180,46 +180,70 @@ __device__ __forceinline__ bool held_value(const HaloSpec& h, int x, int y, int 
     return any;
 }
 
-// Write the held layers and the halo of one padded buffer: periodic twins,
-// the face value in the ghost layers of Dirichlet faces, 0 elsewhere. Every
-// cell of the padded box is visited once.
+// One cell (x, y, z) of the padded box of a field buffer: held layers get
+// their value, periodic twins a copy, the ghost layers of Dirichlet faces
+// the face value, every other halo cell 0; other domain cells are left alone.
 template <typename S>
-__global__ void halo_kernel(S* __restrict__ base, const __grid_constant__ HaloSpec h, long long total) {
-    const long long ex = h.n[0] + 2 * HALO, ey = h.n[1] + 2 * HALO;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % ex) - HALO;
-        const long long r = i / ex;
-        const int y = (int)(r % ey) - HALO;
+__device__ __forceinline__ void halo_cell(S* __restrict__ base, const HaloSpec& h, int x, int y, int z) {
+    const int c[3] = {x, y, z};
+    bool outside = false, fill_zero = false;
+    int w[3];
+    for (int a = 0; a < 3; ++a) {
+        w[a] = c[a];
+        if (c[a] < 0 || c[a] >= h.n[a]) {
+            outside = true;
+            if (h.periodic[a]) w[a] = ((c[a] % h.n[a]) + h.n[a]) % h.n[a];
+            else fill_zero = true;
+        }
+    }
+    S* dst = base + ((long long)(z + HALO) * h.py + (y + HALO)) * h.px + (x + HALO);
+    float v;
+    if (!outside) {
+        if (held_value(h, x, y, z, &v)) *dst = from_f32<S>(v);
+        return;
+    }
+    if (fill_zero) {
+        const int f = ghost_face(h, c);
+        *dst = from_f32<S>(f >= 0 ? h.gam[f] : 0.0f);
+        return;
+    }
+    if (held_value(h, w[0], w[1], w[2], &v)) {
+        *dst = from_f32<S>(v);
+    } else {
+        const S* src = base + ((long long)(w[2] + HALO) * h.py + (w[1] + HALO)) * h.px + (w[0] + HALO);
+        *dst = *src;
+    }
+}
+
+// x positions of row (y, z) of the padded box that can need a write: all of
+// them when the row lies outside the domain or on a held y / z layer, else
+// the x halo and the two end cells (held x layers).
+__device__ __forceinline__ bool full_row(const HaloSpec& h, int y, int z) {
+    if (y < 0 || y >= h.n[1] || z < 0 || z >= h.n[2]) return true;
+    return (h.held[2] && y == 0) || (h.held[3] && y == h.n[1] - 1) || (h.held[4] && z == 0) ||
+           (h.held[5] && z == h.n[2] - 1);
+}
+__device__ __forceinline__ int row_x(const HaloSpec& h, bool full, int t) {
+    if (full) return t - HALO;
+    if (t < HALO) return t - HALO;                     // -HALO .. -1
+    if (t < 2 * HALO) return h.n[0] + (t - HALO);      // n .. n + HALO - 1
+    return t == 2 * HALO ? 0 : h.n[0] - 1;             // end cells
+}
+
+// Halo and held layers of one padded buffer, one warp per row of the padded
+// box (no per-cell 64-bit index arithmetic; interior rows touch 18 cells).
+template <typename S>
+__global__ void halo_kernel(S* __restrict__ base, const __grid_constant__ HaloSpec h) {
+    const int ey = h.n[1] + 2 * HALO;
+    const long long rows = (long long)ey * (h.n[2] + 2 * HALO);
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long r = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
         const int z = (int)(r / ey) - HALO;
-        const int c[3] = {x, y, z};
-        bool outside = false, fill_zero = false;
-        int w[3];
-        for (int a = 0; a < 3; ++a) {
-            w[a] = c[a];
-            if (c[a] < 0 || c[a] >= h.n[a]) {
-                outside = true;
-                if (h.periodic[a]) w[a] = ((c[a] % h.n[a]) + h.n[a]) % h.n[a];
-                else fill_zero = true;
-            }
-        }
-        S* dst = base + ((long long)(z + HALO) * h.py + (y + HALO)) * h.px + (x + HALO);
-        float v;
-        if (!outside) {
-            if (held_value(h, x, y, z, &v)) *dst = from_f32<S>(v);
-            continue;
-        }
-        if (fill_zero) {
-            const int f = ghost_face(h, c);
-            *dst = from_f32<S>(f >= 0 ? h.gam[f] : 0.0f);
-            continue;
-        }
-        if (held_value(h, w[0], w[1], w[2], &v)) {
-            *dst = from_f32<S>(v);
-        } else {
-            const S* src = base + ((long long)(w[2] + HALO) * h.py + (w[1] + HALO)) * h.px + (w[0] + HALO);
-            *dst = *src;
-        }
+        const int y = (int)(r - (long long)(z + HALO) * ey) - HALO;
+        const bool full = full_row(h, y, z);
+        const int count = full ? h.n[0] + 2 * HALO : 2 * HALO + 2;
+        for (int t = lane; t < count; t += 32) halo_cell<S>(base, h, row_x(h, full, t), y, z);
     }
 }
 
@@ -251,14 +275,13 @@ static HaloSpec halo_spec(const wfa_grid_s* g) {
 // other buffer's twins and held cells are rewritten by the next pass.)
 int refresh_halo(wfa_grid_s* g, int buf) {
     HaloSpec h = halo_spec(g);
-    const long long total = (long long)(g->n[0] + 2 * HALO) * (g->n[1] + 2 * HALO) * (g->n[2] + 2 * HALO);
+    const long long rows = (long long)(g->n[1] + 2 * HALO) * (g->n[2] + 2 * HALO);
     const int thr = 256;
     for (int b : {buf, 1 - buf}) {
         if (g->storage == WFA_BF16)
-            halo_kernel<__nv_bfloat16><<<grid_blocks(total, thr), thr, 0, g->stream>>>(
-                (__nv_bfloat16*)g->T[b], h, total);
+            halo_kernel<__nv_bfloat16><<<grid_blocks(rows * 32, thr), thr, 0, g->stream>>>((__nv_bfloat16*)g->T[b], h);
         else
-            halo_kernel<float><<<grid_blocks(total, thr), thr, 0, g->stream>>>((float*)g->T[b], h, total);
+            halo_kernel<float><<<grid_blocks(rows * 32, thr), thr, 0, g->stream>>>((float*)g->T[b], h);
         WFA_CUDA(cudaGetLastError());
     }
     return WFA_OK;
@@ -353,10 +376,12 @@ __device__ __forceinline__ double rate64(const float* __restrict__ korigin, cons
     return D;
 }
 
-// The same sum in fp32 with the harmonic mean as 2 / (1/a + 1/b): every
-// operation is correctly rounded and every term is >= 0, so for a cell whose
-// k values lie in [1e-15, 1e15] (or are 0) the result is within 18 units of
-// 2^-24, relative, of the fp64 one. A cell with other k values is `risky`.
+// The same sum in fp32: every operation is correctly rounded and every term
+// is >= 0, so for a cell whose k values lie in [1e-15, 1e15] (or are 0) no
+// product leaves the normal range and the result is within 18 units of
+// 2^-24, relative, of the fp64 one (3 roundings per harmonic mean, 2 per
+// product with 1/h^2 and its conversion, at most 12 additions). A cell with
+// other k values is `risky`.
 __device__ __forceinline__ float rate32(const float* __restrict__ korigin, const RateSpec& r, const int c[3],
                                         long long idx, bool* risky) {
     const long long st[3] = {1, r.px, r.px * r.py};
@@ -374,9 +399,8 @@ __device__ __forceinline__ float rate32(const float* __restrict__ korigin, const
             } else {
                 const float kD = korigin[idx + (side ? st[a] : -st[a])];
                 bad = bad || (kD != 0.0f && !(kD >= 1e-15f && kD <= 1e15f));
-                const float h = (kC > 0.0f && kD > 0.0f)
-                                    ? __fdiv_rn(2.0f, __fadd_rn(__fdiv_rn(1.0f, kC), __fdiv_rn(1.0f, kD)))
-                                    : 0.0f;
+                const float s2 = __fadd_rn(kC, kD);
+                const float h = s2 > 0.0f ? __fdiv_rn(__fmul_rn(__fmul_rn(2.0f, kC), kD), s2) : 0.0f;
                 D = __fadd_rn(D, __fmul_rn(h, r.inv_h2f[a]));
             }
             if (active) D = __fadd_rn(D, side ? r.upf[a] : r.umf[a]);
@@ -386,12 +410,23 @@ __device__ __forceinline__ float rate32(const float* __restrict__ korigin, const
     return D;
 }
 
-__device__ __forceinline__ void cell_of(const RateSpec& r, long long i, int c[3], long long* idx) {
-    c[0] = (int)(i % r.n[0]);
-    const long long q = i / r.n[0];
-    c[1] = (int)(q % r.n[1]);
-    c[2] = (int)(q / r.n[1]);
-    *idx = (long long)c[2] * r.px * r.py + (long long)c[1] * r.px + c[0];
+// Every domain cell once: warp w of the launch takes rows (y, z) w, w + W, ...
+// and its lanes the x of a row; f(c, idx) gets the cell and its padded offset.
+template <typename F>
+__device__ __forceinline__ void for_each_cell(const RateSpec& r, F f) {
+    const long long rows = (long long)r.n[1] * r.n[2];
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long row = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += warps) {
+        int c[3];
+        c[2] = (int)(row / r.n[1]);
+        c[1] = (int)(row - (long long)c[2] * r.n[1]);
+        const long long base = (long long)c[2] * r.px * r.py + (long long)c[1] * r.px;
+        for (int x = lane; x < r.n[0]; x += 32) {
+            c[0] = x;
+            f(c, base + x);
+        }
+    }
 }
 
 __device__ __forceinline__ void block_max_out(double best, double* __restrict__ out) {
@@ -409,15 +444,10 @@ __device__ __forceinline__ void block_max_out(double best, double* __restrict__ 
 __global__ void __launch_bounds__(RED_THREADS) rate_partial_kernel(const float* __restrict__ korigin,
                                                                    const __grid_constant__ RateSpec r,
                                                                    double* __restrict__ partials) {
-    const long long N = (long long)r.n[0] * r.n[1] * r.n[2];
     double best = 0.0;
-    for (long long i = blockIdx.x * (long long)RED_THREADS + threadIdx.x; i < N;
-         i += (long long)RED_BLOCKS * RED_THREADS) {
-        int c[3];
-        long long idx;
-        cell_of(r, i, c, &idx);
+    for_each_cell(r, [&](const int c[3], long long idx) {
         if (!rate_held(r, c)) best = fmax(best, rate64(korigin, r, c, idx));
-    }
+    });
     block_max_out(best, &partials[blockIdx.x]);
 }
 
@@ -426,18 +456,13 @@ __global__ void __launch_bounds__(RED_THREADS) rate_partial_kernel(const float* 
 __global__ void __launch_bounds__(RED_THREADS) rate32_partial_kernel(const float* __restrict__ korigin,
                                                                      const __grid_constant__ RateSpec r,
                                                                      double* __restrict__ partials) {
-    const long long N = (long long)r.n[0] * r.n[1] * r.n[2];
     float best = 0.0f;
-    for (long long i = blockIdx.x * (long long)RED_THREADS + threadIdx.x; i < N;
-         i += (long long)RED_BLOCKS * RED_THREADS) {
-        int c[3];
-        long long idx;
-        cell_of(r, i, c, &idx);
-        if (rate_held(r, c)) continue;
+    for_each_cell(r, [&](const int c[3], long long idx) {
+        if (rate_held(r, c)) return;
         bool risky;
         const float d = rate32(korigin, r, c, idx, &risky);
         if (!risky) best = fmaxf(best, d);
-    }
+    });
     block_max_out((double)best, &partials[blockIdx.x]);
 }
 
@@ -451,20 +476,15 @@ __global__ void __launch_bounds__(RED_THREADS) rate_cand_kernel(const float* __r
                                                                 const __grid_constant__ RateSpec r,
                                                                 const double* __restrict__ m32,
                                                                 double* __restrict__ partials) {
-    const long long N = (long long)r.n[0] * r.n[1] * r.n[2];
     const float m = (float)*m32;
     const float thr = __fsub_rn(m, __fmul_rn(m, 0x1p-12f));
     double best = 0.0;
-    for (long long i = blockIdx.x * (long long)RED_THREADS + threadIdx.x; i < N;
-         i += (long long)RED_BLOCKS * RED_THREADS) {
-        int c[3];
-        long long idx;
-        cell_of(r, i, c, &idx);
-        if (rate_held(r, c)) continue;
+    for_each_cell(r, [&](const int c[3], long long idx) {
+        if (rate_held(r, c)) return;
         bool risky;
         const float d = rate32(korigin, r, c, idx, &risky);
         if (risky || d >= thr) best = fmax(best, rate64(korigin, r, c, idx));
-    }
+    });
     block_max_out(best, &partials[blockIdx.x]);
 }
 
@@ -482,25 +502,44 @@ __global__ void __launch_bounds__(512) finish_max_kernel(const double* __restric
 
 // k halo: periodic twins (the harmonic mean across a wrap face reads them),
 // inf in the ghost layers of Dirichlet faces, 0 elsewhere (see build_coef).
-__global__ void k_halo_kernel(float* __restrict__ base, const __grid_constant__ HaloSpec h, long long total) {
-    const long long ex = h.n[0] + 2 * HALO, ey = h.n[1] + 2 * HALO;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int c[3] = {(int)(i % ex) - HALO, (int)((i / ex) % ey) - HALO, (int)(i / (ex * ey)) - HALO};
-        bool outside = false, zero = false;
-        int w[3];
-        for (int a = 0; a < 3; ++a) {
-            w[a] = c[a];
-            if (c[a] < 0 || c[a] >= h.n[a]) {
-                outside = true;
-                if (h.periodic[a]) w[a] = ((c[a] % h.n[a]) + h.n[a]) % h.n[a];
-                else zero = true;
+// One warp per row of the padded box; interior rows touch only the x halo.
+__global__ void k_halo_kernel(float* __restrict__ base, const __grid_constant__ HaloSpec h) {
+    const int ey = h.n[1] + 2 * HALO;
+    const long long rows = (long long)ey * (h.n[2] + 2 * HALO);
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long r = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
+        const int cz = (int)(r / ey) - HALO;
+        const int cy = (int)(r - (long long)(cz + HALO) * ey) - HALO;
+        const bool full = cy < 0 || cy >= h.n[1] || cz < 0 || cz >= h.n[2];
+        const int count = full ? h.n[0] + 2 * HALO : 2 * HALO;
+        for (int t = lane; t < count; t += 32) {
+            const int cx = full ? t - HALO : (t < HALO ? t - HALO : h.n[0] + (t - HALO));
+            const int c[3] = {cx, cy, cz};
+            bool outside = false, zero = false;
+            int w[3];
+            for (int a = 0; a < 3; ++a) {
+                w[a] = c[a];
+                if (c[a] < 0 || c[a] >= h.n[a]) {
+                    outside = true;
+                    if (h.periodic[a]) w[a] = ((c[a] % h.n[a]) + h.n[a]) % h.n[a];
+                    else zero = true;
+                }
             }
+            if (!outside) continue;
+            float* dst = base + ((long long)(c[2] + HALO) * h.py + (c[1] + HALO)) * h.px + (c[0] + HALO);
+            *dst = zero ? (ghost_face(h, c) >= 0 ? INFINITY : 0.0f)
+                        : base[((long long)(w[2] + HALO) * h.py + (w[1] + HALO)) * h.px + (w[0] + HALO)];
         }
-        if (!outside) continue;
-        float* dst = base + ((long long)(c[2] + HALO) * h.py + (c[1] + HALO)) * h.px + (c[0] + HALO);
-        *dst = zero ? (ghost_face(h, c) >= 0 ? INFINITY : 0.0f)
-                    : base[((long long)(w[2] + HALO) * h.py + (w[1] + HALO)) * h.px + (w[0] + HALO)];
+    }
+}
+
+// Smallest index of a negative or non-finite k (bad stays at its initial
+// value when every k is valid).
+__global__ void check_k_kernel(const float* __restrict__ k, long long n, unsigned long long* bad) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float v = k[i];
+        if (!(v >= 0.0f && v <= 3.402823466e38f)) atomicMin(bad, (unsigned long long)i);
     }
 }
 
@@ -641,24 +680,30 @@ int wfa_set_coeffs(wfa_grid g, const float* k_host, double k_uniform, double ux,
         return fail(WFA_ERR_ARG, "k_uniform must be finite and >= 0");
     const long long N = (long long)g->n[0] * g->n[1] * g->n[2];
     if (k_host) {
-        for (long long i = 0; i < N; ++i)
-            if (!(k_host[i] >= 0.0f) || !std::isfinite(k_host[i]))
-                return fail(WFA_ERR_ARG, "k[%lld] = %g is negative or not finite", i, (double)k_host[i]);
+        int rc = ensure_stage(g);
+        if (rc) return rc;
+        WFA_CUDA(cudaMemcpyAsync(g->d_stage, k_host, N * sizeof(float), cudaMemcpyHostToDevice, g->stream));
+        // validate on the device before anything of the grid changes
+        unsigned long long* bad = reinterpret_cast<unsigned long long*>(g->d_partials + 4095);
+        WFA_CUDA(cudaMemsetAsync(bad, 0xFF, sizeof(unsigned long long), g->stream));
+        check_k_kernel<<<grid_blocks(N, 256), 256, 0, g->stream>>>(g->d_stage, N, bad);
+        WFA_CUDA(cudaGetLastError());
+        WFA_CUDA(cudaMemcpyAsync(g->h_result, bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, g->stream));
+        WFA_CUDA(cudaStreamSynchronize(g->stream));
+        unsigned long long first;
+        memcpy(&first, g->h_result, sizeof first);
+        if (first != ~0ull)
+            return fail(WFA_ERR_ARG, "k[%llu] = %g is negative or not finite", first, (double)k_host[first]);
         if (!g->k) {
             WFA_CUDA(cudaMalloc(&g->k, field_elems(g) * sizeof(float)));
             WFA_CUDA(cudaMemsetAsync(g->k, 0, field_elems(g) * sizeof(float), g->stream));
             WFA_CUDA(cudaMalloc(&g->r, field_elems(g) * sizeof(float)));
         }
-        int rc = ensure_stage(g);
-        if (rc) return rc;
-        WFA_CUDA(cudaMemcpyAsync(g->d_stage, k_host, N * sizeof(float), cudaMemcpyHostToDevice, g->stream));
         const int thr = 256;
         pack_kernel<float><<<grid_blocks(N, thr), thr, 0, g->stream>>>(g->d_stage, g->k + domain_offset(g),
                                                                          geo_of(g));
         WFA_CUDA(cudaGetLastError());
-        int rc2 = prepare_k_halo(g);
-        if (rc2) return rc2;
-        WFA_CUDA(cudaStreamSynchronize(g->stream));
+        g->k_halo_dirty = true;   // twins, ghost layers and 1/k follow before the next use
         g->k_uniform = 0.0;
     } else {
         if (g->k) {
@@ -689,6 +734,7 @@ int wfa_set_bc(wfa_grid g, int face, int kind, double value) {
     g->bc_kind[face] = kind;
     g->bc_value[face] = value;
     g->halo_dirty = true;
+    g->k_halo_dirty = true;
     g->dt_set = false;
     g->limit_valid = false;
     return WFA_OK;
@@ -774,13 +820,15 @@ static double uniform_rate_max(const RateSpec& r) {
 // k halo (periodic twins), then r = 1/k over the whole padded buffer.
 static int prepare_k_halo(wfa_grid g) {
     if (!g->k) return WFA_OK;
+    if (!g->k_halo_dirty) return WFA_OK;
     HaloSpec h = halo_spec(g);
-    const long long total = (long long)(g->n[0] + 2 * HALO) * (g->n[1] + 2 * HALO) * (g->n[2] + 2 * HALO);
-    k_halo_kernel<<<grid_blocks(total, 256), 256, 0, g->stream>>>(g->k, h, total);
+    const long long rows = (long long)(g->n[1] + 2 * HALO) * (g->n[2] + 2 * HALO);
+    k_halo_kernel<<<grid_blocks(rows * 32, 256), 256, 0, g->stream>>>(g->k, h);
     WFA_CUDA(cudaGetLastError());
     const long long all = (long long)field_elems(g);
     recip_kernel<<<grid_blocks(all, 256), 256, 0, g->stream>>>(g->k, g->r, all);
     WFA_CUDA(cudaGetLastError());
+    g->k_halo_dirty = false;
     return WFA_OK;
 }
 

@@ -102,6 +102,7 @@ struct wfa_grid_s {
     double limit;         // stability limit dt_max of the current coefficients and faces
     bool limit_valid;
     bool field_set, coeffs_set, dt_set, halo_dirty;
+    bool k_halo_dirty;    // k twins / ghost layers and 1/k must be rebuilt before use
     long long steps_done;
     int force_depth, force_variant;   // wfa_set_tuning (0 = automatic)
     double* d_partials;   // fp64 reduction partials (scratch)

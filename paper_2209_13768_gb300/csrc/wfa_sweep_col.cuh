@@ -306,9 +306,14 @@ cudaError_t col_launch(const SweepArgs& a_in, cudaStream_t st, int nsm, const cu
     dim3 block(16, 16);
     const int gxb = (a.c.n[0] + 63) / 64, gyb = (a.c.n[1] + 15) / 16;
     // z chunks of about 16 planes: many short columns stream the grid at once
-    long long want = (long long)nsm * ColOcc<KVAR>::blocks * 16;
-    int nch = (int)std::max<long long>(1, want / std::max(1, gxb * gyb));
-    nch = std::min(nch, std::max(1, a.c.n[2] / 16));
+    const long long cols = (long long)gxb * gyb, resident = (long long)nsm * ColOcc<KVAR>::blocks;
+    long long want = resident * 16;
+    int nch = (int)std::max<long long>(1, want / cols);
+    // chunks of at least 16 planes, unless that leaves SMs idle (small grids,
+    // which sit in L2 anyway): then down to 2 planes
+    int cap = std::max(1, a.c.n[2] / 16);
+    if (cols * cap < resident) cap = std::max(1, a.c.n[2] / 2);
+    nch = std::min(nch, cap);
     a.zchunk = (a.c.n[2] + nch - 1) / nch;
     nch = (a.c.n[2] + a.zchunk - 1) / a.zchunk;
     dim3 grid(gxb, gyb, nch);
