@@ -211,7 +211,9 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
             }
         }
         const bool plain = plain_xy && !(perz && (z < HALO || z >= c.n[2] - HALO));
-        if (FIX && gx + 3 >= c.n[0]) {   // partial vector at the x end: the halo keeps its ghost values
+        // partial vector at the x end with per-cell k: the halo keeps its ghost
+        // values (uniform k never reads them, and the unmasked store is faster)
+        if (FIX && KVAR && gx + 3 >= c.n[0]) {
 #pragma unroll
             for (int i = 0; i < 4; ++i)
                 if (gx + i < c.n[0]) tout[(long long)z * sz + col + i] = from_f32<S>(out[i]);
