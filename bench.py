@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-solo", action="store_true", help="batch: skip the one-grid-per-launch comparison")
     return ap.parse_args()
 
 
@@ -291,12 +292,14 @@ def batch_bench(args):
         wfa.batch_run(grids, steps)
         times.append(time.perf_counter() - t0)
     t_batch = sum(times[args.warmup:]) / args.steps
-    t0 = time.perf_counter()
-    for g, n in zip(grids, steps):
-        g.step(n)
-    for g in grids:
-        g.sync()
-    t_solo = time.perf_counter() - t0
+    t_solo = float("nan")
+    if not args.no_solo:
+        t0 = time.perf_counter()
+        for g, n in zip(grids, steps):
+            g.step(n)
+        for g in grids:
+            g.sync()
+        t_solo = time.perf_counter() - t0
     for g in grids:
         g.close()
     line = {"metric": METRIC, "value": updates / t_batch / 1e9, "unit": "GLUPS", "n_gpus": 1, "steps": args.steps,
@@ -304,7 +307,8 @@ def batch_bench(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "256 grids, edges log-uniform [16,128], k lognormal(0,0.5), steps U{50..500}",
                        "cell_updates_per_step": updates},
-            "one_grid_per_launch": {"value": updates / t_solo / 1e9, "unit": "GLUPS", "ms_per_step": 1e3 * t_solo}}
+            "one_grid_per_launch": None if args.no_solo else
+            {"value": updates / t_solo / 1e9, "unit": "GLUPS", "ms_per_step": 1e3 * t_solo}}
     print(json.dumps(line), flush=True)
 
 

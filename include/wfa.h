@@ -189,14 +189,19 @@ const char* wfa_last_error(void);
 /* Advance many grids in one go (Sec. 4.1.2: iteration rate at small
  * workloads per processor). gs[i] advances steps[i] >= 0 steps; grids may mix
  * storage types and conductivity modes. All grids must share the stream of
- * gs[0], appear once, and have their field, coefficients and dt set. Step s
- * of every grid with more than s steps runs in one multi-grid launch per
- * class of grids (storage type, conductivity mode, advection, boundary
- * faces in ghost layers or not); nothing inside a launch waits on another
- * block. Results are bitwise identical to calling wfa_step on each grid.
- * Returns after the work is done (synchronises the stream).
+ * gs[0], appear once, and have their field, coefficients and dt set. Round
+ * r advances every grid with more than r steps by one step, one multi-grid
+ * launch per class of grid; all rounds are captured into one CUDA graph and
+ * launched once. The environment variable WFA_BATCH_MODE selects
+ * "persistent" (all rounds in one persistent kernel whose blocks meet at a
+ * grid-wide barrier with a bounded spin) or "stream" (the per-round launches
+ * without a graph). Results are bitwise identical to calling wfa_step on
+ * each grid, in every mode. Returns after the work is done (synchronises the
+ * stream).
  * Errors: WFA_ERR_ARG (NULL or repeated grid, negative steps, different
- * streams), WFA_ERR_STATE (a grid not ready to step), WFA_ERR_CUDA. */
+ * streams, more steps than the barrier counter holds), WFA_ERR_STATE (a grid
+ * not ready to step), WFA_ERR_TIMEOUT (a device-side wait gave up; the fields
+ * of the grids are then undefined), WFA_ERR_CUDA. */
 int wfa_batch_run(wfa_grid* gs, const long long* steps, int count);
 
 /* ------------------------------------------------------------- serving -- */

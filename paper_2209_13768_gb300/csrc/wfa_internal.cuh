@@ -30,6 +30,7 @@ constexpr int HALO = 8;       // halo width on every side (>= the deepest tempor
 constexpr int MAX_DEPTH = 8;  // steps fused per pass over the grid
 constexpr int NUM_TILE_VARIANTS = 2;  // tile shapes compiled per (storage, k mode, depth)
 constexpr int COL_VARIANT = 3;        // the one-step column-march kernel
+constexpr int FUSED_VARIANT = 4;      // the two-step column-march kernel (uniform k)
 
 // ---------------------------------------------------------------- errors --
 void set_error(const char* fmt, ...);

@@ -151,8 +151,9 @@ static int num_sms() {
 
 // ------------------------------------------------------------ tuning ------
 // Kernel configuration of a pass: variant (COL_VARIANT = column march, one
-// step; 1..NUM_TILE_VARIANTS = tiled TMA kernel, `depth` fused steps; -1 = the
-// plain one-column kernel) and depth.
+// step; FUSED_VARIANT = column march, two steps, uniform k; 1..NUM_TILE_VARIANTS
+// = tiled TMA kernel, `depth` fused steps; -1 = the plain one-column kernel)
+// and depth.
 struct Choice {
     int variant, depth;
 };
@@ -215,6 +216,7 @@ static Choice choose(const wfa_grid_s* g) {
         ch = Choice{v, d};
     }
     if (ch.variant < 0 || ch.variant == COL_VARIANT) ch.depth = 1;
+    if (ch.variant == FUSED_VARIANT) ch.depth = g->k ? 1 : 2;   // per-cell k: the one-step column kernel
     return ch;
 }
 
@@ -274,7 +276,14 @@ static int one_pass(wfa_grid_s* g, const SweepCoef& c, int depth, int variant) {
         g->cur = 1 - g->cur;
         return WFA_OK;
     }
-    if (variant == COL_VARIANT) {   // column-march kernel, one step
+    if (variant == FUSED_VARIANT && depth == 2 && !g->r) {   // two-step column march (uniform k)
+        cudaError_t e = g->storage == WFA_BF16 ? launch_col2_bf16_u(a, g->stream, num_sms(), ev)
+                                               : launch_col2_f32_u(a, g->stream, num_sms(), ev);
+        if (e != cudaSuccess) return cuda_fail(e, "sweep_col2 launch");
+        g->cur = 1 - g->cur;
+        return WFA_OK;
+    }
+    if (variant == COL_VARIANT || variant == FUSED_VARIANT) {   // column-march kernel, one step
         cudaError_t e;
         if (g->storage == WFA_BF16)
             e = g->r ? launch_col_bf16_k(a, g->stream, num_sms(), ev) : launch_col_bf16_u(a, g->stream, num_sms(), ev);
@@ -335,8 +344,8 @@ int autotune(wfa_grid_s* g, int* depth_out, int* variant_out) {
         ~Pause() { g->timing_every = every; }
     } pause{g, g->timing_every};
     g->timing_every = 0;
-    static const Choice cands[] = {{COL_VARIANT, 1}, {1, 1}, {2, 1}, {1, 2}, {2, 2}, {1, 3}, {2, 3},
-                                   {1, 4}, {2, 4}, {1, 6}, {1, 8}};
+    static const Choice cands[] = {{COL_VARIANT, 1}, {FUSED_VARIANT, 2}, {1, 1}, {2, 1}, {1, 2}, {2, 2},
+                                   {1, 3}, {2, 3}, {1, 4}, {2, 4}, {1, 6}, {1, 8}};
     const size_t bytes = field_elems(g) * g->esize;
     void* save = nullptr;
     WFA_CUDA(cudaMalloc(&save, bytes));
@@ -351,6 +360,7 @@ int autotune(wfa_grid_s* g, int* depth_out, int* variant_out) {
     float best_ms = 1e30f;
     for (const Choice& ch : cands) {
         if (e != cudaSuccess) break;
+        if (ch.variant == FUSED_VARIANT && g->k) continue;   // uniform k only
         // one warm-up pass, then the timed passes
         rc = one_pass(g, c, ch.depth, ch.variant);
         if (rc) break;

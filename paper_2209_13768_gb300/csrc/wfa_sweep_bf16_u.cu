@@ -1,5 +1,6 @@
 // Compiled sweep kernels: bf16 storage, uniform conductivity, depths 1..8.
 #include "wfa_sweep_col.cuh"
+#include "wfa_sweep_fused.cuh"
 #include "wfa_sweep_impl.cuh"
 
 namespace wfa {
@@ -58,6 +59,10 @@ cudaError_t launch_simple_bf16_u(const SweepArgs& a, cudaStream_t st) {
 
 cudaError_t launch_col_bf16_u(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev) {
     return col_launch<S, KVAR>(a, st, nsm, ev);
+}
+
+cudaError_t launch_col2_bf16_u(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev) {
+    return col2_launch<S>(a, st, nsm, ev);
 }
 
 }  // namespace wfa

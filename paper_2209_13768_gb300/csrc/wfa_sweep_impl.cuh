@@ -36,6 +36,9 @@ cudaError_t launch_col_f32_u(const SweepArgs& a, cudaStream_t st, int nsm, const
 cudaError_t launch_col_f32_k(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev);
 cudaError_t launch_col_bf16_u(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev);
 cudaError_t launch_col_bf16_k(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev);
+// two-step column-march kernel (variant 4, uniform k only)
+cudaError_t launch_col2_f32_u(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev);
+cudaError_t launch_col2_bf16_u(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev);
 
 template <typename S, bool KVAR, int D, int EX, int EY, int R, int PF>
 cudaError_t tb_launch(const CUtensorMap* tmT, const CUtensorMap* tmK, const SweepArgs& a, int blocks,

@@ -2,6 +2,7 @@
 
 Both run the same per-cell arithmetic as wfa_step, so every result must be
 bit-identical to the grid advanced alone."""
+import os
 import time
 
 import numpy as np
@@ -90,6 +91,51 @@ def test_batch_sizes_steps_and_classes():
     finally:
         for g in grids:
             g.close()
+
+
+def test_batch_modes_agree_bitwise():
+    # the persistent kernel, per-round launches in a graph, and on the stream: the same fields
+    rng = np.random.default_rng(23)
+    probs = [_problem(i, rng) for i in range(12)]
+    outs = []
+    for mode in ("persistent", "rounds", "stream"):
+        os.environ["WFA_BATCH_MODE"] = mode
+        try:
+            grids = [make_grid(p) for p in probs]
+            wfa.batch_run(grids, [p.steps for p in probs])
+            outs.append([g.read_field() for g in grids])
+            for g in grids:
+                g.close()
+        finally:
+            os.environ.pop("WFA_BATCH_MODE", None)
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            np.testing.assert_array_equal(a, b)
+
+
+def test_batch_wait_times_out_cleanly():
+    # a barrier target that no arrival satisfies (host-side test hook): the
+    # bounded device wait gives up, the call reports it, the context lives on
+    p = _problem(0, np.random.default_rng(3))
+    p.steps = 4
+    g = make_grid(p)
+    try:
+        os.environ["WFA_TEST_BATCH_STALL"] = "1"
+        os.environ["WFA_BATCH_MODE"] = "persistent"   # the mode with a device-side wait
+        t0 = time.time()
+        with pytest.raises(wfa.WfaError) as e:
+            wfa.batch_run([g], [4])
+        assert e.value.code == -6
+        assert time.time() - t0 < 30
+    finally:
+        os.environ.pop("WFA_TEST_BATCH_STALL", None)
+        os.environ.pop("WFA_BATCH_MODE", None)
+        g.close()
+    q = _problem(1, np.random.default_rng(4))
+    q.steps = 5
+    with make_grid(q) as g2:
+        wfa.batch_run([g2], [5])
+        np.testing.assert_array_equal(g2.read_field(), run_gpu(q, variant=-1))
 
 
 def test_server_results_equal_alone_and_in_a_mix():

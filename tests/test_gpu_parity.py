@@ -88,9 +88,13 @@ def test_boundary_mixes_all_kernels(mix, kvar, adv):
             T = run_gpu(p, depth=depth, variant=variant)
             np.testing.assert_array_equal(T, base, err_msg=f"variant {variant} depth {depth}")
     np.testing.assert_array_equal(run_gpu(p, variant=3), base, err_msg="column kernel")
+    # two-step column kernel (uniform k; per-cell k falls back to one step)
+    np.testing.assert_array_equal(run_gpu(p, depth=2, variant=4), base, err_msg="two-step column kernel")
+    np.testing.assert_array_equal(run_gpu(p, steps=p.steps - 1, depth=2, variant=4),
+                                  run_gpu(p, steps=p.steps - 1, variant=-1), err_msg="two-step, odd count")
 
 
-@pytest.mark.parametrize("shape", [(2, 2, 2), (3, 2, 5), (5, 7, 3), (64, 3, 9), (131, 67, 4)])
+@pytest.mark.parametrize("shape", [(2, 2, 2), (3, 2, 5), (5, 7, 3), (64, 3, 9), (131, 67, 4), (70, 35, 40)])
 def test_small_and_ragged_shapes(shape):
     for mix in (0, 2, 4):
         if any(k == DC for k, _ in MIXES[mix]) and min(shape) < 3:
@@ -103,6 +107,9 @@ def test_small_and_ragged_shapes(shape):
         for depth in (1, 3, 8):
             np.testing.assert_array_equal(run_gpu(p, depth=depth, variant=1), base)
         np.testing.assert_array_equal(run_gpu(p, variant=3), base)
+        pu = _mixed_problem(mix, shape=shape, kvar=False, seed=7)
+        pu.steps = 9
+        np.testing.assert_array_equal(run_gpu(pu, depth=2, variant=4), run_gpu(pu, variant=-1), err_msg=str(shape))
 
 
 
@@ -171,6 +178,10 @@ def test_bf16_storage(mix):
         for variant in (1, 2):
             np.testing.assert_array_equal(run_gpu(p, storage=wfa.BF16, depth=depth, variant=variant), base)
     np.testing.assert_array_equal(run_gpu(p, storage=wfa.BF16, variant=3), base)
+    pu = _mixed_problem(mix, kvar=False, seed=3)
+    pu.steps = 30
+    np.testing.assert_array_equal(run_gpu(pu, storage=wfa.BF16, depth=2, variant=4),
+                                  run_gpu(pu, storage=wfa.BF16, variant=-1))
 
 
 # ------------------------------------------------------ reductions (fp64) --
@@ -297,6 +308,7 @@ def test_advection_diffusion_reduced(storage):
     T = run_gpu(p, storage=storage)
     err = rel_linf(T, ref)
     assert err <= (F32_TOL if storage == wfa.F32 else bf16_bound(p.steps)), err
+    np.testing.assert_array_equal(run_gpu(p, storage=storage, depth=2, variant=4), run_gpu(p, storage=storage, variant=3))
 
 
 def test_autotune_keeps_state_and_results():
