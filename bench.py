@@ -358,10 +358,6 @@ def main():
     else:   # autotune: time the compiled configurations on this grid, keep the fastest
         depth, variant = g.autotune()
     passes_per_step = math.ceil(p.steps / depth)
-    # kernels per pass: the column-march pass adds a boundary fix-up kernel
-    # (when some axis is not periodic) and one twin copy per periodic axis
-    periodic = [p.bc[2 * a][0] == "periodic" for a in range(3)]
-    kernels_per_pass = 1 + (not all(periodic)) + sum(periodic) if variant == 3 else 1
 
     for _ in range(args.warmup):
         g.step(p.steps)
@@ -370,8 +366,11 @@ def main():
     sampler = ClockSampler(local)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     # the dominant kernel's own launches are bracketed by events inside the
-    # library, on the grid's stream; sample at most about 4000 of them
-    g.set_kernel_timing(max(1, math.ceil(args.steps * passes_per_step / 4000)))
+    # library, on the grid's stream: every 16th pass (two event records per
+    # sampled pass are noise next to a pass, even a 64^3 one), at most about
+    # 4000 samples
+    g.set_kernel_timing(max(16, math.ceil(args.steps * passes_per_step / 4000)))
+    launches0 = g.launch_count()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -384,6 +383,7 @@ def main():
     torch.cuda.synchronize()
     clocks = sampler.stop()
     kernel_ms, kernel_launches = g.kernel_time()
+    gpu_launches = g.launch_count() - launches0   # every kernel of the timed steps
     g.set_kernel_timing(0)
     if dist:
         dist.barrier()
@@ -460,13 +460,14 @@ def main():
                 "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": p.name, "cells": cells, "time_steps_per_step": p.steps, "depth": depth,
-                           "kernel": {3: "sweep_col", -1: "sweep_simple"}.get(variant, f"sweep_tb variant {variant}"),
+                           "kernel": {3: "sweep_col", 4: "sweep_col2 (two steps per pass)", 5: "sweep_col (boundaries in place)",
+                                      -1: "sweep_simple"}.get(variant, f"sweep_tb variant {variant}"),
                            "dt": dt, "storage": "bf16" if storage else "f32",
                            "conductivity": "per-cell lognormal(0,0.5)" if kvar else f"uniform {p.k}",
                            "l2": "inputs larger than L2 (%.0f MiB field)" % (cells * (2 if storage else 4) / 2**20),
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serving": serving,
-                "gpu_launches": args.steps * passes_per_step * kernels_per_pass, "clocks": clocks}
+                "gpu_launches": gpu_launches, "clocks": clocks}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

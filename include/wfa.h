@@ -110,15 +110,20 @@ int wfa_set_dt(wfa_grid g, double dt);
  * depth: time steps fused per pass over the grid (1..8; 0 = automatic).
  * variant: 0 = automatic; 1..2 = one of the compiled tile shapes of the
  * tiled TMA kernel (depth steps per pass); 3 = the column-march kernel (one
- * step per pass, register queue along z, no shared memory); -1 = the plain
- * one-thread-per-column kernel (one step per pass; a second, independent
- * realisation of the same per-cell arithmetic).
+ * step per pass, register queue along z, no shared memory; boundary cells by
+ * ghost layers or a short fix-up launch); 4 = the two-step column-march
+ * kernel (uniform k; two steps per pass, shared-memory stage plane; with
+ * per-cell k it acts as 3); 5 = the column-march kernel with boundary cells
+ * and periodic copies inside the pass (one launch per step; for small
+ * grids); -1 = the plain one-thread-per-column kernel (one step per pass; a
+ * second, independent realisation of the same per-cell arithmetic).
  * Results do not depend on the choice: every kernel evaluates the same fixed
  * per-cell expression, so fields are bit-identical. */
 int wfa_set_tuning(wfa_grid g, int depth, int variant);
 
-/* Time the compiled kernel configurations (column march; tiled TMA kernel at
- * depths 1..8 and two tile shapes) on this grid and use the fastest from now
+/* Time the compiled kernel configurations (the column-march kernels 3, 4, 5;
+ * the tiled TMA kernel at depths 1..8 and two tile shapes) on this grid and
+ * use the fastest from now
  * on. The trials run on a scratch copy of the field: the field and the step
  * count are left as they were, and results never depend on the choice. The
  * choice is also remembered for later grids of the same size class (storage,
@@ -175,6 +180,11 @@ int wfa_sync(wfa_grid g);
  * held; later passes go unsampled until wfa_kernel_time reads them.
  * Errors: WFA_ERR_ARG for a NULL grid or every < 0. */
 int wfa_set_kernel_timing(wfa_grid g, int every);
+
+/* Number of kernels the sweeps of this grid have launched (wfa_step,
+ * autotuning trials included), a profiling aid with no counterpart in the
+ * paper. */
+int wfa_launch_count(wfa_grid g, long long* n);
 
 /* Synchronise the stream, then give the summed duration in milliseconds and
  * the number of the sampled kernel launches since the last call (0 and 0 when

@@ -67,6 +67,7 @@ SIGNATURES = {
     "wfa_sync": (_i, [_vp]),
     "wfa_set_kernel_timing": (_i, [_vp, _i]),
     "wfa_kernel_time": (_i, [_vp, _dp, _llp]),
+    "wfa_launch_count": (_i, [_vp, _llp]),
     "wfa_sum_f32_noalloc": (_i, [_vp, _ll, _d, _vp, _vp]),
     "wfa_last_error": (ctypes.c_char_p, []),
     "wfa_batch_run": (_i, [ctypes.POINTER(_vp), _llp, _i]),
@@ -220,6 +221,12 @@ class Grid:
     def set_kernel_timing(self, every):
         """Time the main sweep kernel of every every-th pass with CUDA events (0: off)."""
         check(lib().wfa_set_kernel_timing(self.handle, int(every)), "wfa_set_kernel_timing")
+
+    def launch_count(self):
+        """Kernels the sweeps of this grid have launched so far."""
+        n = ctypes.c_longlong()
+        check(lib().wfa_launch_count(self.handle, ctypes.byref(n)), "wfa_launch_count")
+        return n.value
 
     def kernel_time(self):
         """(summed milliseconds, launches) of the sampled kernels since the last call."""

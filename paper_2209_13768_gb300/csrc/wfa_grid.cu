@@ -886,7 +886,7 @@ int wfa_set_dt(wfa_grid g, double dt) {
 int wfa_set_tuning(wfa_grid g, int depth, int variant) {
     if (!g) return fail(WFA_ERR_ARG, "NULL grid");
     if (depth < 0 || depth > MAX_DEPTH) return fail(WFA_ERR_ARG, "depth must be 0..%d", MAX_DEPTH);
-    if (variant < -1 || variant > FUSED_VARIANT) return fail(WFA_ERR_ARG, "variant must be -1..%d", FUSED_VARIANT);
+    if (variant < -1 || variant > INPLACE_VARIANT) return fail(WFA_ERR_ARG, "variant must be -1..%d", INPLACE_VARIANT);
     g->force_depth = depth;
     g->force_variant = variant;
     return WFA_OK;

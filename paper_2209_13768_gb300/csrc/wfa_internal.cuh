@@ -31,6 +31,7 @@ constexpr int MAX_DEPTH = 8;  // steps fused per pass over the grid
 constexpr int NUM_TILE_VARIANTS = 2;  // tile shapes compiled per (storage, k mode, depth)
 constexpr int COL_VARIANT = 3;        // the one-step column-march kernel
 constexpr int FUSED_VARIANT = 4;      // the two-step column-march kernel (uniform k)
+constexpr int INPLACE_VARIANT = 5;    // the one-step column-march kernel, boundaries in place
 
 // ---------------------------------------------------------------- errors --
 void set_error(const char* fmt, ...);
@@ -113,6 +114,7 @@ struct wfa_grid_s {
     int* h_status;        // pinned host copy
     void* tmaps;          // wfa::TmapCache (TMA descriptors for the current tile box)
     int tuned_depth, tuned_variant;   // configuration picked by the autotuner (0 = none)
+    long long launches;   // kernels launched by the sweeps so far (wfa_launch_count)
     int timing_every;     // wfa_set_kernel_timing: sample every n-th pass (0 = off)
     long long timing_pass;
     void* timing;         // wfa::KernelTiming (recorded event pairs)

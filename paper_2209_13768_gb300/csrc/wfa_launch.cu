@@ -151,7 +151,8 @@ static int num_sms() {
 
 // ------------------------------------------------------------ tuning ------
 // Kernel configuration of a pass: variant (COL_VARIANT = column march, one
-// step; FUSED_VARIANT = column march, two steps, uniform k; 1..NUM_TILE_VARIANTS
+// step; INPLACE_VARIANT = the same with boundaries and periodic copies in the
+// pass itself; FUSED_VARIANT = column march, two steps, uniform k; 1..NUM_TILE_VARIANTS
 // = tiled TMA kernel, `depth` fused steps; -1 = the plain one-column kernel)
 // and depth.
 struct Choice {
@@ -215,7 +216,7 @@ static Choice choose(const wfa_grid_s* g) {
         int d = g->force_depth ? g->force_depth : (v == COL_VARIANT || v < 0 ? 1 : 2);
         ch = Choice{v, d};
     }
-    if (ch.variant < 0 || ch.variant == COL_VARIANT) ch.depth = 1;
+    if (ch.variant < 0 || ch.variant == COL_VARIANT || ch.variant == INPLACE_VARIANT) ch.depth = 1;
     if (ch.variant == FUSED_VARIANT) ch.depth = g->k ? 1 : 2;   // per-cell k: the one-step column kernel
     return ch;
 }
@@ -260,8 +261,19 @@ static SweepArgs base_args(wfa_grid_s* g, const SweepCoef& c, int in_buf) {
     return a;
 }
 
+// Kernels one pass launches (the column kernels add a boundary fix-up and a
+// copy per periodic axis, see col_launch / col2_launch).
+static int pass_launches(const wfa_grid_s* g, const SweepCoef& c, int depth, int variant) {
+    const int periodic = c.periodic[0] + c.periodic[1] + c.periodic[2];
+    if (variant == FUSED_VARIANT && depth == 2 && !g->r) return 1 + periodic;
+    if (variant == COL_VARIANT || variant == FUSED_VARIANT)
+        return 1 + (periodic < 3 && !c.halo_bc ? 1 : 0) + periodic;
+    return 1;
+}
+
 // One pass of `depth` fused steps from buffer g->cur into the other buffer.
 static int one_pass(wfa_grid_s* g, const SweepCoef& c, int depth, int variant) {
+    g->launches += pass_launches(g, c, depth, variant);
     SweepArgs a = base_args(g, c, g->cur);
     const cudaEvent_t* ev = timing_slot(g);
     if (variant < 0) {   // one-column reference kernel, one step
@@ -283,12 +295,15 @@ static int one_pass(wfa_grid_s* g, const SweepCoef& c, int depth, int variant) {
         g->cur = 1 - g->cur;
         return WFA_OK;
     }
-    if (variant == COL_VARIANT || variant == FUSED_VARIANT) {   // column-march kernel, one step
+    if (variant == COL_VARIANT || variant == FUSED_VARIANT || variant == INPLACE_VARIANT) {   // column march, one step
+        const bool inl = variant == INPLACE_VARIANT;
         cudaError_t e;
         if (g->storage == WFA_BF16)
-            e = g->r ? launch_col_bf16_k(a, g->stream, num_sms(), ev) : launch_col_bf16_u(a, g->stream, num_sms(), ev);
+            e = g->r ? launch_col_bf16_k(a, g->stream, num_sms(), ev, inl)
+                     : launch_col_bf16_u(a, g->stream, num_sms(), ev, inl);
         else
-            e = g->r ? launch_col_f32_k(a, g->stream, num_sms(), ev) : launch_col_f32_u(a, g->stream, num_sms(), ev);
+            e = g->r ? launch_col_f32_k(a, g->stream, num_sms(), ev, inl)
+                     : launch_col_f32_u(a, g->stream, num_sms(), ev, inl);
         if (e != cudaSuccess) return cuda_fail(e, "sweep_col launch");
         g->cur = 1 - g->cur;
         return WFA_OK;
@@ -344,8 +359,8 @@ int autotune(wfa_grid_s* g, int* depth_out, int* variant_out) {
         ~Pause() { g->timing_every = every; }
     } pause{g, g->timing_every};
     g->timing_every = 0;
-    static const Choice cands[] = {{COL_VARIANT, 1}, {FUSED_VARIANT, 2}, {1, 1}, {2, 1}, {1, 2}, {2, 2},
-                                   {1, 3}, {2, 3}, {1, 4}, {2, 4}, {1, 6}, {1, 8}};
+    static const Choice cands[] = {{COL_VARIANT, 1}, {INPLACE_VARIANT, 1}, {FUSED_VARIANT, 2}, {1, 1}, {2, 1},
+                                   {1, 2}, {2, 2}, {1, 3}, {2, 3}, {1, 4}, {2, 4}, {1, 6}, {1, 8}};
     const size_t bytes = field_elems(g) * g->esize;
     void* save = nullptr;
     WFA_CUDA(cudaMalloc(&save, bytes));
@@ -442,3 +457,12 @@ int wfa_kernel_time(wfa_grid g, double* ms, long long* launches) {
 }
 
 }  // extern "C"
+
+extern "C" int wfa_launch_count(wfa_grid g, long long* n) {
+    if (!g || !n) {
+        wfa::set_error("NULL argument");
+        return WFA_ERR_ARG;
+    }
+    *n = g->launches;
+    return WFA_OK;
+}

@@ -70,6 +70,48 @@ __device__ __forceinline__ float ldg1<__nv_bfloat16, false>(const __nv_bfloat16*
     return __bfloat162float(*p);
 }
 
+// One cell with uniform k: boundary faces, held layers and the zero-flux self
+// term chosen by select, in the order and form of boundary_update, so the
+// value is bitwise that of every other kernel (an interior cell reduces to
+// the interior expression: w_in weights, neighbour values, no self term).
+__device__ __forceinline__ float uniform_cell(const SweepCoef& c, float tc, float txm, float txp, float tym,
+                                              float typ, float tzm, float tzp, int x, int y, int z) {
+    const bool e0 = !c.periodic[0] && x == 0, e1 = !c.periodic[0] && x == c.n[0] - 1;
+    const bool e2 = !c.periodic[1] && y == 0, e3 = !c.periodic[1] && y == c.n[1] - 1;
+    const bool e4 = !c.periodic[2] && z == 0, e5 = !c.periodic[2] && z == c.n[2] - 1;
+    auto tface = [&](int f) { return c.bkind[f] == WFA_BC_DIRICHLET ? c.tb[f] : 0.0f; };
+    const float t0 = e0 ? tface(0) : txm, t1 = e1 ? tface(1) : txp;
+    const float t2 = e2 ? tface(2) : tym, t3 = e3 ? tface(3) : typ;
+    const float t4 = e4 ? tface(4) : tzm, t5 = e5 ? tface(5) : tzp;
+    const float w0 = e0 ? c.w_bd[0] : c.w_in[0], w1 = e1 ? c.w_bd[1] : c.w_in[1];
+    const float w2 = e2 ? c.w_bd[2] : c.w_in[2], w3 = e3 ? c.w_bd[3] : c.w_in[3];
+    const float w4 = e4 ? c.w_bd[4] : c.w_in[4], w5 = e5 ? c.w_bd[5] : c.w_in[5];
+    float s = 0.0f;
+    if (c.any_self) {   // self_term: the same sum, a zero added where a face is not on the wall
+        s = __fadd_rn(s, x == 0 ? c.s_lo[0] : 0.0f);
+        s = __fadd_rn(s, x == c.n[0] - 1 ? c.s_hi[0] : 0.0f);
+        s = __fadd_rn(s, y == 0 ? c.s_lo[1] : 0.0f);
+        s = __fadd_rn(s, y == c.n[1] - 1 ? c.s_hi[1] : 0.0f);
+        s = __fadd_rn(s, z == 0 ? c.s_lo[2] : 0.0f);
+        s = __fadd_rn(s, z == c.n[2] - 1 ? c.s_hi[2] : 0.0f);
+    }
+    const float v = finish_update(tc, flux_sum(tc, t0, t1, t2, t3, t4, t5, w0, w1, w2, w3, w4, w5), s);
+    return is_held(c, x, y, z) ? tc : v;
+}
+
+// Interior cell (no face on the boundary, not held, no self term).
+__device__ __forceinline__ float uniform_inner(const SweepCoef& c, float tc, float txm, float txp, float tym,
+                                               float typ, float tzm, float tzp) {
+    return __fadd_rn(tc, flux_sum(tc, txm, txp, tym, typ, tzm, tzp, c.w_in[0], c.w_in[1], c.w_in[2], c.w_in[3],
+                                  c.w_in[4], c.w_in[5]));
+}
+
+// Outside the domain on a non-periodic axis (a ghost or padding cell).
+__device__ __forceinline__ bool outside_np(const SweepCoef& c, int x, int y, int z) {
+    return (!c.periodic[0] && (x < 0 || x >= c.n[0])) || (!c.periodic[1] && (y < 0 || y >= c.n[1])) ||
+           (!c.periodic[2] && (z < 0 || z >= c.n[2]));
+}
+
 // x / y neighbours of one plane for one thread: the 4 cells below and above in
 // y and the x neighbours of the row ends; same for 1/k. They belong to other
 // threads' columns, so they come from L1 (or L2).
@@ -98,7 +140,10 @@ struct ColNb {
 // loads plane z + 1, so most plane loads hit L2 (measured at 512^3: +11% with
 // per-cell k, +7% with uniform k). Register-level prefetch was slower: it
 // costs the occupancy.
-template <bool KVAR> struct ColOcc { static constexpr int blocks = KVAR ? 4 : 6, unroll = KVAR ? 1 : 2; };
+template <bool KVAR, bool INL = false> struct ColOcc {
+    static constexpr int blocks = INL ? (KVAR ? 3 : 4) : (KVAR ? 4 : 6);
+    static constexpr int unroll = KVAR ? 1 : 2;
+};
 
 // One thread's work: cells (gx .. gx+3, gy) of planes [z0, z1), one step,
 // from tin into tout. Shared by the single-grid kernel and the batched one.
@@ -199,7 +244,9 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
                 const float txp = i == 3 ? nb.tx_p : tc[i + 1];
                 const bool edge_cell = bym || byp || bzm || bzp || (!perx && (gx + i == 0 || gx + i == c.n[0] - 1));
                 float v;
-                if (!edge_cell) {
+                if (!KVAR) {   // uniform k: the boundary formula by select, inline
+                    v = uniform_cell(c, tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i], tm[i], tz[i], gx + i, gy, z);
+                } else if (!edge_cell) {
                     v = __fadd_rn(tc[i], flux_sum(tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i], tm[i], tz[i], w[i][0],
                                                   w[i][1], w[i][2], w[i][3], w[i][4], w[i][5]));
                 } else {
@@ -237,17 +284,21 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
 }
 
 // ADV: per-cell k with a nonzero upwind weight on some face (uniform k folds
-// the upwind weights into its constants and never needs it)
-template <typename S, bool KVAR, bool ADV>
-__global__ void __launch_bounds__(256, ColOcc<KVAR>::blocks) sweep_col(const __grid_constant__ SweepArgs a) {
+// the upwind weights into its constants and never needs it).
+// INL: boundary cells and periodic copies in place, one launch per pass
+// (fastest for small grids, where launches dominate); otherwise the
+// branch-free main pass, followed by boundary_fix (unless the ghost layers
+// hold the faces) and twin_copy (fastest for large grids).
+template <typename S, bool KVAR, bool ADV, bool INL>
+__global__ void __launch_bounds__(256, (ColOcc<KVAR, INL>::blocks)) sweep_col(const __grid_constant__ SweepArgs a) {
     const SweepCoef& c = a.c;
     const int gx = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
     const int gy = blockIdx.y * blockDim.y + threadIdx.y;
     if (gx >= c.n[0] || gy >= c.n[1]) return;
     const int z0 = blockIdx.z * a.zchunk;
     const int z1 = min(z0 + a.zchunk, c.n[2]);
-    col_run<S, KVAR, ADV, false, ColOcc<KVAR>::unroll, true, true>(c, (const S*)a.tin, (S*)a.tout, a.rk, a.status,
-                                                                    gx, gy, z0, z1);
+    col_run<S, KVAR, ADV, false, ColOcc<KVAR, INL>::unroll, !INL, true>(c, (const S*)a.tin, (S*)a.tout, a.rk,
+                                                                         a.status, gx, gy, z0, z1);
 }
 
 // Boundary cells (the outer layer on every non-periodic face): recomputed
@@ -303,12 +354,13 @@ __global__ void __launch_bounds__(256) twin_copy(const __grid_constant__ SweepCo
 }
 
 template <typename S, bool KVAR>
-cudaError_t col_launch(const SweepArgs& a_in, cudaStream_t st, int nsm, const cudaEvent_t* ev) {
+cudaError_t col_launch(const SweepArgs& a_in, cudaStream_t st, int nsm, const cudaEvent_t* ev, bool inl) {
     SweepArgs a = a_in;
     dim3 block(16, 16);
     const int gxb = (a.c.n[0] + 63) / 64, gyb = (a.c.n[1] + 15) / 16;
     // z chunks of about 16 planes: many short columns stream the grid at once
-    const long long cols = (long long)gxb * gyb, resident = (long long)nsm * ColOcc<KVAR>::blocks;
+    const long long cols = (long long)gxb * gyb,
+                    resident = (long long)nsm * (inl ? ColOcc<KVAR, true>::blocks : ColOcc<KVAR>::blocks);
     long long want = resident * 16;
     int nch = (int)std::max<long long>(1, want / cols);
     // chunks of at least 16 planes, unless that leaves SMs idle (small grids,
@@ -322,11 +374,16 @@ cudaError_t col_launch(const SweepArgs& a_in, cudaStream_t st, int nsm, const cu
     const bool adv = KVAR && (a.c.adv[0] != 0.0f || a.c.adv[1] != 0.0f || a.c.adv[2] != 0.0f ||
                               a.c.adv[3] != 0.0f || a.c.adv[4] != 0.0f || a.c.adv[5] != 0.0f);
     if (ev) cudaEventRecord(ev[0], st);
-    if (adv) sweep_col<S, KVAR, true><<<grid, block, 0, st>>>(a);
-    else sweep_col<S, KVAR, false><<<grid, block, 0, st>>>(a);
+    if (inl) {
+        if (adv) sweep_col<S, KVAR, true, true><<<grid, block, 0, st>>>(a);
+        else sweep_col<S, KVAR, false, true><<<grid, block, 0, st>>>(a);
+    } else {
+        if (adv) sweep_col<S, KVAR, true, false><<<grid, block, 0, st>>>(a);
+        else sweep_col<S, KVAR, false, false><<<grid, block, 0, st>>>(a);
+    }
     if (ev) cudaEventRecord(ev[1], st);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || inl) return e;   // in place: nothing after the pass
     long long bcells = 0;
     for (int ax = 0; ax < 3; ++ax) {
         if (a.c.periodic[ax]) continue;

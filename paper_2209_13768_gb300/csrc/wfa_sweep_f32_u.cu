@@ -57,8 +57,8 @@ cudaError_t launch_simple_f32_u(const SweepArgs& a, cudaStream_t st) {
     return simple_launch<S, KVAR>(a, st);
 }
 
-cudaError_t launch_col_f32_u(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev) {
-    return col_launch<S, KVAR>(a, st, nsm, ev);
+cudaError_t launch_col_f32_u(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev, bool inl) {
+    return col_launch<S, KVAR>(a, st, nsm, ev, inl);
 }
 
 cudaError_t launch_col2_f32_u(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev) {

@@ -25,48 +25,6 @@ constexpr int F2_W = 72;                 // shared row: x = -4 .. 67, x = 0 at i
 constexpr int F2_PLANE = F2_TY * F2_W;
 constexpr int F2_BLOCKS = 3;             // blocks per SM the register budget targets
 
-// One cell with uniform k: boundary faces, held layers and the zero-flux self
-// term chosen by select, in the order and form of boundary_update, so the
-// value is bitwise that of every other kernel (an interior cell reduces to
-// the interior expression: w_in weights, neighbour values, no self term).
-__device__ __forceinline__ float uniform_cell(const SweepCoef& c, float tc, float txm, float txp, float tym,
-                                              float typ, float tzm, float tzp, int x, int y, int z) {
-    const bool e0 = !c.periodic[0] && x == 0, e1 = !c.periodic[0] && x == c.n[0] - 1;
-    const bool e2 = !c.periodic[1] && y == 0, e3 = !c.periodic[1] && y == c.n[1] - 1;
-    const bool e4 = !c.periodic[2] && z == 0, e5 = !c.periodic[2] && z == c.n[2] - 1;
-    auto tface = [&](int f) { return c.bkind[f] == WFA_BC_DIRICHLET ? c.tb[f] : 0.0f; };
-    const float t0 = e0 ? tface(0) : txm, t1 = e1 ? tface(1) : txp;
-    const float t2 = e2 ? tface(2) : tym, t3 = e3 ? tface(3) : typ;
-    const float t4 = e4 ? tface(4) : tzm, t5 = e5 ? tface(5) : tzp;
-    const float w0 = e0 ? c.w_bd[0] : c.w_in[0], w1 = e1 ? c.w_bd[1] : c.w_in[1];
-    const float w2 = e2 ? c.w_bd[2] : c.w_in[2], w3 = e3 ? c.w_bd[3] : c.w_in[3];
-    const float w4 = e4 ? c.w_bd[4] : c.w_in[4], w5 = e5 ? c.w_bd[5] : c.w_in[5];
-    float s = 0.0f;
-    if (c.any_self) {   // self_term: the same sum, a zero added where a face is not on the wall
-        s = __fadd_rn(s, x == 0 ? c.s_lo[0] : 0.0f);
-        s = __fadd_rn(s, x == c.n[0] - 1 ? c.s_hi[0] : 0.0f);
-        s = __fadd_rn(s, y == 0 ? c.s_lo[1] : 0.0f);
-        s = __fadd_rn(s, y == c.n[1] - 1 ? c.s_hi[1] : 0.0f);
-        s = __fadd_rn(s, z == 0 ? c.s_lo[2] : 0.0f);
-        s = __fadd_rn(s, z == c.n[2] - 1 ? c.s_hi[2] : 0.0f);
-    }
-    const float v = finish_update(tc, flux_sum(tc, t0, t1, t2, t3, t4, t5, w0, w1, w2, w3, w4, w5), s);
-    return is_held(c, x, y, z) ? tc : v;
-}
-
-// Interior cell (no face on the boundary, not held, no self term).
-__device__ __forceinline__ float uniform_inner(const SweepCoef& c, float tc, float txm, float txp, float tym,
-                                               float typ, float tzm, float tzp) {
-    return __fadd_rn(tc, flux_sum(tc, txm, txp, tym, typ, tzm, tzp, c.w_in[0], c.w_in[1], c.w_in[2], c.w_in[3],
-                                  c.w_in[4], c.w_in[5]));
-}
-
-// Outside the domain on a non-periodic axis (a ghost or padding cell).
-__device__ __forceinline__ bool outside_np(const SweepCoef& c, int x, int y, int z) {
-    return (!c.periodic[0] && (x < 0 || x >= c.n[0])) || (!c.periodic[1] && (y < 0 || y >= c.n[1])) ||
-           (!c.periodic[2] && (z < 0 || z >= c.n[2]));
-}
-
 template <typename S>
 __global__ void __launch_bounds__(F2_TX * F2_TY, F2_BLOCKS) sweep_col2(const __grid_constant__ SweepArgs a) {
     const SweepCoef& c = a.c;

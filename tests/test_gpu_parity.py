@@ -90,6 +90,7 @@ def test_boundary_mixes_all_kernels(mix, kvar, adv):
     np.testing.assert_array_equal(run_gpu(p, variant=3), base, err_msg="column kernel")
     # two-step column kernel (uniform k; per-cell k falls back to one step)
     np.testing.assert_array_equal(run_gpu(p, depth=2, variant=4), base, err_msg="two-step column kernel")
+    np.testing.assert_array_equal(run_gpu(p, variant=5), base, err_msg="column kernel, boundaries in place")
     np.testing.assert_array_equal(run_gpu(p, steps=p.steps - 1, depth=2, variant=4),
                                   run_gpu(p, steps=p.steps - 1, variant=-1), err_msg="two-step, odd count")
 
@@ -107,6 +108,7 @@ def test_small_and_ragged_shapes(shape):
         for depth in (1, 3, 8):
             np.testing.assert_array_equal(run_gpu(p, depth=depth, variant=1), base)
         np.testing.assert_array_equal(run_gpu(p, variant=3), base)
+        np.testing.assert_array_equal(run_gpu(p, variant=5), base)
         pu = _mixed_problem(mix, shape=shape, kvar=False, seed=7)
         pu.steps = 9
         np.testing.assert_array_equal(run_gpu(pu, depth=2, variant=4), run_gpu(pu, variant=-1), err_msg=str(shape))
@@ -178,6 +180,7 @@ def test_bf16_storage(mix):
         for variant in (1, 2):
             np.testing.assert_array_equal(run_gpu(p, storage=wfa.BF16, depth=depth, variant=variant), base)
     np.testing.assert_array_equal(run_gpu(p, storage=wfa.BF16, variant=3), base)
+    np.testing.assert_array_equal(run_gpu(p, storage=wfa.BF16, variant=5), base)
     pu = _mixed_problem(mix, kvar=False, seed=3)
     pu.steps = 30
     np.testing.assert_array_equal(run_gpu(pu, storage=wfa.BF16, depth=2, variant=4),
@@ -332,7 +335,10 @@ def test_kernel_timing_samples_and_leaves_results_alone(depth, variant):
     with make_grid(p, depth=depth, variant=variant) as g:
         assert g.kernel_time() == (0.0, 0)          # off: nothing recorded
         g.set_kernel_timing(2)                       # passes 0, 2, 4, ... are sampled
+        n0 = g.launch_count()
         g.step(p.steps)
+        # ghost-layer faces: one kernel per pass for every variant here
+        assert g.launch_count() - n0 == p.steps // depth
         ms, n = g.kernel_time()
         assert n == (p.steps // depth + 1) // 2 and ms > 0
         assert g.kernel_time() == (0.0, 0)           # a read starts a new count
