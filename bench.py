@@ -203,7 +203,7 @@ def reference_arm(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def serving_sample(n_requests, rate=200.0, seed=5, pool=24):
+def serving_sample(n_requests, rate=200.0, seed=5, pool=24, quantum=64):
     """Poisson arrivals (rate per second) of heat / advection-diffusion solves,
     edges log-uniform in [32, 256], steps U{50..2000}, fp32 or bf16.
     Inputs come from a pool of `pool` request shapes (generated once); each
@@ -220,7 +220,7 @@ def serving_sample(n_requests, rate=200.0, seed=5, pool=24):
 
     def run_server():
         lat = []
-        with wfa.Server(budget_bytes=120 << 30, quantum=64) as srv:
+        with wfa.Server(budget_bytes=120 << 30, quantum=quantum) as srv:
             t0 = time.perf_counter()
             tickets = []
             for t, p, n, st in reqs:
@@ -258,7 +258,8 @@ def serving_sample(n_requests, rate=200.0, seed=5, pool=24):
     pct = lambda v, q: v[min(len(v) - 1, int(q * (len(v) - 1) + 0.5))]
     return {"requests": len(reqs), "rate_per_s": rate, "offered_GLUPS": updates / reqs[-1][0] / 1e9,
             "continuous_batching": {"GLUPS": updates / wall_s / 1e9, "p50_s": st["p50_latency_s"],
-                                    "p99_s": st["p99_latency_s"], "wall_s": wall_s, "ticks": st["ticks"]},
+                                    "p99_s": st["p99_latency_s"], "wall_s": wall_s, "ticks": st["ticks"],
+                                    "gpu_busy_s": st["busy_seconds"]},
             "one_grid_per_launch_fifo": {"GLUPS": updates / wall_f / 1e9, "p50_s": pct(lat_f, 0.5),
                                          "p99_s": pct(lat_f, 0.99), "wall_s": wall_f},
             "inputs": f"pool of {pool} request shapes from the serving request stream"}

@@ -176,7 +176,9 @@ int wfa_sync(wfa_grid g);
  * grid's stream just before and just after the main sweep kernel of every
  * every-th pass that wfa_step launches from now on (a pass's boundary fix-up
  * and periodic-copy kernels fall outside the pair; autotuning trials are not
- * sampled); 0 turns timing off and frees the events. At most 4096 pairs are
+ * sampled; on small grids, where wfa_step replays captured runs of 32 passes
+ * as CUDA graphs, a sample brackets a whole run and counts as 32 launches);
+ * 0 turns timing off and frees the events. At most 4096 pairs are
  * held; later passes go unsampled until wfa_kernel_time reads them.
  * Errors: WFA_ERR_ARG for a NULL grid or every < 0. */
 int wfa_set_kernel_timing(wfa_grid g, int every);
@@ -248,10 +250,15 @@ typedef struct {
 /* Start a continuous-batching server on its own scheduler thread.
  * hbm_budget_bytes: admission limit on the device memory of resident
  * requests; max_resident: most requests on the device at once (0 = 1024);
- * quantum: steps each resident request advances per scheduler tick (0 = 64).
+ * quantum: steps a resident request advances per scheduler tick (0 = 64).
  * Requests that arrive while others run are admitted at the next tick as
- * memory and slots free up; all resident requests advance together in one
- * batched launch per tick. */
+ * memory and slots free up. A tick takes the residents with the least
+ * remaining work (cells x steps) until about 64 M cells are in it, plus any
+ * resident passed over 8 ticks in a row, and advances each by up to quantum
+ * steps (all of them when fewer than two quanta are left), together in one
+ * batched launch (wfa_batch_run). A second thread moves inputs to the
+ * device and results back on its own stream while the ticks run. A
+ * request's result is bitwise the result of running it alone. */
 int wfa_server_create(size_t hbm_budget_bytes, int max_resident, long long quantum,
                       wfa_server* out);
 

@@ -6,7 +6,10 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <new>
+#include <vector>
 
 #include "wfa_internal.cuh"
 
@@ -36,6 +39,66 @@ static int fail(int code, const char* fmt, ...) {
     va_end(ap);
     g_last_error = buf;
     return code;
+}
+
+// ----------------------------------------------------------- device memory --
+// Grid buffers come from one stream-ordered memory pool per device that keeps
+// freed memory for reuse: creating and destroying a grid per request (as the
+// server does) costs no device-wide synchronisation, and once the pool has
+// grown no trip to the driver's allocator.
+static std::mutex g_pool_mu;
+static std::map<int, cudaMemPool_t> g_pools;
+
+static cudaMemPool_t grid_pool() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it != g_pools.end()) return it->second;
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = ~0ull;   // never hand freed memory back to the driver
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[dev] = pool;
+    return pool;
+}
+
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st) {
+    cudaMemPool_t pool = grid_pool();
+    if (!pool) return cudaErrorMemoryAllocation;
+    return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
+void dev_free(void* p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+}
+
+// Pinned host words (reduction results, status) carved from shared slabs of
+// 1024 slots of 64 bytes, so a grid costs no pinned allocation of its own.
+static std::mutex g_pin_mu;
+static std::vector<void*> g_pin_free;
+
+void* pinned_word() {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    if (g_pin_free.empty()) {
+        char* slab = nullptr;
+        if (cudaMallocHost(&slab, 1024 * 64) != cudaSuccess) return nullptr;
+        for (int i = 1023; i >= 0; --i) g_pin_free.push_back(slab + 64 * i);
+    }
+    void* w = g_pin_free.back();
+    g_pin_free.pop_back();
+    return w;
+}
+
+void pinned_release(void* w) {
+    if (!w) return;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free.push_back(w);
 }
 
 // ------------------------------------------------------------ coefficients --
@@ -597,11 +660,14 @@ int wfa_create_grid(int nx, int ny, int nz, double hx, double hy, double hz, int
     for (int f = 0; f < 6; ++f) { g->bc_kind[f] = WFA_BC_ZEROFLUX; g->bc_value[f] = 0.0; }
     const size_t bytes = field_elems(g) * g->esize;
     cudaError_t e = cudaSuccess;
-    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&g->T[b], bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&g->d_partials, 4096 * sizeof(double));
-    if (e == cudaSuccess) e = cudaMallocHost(&g->h_result, 64);
-    if (e == cudaSuccess) e = cudaMalloc(&g->d_status, 8 * sizeof(int));
-    if (e == cudaSuccess) e = cudaMallocHost(&g->h_status, 8 * sizeof(int));
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = dev_alloc(&g->T[b], bytes, g->stream);
+    if (e == cudaSuccess) e = dev_alloc((void**)&g->d_partials, 4096 * sizeof(double), g->stream);
+    if (e == cudaSuccess) e = dev_alloc((void**)&g->d_status, 8 * sizeof(int), g->stream);
+    if (e == cudaSuccess) {
+        g->h_result = static_cast<double*>(pinned_word());
+        g->h_status = static_cast<int*>(pinned_word());
+        if (!g->h_result || !g->h_status) e = cudaErrorMemoryAllocation;
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(g->d_status, 0, 8 * sizeof(int), g->stream);
     if (e == cudaSuccess) {
         for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMemsetAsync(g->T[b], 0, bytes, g->stream);
@@ -617,17 +683,18 @@ int wfa_create_grid(int nx, int ny, int nz, double hx, double hy, double hz, int
 
 int wfa_destroy_grid(wfa_grid g) {
     if (!g) return WFA_OK;
-    cudaStreamSynchronize(g->stream);
-    for (int b = 0; b < 2; ++b) if (g->T[b]) cudaFree(g->T[b]);
-    if (g->k) cudaFree(g->k);
-    if (g->r) cudaFree(g->r);
-    if (g->d_partials) cudaFree(g->d_partials);
-    if (g->d_stage) cudaFree(g->d_stage);
-    if (g->h_result) cudaFreeHost(g->h_result);
-    if (g->d_status) cudaFree(g->d_status);
-    if (g->h_status) cudaFreeHost(g->h_status);
+    cudaStreamSynchronize(g->stream);   // nothing of this grid is in flight below
+    for (int b = 0; b < 2; ++b) dev_free(g->T[b], g->stream);
+    dev_free(g->k, g->stream);
+    dev_free(g->r, g->stream);
+    dev_free(g->d_partials, g->stream);
+    dev_free(g->d_stage, g->stream);
+    dev_free(g->d_status, g->stream);
+    pinned_release(g->h_result);
+    pinned_release(g->h_status);
     free_tmaps(g);
     free_timing(g);
+    free_graphs(g);
     delete g;
     return WFA_OK;
 }
@@ -635,7 +702,7 @@ int wfa_destroy_grid(wfa_grid g) {
 static int ensure_stage(wfa_grid g) {
     if (g->d_stage) return WFA_OK;
     const size_t N = (size_t)g->n[0] * g->n[1] * g->n[2];
-    WFA_CUDA(cudaMalloc(&g->d_stage, N * sizeof(float)));
+    WFA_CUDA(dev_alloc((void**)&g->d_stage, N * sizeof(float), g->stream));
     return WFA_OK;
 }
 
@@ -695,9 +762,9 @@ int wfa_set_coeffs(wfa_grid g, const float* k_host, double k_uniform, double ux,
         if (first != ~0ull)
             return fail(WFA_ERR_ARG, "k[%llu] = %g is negative or not finite", first, (double)k_host[first]);
         if (!g->k) {
-            WFA_CUDA(cudaMalloc(&g->k, field_elems(g) * sizeof(float)));
+            WFA_CUDA(dev_alloc((void**)&g->k, field_elems(g) * sizeof(float), g->stream));
             WFA_CUDA(cudaMemsetAsync(g->k, 0, field_elems(g) * sizeof(float), g->stream));
-            WFA_CUDA(cudaMalloc(&g->r, field_elems(g) * sizeof(float)));
+            WFA_CUDA(dev_alloc((void**)&g->r, field_elems(g) * sizeof(float), g->stream));
         }
         const int thr = 256;
         pack_kernel<float><<<grid_blocks(N, thr), thr, 0, g->stream>>>(g->d_stage, g->k + domain_offset(g),
@@ -708,8 +775,8 @@ int wfa_set_coeffs(wfa_grid g, const float* k_host, double k_uniform, double ux,
     } else {
         if (g->k) {
             cudaStreamSynchronize(g->stream);
-            cudaFree(g->k);
-            cudaFree(g->r);
+            dev_free(g->k, g->stream);
+            dev_free(g->r, g->stream);
             g->k = nullptr;
             g->r = nullptr;
             free_tmaps(g);
@@ -991,4 +1058,13 @@ int wfa_sync(wfa_grid g) {
 
 namespace wfa {
 int prepare_coeff_halo(wfa_grid_s* g) { return prepare_k_halo(g); }
+
+// Hand a grid to another stream: its own work is finished first, and later
+// work goes to the new stream (device memory is not tied to a stream once
+// allocated).
+int grid_rebind_stream(wfa_grid_s* g, cudaStream_t st) {
+    WFA_CUDA(cudaStreamSynchronize(g->stream));
+    g->stream = st;
+    return WFA_OK;
+}
 }  // namespace wfa

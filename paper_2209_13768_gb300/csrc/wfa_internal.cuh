@@ -118,6 +118,7 @@ struct wfa_grid_s {
     int timing_every;     // wfa_set_kernel_timing: sample every n-th pass (0 = off)
     long long timing_pass;
     void* timing;         // wfa::KernelTiming (recorded event pairs)
+    void* graphs;         // wfa::StepGraphs (captured runs of passes for small grids)
 };
 
 namespace wfa {
@@ -135,6 +136,10 @@ int autotune(wfa_grid_s* g, int* depth, int* variant);    // pick the fastest ke
 int prepare_coeff_halo(wfa_grid_s* g);                    // k periodic twins, then 1/k
 void free_tmaps(wfa_grid_s* g);
 void free_timing(wfa_grid_s* g);
+void free_graphs(wfa_grid_s* g);
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st);   // grid memory pool, stream-ordered
+void dev_free(void* p, cudaStream_t st);
+int grid_rebind_stream(wfa_grid_s* g, cudaStream_t st);          // move a quiet grid to another stream
 
 // ----------------------------------------------------------- device math --
 // The fixed per-cell arithmetic. Every kernel that updates a cell calls these

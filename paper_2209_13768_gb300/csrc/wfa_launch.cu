@@ -34,6 +34,7 @@ void free_tmaps(wfa_grid_s* g) {
 constexpr int TIMING_MAX_PAIRS = 4096;
 struct KernelTiming {
     std::vector<cudaEvent_t> ev;   // pair i: ev[2i] before, ev[2i + 1] after
+    std::vector<int> weight;       // launches pair i brackets (a replayed run: its passes)
     int used = 0;
 };
 
@@ -47,11 +48,13 @@ void free_timing(wfa_grid_s* g) {
 
 // The pair for this pass, or null when the pass is not sampled (timing off,
 // not an every-th pass, or every pair in use until the next read).
-static const cudaEvent_t* timing_slot(wfa_grid_s* g) {
+static const cudaEvent_t* timing_slot(wfa_grid_s* g, int weight = 1) {
     if (g->timing_every <= 0) return nullptr;
     if (g->timing_pass++ % g->timing_every) return nullptr;
     auto* t = static_cast<KernelTiming*>(g->timing);
     if (!t || t->used >= TIMING_MAX_PAIRS) return nullptr;
+    if ((int)t->weight.size() <= t->used) t->weight.resize(t->used + 1);
+    t->weight[t->used] = weight;
     if (2 * t->used == (int)t->ev.size()) {
         cudaEvent_t a, b;
         if (cudaEventCreate(&a) != cudaSuccess) return nullptr;
@@ -332,11 +335,105 @@ static int one_pass(wfa_grid_s* g, const SweepCoef& c, int depth, int variant) {
     return WFA_OK;
 }
 
+// Small grids: a run of GRAPH_PASSES passes captured once as a CUDA graph
+// and replayed, so that the per-kernel launch cost (which dominates a pass of
+// a few microseconds) is paid once per run. One graph per starting buffer;
+// a graph is rebuilt when anything its kernels were given changes.
+constexpr int GRAPH_PASSES = 32;                // even: a run ends on the buffer it started from
+constexpr long long GRAPH_MAX_CELLS = 1LL << 22;
+
+struct StepGraph {
+    SweepCoef c;
+    const void* T[2];
+    const float* r;
+    int variant = 0, depth = 0;
+    cudaGraphExec_t exec = nullptr;
+};
+struct StepGraphs {
+    StepGraph slot[2];            // by starting buffer
+    cudaStream_t stream = nullptr;  // capture stream
+};
+
+void free_graphs(wfa_grid_s* g) {
+    auto* gs = static_cast<StepGraphs*>(g->graphs);
+    if (!gs) return;
+    for (auto& sl : gs->slot)
+        if (sl.exec) cudaGraphExecDestroy(sl.exec);
+    if (gs->stream) cudaStreamDestroy(gs->stream);
+    delete gs;
+    g->graphs = nullptr;
+}
+
+// The graph of GRAPH_PASSES passes from buffer g->cur with this configuration
+// (captured now if the cached one was made for something else).
+static int run_graph(wfa_grid_s* g, const SweepCoef& c, const Choice& ch, cudaGraphExec_t* out) {
+    if (!g->graphs) g->graphs = new (std::nothrow) StepGraphs();
+    auto* gs = static_cast<StepGraphs*>(g->graphs);
+    if (!gs) {
+        set_error("host allocation failed");
+        return WFA_ERR_OOM;
+    }
+    StepGraph& sl = gs->slot[g->cur];
+    const bool same = sl.exec && !memcmp(&sl.c, &c, sizeof c) && sl.T[0] == g->T[0] && sl.T[1] == g->T[1] &&
+                      sl.r == g->r && sl.variant == ch.variant && sl.depth == ch.depth;
+    if (!same) {
+        if (sl.exec) cudaGraphExecDestroy(sl.exec);
+        sl.exec = nullptr;
+        if (!gs->stream) WFA_CUDA(cudaStreamCreateWithFlags(&gs->stream, cudaStreamNonBlocking));
+        // the passes are issued on the capture stream; g->cur and the launch
+        // count move back to where they were (nothing ran yet)
+        const cudaStream_t user = g->stream;
+        const int cur0 = g->cur;
+        const long long launches0 = g->launches;
+        g->stream = gs->stream;
+        cudaError_t e = cudaStreamBeginCapture(gs->stream, cudaStreamCaptureModeThreadLocal);
+        int rc = WFA_OK;
+        for (int k = 0; k < GRAPH_PASSES && e == cudaSuccess && !rc; ++k) rc = one_pass(g, c, ch.depth, ch.variant);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(gs->stream, &graph) : e;
+        g->stream = user;
+        g->cur = cur0;
+        g->launches = launches0;
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess && !rc) e = cudaGraphInstantiate(&sl.exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (rc) return rc;
+        if (e != cudaSuccess) return cuda_fail(e, "step graph capture");
+        sl.c = c;
+        sl.T[0] = g->T[0];
+        sl.T[1] = g->T[1];
+        sl.r = g->r;
+        sl.variant = ch.variant;
+        sl.depth = ch.depth;
+    }
+    *out = sl.exec;
+    return WFA_OK;
+}
+
 int launch_sweep(wfa_grid_s* g, long long nsteps) {
     SweepCoef c;
     int rc = build_coef(g, &c);
     if (rc) return rc;
     const Choice ch = choose(g);
+    const long long cells = (long long)g->n[0] * g->n[1] * g->n[2];
+    const long long runs = nsteps / ((long long)ch.depth * GRAPH_PASSES);
+    if (cells <= GRAPH_MAX_CELLS && runs >= 2) {
+        cudaGraphExec_t exec = nullptr;
+        const int every = g->timing_every;
+        g->timing_every = 0;   // no event records inside the captured passes
+        rc = run_graph(g, c, ch, &exec);
+        g->timing_every = every;
+        if (rc) return rc;
+        for (long long r = 0; r < runs; ++r) {
+            // kernel timing samples a whole run (its passes, fix-up kernels included)
+            const cudaEvent_t* ev = every > 0 ? timing_slot(g, GRAPH_PASSES) : nullptr;
+            if (ev) cudaEventRecord(ev[0], g->stream);
+            WFA_CUDA(cudaGraphLaunch(exec, g->stream));
+            if (ev) cudaEventRecord(ev[1], g->stream);
+        }
+        g->launches += runs * GRAPH_PASSES * pass_launches(g, c, ch.depth, ch.variant);
+        nsteps -= runs * GRAPH_PASSES * ch.depth;
+    }
     while (nsteps > 0) {
         const int d = (int)std::min<long long>(ch.depth, nsteps);
         rc = one_pass(g, c, d, ch.variant);
@@ -363,7 +460,7 @@ int autotune(wfa_grid_s* g, int* depth_out, int* variant_out) {
                                    {1, 2}, {2, 2}, {1, 3}, {2, 3}, {1, 4}, {2, 4}, {1, 6}, {1, 8}};
     const size_t bytes = field_elems(g) * g->esize;
     void* save = nullptr;
-    WFA_CUDA(cudaMalloc(&save, bytes));
+    WFA_CUDA(dev_alloc(&save, bytes, g->stream));
     const int cur0 = g->cur;
     cudaError_t e = cudaMemcpyAsync(save, g->T[cur0], bytes, cudaMemcpyDeviceToDevice, g->stream);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -398,7 +495,7 @@ int autotune(wfa_grid_s* g, int* depth_out, int* variant_out) {
     g->halo_dirty = true;   // the other buffer's halo was rewritten by the trials
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    cudaFree(save);
+    dev_free(save, g->stream);
     if (rc) return rc;
     if (e != cudaSuccess) return cuda_fail(e, "autotune");
     g->tuned_variant = best.variant;
@@ -443,12 +540,13 @@ int wfa_kernel_time(wfa_grid g, double* ms, long long* launches) {
     if (!t) return WFA_OK;
     cudaError_t e = cudaStreamSynchronize(g->stream);
     double sum = 0.0;
+    long long n = 0;
     for (int i = 0; i < t->used && e == cudaSuccess; ++i) {
         float m = 0.0f;
         e = cudaEventElapsedTime(&m, t->ev[2 * i], t->ev[2 * i + 1]);
         sum += m;
+        n += t->weight[i];
     }
-    const int n = t->used;
     t->used = 0;
     if (e != cudaSuccess) return wfa::cuda_fail(e, "wfa_kernel_time");
     *ms = sum;

@@ -1,9 +1,15 @@
 // Continuous-batching request server: transient solves of different sizes
 // and step counts are admitted by device-memory budget, kept resident, and
-// advanced together — every scheduler tick moves each resident request by up
-// to `quantum` steps in one batched launch (wfa_batch_run). Requests that
-// arrive while others run join at the next tick; finished requests are
-// copied to their host buffers and their memory is released at once.
+// advanced together. Every scheduler tick picks the residents with the least
+// remaining work (cells x steps) until about 64 M cells are in the tick
+// (shortest remaining work first, with no resident passed over more than 8
+// ticks in a row) and moves each by up to `quantum` steps (all of its steps
+// when fewer than two quanta are left), all of them together in one batched
+// launch (wfa_batch_run; measured faster than stepping the large ones alone,
+// which serialises them). Requests that arrive while others run join at the next
+// tick. A second thread moves inputs to the device and results back on its
+// own stream while the ticks run; a finished request's memory is released
+// as soon as its result is on the host.
 #include <cuda_runtime.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -24,11 +30,15 @@
 
 namespace wfa {
 void set_error(const char* fmt, ...);
+int grid_rebind_stream(wfa_grid g, cudaStream_t st);
 }
 
 namespace {
 
 using clk = std::chrono::steady_clock;
+
+constexpr double TICK_CELLS = 64.0 * 1024 * 1024;   // cells advanced per tick, at least
+constexpr int MAX_SKIP = 8;                          // ticks a resident may be passed over
 
 struct Req {
     long long ticket = 0;
@@ -36,6 +46,7 @@ struct Req {
     std::vector<float> T0, k;
     wfa_grid g = nullptr;
     long long remaining = 0;
+    int skipped = 0;   // ticks in a row this resident was not advanced
     size_t bytes = 0;
     int state = 0;   // 0 queued, 1 resident, 2 done, -1 failed
     std::string err;
@@ -63,16 +74,21 @@ struct wfa_server_s {
     int max_resident = 1024;
     long long quantum = 64;
     int device = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;   // ticks
+    cudaStream_t prep = nullptr;     // set-up and read-back, beside the ticks
 
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
-    std::deque<Req*> pending;
-    std::vector<Req*> resident;
+    std::condition_variable cv_work, cv_done, cv_prep;
+    std::deque<Req*> pending;        // submitted, not admitted
+    std::deque<Req*> to_setup;       // admitted, inputs not yet on the device
+    std::vector<Req*> ready;         // on the device, joining at the next tick
+    std::vector<Req*> resident;      // advanced by the ticks
+    std::deque<Req*> to_retire;      // finished, result not yet on the host
     std::unordered_map<long long, Req*> all;
     long long next_ticket = 1;
-    bool stop = false;
-    std::thread th;
+    int in_setup = 0;                // taken from to_setup, not yet ready
+    bool stop = false, sched_done = false;
+    std::thread th, prep_th;
 
     // stats
     long long submitted = 0, admitted = 0, completed = 0, rejected = 0, ticks = 0;
@@ -81,13 +97,14 @@ struct wfa_server_s {
     std::vector<double> latencies;
 
     void run();
+    void prep_loop();
     int setup(Req* r);
     void finish(Req* r, bool ok, const std::string& why);
 };
 
 int wfa_server_s::setup(Req* r) {
     const wfa_request& s = r->spec;
-    int rc = wfa_create_grid(s.nx, s.ny, s.nz, s.hx, s.hy, s.hz, s.storage, stream, &r->g);
+    int rc = wfa_create_grid(s.nx, s.ny, s.nz, s.hx, s.hy, s.hz, s.storage, prep, &r->g);
     if (rc) return rc;
     for (int f = 0; f < 6 && !rc; ++f) rc = wfa_set_bc(r->g, f, s.bc_kind[f], s.bc_value[f]);
     if (!rc) rc = wfa_set_coeffs(r->g, r->k.empty() ? nullptr : r->k.data(), s.k_uniform, s.ux, s.uy, s.uz);
@@ -120,21 +137,61 @@ void wfa_server_s::finish(Req* r, bool ok, const std::string& why) {
         latencies.push_back(std::chrono::duration<double>(r->t_done - r->t_submit).count());
     }
     cv_done.notify_all();
+    cv_work.notify_all();   // memory freed: more requests may be admitted
+}
+
+// The set-up / read-back thread: inputs of admitted requests go to the
+// device and results of finished ones come back on its own stream while the
+// scheduler's ticks run, so the GPU does not wait for host transfers.
+void wfa_server_s::prep_loop() {
+    cudaSetDevice(device);
+    for (;;) {
+        Req* r = nullptr;
+        bool retire = false;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv_prep.wait(lk, [&] { return sched_done || !to_setup.empty() || !to_retire.empty(); });
+            if (!to_retire.empty()) {   // finishing first: it frees memory and completes a request
+                r = to_retire.front();
+                to_retire.pop_front();
+                retire = true;
+            } else if (!to_setup.empty()) {
+                r = to_setup.front();
+                to_setup.pop_front();
+                ++in_setup;
+            } else {
+                return;   // the scheduler has stopped and nothing is left to do
+            }
+        }
+        if (retire) {
+            int rc = r->err.empty() ? wfa::grid_rebind_stream(r->g, prep) : WFA_ERR_STATE;
+            if (!rc) rc = wfa_read_field(r->g, r->spec.out_host);
+            finish(r, rc == 0, rc ? (r->err.empty() ? std::string(wfa_last_error()) : r->err) : std::string());
+            continue;
+        }
+        int rc = setup(r);
+        if (!rc) rc = wfa::grid_rebind_stream(r->g, stream);
+        if (rc) finish(r, false, wfa_last_error());
+        std::lock_guard<std::mutex> lk(mu);
+        if (!rc) ready.push_back(r);
+        --in_setup;
+        cv_work.notify_all();
+    }
 }
 
 void wfa_server_s::run() {
     cudaSetDevice(device);
-    std::vector<Req*> fresh;
     std::vector<wfa_grid> gs;
     std::vector<long long> steps;
     for (;;) {
-        fresh.clear();
+        std::vector<Req*> work;
         {
             std::unique_lock<std::mutex> lk(mu);
-            cv_work.wait(lk, [&] { return stop || !pending.empty() || !resident.empty(); });
-            if (stop && pending.empty() && resident.empty()) break;
+            cv_work.wait(lk, [&] {
+                return stop || !pending.empty() || !resident.empty() || !ready.empty();
+            });
             // admission: first come, first served, while memory and slots allow
-            while (!pending.empty() && (int)resident.size() < max_resident) {
+            while (!pending.empty() && (int)(resident.size() + ready.size() + to_setup.size()) < max_resident) {
                 Req* r = pending.front();
                 if (used + r->bytes > budget) break;
                 pending.pop_front();
@@ -142,56 +199,73 @@ void wfa_server_s::run() {
                 peak_used = std::max(peak_used, used);
                 r->state = 1;
                 ++admitted;
-                resident.push_back(r);
-                fresh.push_back(r);
+                to_setup.push_back(r);
+                cv_prep.notify_all();
             }
-        }
-        for (Req* r : fresh) {
-            int rc = setup(r);
-            if (rc) {
-                std::string why = wfa_last_error();
-                {
-                    std::lock_guard<std::mutex> lk(mu);
-                    resident.erase(std::find(resident.begin(), resident.end(), r));
+            for (Req* r : ready) resident.push_back(r);
+            ready.clear();
+            if (resident.empty()) {
+                if (stop && pending.empty() && to_setup.empty() && in_setup == 0) {
+                    sched_done = true;
+                    cv_prep.notify_all();
+                    break;
                 }
-                finish(r, false, why);
+                // nothing to advance yet: wait for set-up (or new requests)
+                cv_work.wait_for(lk, std::chrono::milliseconds(2));
+                continue;
             }
-        }
-        std::vector<Req*> work;
-        {
-            std::lock_guard<std::mutex> lk(mu);
             work = resident;
         }
-        if (work.empty()) continue;
+        // this tick: the residents with the least remaining work first, up to
+        // about TICK_CELLS cells (enough to fill the GPU), plus any resident
+        // passed over MAX_SKIP ticks in a row; one that is nearly done gets
+        // all its remaining steps
+        auto cells = [](const Req* r) { return (double)r->spec.nx * r->spec.ny * r->spec.nz; };
+        std::stable_sort(work.begin(), work.end(),
+                         [&](const Req* a, const Req* b) { return cells(a) * a->remaining < cells(b) * b->remaining; });
+        std::vector<Req*> sel;
+        double sel_cells = 0.0;
+        for (Req* r : work) {
+            if (sel_cells < TICK_CELLS || r->skipped >= MAX_SKIP) {
+                sel.push_back(r);
+                sel_cells += cells(r);
+                r->skipped = 0;
+            } else {
+                ++r->skipped;
+            }
+        }
+        work.swap(sel);
         gs.clear();
         steps.clear();
+        std::vector<long long> q_of(work.size());
         double upd = 0.0;
-        for (Req* r : work) {
-            const long long q = std::min(r->remaining, quantum);
+        int rc = 0;
+        const auto t0 = clk::now();
+        for (size_t i = 0; i < work.size(); ++i) {
+            Req* r = work[i];
+            const long long q = r->remaining <= 2 * quantum ? r->remaining : quantum;
+            q_of[i] = q;
+            upd += (double)q * cells(r);
             gs.push_back(r->g);
             steps.push_back(q);
-            upd += (double)q * r->spec.nx * r->spec.ny * r->spec.nz;
         }
-        const auto t0 = clk::now();
-        int rc = wfa_batch_run(gs.data(), steps.data(), (int)gs.size());
+        if (!rc && !gs.empty()) rc = wfa_batch_run(gs.data(), steps.data(), (int)gs.size());
         if (!rc) rc = cudaStreamSynchronize(stream) == cudaSuccess ? 0 : WFA_ERR_CUDA;
         const auto t1 = clk::now();
-        std::vector<Req*> done;
-        {
-            std::lock_guard<std::mutex> lk(mu);
-            ++ticks;
-            busy_s += std::chrono::duration<double>(t1 - t0).count();
-            if (!rc) cell_updates += upd;
-            for (size_t i = 0; i < work.size(); ++i) {
-                if (rc || (work[i]->remaining -= steps[i]) <= 0) done.push_back(work[i]);
+        const std::string why = rc ? std::string(wfa_last_error()) : std::string();
+        std::lock_guard<std::mutex> lk(mu);
+        ++ticks;
+        busy_s += std::chrono::duration<double>(t1 - t0).count();
+        if (!rc) cell_updates += upd;
+        for (size_t i = 0; i < work.size(); ++i) {
+            Req* r = work[i];
+            if (rc || (r->remaining -= q_of[i]) <= 0) {
+                if (rc) r->err = why.empty() ? "tick failed" : why;
+                resident.erase(std::find(resident.begin(), resident.end(), r));
+                to_retire.push_back(r);
             }
-            for (Req* r : done) resident.erase(std::find(resident.begin(), resident.end(), r));
         }
-        std::string why = rc ? std::string(wfa_last_error()) : std::string();
-        for (Req* r : done) {
-            int rr = rc ? rc : wfa_read_field(r->g, r->spec.out_host);
-            finish(r, rr == 0, rr ? (rc ? why : std::string(wfa_last_error())) : std::string());
-        }
+        cv_prep.notify_all();
     }
 }
 
@@ -208,12 +282,15 @@ int wfa_server_create(size_t hbm_budget_bytes, int max_resident, long long quant
     s->quantum = quantum ? quantum : 64;
     cudaGetDevice(&s->device);
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->prep, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         wfa::set_error("cudaStreamCreate failed: %s", cudaGetErrorString(e));
+        if (s->stream) cudaStreamDestroy(s->stream);
         delete s;
         return WFA_ERR_CUDA;
     }
     s->th = std::thread([s] { s->run(); });
+    s->prep_th = std::thread([s] { s->prep_loop(); });
     *out = s;
     return WFA_OK;
 }
@@ -322,9 +399,15 @@ int wfa_server_destroy(wfa_server s) {
         s->stop = true;
         s->cv_work.notify_all();
     }
-    if (s->th.joinable()) s->th.join();
+    if (s->th.joinable()) s->th.join();   // resident work finished; results queued for read-back
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->cv_prep.notify_all();
+    }
+    if (s->prep_th.joinable()) s->prep_th.join();
     for (auto& kv : s->all) delete kv.second;
     cudaStreamDestroy(s->stream);
+    cudaStreamDestroy(s->prep);
     delete s;
     return WFA_OK;
 }

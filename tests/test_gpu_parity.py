@@ -346,3 +346,32 @@ def test_kernel_timing_samples_and_leaves_results_alone(depth, variant):
         np.testing.assert_array_equal(g.read_field(), ref)
         with pytest.raises(wfa.WfaError):
             g.set_kernel_timing(-1)
+
+
+@pytest.mark.parametrize("depth,variant", [(1, 3), (1, 5), (2, 4), (2, 1)])
+def test_small_grid_step_graphs(depth, variant):
+    # small grids replay captured runs of passes; the fields must be those of
+    # the same passes launched one call at a time, also after the
+    # configuration changes (a stale graph would replay the old one)
+    p = _mixed_problem(6, shape=(40, 24, 20), kvar=variant != 4, seed=5)
+    n = 150
+    with make_grid(p, depth=depth, variant=variant) as g, make_grid(p, depth=depth, variant=variant) as h:
+        g.step(n)
+        for _ in range(n):
+            h.step(1)
+        np.testing.assert_array_equal(g.read_field(), h.read_field())
+        dt2 = 0.5 * g.stability_dt()
+        for grid in (g, h):
+            grid.set_dt(dt2)
+        g.step(n + 1)
+        for _ in range(n + 1):
+            h.step(1)
+        np.testing.assert_array_equal(g.read_field(), h.read_field())
+        g.set_bc(2, D, 0.75)
+        h.set_bc(2, D, 0.75)
+        for grid in (g, h):
+            grid.set_dt(dt2)
+        g.step(2 * n)
+        for _ in range(2 * n):
+            h.step(1)
+        np.testing.assert_array_equal(g.read_field(), h.read_field())
