@@ -220,9 +220,11 @@ int wfa_batch_run(wfa_grid* gs, const long long* steps, int count);
 
 typedef struct wfa_server_s* wfa_server;
 
-/* A transient solve submitted to the server. The server copies every input
- * before wfa_server_submit returns; out_host must stay valid until the
- * ticket is done. dt <= 0 selects 0.9 * dt_max. */
+/* A transient solve submitted to the server. The server reads T0_host and
+ * k_host when it admits the request (it moves them to the device on its own
+ * thread, beside the running work) and writes out_host when the request is
+ * done: all three must stay valid until the ticket is done. dt <= 0 selects
+ * 0.9 * dt_max. */
 typedef struct {
     int nx, ny, nz;
     double hx, hy, hz;
@@ -256,8 +258,8 @@ typedef struct {
  * remaining work (cells x steps) until about 64 M cells are in it, plus any
  * resident passed over 8 ticks in a row, and advances each by up to quantum
  * steps (all of them when fewer than two quanta are left), together in one
- * batched launch (wfa_batch_run). A second thread moves inputs to the
- * device and results back on its own stream while the ticks run. A
+ * batched launch (wfa_batch_run). Four more threads move inputs to the
+ * device and results back, each on its own stream, while the ticks run. A
  * request's result is bitwise the result of running it alone. */
 int wfa_server_create(size_t hbm_budget_bytes, int max_resident, long long quantum,
                       wfa_server* out);

@@ -286,7 +286,7 @@ class Server:
         r.out_host, outk = _host_f32(out, n)
         ticket = ctypes.c_longlong()
         check(lib().wfa_server_submit(self.handle, ctypes.byref(r), ctypes.byref(ticket)), "wfa_server_submit")
-        self._keep[ticket.value] = outk
+        self._keep[ticket.value] = (outk, t0, kk)   # the server reads the inputs later
         return ticket.value
 
     def poll(self, ticket):
@@ -296,7 +296,8 @@ class Server:
 
     def wait(self, ticket, timeout=60.0):
         check(lib().wfa_server_wait(self.handle, int(ticket), float(timeout)), "wfa_server_wait")
-        return self._keep.pop(ticket, None)
+        kept = self._keep.pop(ticket, None)
+        return kept[0] if kept else None
 
     def stats(self):
         st = ServerStats()

@@ -13,8 +13,9 @@
 // Default ("rounds"): every round is one launch per class of grid (storage
 // type x conductivity mode x advection x ghost-layer faces) over the active
 // units, one block per unit; the whole sequence is captured into one CUDA
-// graph and launched once, so the launch boundary is the barrier between
-// rounds and nothing inside a kernel waits on another block.
+// graph, one branch per class (classes share no grid), and launched once, so
+// the launch boundary is the barrier between rounds and nothing inside a
+// kernel waits on another block.
 // WFA_BATCH_MODE=persistent runs the rounds in one persistent kernel instead
 // (replayed as a graph: descriptor copy, counter reset, kernel): every block
 // the GPU can hold is launched, the blocks take the active units of round r
@@ -296,6 +297,8 @@ struct BatchCtx {
     PLayout lay{};
     unsigned* count = nullptr;         // barrier arrivals, the status word, units handed out
     cudaStream_t cap_stream = nullptr; // where per-round launches are captured
+    cudaStream_t cls_stream[NCLASS] = {};   // one branch per class inside the capture
+    cudaEvent_t fork = nullptr, join[NCLASS] = {};
     int blocks[NCLASS + 1] = {};       // launch size per persistent kernel (index cls + 1)
     cudaGraphExec_t exec[NCLASS + 1] = {};
 };
@@ -457,8 +460,9 @@ extern "C" int wfa_batch_run(wfa_grid* gs, const long long* steps, int count) {
         b.steps = steps[order[k]];
     }
     // WFA_BATCH_MODE: "rounds" (default: one launch per round and class,
-    // captured into one graph), "persistent" (one persistent kernel) or
-    // "stream" (the per-round launches issued on the stream)
+    // captured into one graph, a branch per class), "persistent" (one
+    // persistent kernel) or "stream" (the per-round launches issued in order
+    // on the stream)
     const char* mode_env = getenv("WFA_BATCH_MODE");
     const int mode = !mode_env ? 1 : !strcmp(mode_env, "persistent") ? 0 : !strcmp(mode_env, "stream") ? 2 : 1;
     BatchCtx* c = context_for(st);
@@ -563,28 +567,43 @@ extern "C" int wfa_batch_run(wfa_grid* gs, const long long* steps, int count) {
                     for (int b = 0; b < sorted[j].nblocks; ++b) bmap[o++] = j;
             }
         }
-        // mode "rounds": the same sequence captured on a private stream into
-        // one graph, launched on the grids' stream
+        // mode "rounds": captured on a private stream into one graph, launched
+        // on the grids' stream. Classes hold different grids, so each class's
+        // chain of rounds is its own branch of the graph (forked after the
+        // descriptor copy, joined at the end): their launches overlap on the
+        // GPU instead of draining it between classes.
         cudaStream_t ls = st;
         if (mode == 1) {
-            if (!c->cap_stream) WFA_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+            if (!c->cap_stream) {
+                WFA_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+                WFA_CUDA(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
+                for (int t = 0; t < NCLASS; ++t) {
+                    WFA_CUDA(cudaStreamCreateWithFlags(&c->cls_stream[t], cudaStreamNonBlocking));
+                    WFA_CUDA(cudaEventCreateWithFlags(&c->join[t], cudaEventDisableTiming));
+                }
+            }
             ls = c->cap_stream;
             WFA_CUDA(cudaStreamBeginCapture(ls, cudaStreamCaptureModeThreadLocal));
         }
         cudaError_t e = cudaMemcpyAsync(c->dev, c->host, bytes, cudaMemcpyHostToDevice, ls);
+        if (mode == 1 && e == cudaSuccess) e = cudaEventRecord(c->fork, ls);
         const MgGrid* dgrids = reinterpret_cast<const MgGrid*>(c->dev);
         const int* dmap = reinterpret_cast<const int*>(c->dev + grid_bytes);
         int* status = gs[order[0]]->d_status;
-        // step s: per class, the grids with more than s steps are a prefix
-        int active[NCLASS];
-        for (int t = 0; t < NCLASS; ++t) active[t] = cls_first[t + 1];
-        for (long long s = 0; s < max_steps && e == cudaSuccess; ++s) {
-            for (int t = 0; t < NCLASS && e == cudaSuccess; ++t) {
-                while (active[t] > cls_first[t] && sorted[active[t] - 1].steps <= s) --active[t];
-                if (active[t] == cls_first[t]) continue;
-                const MgGrid& last = sorted[active[t] - 1];
-                e = launch_class(t, last.block0 + last.nblocks, dgrids, dmap + cls_map[t], s, status, ls);
+        // per class, the grids with more than s steps are a prefix
+        for (int t = 0; t < NCLASS && e == cudaSuccess; ++t) {
+            if (cls_first[t] == cls_first[t + 1]) continue;
+            cudaStream_t cs = mode == 1 ? c->cls_stream[t] : ls;
+            if (mode == 1) e = cudaStreamWaitEvent(cs, c->fork, 0);
+            int active = cls_first[t + 1];
+            for (long long s = 0; s < max_steps && e == cudaSuccess; ++s) {
+                while (active > cls_first[t] && sorted[active - 1].steps <= s) --active;
+                if (active == cls_first[t]) break;
+                const MgGrid& last = sorted[active - 1];
+                e = launch_class(t, last.block0 + last.nblocks, dgrids, dmap + cls_map[t], s, status, cs);
             }
+            if (mode == 1 && e == cudaSuccess) e = cudaEventRecord(c->join[t], cs);
+            if (mode == 1 && e == cudaSuccess) e = cudaStreamWaitEvent(ls, c->join[t], 0);
         }
         cudaGraph_t gr = nullptr;
         cudaGraphExec_t ex = nullptr;

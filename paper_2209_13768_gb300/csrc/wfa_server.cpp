@@ -7,9 +7,9 @@
 // when fewer than two quanta are left), all of them together in one batched
 // launch (wfa_batch_run; measured faster than stepping the large ones alone,
 // which serialises them). Requests that arrive while others run join at the next
-// tick. A second thread moves inputs to the device and results back on its
-// own stream while the ticks run; a finished request's memory is released
-// as soon as its result is on the host.
+// tick. Four more threads move inputs to the device and results back, each
+// on its own stream, while the ticks run; a finished request's memory is
+// released as soon as its result is on the host.
 #include <cuda_runtime.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -39,11 +39,11 @@ using clk = std::chrono::steady_clock;
 
 constexpr double TICK_CELLS = 64.0 * 1024 * 1024;   // cells advanced per tick, at least
 constexpr int MAX_SKIP = 8;                          // ticks a resident may be passed over
+constexpr int PREP_THREADS = 4;                      // set-up / read-back threads (host copies run in parallel)
 
 struct Req {
     long long ticket = 0;
-    wfa_request spec{};
-    std::vector<float> T0, k;
+    wfa_request spec{};   // T0_host / k_host are read when the request is set up
     wfa_grid g = nullptr;
     long long remaining = 0;
     int skipped = 0;   // ticks in a row this resident was not advanced
@@ -75,7 +75,7 @@ struct wfa_server_s {
     long long quantum = 64;
     int device = 0;
     cudaStream_t stream = nullptr;   // ticks
-    cudaStream_t prep = nullptr;     // set-up and read-back, beside the ticks
+    cudaStream_t prep[PREP_THREADS] = {};   // set-up and read-back, beside the ticks
 
     std::mutex mu;
     std::condition_variable cv_work, cv_done, cv_prep;
@@ -88,7 +88,7 @@ struct wfa_server_s {
     long long next_ticket = 1;
     int in_setup = 0;                // taken from to_setup, not yet ready
     bool stop = false, sched_done = false;
-    std::thread th, prep_th;
+    std::thread th, prep_th[PREP_THREADS];
 
     // stats
     long long submitted = 0, admitted = 0, completed = 0, rejected = 0, ticks = 0;
@@ -97,18 +97,18 @@ struct wfa_server_s {
     std::vector<double> latencies;
 
     void run();
-    void prep_loop();
-    int setup(Req* r);
+    void prep_loop(int w);
+    int setup(Req* r, cudaStream_t st);
     void finish(Req* r, bool ok, const std::string& why);
 };
 
-int wfa_server_s::setup(Req* r) {
+int wfa_server_s::setup(Req* r, cudaStream_t st) {
     const wfa_request& s = r->spec;
-    int rc = wfa_create_grid(s.nx, s.ny, s.nz, s.hx, s.hy, s.hz, s.storage, prep, &r->g);
+    int rc = wfa_create_grid(s.nx, s.ny, s.nz, s.hx, s.hy, s.hz, s.storage, st, &r->g);
     if (rc) return rc;
     for (int f = 0; f < 6 && !rc; ++f) rc = wfa_set_bc(r->g, f, s.bc_kind[f], s.bc_value[f]);
-    if (!rc) rc = wfa_set_coeffs(r->g, r->k.empty() ? nullptr : r->k.data(), s.k_uniform, s.ux, s.uy, s.uz);
-    if (!rc) rc = wfa_set_field(r->g, r->T0.data());
+    if (!rc) rc = wfa_set_coeffs(r->g, s.k_host, s.k_uniform, s.ux, s.uy, s.uz);
+    if (!rc) rc = wfa_set_field(r->g, s.T0_host);
     double dt = s.dt;
     if (!rc && !(dt > 0)) {
         double lim = 0;
@@ -116,9 +116,6 @@ int wfa_server_s::setup(Req* r) {
         dt = std::isfinite(lim) ? 0.9 * lim : 1.0;
     }
     if (!rc) rc = wfa_set_dt(r->g, dt);
-    // the host copies are no longer needed once the device holds them
-    std::vector<float>().swap(r->T0);
-    std::vector<float>().swap(r->k);
     return rc;
 }
 
@@ -140,10 +137,11 @@ void wfa_server_s::finish(Req* r, bool ok, const std::string& why) {
     cv_work.notify_all();   // memory freed: more requests may be admitted
 }
 
-// The set-up / read-back thread: inputs of admitted requests go to the
-// device and results of finished ones come back on its own stream while the
-// scheduler's ticks run, so the GPU does not wait for host transfers.
-void wfa_server_s::prep_loop() {
+// A set-up / read-back thread (one of PREP_THREADS): inputs of admitted
+// requests go to the device and results of finished ones come back, on the
+// thread's own stream, while the scheduler's ticks run, so the GPU does not
+// wait for host transfers.
+void wfa_server_s::prep_loop(int w) {
     cudaSetDevice(device);
     for (;;) {
         Req* r = nullptr;
@@ -164,12 +162,12 @@ void wfa_server_s::prep_loop() {
             }
         }
         if (retire) {
-            int rc = r->err.empty() ? wfa::grid_rebind_stream(r->g, prep) : WFA_ERR_STATE;
+            int rc = r->err.empty() ? wfa::grid_rebind_stream(r->g, prep[w]) : WFA_ERR_STATE;
             if (!rc) rc = wfa_read_field(r->g, r->spec.out_host);
             finish(r, rc == 0, rc ? (r->err.empty() ? std::string(wfa_last_error()) : r->err) : std::string());
             continue;
         }
-        int rc = setup(r);
+        int rc = setup(r, prep[w]);
         if (!rc) rc = wfa::grid_rebind_stream(r->g, stream);
         if (rc) finish(r, false, wfa_last_error());
         std::lock_guard<std::mutex> lk(mu);
@@ -282,15 +280,18 @@ int wfa_server_create(size_t hbm_budget_bytes, int max_resident, long long quant
     s->quantum = quantum ? quantum : 64;
     cudaGetDevice(&s->device);
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->prep, cudaStreamNonBlocking);
+    for (int w = 0; w < PREP_THREADS && e == cudaSuccess; ++w)
+        e = cudaStreamCreateWithFlags(&s->prep[w], cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         wfa::set_error("cudaStreamCreate failed: %s", cudaGetErrorString(e));
         if (s->stream) cudaStreamDestroy(s->stream);
+        for (cudaStream_t p : s->prep)
+            if (p) cudaStreamDestroy(p);
         delete s;
         return WFA_ERR_CUDA;
     }
     s->th = std::thread([s] { s->run(); });
-    s->prep_th = std::thread([s] { s->prep_loop(); });
+    for (int w = 0; w < PREP_THREADS; ++w) s->prep_th[w] = std::thread([s, w] { s->prep_loop(w); });
     *out = s;
     return WFA_OK;
 }
@@ -305,9 +306,6 @@ int wfa_server_submit(wfa_server s, const wfa_request* r, long long* ticket) {
     q->spec = *r;
     q->bytes = device_bytes(*r);
     q->remaining = r->steps;
-    const size_t n = (size_t)r->nx * r->ny * r->nz;
-    q->T0.assign(r->T0_host, r->T0_host + n);
-    if (r->k_host) q->k.assign(r->k_host, r->k_host + n);
     q->t_submit = clk::now();
     std::lock_guard<std::mutex> lk(s->mu);
     if (q->bytes > s->budget) {
@@ -404,10 +402,11 @@ int wfa_server_destroy(wfa_server s) {
         std::lock_guard<std::mutex> lk(s->mu);
         s->cv_prep.notify_all();
     }
-    if (s->prep_th.joinable()) s->prep_th.join();
+    for (std::thread& t : s->prep_th)
+        if (t.joinable()) t.join();
     for (auto& kv : s->all) delete kv.second;
     cudaStreamDestroy(s->stream);
-    cudaStreamDestroy(s->prep);
+    for (cudaStream_t p : s->prep) cudaStreamDestroy(p);
     delete s;
     return WFA_OK;
 }
