@@ -57,6 +57,10 @@ struct MgGrid {
     int nblocks;          // units: ceil(ncols * nch / MG_THREADS)
     int block0;           // first unit of the grid in a per-round launch of its class
     int unit0;            // first unit of the grid in the persistent kernel's table
+    // uniform k, per-round launches: a branch-free main pass, then the
+    // boundary cells and the periodic copies in launches of their own
+    int nbu, bu0;         // boundary-cell units (256 cells) and the first in its class
+    int ntw[3], tw0[3];   // periodic-copy units per axis and the first in its class
     int pad;
     long long steps;
 };
@@ -96,6 +100,81 @@ __global__ void __launch_bounds__(MG_THREADS, MgOcc<KVAR, GHOST>::blocks)
     mg_unit<S, KVAR, ADV, GHOST, false>(sg, (int)blockIdx.x - sg.block0, step, status);
 }
 
+// Uniform k, per-round launches: every cell takes the interior formula
+// (branch-free, the occupancy of the single-grid main pass) ...
+template <typename S>
+__global__ void __launch_bounds__(MG_THREADS, (ColOcc<false>::blocks))
+    mg_sweep_main(const MgGrid* __restrict__ grids, const int* __restrict__ block_grid, long long step) {
+    __shared__ MgGrid sg;
+    load_desc(&sg, &grids[block_grid[blockIdx.x]]);
+    __syncthreads();
+    const int p = ((int)blockIdx.x - sg.block0) * MG_THREADS + (int)threadIdx.x;
+    if (p >= sg.ncols * sg.nch) return;
+    const int chunk = p / sg.ncols, col = p - chunk * sg.ncols;
+    const int gx = 4 * (col % sg.ncx), gy = col / sg.ncx;
+    const int z0 = chunk * sg.zchunk;
+    const int z1 = min(z0 + sg.zchunk, sg.c.n[2]);
+    col_run<S, false, false, false, ColOcc<false>::unroll, true, true>(
+        sg.c, (const S*)sg.tb[step & 1], (S*)sg.tb[(step + 1) & 1], nullptr, nullptr, gx, gy, z0, z1);
+}
+
+// ... then the outer cell layer of every non-periodic face recomputed with
+// the boundary conditions (the cells of a face in 256-cell units) ...
+template <typename S>
+__global__ void __launch_bounds__(MG_THREADS)
+    mg_boundary(const MgGrid* __restrict__ grids, const int* __restrict__ unit_grid, long long step, int* status) {
+    __shared__ MgGrid sg;
+    load_desc(&sg, &grids[unit_grid[blockIdx.x]]);
+    __syncthreads();
+    const SweepCoef& c = sg.c;
+    long long u = (long long)((int)blockIdx.x - sg.bu0) * MG_THREADS + threadIdx.x;
+    int pos[3] = {0, 0, 0};
+    bool found = false;
+    for (int ax = 0; ax < 3 && !found; ++ax) {
+        if (c.periodic[ax]) continue;
+        const int b = ax == 0 ? 1 : 0, d = ax == 2 ? 1 : 2;
+        const long long plane = (long long)c.n[b] * c.n[d];
+        if (u >= 2 * plane) {
+            u -= 2 * plane;
+            continue;
+        }
+        pos[ax] = u >= plane ? c.n[ax] - 1 : 0;
+        u %= plane;
+        pos[b] = (int)(u % c.n[b]);
+        pos[d] = (int)(u / c.n[b]);
+        found = true;
+    }
+    if (!found) return;   // past the last face
+    const S* tin = (const S*)sg.tb[step & 1];
+    const long long i = (long long)pos[2] * c.sz + (long long)pos[1] * c.sy + pos[0];
+    ((S*)sg.tb[(step + 1) & 1])[i] = from_f32<S>(general_cell<S, false>(c, tin, nullptr, i, pos[0], pos[1], pos[2], status));
+}
+
+// ... then the periodic copies of one axis (x, y, z in turn: corners come
+// out right), over the full extent of the other two axes.
+template <typename S>
+__global__ void __launch_bounds__(MG_THREADS)
+    mg_twins(const MgGrid* __restrict__ grids, const int* __restrict__ unit_grid, long long step, int ax) {
+    __shared__ MgGrid sg;
+    load_desc(&sg, &grids[unit_grid[blockIdx.x]]);
+    __syncthreads();
+    const SweepCoef& c = sg.c;
+    const int b = ax == 0 ? 1 : 0, d = ax == 2 ? 1 : 2;
+    const long long eb = c.n[b] + 2 * HALO, ed = c.n[d] + 2 * HALO;
+    const long long t = (long long)((int)blockIdx.x - sg.tw0[ax]) * MG_THREADS + threadIdx.x;
+    if (t >= 2LL * HALO * eb * ed) return;
+    const long long st[3] = {1, c.sy, c.sz};
+    const int k = (int)(t % (2 * HALO));
+    const long long rest = t / (2 * HALO);
+    const int pb = (int)(rest % eb) - HALO, pd = (int)(rest / eb) - HALO;
+    const int dst = k < HALO ? k - HALO : c.n[ax] + (k - HALO);
+    int src = dst % c.n[ax];
+    if (src < 0) src += c.n[ax];
+    S* origin = (S*)sg.tb[(step + 1) & 1];
+    const long long other = pb * st[b] + pd * st[d];
+    origin[other + dst * st[ax]] = origin[other + src * st[ax]];
+}
+
 template <typename S>
 cudaError_t launch_kind(int kind, int blocks, const MgGrid* grids, const int* block_grid, long long step, int* status,
                         cudaStream_t st) {
@@ -113,6 +192,18 @@ cudaError_t launch_class(int cls, int blocks, const MgGrid* grids, const int* bl
                          cudaStream_t st) {
     return cls < NKIND ? launch_kind<float>(cls, blocks, grids, block_grid, step, status, st)
                        : launch_kind<__nv_bfloat16>(cls - NKIND, blocks, grids, block_grid, step, status, st);
+}
+
+// One round of a uniform-k class: main pass, boundary cells, periodic copies
+// (block counts 0 skip a launch).
+template <typename S>
+cudaError_t uniform_round(int blocks, int bblocks, const int tblocks[3], const MgGrid* grids, const int* map,
+                          const int* bmap, const int* const tmap[3], long long step, int* status, cudaStream_t st) {
+    mg_sweep_main<S><<<blocks, MG_THREADS, 0, st>>>(grids, map, step);
+    if (bblocks > 0) mg_boundary<S><<<bblocks, MG_THREADS, 0, st>>>(grids, bmap, step, status);
+    for (int ax = 0; ax < 3; ++ax)
+        if (tblocks[ax] > 0) mg_twins<S><<<tblocks[ax], MG_THREADS, 0, st>>>(grids, tmap[ax], step, ax);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------- persistent launch
@@ -537,34 +628,63 @@ extern "C" int wfa_batch_run(wfa_grid* gs, const long long* steps, int count) {
         for (int t = NCLASS - 1; t >= 0; --t) cls_first[t] = std::min(cls_first[t], cls_first[t + 1]);
         std::vector<MgGrid> sorted(ng);
         long long total_blocks = 0;
+        auto uniform_class = [](int t) { return t % NKIND == 0; };
         for (int t = 0; t < NCLASS; ++t) {
-            long long b0 = 0;
+            long long b0 = 0, bu = 0, tw[3] = {0, 0, 0};
             for (int j = cls_first[t]; j < cls_first[t + 1]; ++j) {
-                sorted[j] = mg[idx[j]];
-                sorted[j].cls = t;
-                sorted[j].block0 = (int)b0;
-                b0 += sorted[j].nblocks;
+                MgGrid& m = sorted[j];
+                m = mg[idx[j]];
+                m.cls = t;
+                m.block0 = (int)b0;
+                b0 += m.nblocks;
+                if (uniform_class(t)) {   // boundary-cell and periodic-copy units
+                    long long bcells = 0;
+                    for (int ax = 0; ax < 3; ++ax) {
+                        const int b = ax == 0 ? 1 : 0, d = ax == 2 ? 1 : 2;
+                        if (!m.c.periodic[ax]) bcells += 2LL * m.c.n[b] * m.c.n[d];
+                        const long long twins =
+                            m.c.periodic[ax] ? 2LL * HALO * (m.c.n[b] + 2 * HALO) * (m.c.n[d] + 2 * HALO) : 0;
+                        m.ntw[ax] = (int)((twins + MG_THREADS - 1) / MG_THREADS);
+                        m.tw0[ax] = (int)tw[ax];
+                        tw[ax] += m.ntw[ax];
+                    }
+                    m.nbu = (int)((bcells + MG_THREADS - 1) / MG_THREADS);
+                    m.bu0 = (int)bu;
+                    bu += m.nbu;
+                }
             }
-            if (b0 > (1LL << 30)) {
+            if (b0 > (1LL << 30) || bu > (1LL << 30) || tw[0] > (1LL << 30) || tw[1] > (1LL << 30) ||
+                tw[2] > (1LL << 30)) {
                 set_error("wfa_batch_run: too many blocks in one launch");
                 return WFA_ERR_ARG;
             }
-            total_blocks += b0;
+            total_blocks += b0 + bu + tw[0] + tw[1] + tw[2];
         }
-        // device tables: the descriptors, then per class the block -> grid map
+        // device tables: the descriptors, then per class the block -> grid
+        // maps (main units; for uniform k also boundary and copy units)
         const size_t grid_bytes = ((size_t)ng * sizeof(MgGrid) + 255) / 256 * 256;
         const size_t bytes = grid_bytes + (size_t)total_blocks * sizeof(int);
         rc = reserve(c, bytes, 0, 0);
         if (rc) return rc;
         memcpy(c->host, sorted.data(), (size_t)ng * sizeof(MgGrid));
         int* bmap = reinterpret_cast<int*>(c->host + grid_bytes);
-        long long cls_map[NCLASS];   // offset of each class's block map (ints)
+        long long cls_map[NCLASS], cls_bmap[NCLASS], cls_tmap[NCLASS][3];   // offsets (ints)
         {
             long long o = 0;
             for (int t = 0; t < NCLASS; ++t) {
                 cls_map[t] = o;
                 for (int j = cls_first[t]; j < cls_first[t + 1]; ++j)
                     for (int b = 0; b < sorted[j].nblocks; ++b) bmap[o++] = j;
+                cls_bmap[t] = o;
+                if (uniform_class(t))
+                    for (int j = cls_first[t]; j < cls_first[t + 1]; ++j)
+                        for (int b = 0; b < sorted[j].nbu; ++b) bmap[o++] = j;
+                for (int ax = 0; ax < 3; ++ax) {
+                    cls_tmap[t][ax] = o;
+                    if (uniform_class(t))
+                        for (int j = cls_first[t]; j < cls_first[t + 1]; ++j)
+                            for (int b = 0; b < sorted[j].ntw[ax]; ++b) bmap[o++] = j;
+                }
             }
         }
         // mode "rounds": captured on a private stream into one graph, launched
@@ -596,11 +716,23 @@ extern "C" int wfa_batch_run(wfa_grid* gs, const long long* steps, int count) {
             cudaStream_t cs = mode == 1 ? c->cls_stream[t] : ls;
             if (mode == 1) e = cudaStreamWaitEvent(cs, c->fork, 0);
             int active = cls_first[t + 1];
+            const int* tmaps[3] = {dmap + cls_tmap[t][0], dmap + cls_tmap[t][1], dmap + cls_tmap[t][2]};
             for (long long s = 0; s < max_steps && e == cudaSuccess; ++s) {
                 while (active > cls_first[t] && sorted[active - 1].steps <= s) --active;
                 if (active == cls_first[t]) break;
                 const MgGrid& last = sorted[active - 1];
-                e = launch_class(t, last.block0 + last.nblocks, dgrids, dmap + cls_map[t], s, status, cs);
+                if (uniform_class(t)) {
+                    const int tblocks[3] = {last.tw0[0] + last.ntw[0], last.tw0[1] + last.ntw[1],
+                                            last.tw0[2] + last.ntw[2]};
+                    e = t < NKIND ? uniform_round<float>(last.block0 + last.nblocks, last.bu0 + last.nbu, tblocks,
+                                                         dgrids, dmap + cls_map[t], dmap + cls_bmap[t], tmaps, s,
+                                                         status, cs)
+                                  : uniform_round<__nv_bfloat16>(last.block0 + last.nblocks, last.bu0 + last.nbu,
+                                                                 tblocks, dgrids, dmap + cls_map[t],
+                                                                 dmap + cls_bmap[t], tmaps, s, status, cs);
+                } else {
+                    e = launch_class(t, last.block0 + last.nblocks, dgrids, dmap + cls_map[t], s, status, cs);
+                }
             }
             if (mode == 1 && e == cudaSuccess) e = cudaEventRecord(c->join[t], cs);
             if (mode == 1 && e == cudaSuccess) e = cudaStreamWaitEvent(ls, c->join[t], 0);
