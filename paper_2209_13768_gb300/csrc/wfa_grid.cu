@@ -352,6 +352,12 @@ int refresh_halo(wfa_grid_s* g, int buf) {
 
 // --------------------------------------------------------------- reductions --
 constexpr int RED_BLOCKS = 304;
+// the stability passes are latency-bound (divisions, seven k reads a cell):
+// more warps per SM; their partials fit the 4096-double scratch below the
+// word kept for the k check (index 4095)
+constexpr int RATE_BLOCKS = 152 * 8;
+constexpr int RATE_P2 = 1280;
+static_assert(RATE_P2 > RATE_BLOCKS + 1 && RATE_P2 + RATE_BLOCKS < 4095, "scratch layout");
 constexpr int RED_THREADS = 256;
 
 template <typename S>
@@ -554,7 +560,9 @@ __global__ void __launch_bounds__(RED_THREADS) rate_cand_kernel(const float* __r
 __global__ void __launch_bounds__(512) finish_max_kernel(const double* __restrict__ partials, int n,
                                                          double* __restrict__ out) {
     __shared__ double sh[512];
-    sh[threadIdx.x] = threadIdx.x < n ? partials[threadIdx.x] : 0.0;
+    double m = 0.0;
+    for (int i = threadIdx.x; i < n; i += 512) m = fmax(m, partials[i]);
+    sh[threadIdx.x] = m;
     __syncthreads();
     for (int s = 256; s > 0; s >>= 1) {
         if (threadIdx.x < s) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + s]);
@@ -916,17 +924,18 @@ int wfa_stability_dt(wfa_grid g, double* dt_max) {
             const float* ko = g->k + domain_offset(g);
             double* part = g->d_partials;
             if (rate32_applies(r)) {
-                rate32_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, g->stream>>>(ko, r, part);
-                finish_max_kernel<<<1, 512, 0, g->stream>>>(part, RED_BLOCKS, part + RED_BLOCKS);
-                rate_cand_kernel<<<RED_BLOCKS, RED_THREADS, 0, g->stream>>>(ko, r, part + RED_BLOCKS,
-                                                                            part + 2 * RED_BLOCKS);
-                finish_max_kernel<<<1, 512, 0, g->stream>>>(part + 2 * RED_BLOCKS, RED_BLOCKS, part + RED_BLOCKS + 1);
+                // partials of pass 1 at [0, RATE_BLOCKS), its maximum at RATE_BLOCKS,
+                // partials of pass 2 at [RATE_P2, RATE_P2 + RATE_BLOCKS), the result at RATE_BLOCKS + 1
+                rate32_partial_kernel<<<RATE_BLOCKS, RED_THREADS, 0, g->stream>>>(ko, r, part);
+                finish_max_kernel<<<1, 512, 0, g->stream>>>(part, RATE_BLOCKS, part + RATE_BLOCKS);
+                rate_cand_kernel<<<RATE_BLOCKS, RED_THREADS, 0, g->stream>>>(ko, r, part + RATE_BLOCKS, part + RATE_P2);
+                finish_max_kernel<<<1, 512, 0, g->stream>>>(part + RATE_P2, RATE_BLOCKS, part + RATE_BLOCKS + 1);
             } else {
-                rate_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, g->stream>>>(ko, r, part + 2 * RED_BLOCKS);
-                finish_max_kernel<<<1, 512, 0, g->stream>>>(part + 2 * RED_BLOCKS, RED_BLOCKS, part + RED_BLOCKS + 1);
+                rate_partial_kernel<<<RATE_BLOCKS, RED_THREADS, 0, g->stream>>>(ko, r, part + RATE_P2);
+                finish_max_kernel<<<1, 512, 0, g->stream>>>(part + RATE_P2, RATE_BLOCKS, part + RATE_BLOCKS + 1);
             }
             WFA_CUDA(cudaGetLastError());
-            WFA_CUDA(cudaMemcpyAsync(g->h_result, part + RED_BLOCKS + 1, sizeof(double), cudaMemcpyDeviceToHost,
+            WFA_CUDA(cudaMemcpyAsync(g->h_result, part + RATE_BLOCKS + 1, sizeof(double), cudaMemcpyDeviceToHost,
                                      g->stream));
             WFA_CUDA(cudaStreamSynchronize(g->stream));
             dmax = g->h_result[0];
