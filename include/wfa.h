@@ -68,7 +68,9 @@ enum wfa_face { WFA_XLO = 0, WFA_XHI = 1, WFA_YLO = 2, WFA_YHI = 3, WFA_ZLO = 4,
  * Sec. 2.1, uniform Cartesian grid). storage: WFA_F32 or WFA_BF16 (field stored
  * in bf16, arithmetic in fp32, rounded to nearest-even after every step).
  * cuda_stream: a cudaStream_t (NULL = the legacy default stream).
- * Each edge must be >= 2 and the cell count <= 2^40. Boundary faces start as
+ * Each edge must be >= 2, the cell count <= 2^40, and 16 (a + 16)(b + 16) <
+ * 2^32 for every pair of edges a, b (a face with its halo layers is indexed in
+ * 32 bits). Boundary faces start as
  * zero-flux; the field starts at 0. Errors: WFA_ERR_ARG, WFA_ERR_OOM, WFA_ERR_CUDA. */
 int wfa_create_grid(int nx, int ny, int nz, double hx, double hy, double hz, int storage,
                     void* cuda_stream, wfa_grid* out);

@@ -654,6 +654,11 @@ int wfa_create_grid(int nx, int ny, int nz, double hx, double hy, double hz, int
         return fail(WFA_ERR_ARG, "cell sizes must be finite and > 0");
     if (storage != WFA_F32 && storage != WFA_BF16) return fail(WFA_ERR_ARG, "storage must be WFA_F32 or WFA_BF16");
     if ((double)nx * ny * nz > (double)(1LL << 40)) return fail(WFA_ERR_ARG, "grid too large");
+    // face-wise kernels index a padded face (with its 16 halo layers) in 32 bits
+    const double pfx = (double)(nx + 16), pfy = (double)(ny + 16), pfz = (double)(nz + 16);
+    if (16.0 * std::max(pfx * pfy, std::max(pfx * pfz, pfy * pfz)) >= 4294967296.0)
+        return fail(WFA_ERR_ARG, "a face of %d x %d x %d cells is too large (padded face x 16 must stay below 2^32)",
+                    nx, ny, nz);
     wfa_grid_s* g = new (std::nothrow) wfa_grid_s();
     if (!g) return fail(WFA_ERR_OOM, "host allocation failed");
     g->n[0] = nx; g->n[1] = ny; g->n[2] = nz;

@@ -302,30 +302,24 @@ __global__ void __launch_bounds__(256, (ColOcc<KVAR, INL>::blocks)) sweep_col(co
 }
 
 // Boundary cells (the outer layer on every non-periodic face): recomputed
-// from the input field with the boundary conditions, one thread per cell
-// (cells on an edge are visited once per face; they get the same value).
+// from the input field with the boundary conditions. blockIdx.y is the face
+// (-x, +x, -y, +y, -z, +z; periodic axes have none); the threads of a block
+// walk the face's plane x-fastest where the face has an x extent, so y and z
+// faces are read and written in whole rows (cells on an edge are visited once
+// per face and get the same value). Plane sizes fit 32-bit arithmetic (the
+// caller checks).
 template <typename S, bool KVAR>
-__global__ void __launch_bounds__(256) boundary_fix(const __grid_constant__ SweepArgs a, long long total) {
+__global__ void __launch_bounds__(256) boundary_fix(const __grid_constant__ SweepArgs a) {
     const SweepCoef& c = a.c;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        long long u = t;
-        int pos[3] = {0, 0, 0};
-        for (int ax = 0; ax < 3; ++ax) {
-            if (c.periodic[ax]) continue;
-            const int b = ax == 0 ? 1 : 0, d = ax == 2 ? 1 : 2;
-            const long long face = 2LL * c.n[b] * c.n[d];
-            if (u >= face) {
-                u -= face;
-                continue;
-            }
-            const long long plane = (long long)c.n[b] * c.n[d];
-            pos[ax] = u >= plane ? c.n[ax] - 1 : 0;
-            u %= plane;
-            pos[b] = (int)(u % c.n[b]);
-            pos[d] = (int)(u / c.n[b]);
-            break;
-        }
+    const int f = blockIdx.y, ax = f >> 1;
+    if (c.periodic[ax]) return;
+    const int b = ax == 0 ? 1 : 0, d = ax == 2 ? 1 : 2;
+    const unsigned nb = (unsigned)c.n[b], plane = nb * (unsigned)c.n[d];
+    int pos[3];
+    pos[ax] = (f & 1) ? c.n[ax] - 1 : 0;
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < plane; t += gridDim.x * blockDim.x) {
+        pos[b] = (int)(t % nb);
+        pos[d] = (int)(t / nb);
         const long long i = (long long)pos[2] * c.sz + (long long)pos[1] * c.sy + pos[0];
         const float v = general_cell<S, KVAR>(c, (const S*)a.tin, a.rk, i, pos[0], pos[1], pos[2], a.status);
         ((S*)a.tout)[i] = from_f32<S>(v);
@@ -334,23 +328,68 @@ __global__ void __launch_bounds__(256) boundary_fix(const __grid_constant__ Swee
 
 // Periodic halo copies of one axis, over the full extent of the other two
 // (their halos included, so corners are right when the axes go x, y, z).
+// Element order: for x copies the 16 halo columns of a row are consecutive,
+// for y and z copies whole padded rows are, so loads and stores coalesce.
+// Totals fit 32-bit arithmetic (the caller checks).
 template <typename S>
 __global__ void __launch_bounds__(256) twin_copy(const __grid_constant__ SweepCoef c, S* origin, int ax) {
-    const int b = ax == 0 ? 1 : 0, d = ax == 2 ? 1 : 2;
-    const long long eb = c.n[b] + 2 * HALO, ed = c.n[d] + 2 * HALO;
-    const long long total = 2LL * HALO * eb * ed;
-    const long long st[3] = {1, c.sy, c.sz};
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(t % (2 * HALO));   // halo layer: 0..HALO-1 below, HALO..2 HALO-1 above
-        const long long rest = t / (2 * HALO);
-        const int pb = (int)(rest % eb) - HALO, pd = (int)(rest / eb) - HALO;
-        const int dst = k < HALO ? k - HALO : c.n[ax] + (k - HALO);
-        int src = dst % c.n[ax];
-        if (src < 0) src += c.n[ax];
-        const long long other = pb * st[b] + pd * st[d];
-        origin[other + dst * st[ax]] = origin[other + src * st[ax]];
+    const unsigned ex = c.n[0] + 2 * HALO, ey = c.n[1] + 2 * HALO, ez = c.n[2] + 2 * HALO;
+    const unsigned total = 2u * HALO * (ax == 0 ? ey * ez : ex * (ax == 1 ? ez : ey));
+    const int n = c.n[ax];
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        int p[3], k;
+        if (ax == 0) {            // (layer, y, z)
+            k = (int)(t & (2 * HALO - 1));
+            const unsigned r = t / (2 * HALO);
+            p[1] = (int)(r % ey) - HALO;
+            p[2] = (int)(r / ey) - HALO;
+        } else if (ax == 1) {     // (x, layer, z)
+            p[0] = (int)(t % ex) - HALO;
+            const unsigned r = t / ex;
+            k = (int)(r & (2 * HALO - 1));
+            p[2] = (int)(r / (2 * HALO)) - HALO;
+        } else {                  // (x, y, layer)
+            p[0] = (int)(t % ex) - HALO;
+            const unsigned r = t / ex;
+            p[1] = (int)(r % ey) - HALO;
+            k = (int)(r / ey);
+        }
+        const int dst = k < HALO ? k - HALO : n + (k - HALO);
+        int src = dst % n;
+        if (src < 0) src += n;
+        p[ax] = dst;
+        const long long od = (long long)p[2] * c.sz + (long long)p[1] * c.sy + p[0];
+        p[ax] = src;
+        const long long os = (long long)p[2] * c.sz + (long long)p[1] * c.sy + p[0];
+        origin[od] = origin[os];
     }
+}
+
+// After a branch-free main pass: the boundary cells (unless the ghost layers
+// hold the faces), then the periodic copies of the written buffer.
+template <typename S, bool KVAR>
+cudaError_t fix_and_twins(const SweepArgs& a, cudaStream_t st, int nsm) {
+    long long plane = 0;   // the largest face
+    for (int ax = 0; ax < 3; ++ax) {
+        const int b = ax == 0 ? 1 : 0, d = ax == 2 ? 1 : 2;
+        if (!a.c.periodic[ax]) plane = std::max(plane, (long long)a.c.n[b] * a.c.n[d]);
+    }
+    if (plane > 0 && !a.c.halo_bc) {
+        const int nb = (int)std::min<long long>((plane + 255) / 256, (long long)nsm * 2);
+        boundary_fix<S, KVAR><<<dim3(nb, 6), 256, 0, st>>>(a);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    for (int ax = 0; ax < 3; ++ax) {
+        if (!a.c.periodic[ax]) continue;
+        const int b = ax == 0 ? 1 : 0, d = ax == 2 ? 1 : 2;
+        const long long total = 2LL * HALO * (a.c.n[b] + 2 * HALO) * (a.c.n[d] + 2 * HALO);
+        const int nb = (int)std::min<long long>((total + 255) / 256, (long long)nsm * 8);
+        twin_copy<S><<<nb, 256, 0, st>>>(a.c, (S*)a.tout, ax);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <typename S, bool KVAR>
@@ -384,28 +423,7 @@ cudaError_t col_launch(const SweepArgs& a_in, cudaStream_t st, int nsm, const cu
     if (ev) cudaEventRecord(ev[1], st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || inl) return e;   // in place: nothing after the pass
-    long long bcells = 0;
-    for (int ax = 0; ax < 3; ++ax) {
-        if (a.c.periodic[ax]) continue;
-        const int b = ax == 0 ? 1 : 0, d = ax == 2 ? 1 : 2;
-        bcells += 2LL * a.c.n[b] * a.c.n[d];
-    }
-    if (bcells > 0 && !a.c.halo_bc) {
-        const int nb = (int)std::min<long long>((bcells + 255) / 256, (long long)nsm * 8);
-        boundary_fix<S, KVAR><<<nb, 256, 0, st>>>(a, bcells);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    for (int ax = 0; ax < 3; ++ax) {
-        if (!a.c.periodic[ax]) continue;
-        const int b = ax == 0 ? 1 : 0, d = ax == 2 ? 1 : 2;
-        const long long total = 2LL * HALO * (a.c.n[b] + 2 * HALO) * (a.c.n[d] + 2 * HALO);
-        const int nb = (int)std::min<long long>((total + 255) / 256, (long long)nsm * 8);
-        twin_copy<S><<<nb, 256, 0, st>>>(a.c, (S*)a.tout, ax);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    return fix_and_twins<S, KVAR>(a, st, nsm);
 }
 
 }  // namespace wfa
