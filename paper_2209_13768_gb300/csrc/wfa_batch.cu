@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(MG_THREADS, MgOcc<KVAR, GHOST>::blocks)
 // Uniform k, per-round launches: every cell takes the interior formula
 // (branch-free, the occupancy of the single-grid main pass) ...
 template <typename S>
-__global__ void __launch_bounds__(MG_THREADS, (ColOcc<false>::blocks))
+__global__ void __launch_bounds__(MG_THREADS, (ColOcc<false, false, sizeof(S)>::blocks))
     mg_sweep_main(const MgGrid* __restrict__ grids, const int* __restrict__ block_grid, long long step) {
     __shared__ MgGrid sg;
     load_desc(&sg, &grids[block_grid[blockIdx.x]]);
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(MG_THREADS, (ColOcc<false>::blocks))
     const int gx = 4 * (col % sg.ncx), gy = col / sg.ncx;
     const int z0 = chunk * sg.zchunk;
     const int z1 = min(z0 + sg.zchunk, sg.c.n[2]);
-    col_run<S, false, false, false, ColOcc<false>::unroll, true, true>(
+    col_run<S, false, false, false, ColOcc<false, false, sizeof(S)>::unroll, true, true>(
         sg.c, (const S*)sg.tb[step & 1], (S*)sg.tb[(step + 1) & 1], nullptr, nullptr, gx, gy, z0, z1);
 }
 

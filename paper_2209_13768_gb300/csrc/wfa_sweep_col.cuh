@@ -140,9 +140,10 @@ struct ColNb {
 // loads plane z + 1, so most plane loads hit L2 (measured at 512^3: +11% with
 // per-cell k, +7% with uniform k). Register-level prefetch was slower: it
 // costs the occupancy.
-template <bool KVAR, bool INL = false> struct ColOcc {
+template <bool KVAR, bool INL = false, int ES = 4> struct ColOcc {
     static constexpr int blocks = INL ? (KVAR ? 3 : 4) : (KVAR ? 4 : 6);
-    static constexpr int unroll = KVAR ? 1 : 2;
+    // measured: fp32 uniform k prefers the z loop unrolled twice, bf16 not
+    static constexpr int unroll = (KVAR || ES == 2) ? 1 : 2;
 };
 
 // One thread's work: cells (gx .. gx+3, gy) of planes [z0, z1), one step,
@@ -290,14 +291,14 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
 // branch-free main pass, followed by boundary_fix (unless the ghost layers
 // hold the faces) and twin_copy (fastest for large grids).
 template <typename S, bool KVAR, bool ADV, bool INL>
-__global__ void __launch_bounds__(256, (ColOcc<KVAR, INL>::blocks)) sweep_col(const __grid_constant__ SweepArgs a) {
+__global__ void __launch_bounds__(256, (ColOcc<KVAR, INL, sizeof(S)>::blocks)) sweep_col(const __grid_constant__ SweepArgs a) {
     const SweepCoef& c = a.c;
     const int gx = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
     const int gy = blockIdx.y * blockDim.y + threadIdx.y;
     if (gx >= c.n[0] || gy >= c.n[1]) return;
     const int z0 = blockIdx.z * a.zchunk;
     const int z1 = min(z0 + a.zchunk, c.n[2]);
-    col_run<S, KVAR, ADV, false, ColOcc<KVAR, INL>::unroll, !INL, true>(c, (const S*)a.tin, (S*)a.tout, a.rk,
+    col_run<S, KVAR, ADV, false, ColOcc<KVAR, INL, sizeof(S)>::unroll, !INL, true>(c, (const S*)a.tin, (S*)a.tout, a.rk,
                                                                          a.status, gx, gy, z0, z1);
 }
 
