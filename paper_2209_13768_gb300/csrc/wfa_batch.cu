@@ -13,9 +13,11 @@
 // Default ("rounds"): every round is one launch per class of grid (storage
 // type x conductivity mode x advection x ghost-layer faces) over the active
 // units, one block per unit; the whole sequence is captured into one CUDA
-// graph, one branch per class (classes share no grid), and launched once, so
-// the launch boundary is the barrier between rounds and nothing inside a
-// kernel waits on another block.
+// graph and launched once, so the launch boundary is the barrier between
+// rounds and nothing inside a kernel waits on another block. Grids are
+// independent, so the graph has a branch per class and group of grids
+// (a class of many grids is dealt round-robin into up to four groups): one
+// branch's round fills the GPU while another's drains.
 // WFA_BATCH_MODE=persistent runs the rounds in one persistent kernel instead
 // (replayed as a graph: descriptor copy, counter reset, kernel): every block
 // the GPU can hold is launched, the blocks take the active units of round r
@@ -45,6 +47,11 @@ constexpr int MG_THREADS = 256;
 // last two with every boundary face in the ghost layers}
 constexpr int NKIND = 5;
 constexpr int NCLASS = 2 * NKIND;
+// per-round launches: the grids of a class are dealt round-robin (by step
+// count) into NGROUP groups, each its own branch of the graph, so one
+// group's round can fill the GPU while another's drains
+constexpr int NGROUP = 4;
+constexpr int NBRANCH = NCLASS * NGROUP;
 
 struct MgGrid {
     SweepCoef c;
@@ -388,8 +395,8 @@ struct BatchCtx {
     PLayout lay{};
     unsigned* count = nullptr;         // barrier arrivals, the status word, units handed out
     cudaStream_t cap_stream = nullptr; // where per-round launches are captured
-    cudaStream_t cls_stream[NCLASS] = {};   // one branch per class inside the capture
-    cudaEvent_t fork = nullptr, join[NCLASS] = {};
+    cudaStream_t cls_stream[NBRANCH] = {};   // one branch per (class, group) inside the capture
+    cudaEvent_t fork = nullptr, join[NBRANCH] = {};
     int blocks[NCLASS + 1] = {};       // launch size per persistent kernel (index cls + 1)
     cudaGraphExec_t exec[NCLASS + 1] = {};
 };
@@ -535,10 +542,10 @@ extern "C" int wfa_batch_run(wfa_grid* gs, const long long* steps, int count) {
         cls[k] = (g->storage == WFA_BF16 ? NKIND : 0) + kind;
         b.ncx = (g->n[0] + 3) / 4;
         b.ncols = b.ncx * g->n[1];
-        // z chunks of about 16 planes, shorter (down to 4) while a grid has
+        // z chunks of about 8 planes (measured faster than 16 for these small
+        // grids: more units in flight), shorter (down to 4) while a grid has
         // fewer pairs than a block has threads
-        const int nz = g->n[2];
-        int nch = std::max((nz + 15) / 16, (MG_THREADS + b.ncols - 1) / b.ncols);
+        int nch = std::max((nz + 7) / 8, (MG_THREADS + b.ncols - 1) / b.ncols);
         nch = std::max(1, std::min(nch, nz / 4));
         b.zchunk = (nz + nch - 1) / nch;
         b.nch = (nz + b.zchunk - 1) / b.zchunk;
@@ -616,25 +623,40 @@ extern "C" int wfa_batch_run(wfa_grid* gs, const long long* steps, int count) {
         rc = check_status(gs[order[0]]);
         if (rc) return rc;
     } else {
-        // one launch per round and class; each class sorted by step count (descending)
+        // one launch per round and branch (class x group); each branch sorted
+        // by step count (descending)
         std::vector<int> idx(ng);
         for (int k = 0; k < ng; ++k) idx[k] = k;
         std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
             return cls[a] != cls[b] ? cls[a] < cls[b] : mg[a].steps > mg[b].steps;
         });
-        int cls_first[NCLASS + 1];   // sorted positions of each class
-        for (int t = 0; t <= NCLASS; ++t) cls_first[t] = ng;
-        for (int j = ng - 1; j >= 0; --j) cls_first[cls[idx[j]]] = j;
-        for (int t = NCLASS - 1; t >= 0; --t) cls_first[t] = std::min(cls_first[t], cls_first[t + 1]);
+        // groups per class: one per 32 grids, at most NGROUP (a few large
+        // batches gain from overlapping rounds; a tick of the server, rebuilt
+        // every time, would only pay for more graph nodes)
+        int ncls[NCLASS] = {};
+        for (int k = 0; k < ng; ++k) ++ncls[cls[k]];
+        std::vector<int> br(ng);   // branch of each grid
+        for (int j = 0, rank = 0; j < ng; ++j) {
+            rank = (j > 0 && cls[idx[j]] == cls[idx[j - 1]]) ? rank + 1 : 0;
+            const int groups = std::max(1, std::min(NGROUP, ncls[cls[idx[j]]] / 32));
+            br[idx[j]] = cls[idx[j]] * NGROUP + rank % groups;
+        }
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+            return br[a] != br[b] ? br[a] < br[b] : mg[a].steps > mg[b].steps;
+        });
+        int cls_first[NBRANCH + 1];   // sorted positions of each branch
+        for (int t = 0; t <= NBRANCH; ++t) cls_first[t] = ng;
+        for (int j = ng - 1; j >= 0; --j) cls_first[br[idx[j]]] = j;
+        for (int t = NBRANCH - 1; t >= 0; --t) cls_first[t] = std::min(cls_first[t], cls_first[t + 1]);
         std::vector<MgGrid> sorted(ng);
         long long total_blocks = 0;
-        auto uniform_class = [](int t) { return t % NKIND == 0; };
-        for (int t = 0; t < NCLASS; ++t) {
+        auto uniform_class = [](int t) { return (t / NGROUP) % NKIND == 0; };   // t: a branch
+        for (int t = 0; t < NBRANCH; ++t) {
             long long b0 = 0, bu = 0, tw[3] = {0, 0, 0};
             for (int j = cls_first[t]; j < cls_first[t + 1]; ++j) {
                 MgGrid& m = sorted[j];
                 m = mg[idx[j]];
-                m.cls = t;
+                m.cls = t / NGROUP;
                 m.block0 = (int)b0;
                 b0 += m.nblocks;
                 if (uniform_class(t)) {   // boundary-cell and periodic-copy units
@@ -668,10 +690,10 @@ extern "C" int wfa_batch_run(wfa_grid* gs, const long long* steps, int count) {
         if (rc) return rc;
         memcpy(c->host, sorted.data(), (size_t)ng * sizeof(MgGrid));
         int* bmap = reinterpret_cast<int*>(c->host + grid_bytes);
-        long long cls_map[NCLASS], cls_bmap[NCLASS], cls_tmap[NCLASS][3];   // offsets (ints)
+        long long cls_map[NBRANCH], cls_bmap[NBRANCH], cls_tmap[NBRANCH][3];   // offsets (ints)
         {
             long long o = 0;
-            for (int t = 0; t < NCLASS; ++t) {
+            for (int t = 0; t < NBRANCH; ++t) {
                 cls_map[t] = o;
                 for (int j = cls_first[t]; j < cls_first[t + 1]; ++j)
                     for (int b = 0; b < sorted[j].nblocks; ++b) bmap[o++] = j;
@@ -688,16 +710,16 @@ extern "C" int wfa_batch_run(wfa_grid* gs, const long long* steps, int count) {
             }
         }
         // mode "rounds": captured on a private stream into one graph, launched
-        // on the grids' stream. Classes hold different grids, so each class's
-        // chain of rounds is its own branch of the graph (forked after the
-        // descriptor copy, joined at the end): their launches overlap on the
-        // GPU instead of draining it between classes.
+        // on the grids' stream. Branches hold different grids, so each
+        // branch's chain of rounds is its own branch of the graph (forked
+        // after the descriptor copy, joined at the end): their launches
+        // overlap on the GPU instead of draining it between rounds.
         cudaStream_t ls = st;
         if (mode == 1) {
             if (!c->cap_stream) {
                 WFA_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
                 WFA_CUDA(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
-                for (int t = 0; t < NCLASS; ++t) {
+                for (int t = 0; t < NBRANCH; ++t) {
                     WFA_CUDA(cudaStreamCreateWithFlags(&c->cls_stream[t], cudaStreamNonBlocking));
                     WFA_CUDA(cudaEventCreateWithFlags(&c->join[t], cudaEventDisableTiming));
                 }
@@ -710,8 +732,8 @@ extern "C" int wfa_batch_run(wfa_grid* gs, const long long* steps, int count) {
         const MgGrid* dgrids = reinterpret_cast<const MgGrid*>(c->dev);
         const int* dmap = reinterpret_cast<const int*>(c->dev + grid_bytes);
         int* status = gs[order[0]]->d_status;
-        // per class, the grids with more than s steps are a prefix
-        for (int t = 0; t < NCLASS && e == cudaSuccess; ++t) {
+        // per branch, the grids with more than s steps are a prefix
+        for (int t = 0; t < NBRANCH && e == cudaSuccess; ++t) {
             if (cls_first[t] == cls_first[t + 1]) continue;
             cudaStream_t cs = mode == 1 ? c->cls_stream[t] : ls;
             if (mode == 1) e = cudaStreamWaitEvent(cs, c->fork, 0);
@@ -721,17 +743,18 @@ extern "C" int wfa_batch_run(wfa_grid* gs, const long long* steps, int count) {
                 while (active > cls_first[t] && sorted[active - 1].steps <= s) --active;
                 if (active == cls_first[t]) break;
                 const MgGrid& last = sorted[active - 1];
+                const int type = t / NGROUP;
                 if (uniform_class(t)) {
                     const int tblocks[3] = {last.tw0[0] + last.ntw[0], last.tw0[1] + last.ntw[1],
                                             last.tw0[2] + last.ntw[2]};
-                    e = t < NKIND ? uniform_round<float>(last.block0 + last.nblocks, last.bu0 + last.nbu, tblocks,
+                    e = type < NKIND ? uniform_round<float>(last.block0 + last.nblocks, last.bu0 + last.nbu, tblocks,
                                                          dgrids, dmap + cls_map[t], dmap + cls_bmap[t], tmaps, s,
                                                          status, cs)
                                   : uniform_round<__nv_bfloat16>(last.block0 + last.nblocks, last.bu0 + last.nbu,
                                                                  tblocks, dgrids, dmap + cls_map[t],
                                                                  dmap + cls_bmap[t], tmaps, s, status, cs);
                 } else {
-                    e = launch_class(t, last.block0 + last.nblocks, dgrids, dmap + cls_map[t], s, status, cs);
+                    e = launch_class(type, last.block0 + last.nblocks, dgrids, dmap + cls_map[t], s, status, cs);
                 }
             }
             if (mode == 1 && e == cudaSuccess) e = cudaEventRecord(c->join[t], cs);
