@@ -545,6 +545,7 @@ extern "C" int wfa_batch_run(wfa_grid* gs, const long long* steps, int count) {
         // z chunks of about 8 planes (measured faster than 16 for these small
         // grids: more units in flight), shorter (down to 4) while a grid has
         // fewer pairs than a block has threads
+        const int nz = g->n[2];
         int nch = std::max((nz + 7) / 8, (MG_THREADS + b.ncols - 1) / b.ncols);
         nch = std::max(1, std::min(nch, nz / 4));
         b.zchunk = (nz + nch - 1) / nch;
