@@ -177,32 +177,49 @@ struct Geo {
     long long px, py;
 };
 
+// Dense (x fastest, no halo) <-> padded layout, one warp per (y, z) row: the
+// row index is split once per row in 32-bit arithmetic and the warp's
+// accesses are consecutive on both sides. `dense` may be device memory or
+// pinned host memory (read or written directly over the host link).
 template <typename S>
 __global__ void pack_kernel(const float* __restrict__ dense, S* __restrict__ origin, const __grid_constant__ Geo geo) {
-    const long long N = (long long)geo.n[0] * geo.n[1] * geo.n[2];
+    const unsigned ny = (unsigned)geo.n[1];
+    const long long rows = (long long)geo.n[1] * geo.n[2];
     const long long sz = geo.px * geo.py;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % geo.n[0]);
-        const long long r = i / geo.n[0];
-        const int y = (int)(r % geo.n[1]);
-        const int z = (int)(r / geo.n[1]);
-        origin[z * sz + y * geo.px + x] = from_f32<S>(dense[i]);
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long r = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
+        const long long z = r / ny, y = r - z * ny;
+        const float* src = dense + r * geo.n[0];
+        S* dst = origin + z * sz + y * geo.px;
+        for (int x = lane; x < geo.n[0]; x += 32) dst[x] = from_f32<S>(src[x]);
     }
 }
 
 template <typename S>
 __global__ void unpack_kernel(const S* __restrict__ origin, float* __restrict__ dense, const __grid_constant__ Geo geo) {
-    const long long N = (long long)geo.n[0] * geo.n[1] * geo.n[2];
+    const unsigned ny = (unsigned)geo.n[1];
+    const long long rows = (long long)geo.n[1] * geo.n[2];
     const long long sz = geo.px * geo.py;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % geo.n[0]);
-        const long long r = i / geo.n[0];
-        const int y = (int)(r % geo.n[1]);
-        const int z = (int)(r / geo.n[1]);
-        dense[i] = to_f32<S>(origin[z * sz + y * geo.px + x]);
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long r = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
+        const long long z = r / ny, y = r - z * ny;
+        const S* src = origin + z * sz + y * geo.px;
+        float* dst = dense + r * geo.n[0];
+        for (int x = lane; x < geo.n[0]; x += 32) dst[x] = to_f32<S>(src[x]);
     }
+}
+
+// Device address of a host buffer the GPU can read and write directly
+// (pinned, or mapped), or nullptr (pageable: go through the staging buffer).
+static const void* host_device_view(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();   // clear: an unknown pointer is just not device-accessible
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
 struct HaloSpec {
@@ -729,18 +746,25 @@ static Geo geo_of(const wfa_grid_s* g) {
 
 int wfa_set_field(wfa_grid g, const float* host_dense) {
     if (!g || !host_dense) return fail(WFA_ERR_ARG, "NULL argument");
-    int rc = ensure_stage(g);
-    if (rc) return rc;
     const long long N = (long long)g->n[0] * g->n[1] * g->n[2];
-    WFA_CUDA(cudaMemcpyAsync(g->d_stage, host_dense, N * sizeof(float), cudaMemcpyHostToDevice, g->stream));
+    // pinned host memory is read by the packing kernel itself; pageable
+    // memory goes through the staging buffer
+    const float* src = static_cast<const float*>(host_device_view(host_dense));
+    if (!src) {
+        int rc = ensure_stage(g);
+        if (rc) return rc;
+        WFA_CUDA(cudaMemcpyAsync(g->d_stage, host_dense, N * sizeof(float), cudaMemcpyHostToDevice, g->stream));
+        src = g->d_stage;
+    }
     const int thr = 256;
     const Geo geo = geo_of(g);
+    const long long rows = (long long)g->n[1] * g->n[2];
     if (g->storage == WFA_BF16)
-        pack_kernel<__nv_bfloat16><<<grid_blocks(N, thr), thr, 0, g->stream>>>(
-            g->d_stage, (__nv_bfloat16*)g->T[g->cur] + domain_offset(g), geo);
+        pack_kernel<__nv_bfloat16><<<grid_blocks(rows * 32, thr), thr, 0, g->stream>>>(
+            src, (__nv_bfloat16*)g->T[g->cur] + domain_offset(g), geo);
     else
-        pack_kernel<float><<<grid_blocks(N, thr), thr, 0, g->stream>>>(
-            g->d_stage, (float*)g->T[g->cur] + domain_offset(g), geo);
+        pack_kernel<float><<<grid_blocks(rows * 32, thr), thr, 0, g->stream>>>(
+            src, (float*)g->T[g->cur] + domain_offset(g), geo);
     WFA_CUDA(cudaGetLastError());
     // the host buffer may be reused as soon as we return
     WFA_CUDA(cudaStreamSynchronize(g->stream));
@@ -780,8 +804,9 @@ int wfa_set_coeffs(wfa_grid g, const float* k_host, double k_uniform, double ux,
             WFA_CUDA(dev_alloc((void**)&g->r, field_elems(g) * sizeof(float), g->stream));
         }
         const int thr = 256;
-        pack_kernel<float><<<grid_blocks(N, thr), thr, 0, g->stream>>>(g->d_stage, g->k + domain_offset(g),
-                                                                         geo_of(g));
+        const long long rows = (long long)g->n[1] * g->n[2];
+        pack_kernel<float><<<grid_blocks(rows * 32, thr), thr, 0, g->stream>>>(g->d_stage, g->k + domain_offset(g),
+                                                                                geo_of(g));
         WFA_CUDA(cudaGetLastError());
         g->k_halo_dirty = true;   // twins, ghost layers and 1/k follow before the next use
         g->k_uniform = 0.0;
@@ -1018,24 +1043,33 @@ int wfa_steps_done(wfa_grid g, long long* n) {
 int wfa_read_field(wfa_grid g, float* host_dense) {
     if (!g || !host_dense) return fail(WFA_ERR_ARG, "NULL argument");
     if (!g->field_set) return fail(WFA_ERR_STATE, "no field set");
-    int rc = ensure_stage(g);
-    if (rc) return rc;
     if (g->halo_dirty) {   // held layers show their value even before the first step
-        rc = refresh_halo(g, g->cur);
+        int rc = refresh_halo(g, g->cur);
         if (rc) return rc;
     }
     const long long N = (long long)g->n[0] * g->n[1] * g->n[2];
+    // pinned host memory is written by the unpacking kernel itself; pageable
+    // memory is filled from the staging buffer
+    float* dst = static_cast<float*>(const_cast<void*>(host_device_view(host_dense)));
+    const bool staged = !dst;
+    if (staged) {
+        int rc = ensure_stage(g);
+        if (rc) return rc;
+        dst = g->d_stage;
+    }
     const int thr = 256;
     const Geo geo = geo_of(g);
+    const long long rows = (long long)g->n[1] * g->n[2];
     if (g->storage == WFA_BF16)
-        unpack_kernel<__nv_bfloat16><<<grid_blocks(N, thr), thr, 0, g->stream>>>(
-            (const __nv_bfloat16*)g->T[g->cur] + domain_offset(g), g->d_stage, geo);
+        unpack_kernel<__nv_bfloat16><<<grid_blocks(rows * 32, thr), thr, 0, g->stream>>>(
+            (const __nv_bfloat16*)g->T[g->cur] + domain_offset(g), dst, geo);
     else
-        unpack_kernel<float><<<grid_blocks(N, thr), thr, 0, g->stream>>>(
-            (const float*)g->T[g->cur] + domain_offset(g), g->d_stage, geo);
+        unpack_kernel<float><<<grid_blocks(rows * 32, thr), thr, 0, g->stream>>>(
+            (const float*)g->T[g->cur] + domain_offset(g), dst, geo);
     WFA_CUDA(cudaGetLastError());
-    WFA_CUDA(cudaMemcpyAsync(host_dense, g->d_stage, N * sizeof(float), cudaMemcpyDeviceToHost, g->stream));
-    return check_status(g);
+    if (staged)
+        WFA_CUDA(cudaMemcpyAsync(host_dense, g->d_stage, N * sizeof(float), cudaMemcpyDeviceToHost, g->stream));
+    return check_status(g);   // synchronises: the host buffer is complete
 }
 
 int wfa_total_heat(wfa_grid g, double* e) {

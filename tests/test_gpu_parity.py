@@ -375,3 +375,21 @@ def test_small_grid_step_graphs(depth, variant):
         for _ in range(2 * n):
             h.step(1)
         np.testing.assert_array_equal(g.read_field(), h.read_field())
+
+
+@pytest.mark.parametrize("storage", [wfa.F32, wfa.BF16])
+def test_pinned_host_buffers_go_direct(storage):
+    # pinned host memory is packed / unpacked by the kernels themselves,
+    # pageable memory through the staging buffer: same fields either way
+    torch = pytest.importorskip("torch")
+    p = _mixed_problem(5, shape=(37, 29, 23), seed=4)
+    with make_grid(p, storage=storage) as g:
+        g.step(7)
+        pageable = g.read_field()
+        pinned = torch.empty(tuple(p.T0.shape), dtype=torch.float32).pin_memory()
+        g.read_field(pinned)
+        np.testing.assert_array_equal(pinned.numpy(), pageable)
+        T0 = torch.from_numpy(np.ascontiguousarray(p.T0)).pin_memory()
+        g.set_field(T0)
+        g.step(7)
+        np.testing.assert_array_equal(g.read_field(), pageable)
