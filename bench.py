@@ -421,6 +421,9 @@ def main():
                 "traffic": traffic, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "bytes_per_cell_per_launch": bpc, "steps_per_launch": depth,
                 "kernel_ms_mean": launch_s * 1e3, "kernel_launches_timed": kernel_launches,
+                # DRAM bytes per launch from ncu over this run's mean launch time
+                "ncu_dram_GBps": traffic / launch_s / 1e9 if traffic else None,
+                "ncu_dram_frac": traffic / launch_s / 1e9 / peak if traffic else None,
                 "pass_ms_mean": pass_s * 1e3, "pass_GBps": bpc * cells / pass_s / 1e9,
                 "effective_GBps_paper_Teff": bpc * depth * cells / pass_s / 1e9}
 

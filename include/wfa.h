@@ -170,6 +170,22 @@ int wfa_total_heat(wfa_grid g, double* e);
  * Errors: WFA_ERR_ARG (null pointer, negative or too large n), WFA_ERR_CUDA. */
 int wfa_sum_f32_noalloc(const float* d_x, long long n, double scale, double* d_out, void* stream);
 
+/* Bytes of one padded field buffer and of one padded k (or 1/k) buffer of
+ * this grid, for callers that own the device memory (below). */
+int wfa_grid_buffer_bytes(wfa_grid g, size_t* field_bytes, size_t* k_bytes);
+
+/* Let caller-owned device memory hold the grid's data (e.g. tensors of a
+ * framework that manages all device memory): d_Ta and d_Tb, field_bytes
+ * each, take the two field buffers; d_k and d_r, k_bytes each (both or both
+ * NULL), take the per-cell conductivity and its reciprocal, now if the grid
+ * has per-cell k and from the next wfa_set_coeffs with k otherwise. All
+ * must be distinct, 256-byte aligned device memory; the grid's current
+ * contents are copied in and its own buffers released. The caller keeps the
+ * buffers alive until wfa_destroy_grid, which does not free them; their
+ * layout is the library's padded layout (opaque to the caller).
+ * Synchronises the stream. Errors: WFA_ERR_ARG, WFA_ERR_CUDA. */
+int wfa_grid_attach_buffers(wfa_grid g, void* d_Ta, void* d_Tb, float* d_k, float* d_r);
+
 /* Wait for the grid's queued work; reports a device-side error. */
 int wfa_sync(wfa_grid g);
 

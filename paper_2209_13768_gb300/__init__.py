@@ -65,6 +65,8 @@ SIGNATURES = {
     "wfa_read_field": (_i, [_vp, _fp]),
     "wfa_total_heat": (_i, [_vp, _dp]),
     "wfa_sync": (_i, [_vp]),
+    "wfa_grid_buffer_bytes": (_i, [_vp, ctypes.POINTER(_sz), ctypes.POINTER(_sz)]),
+    "wfa_grid_attach_buffers": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "wfa_set_kernel_timing": (_i, [_vp, _i]),
     "wfa_kernel_time": (_i, [_vp, _dp, _llp]),
     "wfa_launch_count": (_i, [_vp, _llp]),
@@ -217,6 +219,19 @@ class Grid:
 
     def sync(self):
         check(lib().wfa_sync(self.handle), "wfa_sync")
+
+    def buffer_bytes(self):
+        """(bytes of one padded field buffer, bytes of one padded k buffer)."""
+        fb, kb = _sz(), _sz()
+        check(lib().wfa_grid_buffer_bytes(self.handle, ctypes.byref(fb), ctypes.byref(kb)), "wfa_grid_buffer_bytes")
+        return fb.value, kb.value
+
+    def attach_buffers(self, Ta, Tb, k=None, r=None):
+        """Hold the grid's data in caller-owned device memory (device pointers
+        or CUDA tensors, kept alive by this object until close)."""
+        ptr = lambda t: None if t is None else _vp(t.data_ptr() if hasattr(t, "data_ptr") else int(t))
+        check(lib().wfa_grid_attach_buffers(self.handle, ptr(Ta), ptr(Tb), ptr(k), ptr(r)), "wfa_grid_attach_buffers")
+        self._attached = (Ta, Tb, k, r)
 
     def set_kernel_timing(self, every):
         """Time the main sweep kernel of every every-th pass with CUDA events (0: off)."""

@@ -1,6 +1,7 @@
 // Grid handles, field transfer (pack / unpack), halo maintenance and the fp64
 // reductions (total heat, stability limit) behind the C ABI in include/wfa.h.
 #include <stdarg.h>
+#include <stdint.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -690,6 +691,8 @@ int wfa_create_grid(int nx, int ny, int nz, double hx, double hy, double hz, int
     for (int f = 0; f < 6; ++f) { g->bc_kind[f] = WFA_BC_ZEROFLUX; g->bc_value[f] = 0.0; }
     const size_t bytes = field_elems(g) * g->esize;
     cudaError_t e = cudaSuccess;
+    g->own_T = true;
+    g->own_k = true;
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = dev_alloc(&g->T[b], bytes, g->stream);
     if (e == cudaSuccess) e = dev_alloc((void**)&g->d_partials, 4096 * sizeof(double), g->stream);
     if (e == cudaSuccess) e = dev_alloc((void**)&g->d_status, 8 * sizeof(int), g->stream);
@@ -714,9 +717,12 @@ int wfa_create_grid(int nx, int ny, int nz, double hx, double hy, double hz, int
 int wfa_destroy_grid(wfa_grid g) {
     if (!g) return WFA_OK;
     cudaStreamSynchronize(g->stream);   // nothing of this grid is in flight below
-    for (int b = 0; b < 2; ++b) dev_free(g->T[b], g->stream);
-    dev_free(g->k, g->stream);
-    dev_free(g->r, g->stream);
+    if (g->own_T)
+        for (int b = 0; b < 2; ++b) dev_free(g->T[b], g->stream);
+    if (g->own_k) {
+        dev_free(g->k, g->stream);
+        dev_free(g->r, g->stream);
+    }
     dev_free(g->d_partials, g->stream);
     dev_free(g->d_stage, g->stream);
     dev_free(g->d_status, g->stream);
@@ -799,9 +805,16 @@ int wfa_set_coeffs(wfa_grid g, const float* k_host, double k_uniform, double ux,
         if (first != ~0ull)
             return fail(WFA_ERR_ARG, "k[%llu] = %g is negative or not finite", first, (double)k_host[first]);
         if (!g->k) {
-            WFA_CUDA(dev_alloc((void**)&g->k, field_elems(g) * sizeof(float), g->stream));
+            if (g->ext_k) {   // the caller's buffers (wfa_grid_attach_buffers)
+                g->k = g->ext_k;
+                g->r = g->ext_r;
+                g->own_k = false;
+            } else {
+                WFA_CUDA(dev_alloc((void**)&g->k, field_elems(g) * sizeof(float), g->stream));
+                WFA_CUDA(dev_alloc((void**)&g->r, field_elems(g) * sizeof(float), g->stream));
+                g->own_k = true;
+            }
             WFA_CUDA(cudaMemsetAsync(g->k, 0, field_elems(g) * sizeof(float), g->stream));
-            WFA_CUDA(dev_alloc((void**)&g->r, field_elems(g) * sizeof(float), g->stream));
         }
         const int thr = 256;
         const long long rows = (long long)g->n[1] * g->n[2];
@@ -813,8 +826,10 @@ int wfa_set_coeffs(wfa_grid g, const float* k_host, double k_uniform, double ux,
     } else {
         if (g->k) {
             cudaStreamSynchronize(g->stream);
-            dev_free(g->k, g->stream);
-            dev_free(g->r, g->stream);
+            if (g->own_k) {
+                dev_free(g->k, g->stream);
+                dev_free(g->r, g->stream);
+            }
             g->k = nullptr;
             g->r = nullptr;
             free_tmaps(g);
@@ -1095,6 +1110,56 @@ int wfa_total_heat(wfa_grid g, double* e) {
     rc_ = check_status(g);
     *e = g->h_result[0];
     return rc_;
+}
+
+int wfa_grid_buffer_bytes(wfa_grid g, size_t* field_bytes, size_t* k_bytes) {
+    if (!g || !field_bytes || !k_bytes) return fail(WFA_ERR_ARG, "NULL argument");
+    *field_bytes = field_elems(g) * g->esize;
+    *k_bytes = field_elems(g) * sizeof(float);
+    return WFA_OK;
+}
+
+int wfa_grid_attach_buffers(wfa_grid g, void* d_Ta, void* d_Tb, float* d_k, float* d_r) {
+    if (!g || !d_Ta || !d_Tb || d_Ta == d_Tb) return fail(WFA_ERR_ARG, "two distinct field buffers are needed");
+    if ((d_k == nullptr) != (d_r == nullptr)) return fail(WFA_ERR_ARG, "give both k and 1/k buffers, or neither");
+    for (const void* p : {(const void*)d_Ta, (const void*)d_Tb, (const void*)d_k, (const void*)d_r}) {
+        if (!p) continue;
+        if ((uintptr_t)p % 256) return fail(WFA_ERR_ARG, "attached buffers must be 256-byte aligned");
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, p) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+            cudaGetLastError();
+            return fail(WFA_ERR_ARG, "attached buffers must be device memory");
+        }
+    }
+    const size_t fb = field_elems(g) * g->esize, kb = field_elems(g) * sizeof(float);
+    // the grid's current contents move into the caller's buffers
+    WFA_CUDA(cudaMemcpyAsync(d_Ta, g->T[0], fb, cudaMemcpyDeviceToDevice, g->stream));
+    WFA_CUDA(cudaMemcpyAsync(d_Tb, g->T[1], fb, cudaMemcpyDeviceToDevice, g->stream));
+    if (d_k && g->k) {
+        WFA_CUDA(cudaMemcpyAsync(d_k, g->k, kb, cudaMemcpyDeviceToDevice, g->stream));
+        WFA_CUDA(cudaMemcpyAsync(d_r, g->r, kb, cudaMemcpyDeviceToDevice, g->stream));
+    }
+    WFA_CUDA(cudaStreamSynchronize(g->stream));
+    if (g->own_T)
+        for (int b = 0; b < 2; ++b) dev_free(g->T[b], g->stream);
+    g->T[0] = d_Ta;
+    g->T[1] = d_Tb;
+    g->own_T = false;
+    if (d_k) {
+        if (g->k) {
+            if (g->own_k) {
+                dev_free(g->k, g->stream);
+                dev_free(g->r, g->stream);
+            }
+            g->k = d_k;
+            g->r = d_r;
+            g->own_k = false;
+        }
+        g->ext_k = d_k;
+        g->ext_r = d_r;
+    }
+    free_tmaps(g);   // descriptors name the old buffers
+    return WFA_OK;
 }
 
 int wfa_sync(wfa_grid g) {

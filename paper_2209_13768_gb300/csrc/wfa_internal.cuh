@@ -114,6 +114,9 @@ struct wfa_grid_s {
     int* h_status;        // pinned host copy
     void* tmaps;          // wfa::TmapCache (TMA descriptors for the current tile box)
     int tuned_depth, tuned_variant;   // configuration picked by the autotuner (0 = none)
+    bool own_T, own_k;    // the library allocated T[] / k and r (else the caller attached them)
+    float* ext_k;         // caller buffers for k and 1/k, used when per-cell k is set
+    float* ext_r;
     long long launches;   // kernels launched by the sweeps so far (wfa_launch_count)
     int timing_every;     // wfa_set_kernel_timing: sample every n-th pass (0 = off)
     long long timing_pass;

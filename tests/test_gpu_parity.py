@@ -393,3 +393,36 @@ def test_pinned_host_buffers_go_direct(storage):
         g.set_field(T0)
         g.step(7)
         np.testing.assert_array_equal(g.read_field(), pageable)
+
+
+def test_caller_owned_buffers():
+    # fields and k in caller-owned device memory (torch tensors): the same
+    # results, before and after set_coeffs, and the caller's memory is used
+    torch = pytest.importorskip("torch")
+    p = _mixed_problem(6, shape=(41, 30, 22), kvar=True, adv=False, seed=8)
+    ref = run_gpu(p, steps=9)
+    with make_grid(p) as g:
+        fb, kb = g.buffer_bytes()
+        Ta = torch.empty(fb, dtype=torch.uint8, device="cuda")
+        Tb = torch.empty(fb, dtype=torch.uint8, device="cuda")
+        k = torch.empty(kb, dtype=torch.uint8, device="cuda")
+        r = torch.empty(kb, dtype=torch.uint8, device="cuda")
+        g.attach_buffers(Ta, Tb, k, r)
+        g.step(9)
+        np.testing.assert_array_equal(g.read_field(), ref)
+        assert Ta.any() and Tb.any() and k.any() and r.any()
+    # attached while k is uniform: per-cell k set later lands in the caller's buffers
+    with wfa.Grid(p.shape, h=p.h) as g:
+        fb, kb = g.buffer_bytes()
+        bufs = [torch.empty(b, dtype=torch.uint8, device="cuda") for b in (fb, fb, kb, kb)]
+        g.attach_buffers(*bufs)
+        g.set_bcs(p.bc)
+        g.set_coeffs(p.k, p.u)
+        g.set_field(p.T0)
+        g.set_dt(p.dt_factor * g.stability_dt())
+        g.step(9)
+        np.testing.assert_array_equal(g.read_field(), ref)
+        assert bufs[2].any()
+    with wfa.Grid(p.shape) as g:
+        with pytest.raises(wfa.WfaError):
+            g.attach_buffers(Ta, Ta)
