@@ -276,6 +276,63 @@ def test_call_order_errors():
     g.close()
 
 
+
+def test_argument_limits():
+    # edges, cell sizes, storage, faces larger than the 32-bit face kernels
+    # take, values and kinds out of range: refused with WFA_ERR_ARG / _BC
+    bad = [((1, 8, 8), {}), ((8, 8, 8), {"h": (1.0, 0.0, 1.0)}), ((8, 8, 8), {"h": (1.0, float("nan"), 1.0)}),
+           ((8, 8, 8), {"storage": 7}), ((70000, 70000, 2), {})]
+    for shape, kw in bad:
+        with pytest.raises(wfa.WfaError) as e:
+            wfa.Grid(shape, **kw)
+        assert e.value.code == -1, (shape, kw)
+    with wfa.Grid((8, 8, 8)) as g:
+        for call, code in [(lambda: g.set_bc(6, ZF, 0.0), -1), (lambda: g.set_bc(0, 9, 0.0), -1),
+                           (lambda: g.set_bc(0, D, float("inf")), -1), (lambda: g.set_coeffs(-1.0), -1),
+                           (lambda: g.set_tuning(9, 0), -1), (lambda: g.set_tuning(1, 6), -1)]:
+            with pytest.raises(wfa.WfaError) as e:
+                call()
+            assert e.value.code == code
+        k = np.ones((8, 8, 8), np.float32)
+        k[3, 4, 5] = np.nan
+        with pytest.raises(wfa.WfaError) as e:
+            g.set_coeffs(k)
+        assert e.value.code == -1 and "k[" in str(e.value)
+    with wfa.Grid((2, 8, 8)) as g:
+        with pytest.raises(wfa.WfaError) as e:
+            g.set_bc(0, DC, 1.0)   # a held layer needs an edge of 3
+        assert e.value.code == -3
+
+
+def test_degenerate_coefficients():
+    # k = 0 and no advection: nothing moves, the limit is infinite
+    rng = np.random.default_rng(13)
+    T0 = rng.random((9, 10, 11), dtype=np.float32)
+    p = W.Problem(shape=(11, 10, 9), T0=T0, k=0.0, bc=[(D, 1.0)] * 6, steps=5)
+    with wfa.Grid(p.shape) as g:
+        g.set_bcs(p.bc)
+        g.set_coeffs(0.0)
+        g.set_field(T0)
+        assert g.stability_dt() == float("inf")
+        g.set_dt(1e6)
+        g.step(5)
+        np.testing.assert_array_equal(g.read_field(), T0)
+    # pure advection at Courant number 1 on a periodic box: a shift by one
+    # cell per step (to rounding: T + (T_up - T))
+    p = W.Problem(shape=(16, 12, 10), T0=rng.random((10, 12, 16), dtype=np.float32), k=0.0, u=(1.0, 0.0, 0.0),
+                  bc=[(P, 0.0)] * 6, dt=1.0, steps=3)
+    T = run_gpu(p)
+    np.testing.assert_allclose(T, np.roll(p.T0, 3, axis=2), rtol=0, atol=5e-7)
+    # a single zero-conductivity cell insulates itself: it keeps its value
+    p = _mixed_problem(1, shape=(12, 11, 10), kvar=True, adv=False, seed=3)
+    k = np.asarray(p.k).copy()
+    k[4, 5, 6] = 0.0
+    p.k = k
+    T = run_gpu(p, steps=6)
+    assert T[4, 5, 6] == p.T0[4, 5, 6]
+    assert rel_linf(T, run_oracle(p, steps=6)) <= F32_TOL
+
+
 def test_checkpoint_resume_is_bitwise():
     p = _mixed_problem(4, seed=9)
     full = run_gpu(p, steps=23, depth=3, variant=1)
