@@ -170,6 +170,17 @@ int wfa_total_heat(wfa_grid g, double* e);
  * Errors: WFA_ERR_ARG (null pointer, negative or too large n), WFA_ERR_CUDA. */
 int wfa_sum_f32_noalloc(const float* d_x, long long n, double scale, double* d_out, void* stream);
 
+/* Heat that one time step from the current field brings in through the
+ * Dirichlet faces (Sec. 3's reduction, applied to the boundary), in fp64:
+ * dt * hx*hy*hz * sum over the cells on Dirichlet faces of
+ * 2 k_C (T_b - T_C) / h^2 plus the upwind advective flux (T_b upwind for
+ * inflow, T_C for outflow). With zero-flux and periodic faces elsewhere,
+ * E(n+1) - E(n) equals it up to the rounding of the step. Synchronises the
+ * stream. Errors: WFA_ERR_STATE before field, coefficients and dt are set;
+ * WFA_ERR_BC with held layers (they are cells, not faces). No counterpart
+ * call in the paper. */
+int wfa_boundary_flux(wfa_grid g, double* flux);
+
 /* Bytes of one padded field buffer and of one padded k (or 1/k) buffer of
  * this grid, for callers that own the device memory (below). */
 int wfa_grid_buffer_bytes(wfa_grid g, size_t* field_bytes, size_t* k_bytes);

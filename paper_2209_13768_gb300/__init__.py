@@ -64,6 +64,7 @@ SIGNATURES = {
     "wfa_steps_done": (_i, [_vp, _llp]),
     "wfa_read_field": (_i, [_vp, _fp]),
     "wfa_total_heat": (_i, [_vp, _dp]),
+    "wfa_boundary_flux": (_i, [_vp, _dp]),
     "wfa_sync": (_i, [_vp]),
     "wfa_grid_buffer_bytes": (_i, [_vp, ctypes.POINTER(_sz), ctypes.POINTER(_sz)]),
     "wfa_grid_attach_buffers": (_i, [_vp, _vp, _vp, _vp, _vp]),
@@ -215,6 +216,12 @@ class Grid:
     def total_heat(self):
         v = ctypes.c_double()
         check(lib().wfa_total_heat(self.handle, ctypes.byref(v)), "wfa_total_heat")
+        return v.value
+
+    def boundary_flux(self):
+        """fp64 heat one step brings in through the Dirichlet faces (wfa_boundary_flux)."""
+        v = ctypes.c_double()
+        check(lib().wfa_boundary_flux(self.handle, ctypes.byref(v)), "wfa_boundary_flux")
         return v.value
 
     def sync(self):

@@ -406,13 +406,65 @@ __global__ void __launch_bounds__(RED_THREADS) heat_partial_kernel(const S* __re
 __global__ void __launch_bounds__(512) finish_sum_kernel(const double* __restrict__ partials, int n,
                                                          double scale, double* __restrict__ out) {
     __shared__ double sh[512];
-    sh[threadIdx.x] = threadIdx.x < n ? partials[threadIdx.x] : 0.0;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += 512) acc += partials[i];
+    sh[threadIdx.x] = acc;
     __syncthreads();
     for (int s = 256; s > 0; s >>= 1) {
         if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
         __syncthreads();
     }
     if (threadIdx.x == 0) *out = sh[0] * scale;
+}
+
+// Heat that one explicit step from the current field brings in through the
+// Dirichlet faces, per unit volume and time, block partial sums in fp64 (see
+// wfa_boundary_flux). blockIdx.y is the face; a block of 256 threads walks
+// its plane. Diffusion through the face: 2 k_C (T_b - T_C) / h^2 (value on
+// the face, half a cell away); advection: the upwind value is T_b for
+// inflow and T_C for outflow.
+struct FluxSpec {
+    int n[3];
+    long long px, py;
+    int dirichlet[6];
+    double tb[6];
+    double inv_h2[3], u_h[3];   // 1/h^2, u / h
+    double k_uniform;
+};
+
+template <typename S>
+__global__ void __launch_bounds__(RED_THREADS) flux_partial_kernel(const S* __restrict__ origin,
+                                                                   const float* __restrict__ korigin,
+                                                                   const __grid_constant__ FluxSpec fs,
+                                                                   double* __restrict__ partials) {
+    __shared__ double sh[RED_THREADS];
+    const int f = blockIdx.y, ax = f >> 1, side = f & 1;
+    double acc = 0.0;
+    if (fs.dirichlet[f]) {
+        const int b = ax == 0 ? 1 : 0, d = ax == 2 ? 1 : 2;
+        const unsigned nb = (unsigned)fs.n[b], plane = nb * (unsigned)fs.n[d];
+        for (unsigned t = blockIdx.x * RED_THREADS + threadIdx.x; t < plane; t += gridDim.x * RED_THREADS) {
+            int c[3];
+            c[ax] = side ? fs.n[ax] - 1 : 0;
+            c[b] = (int)(t % nb);
+            c[d] = (int)(t / nb);
+            const long long i = ((long long)c[2] * fs.py + c[1]) * fs.px + c[0];
+            const double tc = (double)to_f32<S>(origin[i]);
+            const double kc = korigin ? (double)korigin[i] : fs.k_uniform;
+            const double tb = fs.tb[f], u = fs.u_h[ax];
+            acc += 2.0 * kc * (tb - tc) * fs.inv_h2[ax];
+            // inflow through the low face when u > 0, through the high face when u < 0
+            if (side == 0) acc += u > 0 ? u * tb : u * tc;
+            else acc -= u > 0 ? u * tc : u * tb;
+        }
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int st = RED_THREADS / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = sh[0];
 }
 
 struct RateSpec {
@@ -1110,6 +1162,53 @@ int wfa_total_heat(wfa_grid g, double* e) {
     rc_ = check_status(g);
     *e = g->h_result[0];
     return rc_;
+}
+
+int wfa_boundary_flux(wfa_grid g, double* flux) {
+    if (!g || !flux) return fail(WFA_ERR_ARG, "NULL argument");
+    if (!g->field_set || !g->coeffs_set || !g->dt_set)
+        return fail(WFA_ERR_STATE, "set the field, the coefficients and dt first");
+    for (int f = 0; f < 6; ++f)
+        if (g->bc_kind[f] == WFA_BC_DIRICHLET_CELL)
+            return fail(WFA_ERR_BC, "held boundary layers are not faces: no face flux to report");
+    if (g->halo_dirty) {
+        int rc = refresh_halo(g, g->cur);
+        if (rc) return rc;
+    }
+    FluxSpec fs;
+    memset(&fs, 0, sizeof fs);
+    for (int a = 0; a < 3; ++a) {
+        fs.n[a] = g->n[a];
+        fs.inv_h2[a] = 1.0 / (g->h[a] * g->h[a]);
+        fs.u_h[a] = g->u[a] / g->h[a];
+    }
+    for (int f = 0; f < 6; ++f) {
+        fs.dirichlet[f] = g->bc_kind[f] == WFA_BC_DIRICHLET;
+        fs.tb[f] = g->bc_value[f];
+    }
+    fs.px = g->px;
+    fs.py = g->py;
+    fs.k_uniform = g->k_uniform;
+    // 6 faces x FLUX_BLOCKS partials, then one fixed-order sum (scaled by dt
+    // and the cell volume)
+    constexpr int FLUX_BLOCKS = 96;
+    static_assert(6 * FLUX_BLOCKS + 1 < 4095, "scratch layout");
+    const dim3 grid(FLUX_BLOCKS, 6);
+    const float* ko = g->k ? g->k + domain_offset(g) : nullptr;
+    if (g->storage == WFA_BF16)
+        flux_partial_kernel<__nv_bfloat16><<<grid, RED_THREADS, 0, g->stream>>>(
+            (const __nv_bfloat16*)g->T[g->cur] + domain_offset(g), ko, fs, g->d_partials);
+    else
+        flux_partial_kernel<float><<<grid, RED_THREADS, 0, g->stream>>>(
+            (const float*)g->T[g->cur] + domain_offset(g), ko, fs, g->d_partials);
+    finish_sum_kernel<<<1, 512, 0, g->stream>>>(g->d_partials, 6 * FLUX_BLOCKS,
+                                                g->dt * g->h[0] * g->h[1] * g->h[2], g->d_partials + 6 * FLUX_BLOCKS);
+    WFA_CUDA(cudaGetLastError());
+    WFA_CUDA(cudaMemcpyAsync(g->h_result, g->d_partials + 6 * FLUX_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost,
+                             g->stream));
+    const int rc = check_status(g);
+    *flux = g->h_result[0];
+    return rc;
 }
 
 int wfa_grid_buffer_bytes(wfa_grid g, size_t* field_bytes, size_t* k_bytes) {

@@ -483,3 +483,50 @@ def test_caller_owned_buffers():
     with wfa.Grid(p.shape) as g:
         with pytest.raises(wfa.WfaError):
             g.attach_buffers(Ta, Ta)
+
+
+def _face_flux_ref(T, p, dt):
+    """The Dirichlet face flux of one step, in fp64 from its definition."""
+    T = np.asarray(T, np.float64)
+    k = np.broadcast_to(np.asarray(p.k, np.float64), T.shape)
+    tot = 0.0
+    for f, (kind, tb) in enumerate(p.bc):
+        if kind != D:
+            continue
+        ax, side = f // 2, f % 2
+        arr_ax = 2 - ax                                   # arrays are [z, y, x]
+        idx = [slice(None)] * 3
+        idx[arr_ax] = -1 if side else 0
+        tc, kc = T[tuple(idx)], k[tuple(idx)]
+        h, u = p.h[ax], p.u[ax]
+        tot += np.sum(2.0 * kc * (tb - tc) / (h * h))
+        uh = u / h
+        tbf = np.full(tc.shape, float(tb))
+        if side == 0:
+            tot += np.sum(uh * tbf if uh > 0 else uh * tc)
+        else:
+            tot -= np.sum(uh * tc if uh > 0 else uh * tbf)
+    return tot * dt * p.h[0] * p.h[1] * p.h[2]
+
+
+@pytest.mark.parametrize("kvar,adv", [(True, True), (False, True), (True, False)])
+def test_boundary_flux_balances_energy(kvar, adv):
+    # Dirichlet faces (one held at a value per side), zero flux and periodic
+    # elsewhere: the energy change of one step is the face flux (fp64 sum,
+    # fp32 step rounding)
+    p = _mixed_problem(6, shape=(37, 29, 23), kvar=kvar, adv=adv, seed=12)
+    with make_grid(p) as g:
+        g.step(3)
+        dt = p.dt_factor * g.stability_dt()
+        T = g.read_field()
+        e0 = g.total_heat()
+        flux = g.boundary_flux()
+        assert abs(flux - _face_flux_ref(T, p, dt)) <= 1e-12 * max(1.0, abs(flux)) * T.size
+        g.step(1)
+        e1 = g.total_heat()
+        assert abs((e1 - e0) - flux) <= 2e-6 * np.abs(T).sum() * np.prod(p.h), (e1 - e0, flux)
+    pdc = _mixed_problem(3)
+    with make_grid(pdc) as g:
+        with pytest.raises(wfa.WfaError) as e:
+            g.boundary_flux()
+        assert e.value.code == -3

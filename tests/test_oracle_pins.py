@@ -425,6 +425,31 @@ def test_dirichlet_energy_balance():
     assert abs(dE - dt * flux) < 1e-13 * max(1.0, abs(flux)) * vol
 
 
+
+def test_dirichlet_energy_balance_with_advection():
+    # with upwind advection: the net flux through a Dirichlet face carries T_b
+    # where the flow enters and T_C where it leaves; zero-flux faces carry
+    # nothing (the interior and periodic fluxes cancel in the sum)
+    rng = np.random.default_rng(16)
+    shape = (7, 5, 6)
+    h = (1.0, 0.8, 1.3)
+    u = (0.25, -0.2, 0.1)
+    k = np.exp(0.5 * rng.standard_normal(shape[::-1]))
+    bc = _bc([D, D, D, ZF, P, P], [0.7, -0.3, 1.5, 0, 0, 0])
+    dt = 0.5 * oracle.dt_max(shape=shape, h=h, k=k, u=u, bc=bc)
+    T0 = rng.uniform(0, 1, shape[::-1])
+    T1 = oracle.run(T0, 1, shape=shape, h=h, k=k, u=u, bc=bc, dt=dt)
+    ax, ay, az = h[1] * h[2], h[0] * h[2], h[0] * h[1]   # face areas
+    flux = 0.0
+    # -x (value 0.7): diffusion and inflow (u_x > 0 enters here with T_b)
+    flux += np.sum(2 * k[:, :, 0] * (0.7 - T0[:, :, 0])) * ax / h[0] + u[0] * 0.7 * T0[:, :, 0].size * ax
+    # +x (value -0.3): diffusion and outflow (u_x > 0 leaves with T_C)
+    flux += np.sum(2 * k[:, :, -1] * (-0.3 - T0[:, :, -1])) * ax / h[0] - u[0] * np.sum(T0[:, :, -1]) * ax
+    # -y (value 1.5): diffusion and outflow (u_y < 0 leaves through -y with T_C)
+    flux += np.sum(2 * k[:, 0, :] * (1.5 - T0[:, 0, :])) * ay / h[1] + u[1] * np.sum(T0[:, 0, :]) * ay
+    dE = oracle.total_heat(T1, h) - oracle.total_heat(T0, h)
+    assert abs(dE - dt * flux) < 1e-12 * max(1.0, abs(dt * flux))
+
 def test_maximum_principle():
     rng = np.random.default_rng(8)
     shape = (12, 10, 8)
