@@ -50,8 +50,10 @@ __global__ void __launch_bounds__(F2_TX * F2_TY, F2_BLOCKS) sweep_col2(const __g
 
     // x / y faces of this thread's cells never change along z
     const bool perx = c.periodic[0], pery = c.periodic[1];
+    // (self terms and held layers belong to boundary cells only, which
+    // inner_xy already excludes on non-periodic axes)
     const bool inner_xy = (perx || (gx > 0 && gx + 3 < c.n[0] - 1)) && (pery || (gy > 0 && gy < c.n[1] - 1)) &&
-                          gx + 3 < c.n[0] && !c.any_self && !(c.held[0] | c.held[1] | c.held[2] | c.held[3]);
+                          gx + 3 < c.n[0];
     bool out_x[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) out_x[i] = !perx && (gx + i < 0 || gx + i >= c.n[0]);
@@ -80,6 +82,16 @@ __global__ void __launch_bounds__(F2_TX * F2_TY, F2_BLOCKS) sweep_col2(const __g
         float* sp = s1[(q + 3) % 3];
         const bool zin = c.periodic[2] || (q > 0 && q < c.n[2] - 1);
         const bool zout = !c.periodic[2] && (q < 0 || q >= c.n[2]);
+        // ring cell inputs first: their latency overlaps the main stage-1 work
+        float rz = 0.0f, r_xm = 0.0f, r_xp = 0.0f, r_ym = 0.0f, r_yp = 0.0f;
+        if (act_r) {
+            const S* rp = rcolp + (long long)q * sz;
+            rz = ldg1<S, false>(rp + sz);
+            r_xm = ldg1<S, false>(rp - 1);
+            r_xp = ldg1<S, false>(rp + 1);
+            r_ym = ldg1<S, false>(rp - sy);
+            r_yp = ldg1<S, false>(rp + sy);
+        }
         // ---- stage 1 at plane q
         float sn[4];
         if (act1) {
@@ -111,10 +123,7 @@ __global__ void __launch_bounds__(F2_TX * F2_TY, F2_BLOCKS) sweep_col2(const __g
             }
         }
         if (act_r) {
-            const S* rp = rcolp + (long long)q * sz;
-            const float rz = ldg1<S, false>(rp + sz);
-            const float v = uniform_cell(c, rc, ldg1<S, false>(rp - 1), ldg1<S, false>(rp + 1),
-                                         ldg1<S, false>(rp - sy), ldg1<S, false>(rp + sy), rm, rz, rx, ry, q);
+            const float v = uniform_cell(c, rc, r_xm, r_xp, r_ym, r_yp, rm, rz, rx, ry, q);
             sp[(tx + 1) * F2_W + rcol] = outside_np(c, rx, ry, q) ? rc : storage_round<S>(v);
             rm = rc;
             rc = rz;
