@@ -265,6 +265,9 @@ def sum_f32_noalloc(d_x, n, scale, d_out, stream=None):
 
 
 def batch_run(grids, steps):
+    """Advance grids[i] by steps[i] time steps, all grids in one CUDA-graph
+    launch (see wfa_batch_run; the grids share one stream). Bitwise equal to
+    stepping each grid alone."""
     arr = (_vp * len(grids))(*[g.handle for g in grids])
     st = (ctypes.c_longlong * len(steps))(*[int(s) for s in steps])
     check(lib().wfa_batch_run(arr, st, len(grids)), "wfa_batch_run")
