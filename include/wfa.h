@@ -128,7 +128,8 @@ int wfa_set_tuning(wfa_grid g, int depth, int variant);
  * use the fastest from now
  * on. The trials run on a scratch copy of the field: the field and the step
  * count are left as they were, and results never depend on the choice. The
- * choice is also remembered for later grids of the same size class (storage,
+ * choice is also remembered for later grids of the same size class (device
+ * compute capability and SM count, storage,
  * conductivity mode, advection, log2 of each edge) in this process, and in
  * the file named by the environment variable WFA_TUNE_CACHE if it is set.
  * Synchronises the stream; needs one extra field of device memory while it
@@ -224,6 +225,16 @@ int wfa_kernel_time(wfa_grid g, double* ms, long long* launches);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* wfa_last_error(void);
+
+/* Host-side fault injection for testing the out-of-memory paths, with no
+ * counterpart in the paper: after n >= 0 further successful device
+ * allocations from the grid memory pool (field, conductivity, staging and
+ * reduction buffers of wfa_create_grid, wfa_set_coeffs, wfa_set_field and
+ * the autotuner), the next one fails once as if the device were out of
+ * memory, so that call returns WFA_ERR_OOM and leaves the grid as it was;
+ * n < 0 disarms a pending failure. Process-wide; nothing is injected on the
+ * device. Returns WFA_OK. */
+int wfa_inject_alloc_failure(int n);
 
 /* ----------------------------------------------------------- batching -- */
 

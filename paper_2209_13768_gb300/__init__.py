@@ -73,6 +73,7 @@ SIGNATURES = {
     "wfa_launch_count": (_i, [_vp, _llp]),
     "wfa_sum_f32_noalloc": (_i, [_vp, _ll, _d, _vp, _vp]),
     "wfa_last_error": (ctypes.c_char_p, []),
+    "wfa_inject_alloc_failure": (_i, [_i]),
     "wfa_batch_run": (_i, [ctypes.POINTER(_vp), _llp, _i]),
     "wfa_server_create": (_i, [_sz, _i, _ll, ctypes.POINTER(_vp)]),
     "wfa_server_submit": (_i, [_vp, ctypes.POINTER(Request), _llp]),
@@ -111,6 +112,13 @@ def lib():
 
 def last_error() -> str:
     return lib().wfa_last_error().decode()
+
+
+def inject_alloc_failure(n: int) -> None:
+    """Make the device allocation after n further successful ones fail once
+    with WFA_ERR_OOM (host-side fault injection for tests; n < 0 disarms).
+    See wfa_inject_alloc_failure."""
+    check(lib().wfa_inject_alloc_failure(int(n)), "wfa_inject_alloc_failure")
 
 
 def check(code, where=""):

@@ -480,6 +480,7 @@ int graph_for(BatchCtx* c, int cls) {
 using namespace wfa;
 
 extern "C" int wfa_batch_run(wfa_grid* gs, const long long* steps, int count) {
+    NvtxRange nvtx_("wfa_batch_run");
     if (count < 0 || (count > 0 && (!gs || !steps))) {
         set_error("wfa_batch_run: bad arguments");
         return WFA_ERR_ARG;

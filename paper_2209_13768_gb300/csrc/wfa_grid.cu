@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -69,7 +70,21 @@ static cudaMemPool_t grid_pool() {
     return pool;
 }
 
+// Allocations left before an injected failure (-1: none armed).
+static std::atomic<int> g_fail_countdown{-1};
+
+static bool injected_failure() {
+    int cur = g_fail_countdown.load();
+    while (cur >= 0)
+        if (g_fail_countdown.compare_exchange_weak(cur, cur - 1)) return cur == 0;
+    return false;
+}
+
 cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st) {
+    if (injected_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
     cudaMemPool_t pool = grid_pool();
     if (!pool) return cudaErrorMemoryAllocation;
     return cudaMallocFromPoolAsync(p, bytes, pool, st);
@@ -715,6 +730,11 @@ extern "C" {
 
 const char* wfa_last_error(void) { return g_last_error.c_str(); }
 
+int wfa_inject_alloc_failure(int n) {
+    wfa::g_fail_countdown.store(n < 0 ? -1 : n);
+    return WFA_OK;
+}
+
 int wfa_create_grid(int nx, int ny, int nz, double hx, double hy, double hz, int storage,
                     void* cuda_stream, wfa_grid* out) {
     if (!out) return fail(WFA_ERR_ARG, "out is NULL");
@@ -803,6 +823,7 @@ static Geo geo_of(const wfa_grid_s* g) {
 }
 
 int wfa_set_field(wfa_grid g, const float* host_dense) {
+    NvtxRange nvtx_("wfa_set_field");
     if (!g || !host_dense) return fail(WFA_ERR_ARG, "NULL argument");
     const long long N = (long long)g->n[0] * g->n[1] * g->n[2];
     // pinned host memory is read by the packing kernel itself; pageable
@@ -862,8 +883,16 @@ int wfa_set_coeffs(wfa_grid g, const float* k_host, double k_uniform, double ux,
                 g->r = g->ext_r;
                 g->own_k = false;
             } else {
-                WFA_CUDA(dev_alloc((void**)&g->k, field_elems(g) * sizeof(float), g->stream));
-                WFA_CUDA(dev_alloc((void**)&g->r, field_elems(g) * sizeof(float), g->stream));
+                // both or neither: a grid never holds k without 1/k
+                float *kb = nullptr, *rb = nullptr;
+                WFA_CUDA(dev_alloc((void**)&kb, field_elems(g) * sizeof(float), g->stream));
+                const cudaError_t e = dev_alloc((void**)&rb, field_elems(g) * sizeof(float), g->stream);
+                if (e != cudaSuccess) {
+                    dev_free(kb, g->stream);
+                    return cuda_fail(e, "conductivity allocation");
+                }
+                g->k = kb;
+                g->r = rb;
                 g->own_k = true;
             }
             WFA_CUDA(cudaMemsetAsync(g->k, 0, field_elems(g) * sizeof(float), g->stream));
@@ -1005,6 +1034,7 @@ static int prepare_k_halo(wfa_grid g) {
 }
 
 int wfa_stability_dt(wfa_grid g, double* dt_max) {
+    NvtxRange nvtx_("wfa_stability_dt");
     if (!g || !dt_max) return fail(WFA_ERR_ARG, "NULL argument");
     if (!g->coeffs_set) return fail(WFA_ERR_STATE, "set the coefficients first");
     for (int a = 0; a < 3; ++a)
@@ -1066,6 +1096,7 @@ int wfa_set_tuning(wfa_grid g, int depth, int variant) {
 }
 
 int wfa_step(wfa_grid g, long long n) {
+    NvtxRange nvtx_("wfa_step");
     if (!g) return fail(WFA_ERR_ARG, "NULL grid");
     if (n < 0) return fail(WFA_ERR_ARG, "negative step count");
     if (!g->field_set || !g->coeffs_set || !g->dt_set)
@@ -1088,6 +1119,7 @@ int wfa_step(wfa_grid g, long long n) {
 }
 
 int wfa_autotune(wfa_grid g, int* depth, int* variant) {
+    NvtxRange nvtx_("wfa_autotune");
     if (!g) return fail(WFA_ERR_ARG, "NULL grid");
     if (!g->field_set || !g->coeffs_set || !g->dt_set)
         return fail(WFA_ERR_STATE, "set the field, the coefficients and dt before tuning");
@@ -1108,6 +1140,7 @@ int wfa_steps_done(wfa_grid g, long long* n) {
 }
 
 int wfa_read_field(wfa_grid g, float* host_dense) {
+    NvtxRange nvtx_("wfa_read_field");
     if (!g || !host_dense) return fail(WFA_ERR_ARG, "NULL argument");
     if (!g->field_set) return fail(WFA_ERR_STATE, "no field set");
     if (g->halo_dirty) {   // held layers show their value even before the first step
@@ -1140,6 +1173,7 @@ int wfa_read_field(wfa_grid g, float* host_dense) {
 }
 
 int wfa_total_heat(wfa_grid g, double* e) {
+    NvtxRange nvtx_("wfa_total_heat");
     int rc_;
     if (!g || !e) return fail(WFA_ERR_ARG, "NULL argument");
     if (!g->field_set) return fail(WFA_ERR_STATE, "no field set");
@@ -1165,6 +1199,7 @@ int wfa_total_heat(wfa_grid g, double* e) {
 }
 
 int wfa_boundary_flux(wfa_grid g, double* flux) {
+    NvtxRange nvtx_("wfa_boundary_flux");
     if (!g || !flux) return fail(WFA_ERR_ARG, "NULL argument");
     if (!g->field_set || !g->coeffs_set || !g->dt_set)
         return fail(WFA_ERR_STATE, "set the field, the coefficients and dt first");

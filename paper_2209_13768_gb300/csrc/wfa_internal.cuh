@@ -20,6 +20,8 @@
 #include <cuda.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <string>
 
 #include "../../include/wfa.h"
@@ -32,6 +34,15 @@ constexpr int NUM_TILE_VARIANTS = 2;  // tile shapes compiled per (storage, k mo
 constexpr int COL_VARIANT = 3;        // the one-step column-march kernel
 constexpr int FUSED_VARIANT = 4;      // the two-step column-march kernel (uniform k)
 constexpr int INPLACE_VARIANT = 5;    // the one-step column-march kernel, boundaries in place
+
+// NVTX range over one API call: a named span on a profiler's timeline
+// (nothing happens unless a tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---------------------------------------------------------------- errors --
 void set_error(const char* fmt, ...);

@@ -174,11 +174,25 @@ static int ceil_log2(int v) {
     return k;
 }
 
+// The device a choice was measured on: compute capability and SM count, so
+// one cache file can serve different GPUs.
+static const char* device_tag() {
+    static char tag[32] = "";
+    if (!tag[0]) {
+        int dev = 0, major = 0, minor = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+        snprintf(tag, sizeof tag, "cc%d%d.sm%d", major, minor, num_sms());
+    }
+    return tag;
+}
+
 static std::string tune_key(const wfa_grid_s* g) {
     char buf[128];
     const bool adv = g->u[0] != 0.0 || g->u[1] != 0.0 || g->u[2] != 0.0;
-    snprintf(buf, sizeof buf, "%s.%s.%s.%d.%d.%d", g->storage == WFA_BF16 ? "bf16" : "f32", g->r ? "k" : "u",
-             adv ? "adv" : "noadv", ceil_log2(g->n[0]), ceil_log2(g->n[1]), ceil_log2(g->n[2]));
+    snprintf(buf, sizeof buf, "%s.%s.%s.%s.%d.%d.%d", device_tag(), g->storage == WFA_BF16 ? "bf16" : "f32",
+             g->r ? "k" : "u", adv ? "adv" : "noadv", ceil_log2(g->n[0]), ceil_log2(g->n[1]), ceil_log2(g->n[2]));
     return buf;
 }
 

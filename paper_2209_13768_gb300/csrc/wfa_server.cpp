@@ -11,6 +11,7 @@
 // on its own stream, while the ticks run; a finished request's memory is
 // released as soon as its result is on the host.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -99,10 +100,18 @@ struct wfa_server_s {
     void run();
     void prep_loop(int w);
     int setup(Req* r, cudaStream_t st);
+    int setup_grid(Req* r, cudaStream_t st);
     void finish(Req* r, bool ok, const std::string& why);
 };
 
 int wfa_server_s::setup(Req* r, cudaStream_t st) {
+    nvtxRangePushA("wfa_server_setup");
+    const int rc = setup_grid(r, st);
+    nvtxRangePop();
+    return rc;
+}
+
+int wfa_server_s::setup_grid(Req* r, cudaStream_t st) {
     const wfa_request& s = r->spec;
     int rc = wfa_create_grid(s.nx, s.ny, s.nz, s.hx, s.hy, s.hz, s.storage, st, &r->g);
     if (rc) return rc;
@@ -247,8 +256,10 @@ void wfa_server_s::run() {
             gs.push_back(r->g);
             steps.push_back(q);
         }
+        nvtxRangePushA("wfa_server_tick");
         if (!rc && !gs.empty()) rc = wfa_batch_run(gs.data(), steps.data(), (int)gs.size());
         if (!rc) rc = cudaStreamSynchronize(stream) == cudaSuccess ? 0 : WFA_ERR_CUDA;
+        nvtxRangePop();
         const auto t1 = clk::now();
         const std::string why = rc ? std::string(wfa_last_error()) : std::string();
         std::lock_guard<std::mutex> lk(mu);

@@ -180,3 +180,33 @@ def test_server_budget_admission():
     ref = run_gpu(p, variant=-1)
     for out in outs:
         np.testing.assert_array_equal(out, ref)
+
+
+def test_server_request_fails_cleanly_on_injected_oom():
+    # the first device allocation of some request fails (host-side
+    # injection): that request alone reports the error, the others complete
+    # bitwise, and the server's memory accounting returns to zero
+    rng = np.random.default_rng(17)
+    probs = [_problem(i, rng) for i in range(6)]
+    for p in probs:
+        p.steps = max(p.steps, 2)
+    try:
+        with wfa.Server(budget_bytes=4 << 30, quantum=5) as srv:
+            wfa.inject_alloc_failure(0)
+            tickets = [srv.submit(p.shape, p.T0, p.steps, h=p.h, k=p.k, u=p.u, bc=p.bc) for p in probs]
+            outs, failed = [], 0
+            for t in tickets:
+                try:
+                    outs.append(srv.wait(t, timeout=60))
+                except wfa.WfaError as e:
+                    assert "out of memory" in str(e)
+                    outs.append(None)
+                    failed += 1
+            st = srv.stats()
+    finally:
+        wfa.inject_alloc_failure(-1)
+    assert failed == 1 and st["completed"] == len(probs) - 1
+    assert st["resident_bytes"] == 0
+    for p, out in zip(probs, outs):
+        if out is not None:
+            np.testing.assert_array_equal(out, run_gpu(p, variant=-1))

@@ -304,6 +304,37 @@ def test_argument_limits():
         assert e.value.code == -3
 
 
+def test_injected_allocation_failures():
+    # host-side fault injection: an allocation made to fail reports
+    # WFA_ERR_OOM and leaves the grid as it was; nothing faults on the device
+    try:
+        for n in range(4):   # each of wfa_create_grid's four device buffers
+            wfa.inject_alloc_failure(n)
+            with pytest.raises(wfa.WfaError) as e:
+                wfa.Grid((24, 20, 18))
+            assert e.value.code == -2 and "out of memory" in str(e.value)
+        wfa.inject_alloc_failure(-1)
+        p = _mixed_problem(2, shape=(24, 20, 18), kvar=True, adv=False, seed=21)
+        dt = oracle_dt(p)   # within the limits of both conductivities
+        q = W.Problem(shape=p.shape, T0=p.T0, k=0.8, u=p.u, bc=p.bc, h=p.h, dt=dt, steps=4)
+        with make_grid(q) as g:
+            g.step(2)
+            wfa.inject_alloc_failure(1)   # k is allocated, 1/k is not
+            with pytest.raises(wfa.WfaError) as e:
+                g.set_coeffs(p.k)
+            assert e.value.code == -2
+            g.step(2)                     # still the uniform-k grid
+            np.testing.assert_array_equal(g.read_field(), run_gpu(q))
+            g.set_coeffs(p.k)             # and per-cell k works afterwards
+            g.step(3)
+            ref = run_oracle(q, steps=4)
+            ref = run_oracle(W.Problem(shape=p.shape, T0=ref.astype(np.float32), k=p.k, u=p.u, bc=p.bc, h=p.h,
+                                       dt=dt, steps=3))
+            assert rel_linf(g.read_field(), ref) <= F32_TOL
+    finally:
+        wfa.inject_alloc_failure(-1)
+
+
 def test_degenerate_coefficients():
     # k = 0 and no advection: nothing moves, the limit is infinite
     rng = np.random.default_rng(13)
