@@ -233,7 +233,9 @@ const char* wfa_last_error(void);
  * the autotuner), the next one fails once as if the device were out of
  * memory, so that call returns WFA_ERR_OOM and leaves the grid as it was;
  * n < 0 disarms a pending failure. Process-wide; nothing is injected on the
- * device. Returns WFA_OK. */
+ * device. The environment variable WFA_FAULT_ALLOC_AT=n (n >= 1), read at the
+ * first device allocation, arms the same failure for the n-th allocation of
+ * the process. Returns WFA_OK. */
 int wfa_inject_alloc_failure(int n);
 
 /* ----------------------------------------------------------- batching -- */

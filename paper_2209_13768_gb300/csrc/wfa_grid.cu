@@ -3,6 +3,7 @@
 #include <stdarg.h>
 #include <stdint.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -74,6 +75,12 @@ static cudaMemPool_t grid_pool() {
 static std::atomic<int> g_fail_countdown{-1};
 
 static bool injected_failure() {
+    static std::once_flag env_once;   // WFA_FAULT_ALLOC_AT=n: the n-th allocation of the process fails
+    std::call_once(env_once, [] {
+        const char* v = getenv("WFA_FAULT_ALLOC_AT");
+        const long n = v ? strtol(v, nullptr, 10) : 0;
+        if (n >= 1 && n < (1L << 30)) g_fail_countdown.store((int)n - 1);
+    });
     int cur = g_fail_countdown.load();
     while (cur >= 0)
         if (g_fail_countdown.compare_exchange_weak(cur, cur - 1)) return cur == 0;

@@ -10,6 +10,10 @@ bf16 rounding, within a few bf16 ulps where fp32 vs fp64 arithmetic tips a
 rounding. Across kernels (tile shapes, temporal depths, the one-column
 kernel) the per-cell expression is fixed, so fields must be bit-identical.
 """
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
@@ -22,6 +26,7 @@ pytestmark = pytest.mark.gpu
 
 D, ZF, P, DC = W.D, W.ZF, W.P, W.DC
 F32_TOL = 1e-5
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def bf16_bound(steps):
@@ -326,6 +331,7 @@ def test_injected_allocation_failures():
             g.step(2)                     # still the uniform-k grid
             np.testing.assert_array_equal(g.read_field(), run_gpu(q))
             g.set_coeffs(p.k)             # and per-cell k works afterwards
+            g.set_dt(dt)                  # (new coefficients ask for dt again)
             g.step(3)
             ref = run_oracle(q, steps=4)
             ref = run_oracle(W.Problem(shape=p.shape, T0=ref.astype(np.float32), k=p.k, u=p.u, bc=p.bc, h=p.h,
@@ -333,6 +339,15 @@ def test_injected_allocation_failures():
             assert rel_linf(g.read_field(), ref) <= F32_TOL
     finally:
         wfa.inject_alloc_failure(-1)
+    # the same through the environment, in a fresh process: the third
+    # allocation (the reduction buffer of wfa_create_grid) fails
+    code = ("import paper_2209_13768_gb300 as wfa\n"
+            "try:\n    wfa.Grid((8, 8, 8))\nexcept wfa.WfaError as e:\n    print('code', e.code)\n"
+            "g = wfa.Grid((8, 8, 8)); g.close(); print('then ok')\n")
+    env = dict(os.environ, WFA_FAULT_ALLOC_AT="3")
+    r = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert "code -2" in r.stdout and "then ok" in r.stdout
 
 
 def test_degenerate_coefficients():
