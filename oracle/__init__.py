@@ -1,4 +1,5 @@
-"""FP64 CPU oracle for the explicit finite-volume sweep of arXiv 2209.13768.
+"""FP64 CPU oracle for the finite-volume sweeps of arXiv 2209.13768 (explicit
+steps and implicit steps solved by CG).
 
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` use it; the library never does. It shares no
@@ -7,6 +8,8 @@ code with the CUDA path (the C source is ``wfa_oracle.c`` beside this file).
 Functions
 ---------
 run(T0, n_steps, **problem)      -> field after n_steps (Eq. expl_form, face-flux form)
+implicit(T0, n_steps, **problem) -> (field, CG iterations, relative residual) after
+                                    n_steps backward-Euler steps (Eq. impl_form, classic CG)
 dt_max(**problem)                -> positivity limit of the explicit step (Sec. 1.1.1)
 total_heat(T, h)                 -> sum of T times the cell volume
 round_to(x, mode)                -> fp32 / bf16 nearest-even rounding used by ``run``
@@ -65,6 +68,10 @@ def _bind(path):
     lib.wfa_oracle_total_heat.restype = ctypes.c_double
     lib.wfa_oracle_round.argtypes = [ctypes.c_double, ctypes.c_int]
     lib.wfa_oracle_round.restype = ctypes.c_double
+    if hasattr(lib, "wfa_oracle_implicit"):
+        lib.wfa_oracle_implicit.argtypes = [i64p, dp, ctypes.c_double, dp, ip, dp, ctypes.c_double, dp,
+                                            ctypes.c_int64, ctypes.c_double, ctypes.c_int64, i64p, dp, ctypes.c_int]
+        lib.wfa_oracle_implicit.restype = ctypes.c_int
     return lib
 
 
@@ -119,6 +126,29 @@ def run(T0, n_steps, *, shape, h=(1.0, 1.0, 1.0), k=1.0, u=(0.0, 0.0, 0.0), bc, 
     if rc != 0:
         raise ValueError(f"oracle rejected the problem (code {rc})")
     return T
+
+
+def implicit(T0, n_steps, *, shape, h=(1.0, 1.0, 1.0), k=1.0, bc, dt, rtol=1e-12, max_iter=10000,
+             threads=0, lib=None):
+    """Advance T0 by n_steps backward-Euler steps, each solved by classic CG
+    in fp64 (Sec. 1.1.2, Eq. impl_form, face-flux form, no advection).
+
+    Returns (T, iterations of all steps, last step's relative residual
+    sqrt(r.r / b.b)). rtol = 0 runs exactly max_iter iterations per step
+    (fewer only if the residual becomes exactly zero)."""
+    lib = lib or _load()
+    n, hh, _, k_uniform, karr, kinds, vals = _common(shape, h, (0.0, 0.0, 0.0), k, bc)
+    T = np.array(T0, dtype=np.float64, order="C", copy=True)
+    nx, ny, nz = (int(s) for s in shape)
+    if T.shape != (nz, ny, nx):
+        raise ValueError(f"T0 has shape {T.shape}, expected {(nz, ny, nx)}")
+    iters = ctypes.c_int64()
+    res = ctypes.c_double()
+    rc = lib.wfa_oracle_implicit(n, hh, k_uniform, _ptr(karr), kinds, vals, float(dt), _ptr(T), int(n_steps),
+                                 float(rtol), int(max_iter), ctypes.byref(iters), ctypes.byref(res), int(threads))
+    if rc != 0:
+        raise ValueError(f"oracle rejected the problem (code {rc})")
+    return T, iters.value, res.value
 
 
 def dt_max(*, shape, h=(1.0, 1.0, 1.0), k=1.0, u=(0.0, 0.0, 0.0), bc, lib=None):

@@ -286,3 +286,127 @@ double wfa_oracle_total_heat(const int64_t n[3], const double h[3], const double
     for (int64_t c = 0; c < N; ++c) s += T[c];
     return s * h[0] * h[1] * h[2];
 }
+
+/*
+ * Backward-time, centred-space steps solved by classic conjugate gradients
+ * (Sec. 1.1.2, Eq. impl_form, in the face-flux form above; diffusion only:
+ * with advection the system is not symmetric and CG does not apply, so u is
+ * not an argument).
+ *
+ * One step finds T^{n+1} with
+ *   T^{n+1}_C - dt acc(T^{n+1})_C = T^n_C   for every cell that is not held,
+ *   T^{n+1}_C = its face value              for held cells,
+ * where acc is the explicit step's accumulation (face_pass), affine in T
+ * through the Dirichlet face values. Split T^{n+1} = z + y with z the held
+ * values on held cells and 0 elsewhere, y zero on held cells; then on the
+ * free cells
+ *   A y = b,   A y = y - dt acc0(y),   b = T^n + dt acc(z),
+ * acc0 being acc with every Dirichlet face value set to 0 (its linear part).
+ * A is symmetric positive definite (unit diagonal plus a weighted graph
+ * Laplacian; Eq. impl_form is this system for uniform k and held layers,
+ * scaled by psi = 1 / (1 + 6 omega)).
+ *
+ * Classic CG (Hestenes and Stiefel), two inner products per iteration as in
+ * Sec. 1.1.2; every inner product is a plain sequential fp64 sum over the
+ * free cells in index order:
+ *   x = T^n on free cells;  r = b - A x;  p = r;  rr = r.r;  bb = b.b
+ *   while rr > rtol^2 bb and it < max_iter:
+ *     q = A p;  alpha = rr / (p.q);  x += alpha p;  r -= alpha q
+ *     rr' = r.r;  beta = rr' / rr;  p = r + beta p;  rr = rr';  ++it
+ * T^{n+1} = z + x. *iters receives the iterations of all steps together,
+ * *rel_res the last step's sqrt(rr / bb) (sqrt(rr) when bb = 0).
+ * Returns 0, -1 / -3 like wfa_oracle_run, -2 on allocation failure.
+ */
+static void apply_A(const prob_t* p0, const unsigned char* held, const double* y, double* out, double* acc) {
+    const int64_t N = p0->n[0] * p0->n[1] * p0->n[2];
+    memset(acc, 0, (size_t)N * sizeof(double));
+    for (int a = 0; a < 3; ++a) face_pass(p0, y, acc, a);
+    for (int64_t c = 0; c < N; ++c) out[c] = held[c] ? 0.0 : y[c] - p0->dt * acc[c];
+}
+
+static double dot_free(const unsigned char* held, const double* a, const double* b, int64_t N) {
+    double s = 0.0;
+    for (int64_t c = 0; c < N; ++c)
+        if (!held[c]) s += a[c] * b[c];
+    return s;
+}
+
+int wfa_oracle_implicit(const int64_t n[3], const double h[3], double k_uniform, const double* k,
+                        const int kind[6], const double value[6], double dt, double* T, int64_t nsteps,
+                        double rtol, int64_t max_iter, int64_t* iters, double* rel_res, int nthreads) {
+    prob_t p, p0;
+    memcpy(p.n, n, sizeof p.n);
+    memcpy(p.h, h, sizeof p.h);
+    for (int a = 0; a < 3; ++a) p.u[a] = 0.0;
+    p.k_uniform = k_uniform;
+    p.k = k;
+    memcpy(p.kind, kind, sizeof p.kind);
+    memcpy(p.value, value, sizeof p.value);
+    p.dt = dt;
+    int rc = check(&p);
+    if (rc) return rc;
+    if (!(dt >= 0.0) || !(rtol >= 0.0) || max_iter < 0) return -1;
+    p0 = p;
+    for (int f = 0; f < 6; ++f) p0.value[f] = 0.0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    const int64_t N = n[0] * n[1] * n[2];
+    unsigned char* held = held_mask(&p);
+    double* buf = (double*)malloc((size_t)N * 6 * sizeof(double));
+    if (!held || !buf) {
+        free(held);
+        free(buf);
+        return -2;
+    }
+    double *z = buf, *x = buf + N, *r = buf + 2 * N, *pv = buf + 3 * N, *q = buf + 4 * N, *acc = buf + 5 * N;
+    int64_t total = 0;
+    double last = 0.0;
+    for (int64_t c = 0; c < N; ++c) {
+        z[c] = held[c] ? value[held[c] - 1] : 0.0;
+        if (held[c]) T[c] = z[c];
+    }
+    for (int64_t s = 0; s < nsteps; ++s) {
+        /* b = T^n + dt acc(z) on the free cells (kept in r for now) */
+        memset(acc, 0, (size_t)N * sizeof(double));
+        for (int a = 0; a < 3; ++a) face_pass(&p, z, acc, a);
+        for (int64_t c = 0; c < N; ++c) {
+            r[c] = held[c] ? 0.0 : T[c] + dt * acc[c];
+            x[c] = held[c] ? 0.0 : T[c];
+        }
+        const double bb = dot_free(held, r, r, N);
+        apply_A(&p0, held, x, q, acc);
+        for (int64_t c = 0; c < N; ++c) {
+            r[c] -= q[c];
+            pv[c] = r[c];
+        }
+        double rr = dot_free(held, r, r, N);
+        int64_t it = 0;
+        while (rr > rtol * rtol * bb && it < max_iter) {
+            apply_A(&p0, held, pv, q, acc);
+            const double pq = dot_free(held, pv, q, N);
+            if (!(pq > 0.0)) break; /* exact solution reached (p = 0) or breakdown */
+            const double alpha = rr / pq;
+            for (int64_t c = 0; c < N; ++c) {
+                x[c] += alpha * pv[c];
+                r[c] -= alpha * q[c];
+            }
+            const double rr_new = dot_free(held, r, r, N);
+            const double beta = rr_new / rr;
+            for (int64_t c = 0; c < N; ++c) pv[c] = r[c] + beta * pv[c];
+            rr = rr_new;
+            ++it;
+        }
+        for (int64_t c = 0; c < N; ++c)
+            if (!held[c]) T[c] = x[c];
+        total += it;
+        last = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
+    }
+    if (iters) *iters = total;
+    if (rel_res) *rel_res = last;
+    free(held);
+    free(buf);
+    return 0;
+}

@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
+from test_oracle_implicit import dense_implicit
 from test_oracle_pins import BC_MIXES, _apply_held, _bc, brute_matrix, _spectral_solution
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "wfa_oracle.c")
@@ -27,6 +28,13 @@ MUTANTS = {
     "dt limit without the Dirichlet factor": ("D += 2.0 * kc(&p, C) * inv_h2;",
                                               "D += kc(&p, C) * inv_h2;"),
     "dt limit without advection": ("if (side == 1 && u[a] > 0.0) D += u[a] / h[a];", ""),
+    "CG without beta (steepest descent)": ("const double beta = rr_new / rr;", "const double beta = 0.0;"),
+    "implicit right-hand side without boundary terms": ("r[c] = held[c] ? 0.0 : T[c] + dt * acc[c];",
+                                                        "r[c] = held[c] ? 0.0 : T[c];"),
+    "implicit operator sign": ("out[c] = held[c] ? 0.0 : y[c] - p0->dt * acc[c];",
+                               "out[c] = held[c] ? 0.0 : y[c] + p0->dt * acc[c];"),
+    "CG residual update sign": ("r[c] -= alpha * q[c];", "r[c] += alpha * q[c];"),
+    "Dirichlet values left in the linear part": ("for (int f = 0; f < 6; ++f) p0.value[f] = 0.0;", "(void)0;"),
 }
 
 
@@ -71,6 +79,27 @@ def battery(lib):
     ref = _spectral_solution(T0, 10, shape, (1.0, 0.9, 1.2), 0.6, u, kinds, 0.2)
     if not np.allclose(T, ref, rtol=0, atol=1e-12):
         failed.append("spectral")
+    # implicit step: dense solve, and the CG iteration bound
+    rng = np.random.default_rng(102)
+    shape = (5, 4, 6)
+    k = np.exp(0.5 * rng.standard_normal(shape[::-1]))
+    for mix in (BC_MIXES[4], BC_MIXES[5]):
+        bc = _bc(mix, list(rng.uniform(-1, 2, 6)))
+        T0 = rng.uniform(0, 1, shape[::-1])
+        try:
+            T, _, _ = oracle.implicit(T0, 2, shape=shape, h=(1.1, 0.8, 1.3), k=k, bc=bc, dt=0.7, rtol=1e-14,
+                                      max_iter=2000, lib=lib)
+            ref, _, _ = dense_implicit(T0, 2, shape, (1.1, 0.8, 1.3), k, bc, 0.7)
+            if not np.allclose(T, ref, rtol=0, atol=1e-10):
+                failed.append("implicit dense")
+        except ValueError:
+            failed.append("implicit rejected")
+    shape = (5, 4, 4)
+    bc = _bc(["dirichlet_cell"] * 2 + ["periodic"] * 4)
+    T0 = np.random.default_rng(4).uniform(0, 1, shape[::-1])
+    _, iters, res = oracle.implicit(T0, 1, shape=shape, k=1.0, bc=bc, dt=0.9, rtol=1e-12, max_iter=2000, lib=lib)
+    if iters > 15 or res > 1e-12:   # 15 distinct eigenvalues
+        failed.append("implicit iterations")
     return failed
 
 

@@ -281,8 +281,10 @@ def test_integer_shift_courant_one():
 # --------------------------------------------------------------------------
 # whole-field solutions through scipy transforms (uniform k, random field)
 # --------------------------------------------------------------------------
-def _spectral_solution(T0, n, shape, h, kval, u, kinds, dt):
-    """n steps of the uniform-k operator, axis by axis in its eigenbasis."""
+def _spectral_solution(T0, n, shape, h, kval, u, kinds, dt, implicit=False):
+    """n steps of the uniform-k operator, axis by axis in its eigenbasis
+    (explicit: each mode times 1 - dt rate; implicit, backward Euler: divided
+    by 1 + dt rate)."""
     X = np.asarray(T0, dtype=np.float64)
     sl = [slice(None)] * 3
     # forward transforms, axis 2 of the array is x
@@ -323,7 +325,7 @@ def _spectral_solution(T0, n, shape, h, kval, u, kinds, dt):
             total = rate.reshape(shp)
         else:
             total = total + rate.reshape(shp)
-    X = X * (1.0 - dt * total) ** n
+    X = X * ((1.0 / (1.0 + dt * total)) if implicit else (1.0 - dt * total)) ** n
     for ax, kind, N in reversed(plan):
         if kind == D:
             X = sfft.idst(X, type=2, axis=ax, norm="ortho")
