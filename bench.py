@@ -43,8 +43,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["lognormal", "heat64", "advdiff", "advdiff_bf16", "batch", "serve"],
+    ap.add_argument("--workload", choices=["lognormal", "heat64", "advdiff", "advdiff_bf16", "batch", "serve",
+                                           "implicit", "implicit_lognormal"],
                     default="lognormal")
+    ap.add_argument("--rtol", type=float, default=1e-6, help="implicit: CG tolerance ||r|| <= rtol ||b||")
     ap.add_argument("--serve-requests", type=int, default=400,
                     help="requests in the serving sample added to the line (0: none)")
     ap.add_argument("--solve-steps", type=int, default=0, help="time steps per benchmark step (0: workload default)")
@@ -178,6 +180,36 @@ def reference_arm(args, rank):
     import numpy as np
 
     import oracle
+    if args.workload in ("implicit", "implicit_lognormal"):
+        from paper_2209_13768_gb300 import workloads as W
+        shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else W.IMPLICIT_SHAPE
+        p = W.implicit_problem(shape, lognormal=args.workload == "implicit_lognormal")
+        kk = p.k if np.isscalar(p.k) else np.asarray(p.k, dtype=np.float64)
+        cells = shape[0] * shape[1] * shape[2]
+        per_step = 2   # each benchmark step: one time step of two CG iterations on the full grid
+        run = lambda: oracle.implicit(p.T0, 1, shape=p.shape, h=p.h, k=kk, bc=p.bc, dt=p.dt, rtol=0.0,
+                                      max_iter=per_step)
+        for _ in range(args.warmup):
+            run()
+        times = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            run()
+            times.append(time.perf_counter() - t0)
+        total = sum(times)
+        value = cells * per_step * args.steps / total / 1e9
+        unit = "G cell-iterations/s"
+        line = {"impl": "reference", "metric": "CG cell-iterations/s (G) of the implicit step, and % HBM roofline "
+                "on 1 GB300", "value": value, "unit": unit, "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": p.name, "cells": cells,
+                           "sample": f"one time step of {per_step} CG iterations per benchmark step"},
+                "cpu_baseline": {"value": value, "unit": unit, "cores": os.cpu_count(), "kind": "oracle",
+                                 "sample": f"one fp64 time step of {per_step} CG iterations (set-up included)"},
+                "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     p = workload(args.workload, args.solve_steps, args.shape)
     k = p.k if isinstance(p.k, float) else np.asarray(p.k, dtype=np.float64)
     dt = p.dt if p.dt else 0.9 * oracle.dt_max(shape=p.shape, h=p.h, k=k, u=p.u, bc=p.bc)
@@ -313,6 +345,117 @@ def batch_bench(args):
     print(json.dumps(line), flush=True)
 
 
+def cg_bytes_per_cell(kvar):
+    """Algorithmic HBM bytes per cell per CG iteration: cg_spmv reads r and
+    p_old and writes p and q (16 B, + 4 B of 1/k for per-cell k); cg_update
+    reads x, p, q, r and writes x, r (24 B)."""
+    return 40 + (4 if kvar else 0)
+
+
+def implicit_bench(args, rank, world, dist):
+    """Backward-Euler steps solved by classic CG (Sec. 1.1.2, Eq. impl_form):
+    512^3, omega = 1/10, held boundary layers; a benchmark step is
+    --solve-steps time steps (default 10), each CG to --rtol."""
+    import numpy as np
+    import torch
+
+    import paper_2209_13768_gb300 as wfa
+    from paper_2209_13768_gb300 import workloads as W
+    shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else W.IMPLICIT_SHAPE
+    p = W.implicit_problem(shape, steps=args.solve_steps or 10, lognormal=args.workload == "implicit_lognormal")
+    kvar = not np.isscalar(p.k)
+    cells = shape[0] * shape[1] * shape[2]
+    stream = torch.cuda.Stream()
+    g = wfa.Grid(p.shape, h=p.h, stream=stream.cuda_stream)
+    g.set_bcs(p.bc)
+    g.set_coeffs(p.k)
+    g.set_field(p.T0)
+    max_iter = 1000
+    for _ in range(args.warmup):
+        g.implicit_step(p.dt, p.steps, rtol=args.rtol, max_iter=max_iter)
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = g.launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    iters = 0
+    res = 0.0
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        it, res = g.implicit_step(p.dt, p.steps, rtol=args.rtol, max_iter=max_iter)
+        ev[i][1].record(stream)
+        iters += it
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    gpu_launches = g.launch_count() - launches0
+    total_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    total_s = max_over_ranks(total_s, dist, "cuda")
+    value = world * cells * iters / total_s / 1e9
+    bpc = cg_bytes_per_cell(kvar)
+    achieved = bpc * cells * iters / total_s / 1e9
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    e2e = None
+    if not args.no_e2e:
+        T0h = torch.from_numpy(np.ascontiguousarray(p.T0)).pin_memory()
+        outh = torch.empty(tuple(p.T0.shape), dtype=torch.float32).pin_memory()
+        e2e_t, e2e_it = [], 0
+        for i in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.set_field(T0h)
+            it, _ = g.implicit_step(p.dt, p.steps, rtol=args.rtol, max_iter=max_iter)
+            g.read_field(outh)
+            if i:
+                e2e_t.append(time.perf_counter() - t0)
+                e2e_it += it
+        e2e_s = max_over_ranks(sum(e2e_t), dist, "cuda")
+        e2e = {"value": world * cells * e2e_it / e2e_s / 1e9, "unit": "G cell-iterations/s",
+               "h2d_bytes_per_step": cells * 4, "d2h_bytes_per_step": cells * 4,
+               "ms_per_step": 1e3 * e2e_s / len(e2e_t)}
+    g.close()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        kk = p.k if np.isscalar(p.k) else np.asarray(p.k, dtype=np.float64)
+        t0 = time.perf_counter()
+        oracle.implicit(p.T0, 1, shape=p.shape, h=p.h, k=kk, bc=p.bc, dt=p.dt, rtol=0.0, max_iter=1)
+        one = time.perf_counter() - t0
+        m = max(1, min(50, int(args.cpu_seconds / max(one, 1e-6))))
+        t0 = time.perf_counter()
+        oracle.implicit(p.T0, 1, shape=p.shape, h=p.h, k=kk, bc=p.bc, dt=p.dt, rtol=0.0, max_iter=m)
+        el = time.perf_counter() - t0
+        cpu = {"value": cells * m / el / 1e9, "unit": "G cell-iterations/s", "cores": os.cpu_count(),
+               "kind": "oracle", "sample": f"one fp64 time step of {m} CG iterations on the full grid "
+                                           "(set-up and the initial residual included), OpenMP face passes"}
+    if rank == 0:
+        line = {"metric": "CG cell-iterations/s (G) of the implicit step, and % HBM roofline on 1 GB300",
+                "value": value, "unit": "G cell-iterations/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": p.name, "cells": cells, "time_steps_per_step": p.steps, "dt": p.dt,
+                           "omega": p.dt, "rtol": args.rtol, "cg_iterations": iters,
+                           "cg_iterations_per_time_step": iters / (p.steps * args.steps), "last_rel_residual": res,
+                           "conductivity": "per-cell lognormal(0,0.5)" if kvar else "uniform 1",
+                           "l2": "inputs larger than L2 (six 512 MiB vectors)", "parallelism": f"replicas x{world}"},
+                "cg_iterations_per_s": world * iters / total_s,
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": None,
+                             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                             "bytes_per_cell_per_iteration": bpc,
+                             "scope": "every kernel of the timed steps (cg_init, cg_spmv, cg_update) and the "
+                                      "host's flag checks between graph runs"},
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -339,6 +482,9 @@ def main():
         return
     if args.workload == "serve":
         print(json.dumps({"metric": METRIC, "serving": serving_sample(args.serve_requests or 400)}), flush=True)
+        return
+    if args.workload in ("implicit", "implicit_lognormal"):
+        implicit_bench(args, rank, world, dist)
         return
 
     p = workload(args.workload, args.solve_steps, args.shape)

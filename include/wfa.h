@@ -171,6 +171,27 @@ int wfa_total_heat(wfa_grid g, double* e);
  * Errors: WFA_ERR_ARG (null pointer, negative or too large n), WFA_ERR_CUDA. */
 int wfa_sum_f32_noalloc(const float* d_x, long long n, double scale, double* d_out, void* stream);
 
+/* Implicit time steps (Sec. 1.1.2, Eq. impl_form): n >= 0 backward-Euler
+ * steps of size dt >= 0 (no stability limit; dt of wfa_set_dt is not used),
+ * each solving, for every cell that is not held,
+ *   T'_C - dt * [ sum_f K_f (T'_D - T'_C) / h_a^2
+ *                 + sum_{Dirichlet faces} 2 k_C (Tb - T'_C) / h_a^2 ] = T_C
+ * (the explicit step's face terms taken at the new time; held layers keep
+ * their value) by classic conjugate gradients, two inner products per
+ * iteration, started from T. Uniform k = k0, h = 1 and held layers on every
+ * face give Eq. impl_form with omega = k0 dt. A step stops when
+ * ||r|| <= rtol ||b|| (the recursively updated residual; rtol = 0 runs
+ * max_iter iterations) or after max_iter iterations. Work vectors (four fp32
+ * fields) are allocated on the first call and kept with the grid.
+ * *iters (may be NULL) receives the CG iterations of all n steps,
+ * *rel_res (may be NULL) the last step's ||r|| / ||b||. Synchronises the
+ * stream. Needs fp32 storage and no advection (with u != 0 the system is not
+ * symmetric): WFA_ERR_ARG otherwise, or for dt < 0, n < 0, rtol < 0,
+ * max_iter < 0; WFA_ERR_STATE before the field and coefficients are set;
+ * WFA_ERR_BC for a periodic face paired with a non-periodic one. */
+int wfa_implicit_step(wfa_grid g, double dt, long long n, double rtol, int max_iter, long long* iters,
+                      double* rel_res);
+
 /* Heat that one time step from the current field brings in through the
  * Dirichlet faces (Sec. 3's reduction, applied to the boundary), in fp64:
  * dt * hx*hy*hz * sum over the cells on Dirichlet faces of

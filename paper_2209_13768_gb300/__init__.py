@@ -74,6 +74,7 @@ SIGNATURES = {
     "wfa_sum_f32_noalloc": (_i, [_vp, _ll, _d, _vp, _vp]),
     "wfa_last_error": (ctypes.c_char_p, []),
     "wfa_inject_alloc_failure": (_i, [_i]),
+    "wfa_implicit_step": (_i, [_vp, _d, _ll, _d, _i, _llp, _dp]),
     "wfa_batch_run": (_i, [ctypes.POINTER(_vp), _llp, _i]),
     "wfa_server_create": (_i, [_sz, _i, _ll, ctypes.POINTER(_vp)]),
     "wfa_server_submit": (_i, [_vp, ctypes.POINTER(Request), _llp]),
@@ -257,6 +258,15 @@ class Grid:
         n = ctypes.c_longlong()
         check(lib().wfa_launch_count(self.handle, ctypes.byref(n)), "wfa_launch_count")
         return n.value
+
+    def implicit_step(self, dt, n=1, rtol=1e-6, max_iter=1000):
+        """n backward-Euler steps of size dt, each solved by classic CG to
+        ||r|| <= rtol ||b|| (see wfa_implicit_step). Returns (CG iterations of
+        all steps, the last step's relative residual)."""
+        it, res = ctypes.c_longlong(), ctypes.c_double()
+        check(lib().wfa_implicit_step(self.handle, float(dt), int(n), float(rtol), int(max_iter),
+                                      ctypes.byref(it), ctypes.byref(res)), "wfa_implicit_step")
+        return it.value, res.value
 
     def kernel_time(self):
         """(summed milliseconds, launches) of the sampled kernels since the last call."""

@@ -810,6 +810,7 @@ int wfa_destroy_grid(wfa_grid g) {
     free_tmaps(g);
     free_timing(g);
     free_graphs(g);
+    free_cg(g);
     delete g;
     return WFA_OK;
 }
@@ -860,7 +861,6 @@ int wfa_set_field(wfa_grid g, const float* host_dense) {
     return WFA_OK;
 }
 
-static int prepare_k_halo(wfa_grid g);
 
 int wfa_set_coeffs(wfa_grid g, const float* k_host, double k_uniform, double ux, double uy, double uz) {
     if (!g) return fail(WFA_ERR_ARG, "NULL grid");

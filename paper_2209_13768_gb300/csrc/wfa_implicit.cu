@@ -1,0 +1,728 @@
+// Implicit (backward-Euler) time steps solved by classic conjugate gradients
+// (Sec. 1.1.2, Eq. impl_form), in the same face-flux form as the explicit
+// sweep, diffusion only (with advection the system is not symmetric and CG
+// does not apply).
+//
+// One step solves, for every cell that is not held,
+//   T'_C + sum_f c_f (T'_C - T'_D) + sum_{Dirichlet faces} d_f (T'_C - Tb_f) = T_C
+// with c_f = dt K_f / h_a^2 (K_f the harmonic-mean face conductivity) and
+// d_f = 2 dt k_C / h_a^2; held cells keep their value. Moving the known
+// values (Dirichlet faces, held neighbours) to the right-hand side leaves a
+// symmetric positive definite system A y = b on the free cells, solved from
+// y = T by classic CG with its two inner products per iteration:
+//
+//   q = A p,  alpha = r.r / p.q,  x += alpha p,  r -= alpha q,
+//   beta = r.r' / r.r,  p = r + beta p
+//
+// GB300 mapping. The field x is the grid's fp32 buffer, updated in place;
+// r, p (two buffers) and q are fp32 work vectors in the same padded layout.
+// Each iteration is two HBM-bound kernels:
+//   cg_spmv   p = r + beta p_old on the fly (for the cell and its six
+//             neighbours), q = A p, and the block partials of p.q; reads r and
+//             p_old, writes p and q (16 B a cell, + 4 B of 1/k for per-cell k);
+//   cg_update x += alpha p, r -= alpha q, and the block partials of r.r
+//             (reads x, p, q, r, writes x, r: 24 B a cell).
+// The last block of each kernel to finish (an atomic ticket, no waiting) sums
+// the partials in a fixed order and computes alpha (resp. beta and the
+// convergence test) on the device, so no host round trip sits between
+// iterations: runs of iterations are captured once as a CUDA graph and
+// replayed, the host reading the convergence flag between runs, one run ahead.
+// Periodic axes read the neighbour across the boundary from a twin copy
+// that every writer of a boundary cell also stores one cell beyond the
+// opposite face; non-periodic boundary faces are taken by select.
+// Inner products: fp32 products summed per plane, fp64 above that (a
+// thread's planes, the block, the fixed-order sum over blocks); the GPU's
+// fp64 rate is low, so no per-cell fp64 arithmetic sits in the hot loop.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "wfa_internal.cuh"
+
+namespace wfa {
+
+constexpr int CG_TX = 16, CG_TY = 16;   // cg_spmv block: 64 x 16 cells, 4 x cells a thread
+constexpr int CG_THREADS = 256;
+constexpr int CG_MAX_PART = 16384;      // per-block partials of one launch
+constexpr int CG_CHUNK = 8;             // iterations per captured graph (even: p buffer parity)
+
+// Solver scalars on the device (56 bytes; read back as one block).
+struct CgState {   // fits one 64-byte pinned word
+    double rr;        // r.r of the current residual
+    double bb;        // b.b of the step's right-hand side
+    double alpha, beta;
+    double tol2;      // rtol^2
+    int done;         // converged, iteration limit reached, or breakdown
+    int iter;         // iterations of the current step
+    int max_iter;
+    unsigned ticket;  // blocks of the current launch that have finished
+};
+
+static_assert(sizeof(CgState) <= 64, "CgState is read back into a 64-byte pinned word");
+
+struct CgCoef {
+    int n[3];
+    int periodic[3];
+    int dface[6];     // face carries a Dirichlet value (on the face)
+    int held[6];      // face holds its outer cell layer
+    long long sy, sz; // element strides of the padded layout
+    float tb[6];      // Dirichlet face values
+    float cu[3];      // uniform k: dt k / h_a^2
+    float du;         // uniform k: 1 + 2 (cu[0] + cu[1] + cu[2]), an interior row's diagonal
+    float tcd[3];     // per-cell k: 2 dt / h_a^2 (c_f = tcd / (1/k_C + 1/k_D))
+};
+
+struct CgArgs {
+    CgCoef c;
+    float* x;          // domain origins (cell (0,0,0)) of the padded arrays
+    const float* rk;   // 1/k, or nullptr for uniform k
+    float* r;
+    float* p0;
+    float* p1;
+    float* q;
+    double* part;      // per-block partials (two arrays of CG_MAX_PART for cg_init)
+    CgState* s;
+    int zchunk;        // cg_spmv planes per block
+    int nblk;          // blocks of this launch
+};
+
+__device__ __forceinline__ long long cg_at(const CgCoef& c, int x, int y, int z) {
+    return x + (long long)y * c.sy + (long long)z * c.sz;
+}
+
+__device__ __forceinline__ bool cg_held(const CgCoef& c, int x, int y, int z) {
+    return (c.held[0] && x == 0) || (c.held[1] && x == c.n[0] - 1) || (c.held[2] && y == 0) ||
+           (c.held[3] && y == c.n[1] - 1) || (c.held[4] && z == 0) || (c.held[5] && z == c.n[2] - 1);
+}
+
+__device__ __forceinline__ void ld4(const float* p, float v[4]) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+
+// Store 4 cells of row (gx.., y, z), the ones inside the domain, plus the
+// periodic twins of those on a periodic face.
+__device__ __forceinline__ void st4_row(float* o, int gx, int nx, const float v[4]) {
+    if (gx + 3 < nx) {
+        *reinterpret_cast<float4*>(o) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (gx + i < nx) o[i] = v[i];
+    }
+}
+
+__device__ __forceinline__ void st4_twins(float* base, const CgCoef& c, int gx, int y, int z, const float v[4]) {
+    const int nx = c.n[0];
+    st4_row(base + cg_at(c, gx, y, z), gx, nx, v);
+    if (c.periodic[1] && (y == 0 || y == c.n[1] - 1)) st4_row(base + cg_at(c, gx, y == 0 ? c.n[1] : -1, z), gx, nx, v);
+    if (c.periodic[2] && (z == 0 || z == c.n[2] - 1)) st4_row(base + cg_at(c, gx, y, z == 0 ? c.n[2] : -1), gx, nx, v);
+    if (c.periodic[0]) {
+        if (gx == 0) base[cg_at(c, nx, y, z)] = v[0];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (gx + i == nx - 1) base[cg_at(c, -1, y, z)] = v[i];
+    }
+}
+
+// Block sum of one double per thread (fixed shuffle tree, then the warps in
+// order); the result is valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nw = (blockDim.x * blockDim.y + 31) / 32;
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (tid == 0)
+        for (int w = 0; w < nw; ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
+// Publish this block's partial; true in every thread of the last block of
+// the launch to do so (which then owns the finish and resets the ticket).
+__device__ __forceinline__ bool publish(const CgArgs& a, double* slot, double v, bool* last) {
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    if (tid == 0) {
+        *slot = v;
+        __threadfence();
+        const unsigned t = atomicAdd(&a.s->ticket, 1u);
+        *last = t == (unsigned)a.nblk - 1;
+    }
+    __syncthreads();
+    return *last;
+}
+
+// Fixed-order sum of n partials by the whole block; valid in thread 0.
+__device__ __forceinline__ double sum_partials(const double* part, int n, double* red) {
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nt = blockDim.x * blockDim.y;
+    __threadfence();
+    double t = 0.0;
+    for (int i = tid; i < n; i += nt) t += __ldcg(part + i);
+    return block_sum(t, red);
+}
+
+// ---------------------------------------------------------------- cg_init --
+// r = b - A T (which is dt times the explicit step's accumulation), b.b and
+// r.r; neighbours across a periodic face by explicit wrap (the field's own
+// halo copies are not kept current by the solver). One cell a thread.
+template <bool KVAR>
+__global__ void __launch_bounds__(CG_THREADS) cg_init(const __grid_constant__ CgArgs a, double tol2, int max_iter) {
+    __shared__ double red[CG_THREADS / 32];
+    __shared__ bool last;
+    const CgCoef& c = a.c;
+    const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
+    const long long N = (long long)nx * ny * nz;
+    double rr = 0.0, bb = 0.0;
+    for (long long i = blockIdx.x * (long long)CG_THREADS + threadIdx.x; i < N; i += (long long)gridDim.x * CG_THREADS) {
+        const int x = (int)(i % nx);
+        const long long yz = i / nx;
+        const int y = (int)(yz % ny), z = (int)(yz / ny);
+        const long long o = cg_at(c, x, y, z);
+        if (cg_held(c, x, y, z)) {
+            a.r[o] = 0.0f;
+            if (c.periodic[0] && (x == 0 || x == nx - 1)) a.r[cg_at(c, x == 0 ? nx : -1, y, z)] = 0.0f;
+            if (c.periodic[1] && (y == 0 || y == ny - 1)) a.r[cg_at(c, x, y == 0 ? ny : -1, z)] = 0.0f;
+            if (c.periodic[2] && (z == 0 || z == nz - 1)) a.r[cg_at(c, x, y, z == 0 ? nz : -1)] = 0.0f;
+            continue;
+        }
+        const float xc = a.x[o];
+        const float rc = KVAR ? a.rk[o] : 0.0f;
+        float acc = 0.0f, bs = xc;
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            const int ax = f >> 1;
+            int nb[3] = {x, y, z};
+            nb[ax] += (f & 1) ? 1 : -1;
+            bool inside = nb[ax] >= 0 && nb[ax] < c.n[ax];
+            if (!inside && c.periodic[ax]) {
+                nb[ax] = (nb[ax] + c.n[ax]) % c.n[ax];
+                inside = true;
+            }
+            if (inside) {
+                const long long d = cg_at(c, nb[0], nb[1], nb[2]);
+                const float xd = a.x[d];
+                const float cf = KVAR ? face_r(rc, a.rk[d], c.tcd[ax]) : c.cu[ax];
+                acc = __fmaf_rn(cf, __fsub_rn(xd, xc), acc);
+                if (cg_held(c, nb[0], nb[1], nb[2])) bs = __fmaf_rn(cf, xd, bs);
+            } else if (c.dface[f]) {
+                const float df = KVAR ? dirichlet_r(rc, c.tcd[ax]) : 2.0f * c.cu[ax];
+                acc = __fmaf_rn(df, __fsub_rn(c.tb[f], xc), acc);
+                bs = __fmaf_rn(df, c.tb[f], bs);
+            }
+        }
+        a.r[o] = acc;
+        if (c.periodic[0] && (x == 0 || x == nx - 1)) a.r[cg_at(c, x == 0 ? nx : -1, y, z)] = acc;
+        if (c.periodic[1] && (y == 0 || y == ny - 1)) a.r[cg_at(c, x, y == 0 ? ny : -1, z)] = acc;
+        if (c.periodic[2] && (z == 0 || z == nz - 1)) a.r[cg_at(c, x, y, z == 0 ? nz : -1)] = acc;
+        rr += (double)acc * acc;
+        bb += (double)bs * bs;
+    }
+    const double rs = block_sum(rr, red);
+    const double bsum = block_sum(bb, red);
+    if (threadIdx.x == 0) a.part[CG_MAX_PART + blockIdx.x] = bsum;
+    if (!publish(a, a.part + blockIdx.x, rs, &last)) return;
+    const double R = sum_partials(a.part, a.nblk, red);
+    const double B = sum_partials(a.part + CG_MAX_PART, a.nblk, red);
+    if (threadIdx.x == 0) {
+        CgState* s = a.s;
+        s->rr = R;
+        s->bb = B;
+        s->alpha = 0.0;
+        s->beta = 0.0;
+        s->tol2 = tol2;
+        s->iter = 0;
+        s->max_iter = max_iter;
+        s->done = (R <= tol2 * B || max_iter <= 0 || !(R == R)) ? 1 : 0;
+        s->ticket = 0;
+    }
+}
+
+// ---------------------------------------------------------------- cg_spmv --
+// p(this iteration) = r + beta p(previous), formed for each cell where it is
+// read, so p is never re-read from DRAM after being written; q = A p.
+struct PNew {
+    const float* r;
+    const float* po;
+    float beta;
+    bool first;   // first iteration: p = r
+};
+
+__device__ __forceinline__ void pnew4(const PNew& P, long long o, float v[4]) {
+    ld4(P.r + o, v);
+    if (!P.first) {
+        float w[4];
+        ld4(P.po + o, w);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = __fmaf_rn(P.beta, w[i], v[i]);
+    }
+}
+__device__ __forceinline__ float pnew1(const PNew& P, long long o) {
+    const float v = __ldg(P.r + o);
+    return P.first ? v : __fmaf_rn(P.beta, __ldg(P.po + o), v);
+}
+
+template <bool KVAR>
+struct CgOcc {
+    static constexpr int blocks = KVAR ? 3 : 4;
+};
+
+template <bool KVAR>
+__global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv(const __grid_constant__ CgArgs a, int par) {
+    __shared__ double red[CG_TX * CG_TY / 32];
+    __shared__ bool last;
+    const CgCoef& c = a.c;
+    if (a.s->done) return;
+    PNew P;
+    P.r = a.r;
+    P.po = par ? a.p1 : a.p0;
+    P.beta = (float)a.s->beta;
+    P.first = a.s->iter == 0;
+    float* __restrict__ pn = par ? a.p0 : a.p1;
+    float* __restrict__ qv = a.q;
+    const float* __restrict__ rk = a.rk;
+    const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int gx = blockIdx.x * 64 + 4 * tx, gy = blockIdx.y * CG_TY + ty;
+    const int z0 = blockIdx.z * a.zchunk, z1 = min(z0 + a.zchunk, nz);
+    const bool perx = c.periodic[0], pery = c.periodic[1], perz = c.periodic[2];
+    double dot = 0.0;
+    if (gx < nx && gy < ny) {
+        const long long sy = c.sy, sz = c.sz;
+        const long long row = cg_at(c, gx, gy, 0);
+        const bool inner_xy = gx + 3 < nx && (perx || (gx > 0 && gx + 4 < nx)) && (pery || (gy > 0 && gy < ny - 1));
+        float pm[4], pc[4], km[4], kc[4];
+        pnew4(P, row + (long long)(z0 - 1) * sz, pm);
+        pnew4(P, row + (long long)z0 * sz, pc);
+        if (KVAR) {
+            ld4(rk + row + (long long)(z0 - 1) * sz, km);
+            ld4(rk + row + (long long)z0 * sz, kc);
+        }
+        for (int z = z0; z < z1; ++z) {
+            const long long o = row + (long long)z * sz;
+            float pp[4], ym[4], yp[4];
+            pnew4(P, o + sz, pp);
+            pnew4(P, o - sy, ym);
+            pnew4(P, o + sy, yp);
+            const float xm = pnew1(P, o - 1), xp = pnew1(P, o + 4);
+            float kp[4], kym[4], kyp[4], kxm = 0.0f, kxp = 0.0f;
+            if (KVAR) {
+                ld4(rk + o + sz, kp);
+                ld4(rk + o - sy, kym);
+                ld4(rk + o + sy, kyp);
+                kxm = __ldg(rk + o - 1);
+                kxp = __ldg(rk + o + 4);
+            }
+            float q[4];
+            float psum = 0.0f;
+            if (inner_xy && (perz || (z > 0 && z < nz - 1))) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float pw = i == 0 ? xm : pc[i - 1], pe = i == 3 ? xp : pc[i + 1];
+                    if (KVAR) {
+                        const float kw = i == 0 ? kxm : kc[i - 1], ke = i == 3 ? kxp : kc[i + 1];
+                        const float r0 = kc[i];
+                        float acc = __fmul_rn(face_r(r0, kw, c.tcd[0]), __fsub_rn(pc[i], pw));
+                        acc = __fmaf_rn(face_r(r0, ke, c.tcd[0]), __fsub_rn(pc[i], pe), acc);
+                        acc = __fmaf_rn(face_r(r0, kym[i], c.tcd[1]), __fsub_rn(pc[i], ym[i]), acc);
+                        acc = __fmaf_rn(face_r(r0, kyp[i], c.tcd[1]), __fsub_rn(pc[i], yp[i]), acc);
+                        acc = __fmaf_rn(face_r(r0, km[i], c.tcd[2]), __fsub_rn(pc[i], pm[i]), acc);
+                        acc = __fmaf_rn(face_r(r0, kp[i], c.tcd[2]), __fsub_rn(pc[i], pp[i]), acc);
+                        q[i] = __fadd_rn(pc[i], acc);
+                    } else {
+                        float acc = __fmul_rn(c.du, pc[i]);
+                        acc = __fmaf_rn(-c.cu[0], __fadd_rn(pw, pe), acc);
+                        acc = __fmaf_rn(-c.cu[1], __fadd_rn(ym[i], yp[i]), acc);
+                        q[i] = __fmaf_rn(-c.cu[2], __fadd_rn(pm[i], pp[i]), acc);
+                    }
+                    psum = __fmaf_rn(pc[i], q[i], psum);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int xi = gx + i;
+                    const float pw = i == 0 ? xm : pc[i - 1], pe = i == 3 ? xp : pc[i + 1];
+                    const float nbv[6] = {pw, pe, ym[i], yp[i], pm[i], pp[i]};
+                    float nbk[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+                    if (KVAR) {
+                        nbk[0] = i == 0 ? kxm : kc[i - 1];
+                        nbk[1] = i == 3 ? kxp : kc[i + 1];
+                        nbk[2] = kym[i];
+                        nbk[3] = kyp[i];
+                        nbk[4] = km[i];
+                        nbk[5] = kp[i];
+                    }
+                    const bool nbin[6] = {perx || xi > 0, perx || xi < nx - 1, pery || gy > 0, pery || gy < ny - 1,
+                                          perz || z > 0, perz || z < nz - 1};
+                    float acc = 0.0f;
+#pragma unroll
+                    for (int f = 0; f < 6; ++f) {
+                        const int ax = f >> 1;
+                        const float cf = KVAR ? face_r(kc[i], nbk[f], c.tcd[ax]) : c.cu[ax];
+                        const float df = KVAR ? dirichlet_r(kc[i], c.tcd[ax]) : 2.0f * c.cu[ax];
+                        const float t = nbin[f] ? __fmul_rn(cf, __fsub_rn(pc[i], nbv[f]))
+                                                : (c.dface[f] ? __fmul_rn(df, pc[i]) : 0.0f);
+                        acc = __fadd_rn(acc, t);
+                    }
+                    const bool isfree = xi < nx && !cg_held(c, xi, gy, z);
+                    q[i] = isfree ? __fadd_rn(pc[i], acc) : 0.0f;
+                    psum = __fmaf_rn(xi < nx ? pc[i] : 0.0f, q[i], psum);
+                }
+            }
+            dot += (double)psum;
+            st4_twins(pn, c, gx, gy, z, pc);
+            if (gx + 3 < nx) {
+                *reinterpret_cast<float4*>(qv + o) = make_float4(q[0], q[1], q[2], q[3]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (gx + i < nx) qv[o + i] = q[i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                pm[i] = pc[i];
+                pc[i] = pp[i];
+                if (KVAR) {
+                    km[i] = kc[i];
+                    kc[i] = kp[i];
+                }
+            }
+        }
+    }
+    const double bsum = block_sum(dot, red);
+    const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    if (!publish(a, a.part + blk, bsum, &last)) return;
+    const double pq = sum_partials(a.part, a.nblk, red);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        CgState* s = a.s;
+        if (pq > 0.0 && pq < INFINITY) {
+            s->alpha = s->rr / pq;
+        } else {
+            s->alpha = 0.0;
+            s->done = 1;   // p = 0 (exact solution) or a breakdown
+        }
+        s->ticket = 0;
+    }
+}
+
+// -------------------------------------------------------------- cg_update --
+// x += alpha p, r -= alpha q over the domain cells (4 along x per item),
+// r.r partials; then beta and the convergence test.
+__global__ void __launch_bounds__(CG_THREADS) cg_update(const __grid_constant__ CgArgs a, int par) {
+    __shared__ double red[CG_THREADS / 32];
+    __shared__ bool last;
+    const CgCoef& c = a.c;
+    if (a.s->done) return;
+    const float alpha = (float)a.s->alpha;
+    const float* __restrict__ p = par ? a.p0 : a.p1;
+    const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
+    const int xg = (nx + 3) / 4;
+    const long long items = (long long)xg * ny * nz;
+    double rr = 0.0;
+    for (long long it = blockIdx.x * (long long)CG_THREADS + threadIdx.x; it < items;
+         it += (long long)gridDim.x * CG_THREADS) {
+        const long long rowi = it / xg;
+        const int gx = 4 * (int)(it - rowi * xg);
+        const int y = (int)(rowi % ny), z = (int)(rowi / ny);
+        const long long o = cg_at(c, gx, y, z);
+        float xv[4], pv[4], qv[4], rv[4];
+        ld4(a.x + o, xv);
+        ld4(p + o, pv);
+        ld4(a.q + o, qv);
+        ld4(a.r + o, rv);
+        float s = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            xv[i] = __fmaf_rn(alpha, pv[i], xv[i]);
+            rv[i] = __fmaf_rn(-alpha, qv[i], rv[i]);
+            if (gx + i < nx) s = __fmaf_rn(rv[i], rv[i], s);
+        }
+        rr += (double)s;
+        if (gx + 3 < nx) {
+            *reinterpret_cast<float4*>(a.x + o) = make_float4(xv[0], xv[1], xv[2], xv[3]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (gx + i < nx) a.x[o + i] = xv[i];
+        }
+        st4_twins(a.r, c, gx, y, z, rv);
+    }
+    const double bsum = block_sum(rr, red);
+    if (!publish(a, a.part + blockIdx.x, bsum, &last)) return;
+    const double R = sum_partials(a.part, a.nblk, red);
+    if (threadIdx.x == 0) {
+        CgState* s = a.s;
+        s->beta = s->rr > 0.0 ? R / s->rr : 0.0;
+        s->rr = R;
+        s->iter += 1;
+        if (R <= s->tol2 * s->bb || s->iter >= s->max_iter || !(R == R)) s->done = 1;
+        s->ticket = 0;
+    }
+}
+
+// ------------------------------------------------------------------ host --
+struct CgWork {
+    float* r = nullptr;
+    float* p[2] = {nullptr, nullptr};
+    float* q = nullptr;
+    double* part = nullptr;
+    CgState* s = nullptr;
+    CgState* h[2] = {nullptr, nullptr};   // pinned read-back slots
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaGraphExec_t exec = nullptr;
+    CgArgs key;        // arguments the graph was captured with
+    int kvar = -1;
+    int spmv_grid[3] = {0, 0, 0};
+    int upd_blocks = 0;
+};
+
+void free_cg(wfa_grid_s* g) {
+    CgWork* w = static_cast<CgWork*>(g->cg);
+    if (!w) return;
+    cudaStreamSynchronize(g->stream);
+    if (w->exec) cudaGraphExecDestroy(w->exec);
+    for (int b = 0; b < 2; ++b) {
+        if (w->ev[b]) cudaEventDestroy(w->ev[b]);
+        pinned_release(w->h[b]);
+        dev_free(w->p[b], g->stream);
+    }
+    dev_free(w->r, g->stream);
+    dev_free(w->q, g->stream);
+    dev_free(w->part, g->stream);
+    dev_free(w->s, g->stream);
+    delete w;
+    g->cg = nullptr;
+}
+
+static int cg_workspace(wfa_grid_s* g, CgWork** out) {
+    if (g->cg) {
+        *out = static_cast<CgWork*>(g->cg);
+        return WFA_OK;
+    }
+    CgWork* w = new (std::nothrow) CgWork();
+    if (!w) {
+        set_error("host allocation failed");
+        return WFA_ERR_OOM;
+    }
+    g->cg = w;
+    const size_t fb = field_elems(g) * sizeof(float);
+    cudaError_t e = dev_alloc((void**)&w->r, fb, g->stream);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = dev_alloc((void**)&w->p[b], fb, g->stream);
+    if (e == cudaSuccess) e = dev_alloc((void**)&w->q, fb, g->stream);
+    if (e == cudaSuccess) e = dev_alloc((void**)&w->part, 2 * CG_MAX_PART * sizeof(double), g->stream);
+    if (e == cudaSuccess) e = dev_alloc((void**)&w->s, sizeof(CgState), g->stream);
+    // the halos and held cells of the work vectors stay 0 (finite) for good
+    for (float* v : {w->r, w->p[0], w->p[1], w->q})
+        if (e == cudaSuccess) e = cudaMemsetAsync(v, 0, fb, g->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w->s, 0, sizeof(CgState), g->stream);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        w->h[b] = static_cast<CgState*>(pinned_word());
+        if (!w->h[b]) e = cudaErrorMemoryAllocation;
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->ev[b], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        const int rc = cuda_fail(e, "implicit solver workspace");
+        free_cg(g);
+        return rc;
+    }
+    *out = w;
+    return WFA_OK;
+}
+
+static void cg_coef(const wfa_grid_s* g, double dt, CgCoef* c) {
+    memset(c, 0, sizeof *c);
+    for (int a = 0; a < 3; ++a) {
+        c->n[a] = g->n[a];
+        c->periodic[a] = g->bc_kind[2 * a] == WFA_BC_PERIODIC;
+        const double ih2 = 1.0 / (g->h[a] * g->h[a]);
+        c->cu[a] = (float)(dt * g->k_uniform * ih2);
+        c->tcd[a] = (float)(2.0 * dt * ih2);
+    }
+    c->du = 1.0f + 2.0f * (c->cu[0] + c->cu[1] + c->cu[2]);
+    for (int f = 0; f < 6; ++f) {
+        c->dface[f] = g->bc_kind[f] == WFA_BC_DIRICHLET;
+        c->held[f] = g->bc_kind[f] == WFA_BC_DIRICHLET_CELL;
+        c->tb[f] = (float)g->bc_value[f];
+    }
+    c->sy = g->px;
+    c->sz = g->px * g->py;
+}
+
+static int cg_capture(wfa_grid_s* g, CgWork* w, const CgArgs& base, bool kvar) {
+    if (w->exec && w->kvar == (int)kvar && memcmp(&w->key, &base, sizeof base) == 0) return WFA_OK;
+    if (w->exec) {
+        cudaGraphExecDestroy(w->exec);
+        w->exec = nullptr;
+    }
+    CgArgs sp = base, up = base;
+    sp.nblk = w->spmv_grid[0] * w->spmv_grid[1] * w->spmv_grid[2];
+    up.nblk = w->upd_blocks;
+    const dim3 sgrid(w->spmv_grid[0], w->spmv_grid[1], w->spmv_grid[2]), sblock(CG_TX, CG_TY);
+    WFA_CUDA(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int it = 0; it < CG_CHUNK && e == cudaSuccess; ++it) {
+        if (kvar)
+            cg_spmv<true><<<sgrid, sblock, 0, g->stream>>>(sp, it & 1);
+        else
+            cg_spmv<false><<<sgrid, sblock, 0, g->stream>>>(sp, it & 1);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) {
+            cg_update<<<w->upd_blocks, CG_THREADS, 0, g->stream>>>(up, it & 1);
+            e = cudaGetLastError();
+        }
+    }
+    cudaGraph_t gr = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(g->stream, &gr);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&w->exec, gr, 0);
+    if (gr) cudaGraphDestroy(gr);
+    if (e != cudaSuccess) {
+        w->exec = nullptr;
+        return cuda_fail(e, "implicit solver graph");
+    }
+    w->key = base;
+    w->kvar = kvar;
+    return WFA_OK;
+}
+
+}  // namespace wfa
+
+using namespace wfa;
+
+int wfa_implicit_step(wfa_grid g, double dt, long long n, double rtol, int max_iter, long long* iters,
+                      double* rel_res) {
+    NvtxRange nvtx_("wfa_implicit_step");
+    if (!g) {
+        set_error("NULL grid");
+        return WFA_ERR_ARG;
+    }
+    if (!(dt >= 0.0) || !std::isfinite(dt) || n < 0 || !(rtol >= 0.0) || !std::isfinite(rtol) || max_iter < 0) {
+        set_error("wfa_implicit_step: need dt >= 0 (finite), n >= 0, rtol >= 0 (finite), max_iter >= 0");
+        return WFA_ERR_ARG;
+    }
+    if (g->storage != WFA_F32) {
+        set_error("wfa_implicit_step: the implicit solver needs fp32 storage");
+        return WFA_ERR_ARG;
+    }
+    if (!g->field_set || !g->coeffs_set) {
+        set_error("set the field and the coefficients before an implicit step");
+        return WFA_ERR_STATE;
+    }
+    if (g->u[0] != 0.0 || g->u[1] != 0.0 || g->u[2] != 0.0) {
+        set_error("wfa_implicit_step: advection makes the system non-symmetric; CG needs u = 0");
+        return WFA_ERR_ARG;
+    }
+    for (int a = 0; a < 3; ++a)
+        if ((g->bc_kind[2 * a] == WFA_BC_PERIODIC) != (g->bc_kind[2 * a + 1] == WFA_BC_PERIODIC)) {
+            set_error("axis %d: a periodic face needs a periodic opposite face", a);
+            return WFA_ERR_BC;
+        }
+    if (iters) *iters = 0;
+    if (rel_res) *rel_res = 0.0;
+    if (n == 0) return WFA_OK;
+    if (g->halo_dirty) {   // held layers carry their value before the first solve
+        int rc = refresh_halo(g, g->cur);
+        if (rc) return rc;
+        g->halo_dirty = false;
+    }
+    int rc = prepare_coeff_halo(g);
+    if (rc) return rc;
+    CgWork* w = nullptr;
+    rc = cg_workspace(g, &w);
+    if (rc) return rc;
+
+    const bool kvar = g->k != nullptr;
+    const long long off = domain_offset(g);
+    CgArgs base;
+    memset(&base, 0, sizeof base);
+    cg_coef(g, dt, &base.c);
+    base.x = static_cast<float*>(g->T[g->cur]) + off;
+    base.rk = kvar ? g->r + off : nullptr;
+    base.r = w->r + off;
+    base.p0 = w->p[0] + off;
+    base.p1 = w->p[1] + off;
+    base.q = w->q + off;
+    base.part = w->part;
+    base.s = w->s;
+    int nsm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+    {   // cg_spmv grid: 64 x 16 columns, z chunks of >= 8 planes filling two waves
+        const int gxb = (g->n[0] + 63) / 64, gyb = (g->n[1] + CG_TY - 1) / CG_TY;
+        const long long cols = (long long)gxb * gyb;
+        const long long want = 2LL * nsm * (kvar ? CgOcc<true>::blocks : CgOcc<false>::blocks);
+        long long nch = std::max<long long>(1, (want + cols - 1) / cols);
+        nch = std::min<long long>(nch, std::max(1, g->n[2] / 8));
+        nch = std::min<long long>(nch, std::max<long long>(1, CG_MAX_PART / cols));
+        base.zchunk = (int)((g->n[2] + nch - 1) / nch);
+        nch = (g->n[2] + base.zchunk - 1) / base.zchunk;
+        if (cols * nch > CG_MAX_PART) {
+            set_error("wfa_implicit_step: grid too large for the partial-sum buffer");
+            return WFA_ERR_ARG;
+        }
+        w->spmv_grid[0] = gxb;
+        w->spmv_grid[1] = gyb;
+        w->spmv_grid[2] = (int)nch;
+        const long long items = (long long)((g->n[0] + 3) / 4) * g->n[1] * g->n[2];
+        w->upd_blocks = (int)std::max<long long>(1, std::min<long long>((items + CG_THREADS - 1) / CG_THREADS, nsm * 8LL));
+    }
+    rc = cg_capture(g, w, base, kvar);
+    if (rc) return rc;
+
+    const long long N = (long long)g->n[0] * g->n[1] * g->n[2];
+    const int init_blocks = (int)std::max<long long>(1, std::min<long long>((N + CG_THREADS - 1) / CG_THREADS, nsm * 8LL));
+    CgArgs ia = base;
+    ia.nblk = init_blocks;
+    const long long max_runs = (long long)max_iter / CG_CHUNK + 2;
+    long long total = 0;
+    double last_rel = 0.0;
+    for (long long step = 0; step < n; ++step) {
+        if (kvar)
+            cg_init<true><<<init_blocks, CG_THREADS, 0, g->stream>>>(ia, rtol * rtol, max_iter);
+        else
+            cg_init<false><<<init_blocks, CG_THREADS, 0, g->stream>>>(ia, rtol * rtol, max_iter);
+        WFA_CUDA(cudaGetLastError());
+        g->launches += 1;
+        // runs of CG_CHUNK iterations, one run queued ahead of the flag check
+        bool done = false;
+        long long launched = 0;
+        CgState st;
+        memset(&st, 0, sizeof st);
+        auto enqueue = [&](long long k) -> int {
+            WFA_CUDA(cudaGraphLaunch(w->exec, g->stream));
+            WFA_CUDA(cudaMemcpyAsync(w->h[k & 1], w->s, sizeof(CgState), cudaMemcpyDeviceToHost, g->stream));
+            WFA_CUDA(cudaEventRecord(w->ev[k & 1], g->stream));
+            g->launches += 2 * CG_CHUNK;
+            return WFA_OK;
+        };
+        rc = enqueue(launched++);
+        if (rc) return rc;
+        for (long long k = 0; !done; ++k) {
+            if (launched < max_runs) {
+                rc = enqueue(launched++);
+                if (rc) return rc;
+            }
+            WFA_CUDA(cudaEventSynchronize(w->ev[k & 1]));
+            memcpy(&st, w->h[k & 1], sizeof st);
+            done = st.done != 0;
+            if (!done && k + 1 >= launched) {
+                set_error("wfa_implicit_step: the solver did not report completion");
+                return WFA_ERR_STATE;
+            }
+        }
+        WFA_CUDA(cudaStreamSynchronize(g->stream));   // the run queued ahead has ended (no-op kernels)
+        total += st.iter;
+        last_rel = st.bb > 0.0 ? sqrt(st.rr / st.bb) : sqrt(st.rr);
+    }
+    g->halo_dirty = true;   // periodic copies and ghost layers of the field are stale
+    g->steps_done += n;
+    if (iters) *iters = total;
+    if (rel_res) *rel_res = last_rel;
+    return WFA_OK;
+}

@@ -133,6 +133,7 @@ struct wfa_grid_s {
     long long timing_pass;
     void* timing;         // wfa::KernelTiming (recorded event pairs)
     void* graphs;         // wfa::StepGraphs (captured runs of passes for small grids)
+    void* cg;             // wfa::CgWork (work vectors and graph of the implicit solver)
 };
 
 namespace wfa {
@@ -148,6 +149,9 @@ int launch_sweep(wfa_grid_s* g, long long nsteps);        // advance nsteps on g
 int check_status(wfa_grid_s* g);                          // sync + report a device-side timeout
 int autotune(wfa_grid_s* g, int* depth, int* variant);    // pick the fastest kernel configuration
 int prepare_coeff_halo(wfa_grid_s* g);                    // k periodic twins, then 1/k
+void free_cg(wfa_grid_s* g);
+void* pinned_word();                                      // a 64-byte pinned host slot
+void pinned_release(void* w);
 void free_tmaps(wfa_grid_s* g);
 void free_timing(wfa_grid_s* g);
 void free_graphs(wfa_grid_s* g);

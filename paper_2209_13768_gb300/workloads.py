@@ -80,6 +80,19 @@ def advection_diffusion(shape=(1024, 1024, 512), steps=500):
                    name="advection-diffusion %dx%dx%d" % shape)
 
 
+IMPLICIT_SHAPE = (512, 512, 512)
+
+
+def implicit_problem(shape=IMPLICIT_SHAPE, steps=10, lognormal=False):
+    """The implicit workload (Sec. 1.1.2, Eq. impl_form): k = 1, h = 1,
+    omega = k dt / h^2 = 1/10 (dt = 0.1, the paper's testing value), outer cell
+    layers held (-x at 1, the other faces at 0), T0 ~ U[0,1) (seed 3).
+    lognormal: per-cell k ~ lognormal(0, 0.5) (seed 2) instead, same dt."""
+    k = lognormal_k(shape, 2) if lognormal else 1.0
+    return Problem(shape=shape, T0=uniform01(shape, 3), k=k, bc=[(DC, 1.0)] + [(DC, 0.0)] * 5, dt=0.1,
+                   steps=steps, name="implicit CG %s%dx%dx%d" % (("lognormal k " if lognormal else ""), *shape))
+
+
 def batch_grids(count=256, lo=16, hi=128, seed=4, steps=(50, 500)):
     """count grids, every edge log-uniform in [lo, hi], k ~ lognormal(0, 0.5),
     T = 0 on every face, T0 ~ U[0,1), steps uniform in [steps[0], steps[1]]."""
