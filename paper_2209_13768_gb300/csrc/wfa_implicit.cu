@@ -475,6 +475,7 @@ struct CgWork {
     CgState* h[2] = {nullptr, nullptr};   // pinned read-back slots
     cudaEvent_t ev[2] = {nullptr, nullptr};
     cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;   // capture stream (the grid's own may be the legacy default stream)
     CgArgs key;        // arguments the graph was captured with
     int kvar = -1;
     int spmv_grid[3] = {0, 0, 0};
@@ -486,6 +487,7 @@ void free_cg(wfa_grid_s* g) {
     if (!w) return;
     cudaStreamSynchronize(g->stream);
     if (w->exec) cudaGraphExecDestroy(w->exec);
+    if (w->cap) cudaStreamDestroy(w->cap);
     for (int b = 0; b < 2; ++b) {
         if (w->ev[b]) cudaEventDestroy(w->ev[b]);
         pinned_release(w->h[b]);
@@ -563,21 +565,23 @@ static int cg_capture(wfa_grid_s* g, CgWork* w, const CgArgs& base, bool kvar) {
     sp.nblk = w->spmv_grid[0] * w->spmv_grid[1] * w->spmv_grid[2];
     up.nblk = w->upd_blocks;
     const dim3 sgrid(w->spmv_grid[0], w->spmv_grid[1], w->spmv_grid[2]), sblock(CG_TX, CG_TY);
-    WFA_CUDA(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+    if (!w->cap) WFA_CUDA(cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking));
+    const cudaStream_t st = w->cap;
+    WFA_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int it = 0; it < CG_CHUNK && e == cudaSuccess; ++it) {
         if (kvar)
-            cg_spmv<true><<<sgrid, sblock, 0, g->stream>>>(sp, it & 1);
+            cg_spmv<true><<<sgrid, sblock, 0, st>>>(sp, it & 1);
         else
-            cg_spmv<false><<<sgrid, sblock, 0, g->stream>>>(sp, it & 1);
+            cg_spmv<false><<<sgrid, sblock, 0, st>>>(sp, it & 1);
         e = cudaGetLastError();
         if (e == cudaSuccess) {
-            cg_update<<<w->upd_blocks, CG_THREADS, 0, g->stream>>>(up, it & 1);
+            cg_update<<<w->upd_blocks, CG_THREADS, 0, st>>>(up, it & 1);
             e = cudaGetLastError();
         }
     }
     cudaGraph_t gr = nullptr;
-    const cudaError_t e2 = cudaStreamEndCapture(g->stream, &gr);
+    const cudaError_t e2 = cudaStreamEndCapture(st, &gr);
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&w->exec, gr, 0);
     if (gr) cudaGraphDestroy(gr);
