@@ -46,7 +46,8 @@ namespace wfa {
 constexpr int CG_TX = 16, CG_TY = 16;   // cg_spmv block: 64 x 16 cells, 4 x cells a thread
 constexpr int CG_THREADS = 256;
 constexpr int CG_MAX_PART = 16384;      // per-block partials of one launch
-constexpr int CG_CHUNK = 8;             // iterations per captured graph (even: p buffer parity)
+constexpr int CG_NRUN = 4;              // captured runs of 1, 2, 4 and 8 iterations
+constexpr int CG_RUN_LEN[CG_NRUN] = {1, 2, 4, 8};
 
 // Solver scalars on the device (56 bytes; read back as one block).
 struct CgState {   // fits one 64-byte pinned word
@@ -167,69 +168,144 @@ __device__ __forceinline__ double sum_partials(const double* part, int n, double
     return block_sum(t, red);
 }
 
-// ---------------------------------------------------------------- cg_init --
-// r = b - A T (which is dt times the explicit step's accumulation), b.b and
-// r.r; neighbours across a periodic face by explicit wrap (the field's own
-// halo copies are not kept current by the solver). One cell a thread.
 template <bool KVAR>
-__global__ void __launch_bounds__(CG_THREADS) cg_init(const __grid_constant__ CgArgs a, double tol2, int max_iter) {
-    __shared__ double red[CG_THREADS / 32];
+struct CgOcc {
+    static constexpr int blocks = KVAR ? 3 : 4;
+};
+
+// ---------------------------------------------------------------- cg_init --
+// r = b - A T (dt times the explicit step's accumulation), b.b and r.r, on
+// the column-march layout of cg_spmv (4 x cells a thread, z queue). The
+// field's periodic twins are current (refresh_halo before the first step,
+// cg_update after every iteration). b adds to T the known values: Dirichlet
+// faces and held neighbours.
+template <bool KVAR>
+__global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_init(const __grid_constant__ CgArgs a, double tol2,
+                                                                         int max_iter) {
+    __shared__ double red[CG_TX * CG_TY / 32];
     __shared__ bool last;
     const CgCoef& c = a.c;
+    const float* __restrict__ xv = a.x;
+    const float* __restrict__ rk = a.rk;
     const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
-    const long long N = (long long)nx * ny * nz;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int gx = blockIdx.x * 64 + 4 * tx, gy = blockIdx.y * CG_TY + ty;
+    const int z0 = blockIdx.z * a.zchunk, z1 = min(z0 + a.zchunk, nz);
+    const bool perx = c.periodic[0], pery = c.periodic[1], perz = c.periodic[2];
     double rr = 0.0, bb = 0.0;
-    for (long long i = blockIdx.x * (long long)CG_THREADS + threadIdx.x; i < N; i += (long long)gridDim.x * CG_THREADS) {
-        const int x = (int)(i % nx);
-        const long long yz = i / nx;
-        const int y = (int)(yz % ny), z = (int)(yz / ny);
-        const long long o = cg_at(c, x, y, z);
-        if (cg_held(c, x, y, z)) {
-            a.r[o] = 0.0f;
-            if (c.periodic[0] && (x == 0 || x == nx - 1)) a.r[cg_at(c, x == 0 ? nx : -1, y, z)] = 0.0f;
-            if (c.periodic[1] && (y == 0 || y == ny - 1)) a.r[cg_at(c, x, y == 0 ? ny : -1, z)] = 0.0f;
-            if (c.periodic[2] && (z == 0 || z == nz - 1)) a.r[cg_at(c, x, y, z == 0 ? nz : -1)] = 0.0f;
-            continue;
+    if (gx < nx && gy < ny) {
+        const long long sy = c.sy, sz = c.sz;
+        const long long row = cg_at(c, gx, gy, 0);
+        // fast cells: no boundary face and no held neighbour (two cells from
+        // every non-periodic face)
+        const bool inner_xy = gx + 3 < nx && (perx || (gx > 1 && gx + 5 < nx)) && (pery || (gy > 1 && gy < ny - 2));
+        float tm[4], tc[4], km[4], kc[4];
+        ld4(xv + row + (long long)(z0 - 1) * sz, tm);
+        ld4(xv + row + (long long)z0 * sz, tc);
+        if (KVAR) {
+            ld4(rk + row + (long long)(z0 - 1) * sz, km);
+            ld4(rk + row + (long long)z0 * sz, kc);
         }
-        const float xc = a.x[o];
-        const float rc = KVAR ? a.rk[o] : 0.0f;
-        float acc = 0.0f, bs = xc;
+        for (int z = z0; z < z1; ++z) {
+            const long long o = row + (long long)z * sz;
+            float tp[4], ym[4], yp[4];
+            ld4(xv + o + sz, tp);
+            ld4(xv + o - sy, ym);
+            ld4(xv + o + sy, yp);
+            const float xm = __ldg(xv + o - 1), xp = __ldg(xv + o + 4);
+            float kp[4], kym[4], kyp[4], kxm = 0.0f, kxp = 0.0f;
+            if (KVAR) {
+                ld4(rk + o + sz, kp);
+                ld4(rk + o - sy, kym);
+                ld4(rk + o + sy, kyp);
+                kxm = __ldg(rk + o - 1);
+                kxp = __ldg(rk + o + 4);
+            }
+            float rv[4];
+            float sr = 0.0f, sb = 0.0f;
+            if (inner_xy && (perz || (z > 1 && z < nz - 2))) {
 #pragma unroll
-        for (int f = 0; f < 6; ++f) {
-            const int ax = f >> 1;
-            int nb[3] = {x, y, z};
-            nb[ax] += (f & 1) ? 1 : -1;
-            bool inside = nb[ax] >= 0 && nb[ax] < c.n[ax];
-            if (!inside && c.periodic[ax]) {
-                nb[ax] = (nb[ax] + c.n[ax]) % c.n[ax];
-                inside = true;
+                for (int i = 0; i < 4; ++i) {
+                    const float tw = i == 0 ? xm : tc[i - 1], te = i == 3 ? xp : tc[i + 1];
+                    float acc;
+                    if (KVAR) {
+                        const float kw = i == 0 ? kxm : kc[i - 1], ke = i == 3 ? kxp : kc[i + 1];
+                        acc = __fmul_rn(face_r(kc[i], kw, c.tcd[0]), __fsub_rn(tw, tc[i]));
+                        acc = __fmaf_rn(face_r(kc[i], ke, c.tcd[0]), __fsub_rn(te, tc[i]), acc);
+                        acc = __fmaf_rn(face_r(kc[i], kym[i], c.tcd[1]), __fsub_rn(ym[i], tc[i]), acc);
+                        acc = __fmaf_rn(face_r(kc[i], kyp[i], c.tcd[1]), __fsub_rn(yp[i], tc[i]), acc);
+                        acc = __fmaf_rn(face_r(kc[i], km[i], c.tcd[2]), __fsub_rn(tm[i], tc[i]), acc);
+                        acc = __fmaf_rn(face_r(kc[i], kp[i], c.tcd[2]), __fsub_rn(tp[i], tc[i]), acc);
+                    } else {
+                        acc = __fmul_rn(c.cu[0], __fadd_rn(__fsub_rn(tw, tc[i]), __fsub_rn(te, tc[i])));
+                        acc = __fmaf_rn(c.cu[1], __fadd_rn(__fsub_rn(ym[i], tc[i]), __fsub_rn(yp[i], tc[i])), acc);
+                        acc = __fmaf_rn(c.cu[2], __fadd_rn(__fsub_rn(tm[i], tc[i]), __fsub_rn(tp[i], tc[i])), acc);
+                    }
+                    rv[i] = acc;
+                    sr = __fmaf_rn(acc, acc, sr);
+                    sb = __fmaf_rn(tc[i], tc[i], sb);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int xi = gx + i;
+                    const float tv[6] = {i == 0 ? xm : tc[i - 1], i == 3 ? xp : tc[i + 1], ym[i], yp[i], tm[i], tp[i]};
+                    float kv[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+                    if (KVAR) {
+                        kv[0] = i == 0 ? kxm : kc[i - 1];
+                        kv[1] = i == 3 ? kxp : kc[i + 1];
+                        kv[2] = kym[i];
+                        kv[3] = kyp[i];
+                        kv[4] = km[i];
+                        kv[5] = kp[i];
+                    }
+                    const bool nbin[6] = {perx || xi > 0, perx || xi < nx - 1, pery || gy > 0, pery || gy < ny - 1,
+                                          perz || z > 0, perz || z < nz - 1};
+                    // a neighbour inside the domain is held only through its own axis's face
+                    const bool nbheld[6] = {c.held[0] && xi == 1, c.held[1] && xi == nx - 2, c.held[2] && gy == 1,
+                                            c.held[3] && gy == ny - 2, c.held[4] && z == 1, c.held[5] && z == nz - 2};
+                    float acc = 0.0f, bs = tc[i];
+#pragma unroll
+                    for (int f = 0; f < 6; ++f) {
+                        const int ax = f >> 1;
+                        if (nbin[f]) {
+                            const float cf = KVAR ? face_r(kc[i], kv[f], c.tcd[ax]) : c.cu[ax];
+                            acc = __fmaf_rn(cf, __fsub_rn(tv[f], tc[i]), acc);
+                            if (nbheld[f]) bs = __fmaf_rn(cf, tv[f], bs);
+                        } else if (c.dface[f]) {
+                            const float df = KVAR ? dirichlet_r(kc[i], c.tcd[ax]) : 2.0f * c.cu[ax];
+                            acc = __fmaf_rn(df, __fsub_rn(c.tb[f], tc[i]), acc);
+                            bs = __fmaf_rn(df, c.tb[f], bs);
+                        }
+                    }
+                    const bool isfree = xi < nx && !cg_held(c, xi, gy, z);
+                    rv[i] = isfree ? acc : 0.0f;
+                    sr = __fmaf_rn(rv[i], rv[i], sr);
+                    if (isfree) sb = __fmaf_rn(bs, bs, sb);
+                }
             }
-            if (inside) {
-                const long long d = cg_at(c, nb[0], nb[1], nb[2]);
-                const float xd = a.x[d];
-                const float cf = KVAR ? face_r(rc, a.rk[d], c.tcd[ax]) : c.cu[ax];
-                acc = __fmaf_rn(cf, __fsub_rn(xd, xc), acc);
-                if (cg_held(c, nb[0], nb[1], nb[2])) bs = __fmaf_rn(cf, xd, bs);
-            } else if (c.dface[f]) {
-                const float df = KVAR ? dirichlet_r(rc, c.tcd[ax]) : 2.0f * c.cu[ax];
-                acc = __fmaf_rn(df, __fsub_rn(c.tb[f], xc), acc);
-                bs = __fmaf_rn(df, c.tb[f], bs);
+            st4_twins(a.r, c, gx, gy, z, rv);
+            rr += (double)sr;
+            bb += (double)sb;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                tm[i] = tc[i];
+                tc[i] = tp[i];
+                if (KVAR) {
+                    km[i] = kc[i];
+                    kc[i] = kp[i];
+                }
             }
         }
-        a.r[o] = acc;
-        if (c.periodic[0] && (x == 0 || x == nx - 1)) a.r[cg_at(c, x == 0 ? nx : -1, y, z)] = acc;
-        if (c.periodic[1] && (y == 0 || y == ny - 1)) a.r[cg_at(c, x, y == 0 ? ny : -1, z)] = acc;
-        if (c.periodic[2] && (z == 0 || z == nz - 1)) a.r[cg_at(c, x, y, z == 0 ? nz : -1)] = acc;
-        rr += (double)acc * acc;
-        bb += (double)bs * bs;
     }
+    const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const double rs = block_sum(rr, red);
     const double bsum = block_sum(bb, red);
-    if (threadIdx.x == 0) a.part[CG_MAX_PART + blockIdx.x] = bsum;
-    if (!publish(a, a.part + blockIdx.x, rs, &last)) return;
+    if (threadIdx.x == 0 && threadIdx.y == 0) a.part[CG_MAX_PART + blk] = bsum;
+    if (!publish(a, a.part + blk, rs, &last)) return;
     const double R = sum_partials(a.part, a.nblk, red);
     const double B = sum_partials(a.part + CG_MAX_PART, a.nblk, red);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
         CgState* s = a.s;
         s->rr = R;
         s->bb = B;
@@ -268,16 +344,12 @@ __device__ __forceinline__ float pnew1(const PNew& P, long long o) {
 }
 
 template <bool KVAR>
-struct CgOcc {
-    static constexpr int blocks = KVAR ? 3 : 4;
-};
-
-template <bool KVAR>
-__global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv(const __grid_constant__ CgArgs a, int par) {
+__global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv(const __grid_constant__ CgArgs a) {
     __shared__ double red[CG_TX * CG_TY / 32];
     __shared__ bool last;
     const CgCoef& c = a.c;
     if (a.s->done) return;
+    const int par = a.s->iter & 1;   // iteration i reads p[i mod 2], writes p[(i + 1) mod 2]
     PNew P;
     P.r = a.r;
     P.po = par ? a.p1 : a.p0;
@@ -413,11 +485,12 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv(co
 // -------------------------------------------------------------- cg_update --
 // x += alpha p, r -= alpha q over the domain cells (4 along x per item),
 // r.r partials; then beta and the convergence test.
-__global__ void __launch_bounds__(CG_THREADS) cg_update(const __grid_constant__ CgArgs a, int par) {
+__global__ void __launch_bounds__(CG_THREADS) cg_update(const __grid_constant__ CgArgs a) {
     __shared__ double red[CG_THREADS / 32];
     __shared__ bool last;
     const CgCoef& c = a.c;
     if (a.s->done) return;
+    const int par = a.s->iter & 1;
     const float alpha = (float)a.s->alpha;
     const float* __restrict__ p = par ? a.p0 : a.p1;
     const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
@@ -443,13 +516,7 @@ __global__ void __launch_bounds__(CG_THREADS) cg_update(const __grid_constant__ 
             if (gx + i < nx) s = __fmaf_rn(rv[i], rv[i], s);
         }
         rr += (double)s;
-        if (gx + 3 < nx) {
-            *reinterpret_cast<float4*>(a.x + o) = make_float4(xv[0], xv[1], xv[2], xv[3]);
-        } else {
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (gx + i < nx) a.x[o + i] = xv[i];
-        }
+        st4_twins(a.x, c, gx, y, z, xv);   // the field's twins feed the next step's cg_init
         st4_twins(a.r, c, gx, y, z, rv);
     }
     const double bsum = block_sum(rr, red);
@@ -474,19 +541,21 @@ struct CgWork {
     CgState* s = nullptr;
     CgState* h[2] = {nullptr, nullptr};   // pinned read-back slots
     cudaEvent_t ev[2] = {nullptr, nullptr};
-    cudaGraphExec_t exec = nullptr;
+    cudaGraphExec_t exec[CG_NRUN] = {nullptr, nullptr, nullptr, nullptr};
     cudaStream_t cap = nullptr;   // capture stream (the grid's own may be the legacy default stream)
     CgArgs key;        // arguments the graph was captured with
     int kvar = -1;
     int spmv_grid[3] = {0, 0, 0};
     int upd_blocks = 0;
+    long long prev_iters = 0;   // iterations the last step needed (sizes the first run of the next)
 };
 
 void free_cg(wfa_grid_s* g) {
     CgWork* w = static_cast<CgWork*>(g->cg);
     if (!w) return;
     cudaStreamSynchronize(g->stream);
-    if (w->exec) cudaGraphExecDestroy(w->exec);
+    for (cudaGraphExec_t e : w->exec)
+        if (e) cudaGraphExecDestroy(e);
     if (w->cap) cudaStreamDestroy(w->cap);
     for (int b = 0; b < 2; ++b) {
         if (w->ev[b]) cudaEventDestroy(w->ev[b]);
@@ -556,38 +625,41 @@ static void cg_coef(const wfa_grid_s* g, double dt, CgCoef* c) {
 }
 
 static int cg_capture(wfa_grid_s* g, CgWork* w, const CgArgs& base, bool kvar) {
-    if (w->exec && w->kvar == (int)kvar && memcmp(&w->key, &base, sizeof base) == 0) return WFA_OK;
-    if (w->exec) {
-        cudaGraphExecDestroy(w->exec);
-        w->exec = nullptr;
-    }
+    if (w->exec[0] && w->kvar == (int)kvar && memcmp(&w->key, &base, sizeof base) == 0) return WFA_OK;
+    for (cudaGraphExec_t& e : w->exec)
+        if (e) {
+            cudaGraphExecDestroy(e);
+            e = nullptr;
+        }
     CgArgs sp = base, up = base;
     sp.nblk = w->spmv_grid[0] * w->spmv_grid[1] * w->spmv_grid[2];
     up.nblk = w->upd_blocks;
     const dim3 sgrid(w->spmv_grid[0], w->spmv_grid[1], w->spmv_grid[2]), sblock(CG_TX, CG_TY);
     if (!w->cap) WFA_CUDA(cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking));
     const cudaStream_t st = w->cap;
-    WFA_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaSuccess;
-    for (int it = 0; it < CG_CHUNK && e == cudaSuccess; ++it) {
-        if (kvar)
-            cg_spmv<true><<<sgrid, sblock, 0, st>>>(sp, it & 1);
-        else
-            cg_spmv<false><<<sgrid, sblock, 0, st>>>(sp, it & 1);
-        e = cudaGetLastError();
-        if (e == cudaSuccess) {
-            cg_update<<<w->upd_blocks, CG_THREADS, 0, st>>>(up, it & 1);
+    for (int k = 0; k < CG_NRUN; ++k) {
+        WFA_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int it = 0; it < CG_RUN_LEN[k] && e == cudaSuccess; ++it) {
+            if (kvar)
+                cg_spmv<true><<<sgrid, sblock, 0, st>>>(sp);
+            else
+                cg_spmv<false><<<sgrid, sblock, 0, st>>>(sp);
             e = cudaGetLastError();
+            if (e == cudaSuccess) {
+                cg_update<<<w->upd_blocks, CG_THREADS, 0, st>>>(up);
+                e = cudaGetLastError();
+            }
         }
-    }
-    cudaGraph_t gr = nullptr;
-    const cudaError_t e2 = cudaStreamEndCapture(st, &gr);
-    if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&w->exec, gr, 0);
-    if (gr) cudaGraphDestroy(gr);
-    if (e != cudaSuccess) {
-        w->exec = nullptr;
-        return cuda_fail(e, "implicit solver graph");
+        cudaGraph_t gr = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(st, &gr);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&w->exec[k], gr, 0);
+        if (gr) cudaGraphDestroy(gr);
+        if (e != cudaSuccess) {
+            w->exec[k] = nullptr;
+            return cuda_fail(e, "implicit solver graph");
+        }
     }
     w->key = base;
     w->kvar = kvar;
@@ -679,49 +751,60 @@ int wfa_implicit_step(wfa_grid g, double dt, long long n, double rtol, int max_i
     rc = cg_capture(g, w, base, kvar);
     if (rc) return rc;
 
-    const long long N = (long long)g->n[0] * g->n[1] * g->n[2];
-    const int init_blocks = (int)std::max<long long>(1, std::min<long long>((N + CG_THREADS - 1) / CG_THREADS, nsm * 8LL));
     CgArgs ia = base;
-    ia.nblk = init_blocks;
-    const long long max_runs = (long long)max_iter / CG_CHUNK + 2;
+    ia.nblk = w->spmv_grid[0] * w->spmv_grid[1] * w->spmv_grid[2];
+    const dim3 sgrid(w->spmv_grid[0], w->spmv_grid[1], w->spmv_grid[2]), sblock(CG_TX, CG_TY);
     long long total = 0;
     double last_rel = 0.0;
     for (long long step = 0; step < n; ++step) {
         if (kvar)
-            cg_init<true><<<init_blocks, CG_THREADS, 0, g->stream>>>(ia, rtol * rtol, max_iter);
+            cg_init<true><<<sgrid, sblock, 0, g->stream>>>(ia, rtol * rtol, max_iter);
         else
-            cg_init<false><<<init_blocks, CG_THREADS, 0, g->stream>>>(ia, rtol * rtol, max_iter);
+            cg_init<false><<<sgrid, sblock, 0, g->stream>>>(ia, rtol * rtol, max_iter);
         WFA_CUDA(cudaGetLastError());
         g->launches += 1;
-        // runs of CG_CHUNK iterations, one run queued ahead of the flag check
-        bool done = false;
-        long long launched = 0;
-        CgState st;
-        memset(&st, 0, sizeof st);
-        auto enqueue = [&](long long k) -> int {
-            WFA_CUDA(cudaGraphLaunch(w->exec, g->stream));
-            WFA_CUDA(cudaMemcpyAsync(w->h[k & 1], w->s, sizeof(CgState), cudaMemcpyDeviceToHost, g->stream));
-            WFA_CUDA(cudaEventRecord(w->ev[k & 1], g->stream));
-            g->launches += 2 * CG_CHUNK;
+        // Runs of captured iterations with one run queued ahead of the flag
+        // check, so the GPU does not wait for the host: the first run as long
+        // as the last step needed (rounded up to 1, 2, 4 or 8), then 2, then 8s.
+        // Iterations after convergence are kernels that return at once.
+        long long queued = 0, launched = 0;
+        auto enqueue = [&]() -> int {
+            int k = CG_NRUN - 1;
+            if (launched == 0) {
+                const long long want = w->prev_iters > 0 ? w->prev_iters : CG_RUN_LEN[CG_NRUN - 1];
+                k = 0;
+                while (k < CG_NRUN - 1 && CG_RUN_LEN[k] < want) ++k;
+            } else if (launched == 1) {
+                k = 1;
+            }
+            WFA_CUDA(cudaGraphLaunch(w->exec[k], g->stream));
+            WFA_CUDA(cudaMemcpyAsync(w->h[launched & 1], w->s, sizeof(CgState), cudaMemcpyDeviceToHost, g->stream));
+            WFA_CUDA(cudaEventRecord(w->ev[launched & 1], g->stream));
+            g->launches += 2 * CG_RUN_LEN[k];
+            queued += CG_RUN_LEN[k];
+            ++launched;
             return WFA_OK;
         };
-        rc = enqueue(launched++);
+        rc = enqueue();
         if (rc) return rc;
-        for (long long k = 0; !done; ++k) {
-            if (launched < max_runs) {
-                rc = enqueue(launched++);
+        CgState st;
+        memset(&st, 0, sizeof st);
+        for (long long k = 0;; ++k) {
+            if (launched == k + 1 && queued < max_iter) {
+                rc = enqueue();
                 if (rc) return rc;
             }
             WFA_CUDA(cudaEventSynchronize(w->ev[k & 1]));
             memcpy(&st, w->h[k & 1], sizeof st);
-            done = st.done != 0;
-            if (!done && k + 1 >= launched) {
+            if (st.done) break;
+            if (launched == k + 1) {   // nothing left in flight, yet not done
                 set_error("wfa_implicit_step: the solver did not report completion");
                 return WFA_ERR_STATE;
             }
         }
         WFA_CUDA(cudaStreamSynchronize(g->stream));   // the run queued ahead has ended (no-op kernels)
         total += st.iter;
+        w->prev_iters = st.iter;
         last_rel = st.bb > 0.0 ? sqrt(st.rr / st.bb) : sqrt(st.rr);
     }
     g->halo_dirty = true;   // periodic copies and ghost layers of the field are stale
