@@ -30,9 +30,10 @@
 // Periodic axes read the neighbour across the boundary from a twin copy
 // that every writer of a boundary cell also stores one cell beyond the
 // opposite face; non-periodic boundary faces are taken by select.
-// Inner products: fp32 products summed per plane, fp64 above that (a
-// thread's planes, the block, the fixed-order sum over blocks); the GPU's
-// fp64 rate is low, so no per-cell fp64 arithmetic sits in the hot loop.
+// Inner products: fp32 products summed per plane, a compensated fp32 sum over
+// a thread's planes, fp64 above that (the block, the fixed-order sum over
+// blocks); the GPU's fp64 rate is low, so no fp64 arithmetic sits in the
+// hot loops.
 #include <math.h>
 #include <string.h>
 
@@ -98,6 +99,10 @@ __device__ __forceinline__ bool cg_held(const CgCoef& c, int x, int y, int z) {
            (c.held[3] && y == c.n[1] - 1) || (c.held[4] && z == 0) || (c.held[5] && z == c.n[2] - 1);
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ void ld4(const float* p, float v[4]) {
     const float4 t = __ldg(reinterpret_cast<const float4*>(p));
     v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
@@ -127,6 +132,20 @@ __device__ __forceinline__ void st4_twins(float* base, const CgCoef& c, int gx, 
             if (gx + i == nx - 1) base[cg_at(c, -1, y, z)] = v[i];
     }
 }
+
+// Compensated (Kahan) fp32 running sum: a thread's share of an inner product
+// without per-plane fp64 arithmetic (the GPU's fp64 rate is a small fraction
+// of its fp32 rate); the block and the blocks are then summed in fp64.
+struct KahanF {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = __fsub_rn(v, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
 
 // Block sum of one double per thread (fixed shuffle tree, then the warps in
 // order); the result is valid in thread 0.
@@ -192,7 +211,7 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_init(co
     const int gx = blockIdx.x * 64 + 4 * tx, gy = blockIdx.y * CG_TY + ty;
     const int z0 = blockIdx.z * a.zchunk, z1 = min(z0 + a.zchunk, nz);
     const bool perx = c.periodic[0], pery = c.periodic[1], perz = c.periodic[2];
-    double rr = 0.0, bb = 0.0;
+    KahanF rr, bb;
     if (gx < nx && gy < ny) {
         const long long sy = c.sy, sz = c.sz;
         const long long row = cg_at(c, gx, gy, 0);
@@ -208,6 +227,7 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_init(co
         }
         for (int z = z0; z < z1; ++z) {
             const long long o = row + (long long)z * sz;
+            if ((tx & 7) == 0) prefetch_l2(xv + o + 3 * sz);
             float tp[4], ym[4], yp[4];
             ld4(xv + o + sz, tp);
             ld4(xv + o - sy, ym);
@@ -285,8 +305,8 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_init(co
                 }
             }
             st4_twins(a.r, c, gx, gy, z, rv);
-            rr += (double)sr;
-            bb += (double)sb;
+            rr.add(sr);
+            bb.add(sb);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 tm[i] = tc[i];
@@ -299,8 +319,8 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_init(co
         }
     }
     const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-    const double rs = block_sum(rr, red);
-    const double bsum = block_sum(bb, red);
+    const double rs = block_sum(rr.value(), red);
+    const double bsum = block_sum(bb.value(), red);
     if (threadIdx.x == 0 && threadIdx.y == 0) a.part[CG_MAX_PART + blk] = bsum;
     if (!publish(a, a.part + blk, rs, &last)) return;
     const double R = sum_partials(a.part, a.nblk, red);
@@ -363,7 +383,7 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv(co
     const int gx = blockIdx.x * 64 + 4 * tx, gy = blockIdx.y * CG_TY + ty;
     const int z0 = blockIdx.z * a.zchunk, z1 = min(z0 + a.zchunk, nz);
     const bool perx = c.periodic[0], pery = c.periodic[1], perz = c.periodic[2];
-    double dot = 0.0;
+    KahanF dot;
     if (gx < nx && gy < ny) {
         const long long sy = c.sy, sz = c.sz;
         const long long row = cg_at(c, gx, gy, 0);
@@ -377,6 +397,10 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv(co
         }
         for (int z = z0; z < z1; ++z) {
             const long long o = row + (long long)z * sz;
+            if ((tx & 7) == 0) {   // one thread per 128-byte line asks L2 for plane z + 3
+                prefetch_l2(P.r + o + 3 * sz);
+                if (!P.first) prefetch_l2(P.po + o + 3 * sz);
+            }
             float pp[4], ym[4], yp[4];
             pnew4(P, o + sz, pp);
             pnew4(P, o - sy, ym);
@@ -446,7 +470,7 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv(co
                     psum = __fmaf_rn(xi < nx ? pc[i] : 0.0f, q[i], psum);
                 }
             }
-            dot += (double)psum;
+            dot.add(psum);
             st4_twins(pn, c, gx, gy, z, pc);
             if (gx + 3 < nx) {
                 *reinterpret_cast<float4*>(qv + o) = make_float4(q[0], q[1], q[2], q[3]);
@@ -466,7 +490,7 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv(co
             }
         }
     }
-    const double bsum = block_sum(dot, red);
+    const double bsum = block_sum(dot.value(), red);
     const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     if (!publish(a, a.part + blk, bsum, &last)) return;
     const double pq = sum_partials(a.part, a.nblk, red);
@@ -496,7 +520,7 @@ __global__ void __launch_bounds__(CG_THREADS) cg_update(const __grid_constant__ 
     const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
     const int xg = (nx + 3) / 4;
     const long long items = (long long)xg * ny * nz;
-    double rr = 0.0;
+    KahanF rr;
     for (long long it = blockIdx.x * (long long)CG_THREADS + threadIdx.x; it < items;
          it += (long long)gridDim.x * CG_THREADS) {
         const long long rowi = it / xg;
@@ -515,11 +539,11 @@ __global__ void __launch_bounds__(CG_THREADS) cg_update(const __grid_constant__ 
             rv[i] = __fmaf_rn(-alpha, qv[i], rv[i]);
             if (gx + i < nx) s = __fmaf_rn(rv[i], rv[i], s);
         }
-        rr += (double)s;
+        rr.add(s);
         st4_twins(a.x, c, gx, y, z, xv);   // the field's twins feed the next step's cg_init
         st4_twins(a.r, c, gx, y, z, rv);
     }
-    const double bsum = block_sum(rr, red);
+    const double bsum = block_sum(rr.value(), red);
     if (!publish(a, a.part + blockIdx.x, bsum, &last)) return;
     const double R = sum_partials(a.part, a.nblk, red);
     if (threadIdx.x == 0) {
