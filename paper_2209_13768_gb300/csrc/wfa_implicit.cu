@@ -243,7 +243,8 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_init(co
             }
             float rv[4];
             float sr = 0.0f, sb = 0.0f;
-            if (inner_xy && (perz || (z > 1 && z < nz - 2))) {
+            const bool fast = inner_xy && (perz || (z > 1 && z < nz - 2));
+            if (__all_sync(__activemask(), fast)) {   // warp-uniform choice, as in cg_spmv
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const float tw = i == 0 ? xm : tc[i - 1], te = i == 3 ? xp : tc[i + 1];
@@ -416,7 +417,11 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv(co
             }
             float q[4];
             float psum = 0.0f;
-            if (inner_xy && (perz || (z > 0 && z < nz - 1))) {
+            // the lean interior formula only where the whole warp can take it:
+            // a warp with one boundary cell takes the select-based path in
+            // all its threads instead of running both paths
+            const bool fast = inner_xy && (perz || (z > 0 && z < nz - 1));
+            if (__all_sync(__activemask(), fast)) {
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const float pw = i == 0 ? xm : pc[i - 1], pe = i == 3 ? xp : pc[i + 1];
