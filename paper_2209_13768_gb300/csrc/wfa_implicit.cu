@@ -35,6 +35,7 @@
 // blocks); the GPU's fp64 rate is low, so no fp64 arithmetic sits in the
 // hot loops.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -47,6 +48,7 @@ namespace wfa {
 constexpr int CG_TX = 16, CG_TY = 16;   // cg_spmv block: 64 x 16 cells, 4 x cells a thread
 constexpr int CG_THREADS = 256;
 constexpr int CG_MAX_PART = 16384;      // per-block partials of one launch
+constexpr bool CG_SPMV_SM_DEFAULT = false;   // cg_spmv (L1 neighbours) unless WFA_CG_SPMV=sm
 constexpr int CG_NRUN = 4;              // captured runs of 1, 2, 4 and 8 iterations
 constexpr int CG_RUN_LEN[CG_NRUN] = {1, 2, 4, 8};
 
@@ -101,6 +103,14 @@ __device__ __forceinline__ bool cg_held(const CgCoef& c, int x, int y, int z) {
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+__device__ __forceinline__ void sts4(float* p, const float v[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void lds4(const float* p, float v[4]) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
 }
 
 __device__ __forceinline__ void ld4(const float* p, float v[4]) {
@@ -364,6 +374,77 @@ __device__ __forceinline__ float pnew1(const PNew& P, long long o) {
     return P.first ? v : __fmaf_rn(P.beta, __ldg(P.po + o), v);
 }
 
+// q = A p for the 4 cells of a thread at plane z, and their p.q. `fast`
+// (warp-uniform) takes the interior formula: every neighbour inside the
+// domain or across a periodic face, no held cell. Otherwise each face by
+// select: a neighbour inside the domain (or across a periodic face) couples
+// with c_f, a Dirichlet face adds d_f to the diagonal, a zero-flux face
+// nothing; held cells and cells beyond the x end give q = 0 and no p.q.
+template <bool KVAR>
+__device__ __forceinline__ float cg_q4(const CgCoef& c, int gx, int gy, int z, bool fast, const float pc[4],
+                                       const float pm[4], const float pp[4], const float ym[4], const float yp[4],
+                                       float xm, float xp, const float kc[4], const float km[4], const float kp[4],
+                                       const float kym[4], const float kyp[4], float kxm, float kxp, float q[4]) {
+    float psum = 0.0f;
+    if (fast) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float pw = i == 0 ? xm : pc[i - 1], pe = i == 3 ? xp : pc[i + 1];
+            if (KVAR) {
+                const float kw = i == 0 ? kxm : kc[i - 1], ke = i == 3 ? kxp : kc[i + 1];
+                const float r0 = kc[i];
+                float acc = __fmul_rn(face_r(r0, kw, c.tcd[0]), __fsub_rn(pc[i], pw));
+                acc = __fmaf_rn(face_r(r0, ke, c.tcd[0]), __fsub_rn(pc[i], pe), acc);
+                acc = __fmaf_rn(face_r(r0, kym[i], c.tcd[1]), __fsub_rn(pc[i], ym[i]), acc);
+                acc = __fmaf_rn(face_r(r0, kyp[i], c.tcd[1]), __fsub_rn(pc[i], yp[i]), acc);
+                acc = __fmaf_rn(face_r(r0, km[i], c.tcd[2]), __fsub_rn(pc[i], pm[i]), acc);
+                acc = __fmaf_rn(face_r(r0, kp[i], c.tcd[2]), __fsub_rn(pc[i], pp[i]), acc);
+                q[i] = __fadd_rn(pc[i], acc);
+            } else {
+                float acc = __fmul_rn(c.du, pc[i]);
+                acc = __fmaf_rn(-c.cu[0], __fadd_rn(pw, pe), acc);
+                acc = __fmaf_rn(-c.cu[1], __fadd_rn(ym[i], yp[i]), acc);
+                q[i] = __fmaf_rn(-c.cu[2], __fadd_rn(pm[i], pp[i]), acc);
+            }
+            psum = __fmaf_rn(pc[i], q[i], psum);
+        }
+        return psum;
+    }
+    const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
+    const bool perx = c.periodic[0], pery = c.periodic[1], perz = c.periodic[2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int xi = gx + i;
+        const float pw = i == 0 ? xm : pc[i - 1], pe = i == 3 ? xp : pc[i + 1];
+        const float nbv[6] = {pw, pe, ym[i], yp[i], pm[i], pp[i]};
+        float nbk[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (KVAR) {
+            nbk[0] = i == 0 ? kxm : kc[i - 1];
+            nbk[1] = i == 3 ? kxp : kc[i + 1];
+            nbk[2] = kym[i];
+            nbk[3] = kyp[i];
+            nbk[4] = km[i];
+            nbk[5] = kp[i];
+        }
+        const bool nbin[6] = {perx || xi > 0, perx || xi < nx - 1, pery || gy > 0, pery || gy < ny - 1,
+                              perz || z > 0, perz || z < nz - 1};
+        float acc = 0.0f;
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            const int ax = f >> 1;
+            const float cf = KVAR ? face_r(kc[i], nbk[f], c.tcd[ax]) : c.cu[ax];
+            const float df = KVAR ? dirichlet_r(kc[i], c.tcd[ax]) : 2.0f * c.cu[ax];
+            const float t = nbin[f] ? __fmul_rn(cf, __fsub_rn(pc[i], nbv[f]))
+                                    : (c.dface[f] ? __fmul_rn(df, pc[i]) : 0.0f);
+            acc = __fadd_rn(acc, t);
+        }
+        const bool isfree = xi < nx && gy < ny && !cg_held(c, xi, gy, z);
+        q[i] = isfree ? __fadd_rn(pc[i], acc) : 0.0f;
+        psum = isfree ? __fmaf_rn(pc[i], q[i], psum) : psum;
+    }
+    return psum;
+}
+
 template <bool KVAR>
 __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv(const __grid_constant__ CgArgs a) {
     __shared__ double red[CG_TX * CG_TY / 32];
@@ -416,65 +497,9 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv(co
                 kxp = __ldg(rk + o + 4);
             }
             float q[4];
-            float psum = 0.0f;
-            // the lean interior formula only where the whole warp can take it:
-            // a warp with one boundary cell takes the select-based path in
-            // all its threads instead of running both paths
             const bool fast = inner_xy && (perz || (z > 0 && z < nz - 1));
-            if (__all_sync(__activemask(), fast)) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float pw = i == 0 ? xm : pc[i - 1], pe = i == 3 ? xp : pc[i + 1];
-                    if (KVAR) {
-                        const float kw = i == 0 ? kxm : kc[i - 1], ke = i == 3 ? kxp : kc[i + 1];
-                        const float r0 = kc[i];
-                        float acc = __fmul_rn(face_r(r0, kw, c.tcd[0]), __fsub_rn(pc[i], pw));
-                        acc = __fmaf_rn(face_r(r0, ke, c.tcd[0]), __fsub_rn(pc[i], pe), acc);
-                        acc = __fmaf_rn(face_r(r0, kym[i], c.tcd[1]), __fsub_rn(pc[i], ym[i]), acc);
-                        acc = __fmaf_rn(face_r(r0, kyp[i], c.tcd[1]), __fsub_rn(pc[i], yp[i]), acc);
-                        acc = __fmaf_rn(face_r(r0, km[i], c.tcd[2]), __fsub_rn(pc[i], pm[i]), acc);
-                        acc = __fmaf_rn(face_r(r0, kp[i], c.tcd[2]), __fsub_rn(pc[i], pp[i]), acc);
-                        q[i] = __fadd_rn(pc[i], acc);
-                    } else {
-                        float acc = __fmul_rn(c.du, pc[i]);
-                        acc = __fmaf_rn(-c.cu[0], __fadd_rn(pw, pe), acc);
-                        acc = __fmaf_rn(-c.cu[1], __fadd_rn(ym[i], yp[i]), acc);
-                        q[i] = __fmaf_rn(-c.cu[2], __fadd_rn(pm[i], pp[i]), acc);
-                    }
-                    psum = __fmaf_rn(pc[i], q[i], psum);
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int xi = gx + i;
-                    const float pw = i == 0 ? xm : pc[i - 1], pe = i == 3 ? xp : pc[i + 1];
-                    const float nbv[6] = {pw, pe, ym[i], yp[i], pm[i], pp[i]};
-                    float nbk[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-                    if (KVAR) {
-                        nbk[0] = i == 0 ? kxm : kc[i - 1];
-                        nbk[1] = i == 3 ? kxp : kc[i + 1];
-                        nbk[2] = kym[i];
-                        nbk[3] = kyp[i];
-                        nbk[4] = km[i];
-                        nbk[5] = kp[i];
-                    }
-                    const bool nbin[6] = {perx || xi > 0, perx || xi < nx - 1, pery || gy > 0, pery || gy < ny - 1,
-                                          perz || z > 0, perz || z < nz - 1};
-                    float acc = 0.0f;
-#pragma unroll
-                    for (int f = 0; f < 6; ++f) {
-                        const int ax = f >> 1;
-                        const float cf = KVAR ? face_r(kc[i], nbk[f], c.tcd[ax]) : c.cu[ax];
-                        const float df = KVAR ? dirichlet_r(kc[i], c.tcd[ax]) : 2.0f * c.cu[ax];
-                        const float t = nbin[f] ? __fmul_rn(cf, __fsub_rn(pc[i], nbv[f]))
-                                                : (c.dface[f] ? __fmul_rn(df, pc[i]) : 0.0f);
-                        acc = __fadd_rn(acc, t);
-                    }
-                    const bool isfree = xi < nx && !cg_held(c, xi, gy, z);
-                    q[i] = isfree ? __fadd_rn(pc[i], acc) : 0.0f;
-                    psum = __fmaf_rn(xi < nx ? pc[i] : 0.0f, q[i], psum);
-                }
-            }
+            const float psum = cg_q4<KVAR>(c, gx, gy, z, __all_sync(__activemask(), fast), pc, pm, pp, ym, yp, xm, xp,
+                                           kc, km, kp, kym, kyp, kxm, kxp, q);
             dot.add(psum);
             st4_twins(pn, c, gx, gy, z, pc);
             if (gx + 3 < nx) {
@@ -506,6 +531,162 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv(co
         } else {
             s->alpha = 0.0;
             s->done = 1;   // p = 0 (exact solution) or a breakdown
+        }
+        s->ticket = 0;
+    }
+}
+
+// cg_spmv_sm: the same step with the x / y neighbours of p from shared
+// memory. Each thread forms p for its own 4 cells of plane z + 1 (two 128-bit
+// loads), edge threads also for the one-cell ring of the 64 x 16 tile, and
+// writes them into a two-plane shared ring; after one barrier a plane, q at
+// plane z reads its x / y neighbours there (the z neighbours stay in the
+// register queue). Two global loads a thread and plane instead of ten.
+constexpr int SM_W = 72;   // shared row: x = -4 .. 67 of the tile, x = 0 at index 4
+
+template <bool KVAR>
+__global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv_sm(const __grid_constant__ CgArgs a) {
+    __shared__ double red[CG_TX * CG_TY / 32];
+    __shared__ bool last;
+    __shared__ __align__(16) float sp[2][CG_TY + 2][SM_W];
+    const CgCoef& c = a.c;
+    if (a.s->done) return;
+    const int par = a.s->iter & 1;
+    PNew P;
+    P.r = a.r;
+    P.po = par ? a.p1 : a.p0;
+    P.beta = (float)a.s->beta;
+    P.first = a.s->iter == 0;
+    float* __restrict__ pn = par ? a.p0 : a.p1;
+    float* __restrict__ qv = a.q;
+    const float* __restrict__ rk = a.rk;
+    const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x0 = blockIdx.x * 64, y0 = blockIdx.y * CG_TY;
+    const int gx = x0 + 4 * tx, gy = y0 + ty;
+    const int z0 = blockIdx.z * a.zchunk, z1 = min(z0 + a.zchunk, nz);
+    const bool perx = c.periodic[0], pery = c.periodic[1], perz = c.periodic[2];
+    const long long sy = c.sy, sz = c.sz;
+    // every load below stays within the one-cell ring of the domain
+    // ([-1, n] on each axis), inside the padded arrays' halo
+    const bool own = gx < nx && gy < ny;
+    const int ry = ty == 0 ? y0 - 1 : y0 + CG_TY;                       // y-ring row of this thread (ty 0 / 15)
+    const bool yr = (ty == 0 || ty == CG_TY - 1) && gx < nx && ry <= ny;
+    const int rx = tx == 0 ? x0 - 1 : x0 + 64;                          // x-ring cell of this row (tx 0 / 15)
+    const bool xr = gy < ny && (tx == 0 || (tx == CG_TX - 1 && x0 + 63 < nx));
+    const int srow = ty + 1, scol = 4 + 4 * tx;
+    const int yrow = ty == 0 ? 0 : CG_TY + 1, xcol = tx == 0 ? 3 : 4 + 64;
+    const long long own_o = cg_at(c, gx, gy, 0), yr_o = cg_at(c, gx, ry, 0), xr_o = cg_at(c, rx, gy, 0);
+    const bool inner_xy = own && gx + 3 < nx && (perx || (gx > 0 && gx + 4 < nx)) && (pery || (gy > 0 && gy < ny - 1));
+
+    // shared planes start at 0: cells no thread writes (outside the ring of
+    // the domain) stay finite
+    for (int i = threadIdx.x + CG_TX * threadIdx.y; i < 2 * (CG_TY + 2) * SM_W; i += CG_TX * CG_TY)
+        (&sp[0][0][0])[i] = 0.0f;
+    __syncthreads();
+
+    float pm[4], pc[4], km[4], kc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) pm[i] = pc[i] = km[i] = kc[i] = 0.0f;
+    if (own) {
+        pnew4(P, own_o + (long long)(z0 - 1) * sz, pm);
+        pnew4(P, own_o + (long long)z0 * sz, pc);
+        if (KVAR) {
+            ld4(rk + own_o + (long long)(z0 - 1) * sz, km);
+            ld4(rk + own_o + (long long)z0 * sz, kc);
+        }
+    }
+    {   // plane z0 into shared slot z0 & 1
+        float* sl = &sp[z0 & 1][0][0];
+        sts4(sl + srow * SM_W + scol, pc);
+        if (yr) {
+            float v[4];
+            pnew4(P, yr_o + (long long)z0 * sz, v);
+            sts4(sl + yrow * SM_W + scol, v);
+        }
+        if (xr) sl[srow * SM_W + xcol] = pnew1(P, xr_o + (long long)z0 * sz);
+    }
+    __syncthreads();
+
+    KahanF dot;
+    for (int z = z0; z < z1; ++z) {
+        const int cs = z & 1;
+        const long long o = own_o + (long long)z * sz;
+        float pp[4];
+        if (own) {
+            if ((tx & 7) == 0) {   // one thread per 128-byte line asks L2 for plane z + 3
+                prefetch_l2(P.r + o + 3 * sz);
+                if (!P.first) prefetch_l2(P.po + o + 3 * sz);
+            }
+            pnew4(P, o + sz, pp);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) pp[i] = 0.0f;
+        }
+        {   // plane z + 1 into the other slot (free since the last barrier)
+            float* sl = &sp[cs ^ 1][0][0];
+            sts4(sl + srow * SM_W + scol, pp);
+            if (yr) {
+                float v[4];
+                pnew4(P, yr_o + (long long)(z + 1) * sz, v);
+                sts4(sl + yrow * SM_W + scol, v);
+            }
+            if (xr) sl[srow * SM_W + xcol] = pnew1(P, xr_o + (long long)(z + 1) * sz);
+        }
+        float kp[4], kym[4], kyp[4], kxm = 0.0f, kxp = 0.0f;
+        if (KVAR) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) kp[i] = kym[i] = kyp[i] = 1.0f;
+            if (own) {
+                ld4(rk + o + sz, kp);
+                ld4(rk + o - sy, kym);
+                ld4(rk + o + sy, kyp);
+                kxm = __ldg(rk + o - 1);
+                kxp = __ldg(rk + o + 4);
+            }
+        }
+        const float* sl = &sp[cs][0][0];
+        float ym[4], yp[4];
+        lds4(sl + (srow - 1) * SM_W + scol, ym);
+        lds4(sl + (srow + 1) * SM_W + scol, yp);
+        const float xm = sl[srow * SM_W + scol - 1], xp = sl[srow * SM_W + scol + 4];
+        float q[4];
+        const bool fast = inner_xy && (perz || (z > 0 && z < nz - 1));
+        const float psum = cg_q4<KVAR>(c, gx, gy, z, __all_sync(__activemask(), fast), pc, pm, pp, ym, yp, xm, xp,
+                                       kc, km, kp, kym, kyp, kxm, kxp, q);
+        if (own) {
+            dot.add(psum);
+            st4_twins(pn, c, gx, gy, z, pc);
+            if (gx + 3 < nx) {
+                *reinterpret_cast<float4*>(qv + o) = make_float4(q[0], q[1], q[2], q[3]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (gx + i < nx) qv[o + i] = q[i];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            pm[i] = pc[i];
+            pc[i] = pp[i];
+            if (KVAR) {
+                km[i] = kc[i];
+                kc[i] = kp[i];
+            }
+        }
+        __syncthreads();
+    }
+    const double bsum = block_sum(dot.value(), red);
+    const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    if (!publish(a, a.part + blk, bsum, &last)) return;
+    const double pq = sum_partials(a.part, a.nblk, red);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        CgState* s = a.s;
+        if (pq > 0.0 && pq < INFINITY) {
+            s->alpha = s->rr / pq;
+        } else {
+            s->alpha = 0.0;
+            s->done = 1;
         }
         s->ticket = 0;
     }
@@ -666,12 +847,20 @@ static int cg_capture(wfa_grid_s* g, CgWork* w, const CgArgs& base, bool kvar) {
     const dim3 sgrid(w->spmv_grid[0], w->spmv_grid[1], w->spmv_grid[2]), sblock(CG_TX, CG_TY);
     if (!w->cap) WFA_CUDA(cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking));
     const cudaStream_t st = w->cap;
+    // q = A p from L1-cached neighbour loads (cg_spmv) or through a shared
+    // plane (cg_spmv_sm); WFA_CG_SPMV=l1|sm overrides the default
+    const char* pick = getenv("WFA_CG_SPMV");
+    const bool use_sm = pick ? strcmp(pick, "sm") == 0 : CG_SPMV_SM_DEFAULT;
     for (int k = 0; k < CG_NRUN; ++k) {
         WFA_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaSuccess;
         for (int it = 0; it < CG_RUN_LEN[k] && e == cudaSuccess; ++it) {
-            if (kvar)
+            if (kvar && use_sm)
+                cg_spmv_sm<true><<<sgrid, sblock, 0, st>>>(sp);
+            else if (kvar)
                 cg_spmv<true><<<sgrid, sblock, 0, st>>>(sp);
+            else if (use_sm)
+                cg_spmv_sm<false><<<sgrid, sblock, 0, st>>>(sp);
             else
                 cg_spmv<false><<<sgrid, sblock, 0, st>>>(sp);
             e = cudaGetLastError();

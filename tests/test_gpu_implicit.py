@@ -11,6 +11,8 @@ covers three steps with a margin. Fixed iteration counts (rtol = 0) compare
 the CG iterates themselves: fp32 rounding of each product, amplified by no
 more than the same condition number, stays below 1e-5.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -238,3 +240,27 @@ def test_implicit_paper_workload_residual_at_full_size():
     assert np.abs(resid).max() <= 2e-5 * np.abs(T0).max()
     # held layers untouched (-x at 1 away from the other held faces)
     np.testing.assert_array_equal(T1[1:-1, 1:-1, 0], p.bc[0][1])
+
+
+@pytest.mark.parametrize("kvar", [False, True])
+def test_implicit_shared_memory_spmv_is_bitwise_equal(kvar):
+    # cg_spmv_sm (x / y neighbours of p through shared memory) runs the same
+    # per-cell arithmetic and the same inner-product order as cg_spmv
+    shapes = [(37, 29, 23), (65, 17, 9), (130, 33, 20), (3, 5, 7)]
+    for mix in (0, 2, 4, 5):
+        for shape in shapes:
+            if any(kind == DC and shape[f // 2] < 3 for f, (kind, _) in enumerate(MIXES[mix])):
+                continue
+            p = _problem(mix, shape=shape, kvar=kvar, seed=70 + mix)
+            dt = _dt(p, 4.0)
+            out = {}
+            for kind in ("l1", "sm"):
+                os.environ["WFA_CG_SPMV"] = kind
+                try:
+                    with _grid(p) as g:
+                        it, _ = g.implicit_step(dt, 2, rtol=1e-7, max_iter=300)
+                        out[kind] = (it, g.read_field())
+                finally:
+                    os.environ.pop("WFA_CG_SPMV", None)
+            assert out["l1"][0] == out["sm"][0], (mix, shape)
+            np.testing.assert_array_equal(out["l1"][1], out["sm"][1], err_msg=f"{mix} {shape}")
