@@ -570,6 +570,9 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv_sm
     // every load below stays within the one-cell ring of the domain
     // ([-1, n] on each axis), inside the padded arrays' halo
     const bool own = gx < nx && gy < ny;
+    // threads on the one-cell ring of the domain load too: on a periodic
+    // axis their cells are the twins the domain's edge cells read
+    const bool ld = gx <= nx && gy <= ny;
     const int ry = ty == 0 ? y0 - 1 : y0 + CG_TY;                       // y-ring row of this thread (ty 0 / 15)
     const bool yr = (ty == 0 || ty == CG_TY - 1) && gx < nx && ry <= ny;
     const int rx = tx == 0 ? x0 - 1 : x0 + 64;                          // x-ring cell of this row (tx 0 / 15)
@@ -588,9 +591,11 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv_sm
     float pm[4], pc[4], km[4], kc[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) pm[i] = pc[i] = km[i] = kc[i] = 0.0f;
-    if (own) {
+    if (ld) {
         pnew4(P, own_o + (long long)(z0 - 1) * sz, pm);
         pnew4(P, own_o + (long long)z0 * sz, pc);
+    }
+    if (own) {
         if (KVAR) {
             ld4(rk + own_o + (long long)(z0 - 1) * sz, km);
             ld4(rk + own_o + (long long)z0 * sz, kc);
@@ -613,7 +618,7 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv_sm
         const int cs = z & 1;
         const long long o = own_o + (long long)z * sz;
         float pp[4];
-        if (own) {
+        if (ld) {
             if ((tx & 7) == 0) {   // one thread per 128-byte line asks L2 for plane z + 3
                 prefetch_l2(P.r + o + 3 * sz);
                 if (!P.first) prefetch_l2(P.po + o + 3 * sz);
