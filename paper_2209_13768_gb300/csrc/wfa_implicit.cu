@@ -656,7 +656,9 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv_sm
         lds4(sl + (srow + 1) * SM_W + scol, yp);
         const float xm = sl[srow * SM_W + scol - 1], xp = sl[srow * SM_W + scol + 4];
         float q[4];
-        const bool fast = inner_xy && (perz || (z > 0 && z < nz - 1));
+        // threads without own cells do not hold the warp back from the
+        // interior formula (as in cg_spmv, where they do not take part)
+        const bool fast = !own || (inner_xy && (perz || (z > 0 && z < nz - 1)));
         const float psum = cg_q4<KVAR>(c, gx, gy, z, __all_sync(__activemask(), fast), pc, pm, pp, ym, yp, xm, xp,
                                        kc, km, kp, kym, kyp, kxm, kxp, q);
         if (own) {
