@@ -374,73 +374,87 @@ __device__ __forceinline__ float pnew1(const PNew& P, long long o) {
     return P.first ? v : __fmaf_rn(P.beta, __ldg(P.po + o), v);
 }
 
-// q = A p for the 4 cells of a thread at plane z, and their p.q. `fast`
-// (warp-uniform) takes the interior formula: every neighbour inside the
-// domain or across a periodic face, no held cell. Otherwise each face by
-// select: a neighbour inside the domain (or across a periodic face) couples
-// with c_f, a Dirichlet face adds d_f to the diagonal, a zero-flux face
-// nothing; held cells and cells beyond the x end give q = 0 and no p.q.
-template <bool KVAR>
-__device__ __forceinline__ float cg_q4(const CgCoef& c, int gx, int gy, int z, bool fast, const float pc[4],
+// Boundary faces a thread's cells touch (non-periodic axes only). A face is
+// taken as a ghost neighbour that makes the interior formula exact: across a
+// Dirichlet face (value 0 in A) p_ghost = -p_C, across a zero-flux face
+// p_ghost = p_C, with the ghost's conductivity that of the cell (so the face
+// coefficient is tcd / (2 r_C): twice it is the Dirichlet coefficient
+// 2 k_C dt / h^2). Held cells are masked (q = 0).
+struct CgEdge {
+    int ih;            // index 0..3 of the thread's cell on the +x face (4: none)
+    unsigned bits;     // 1: cell 0 on the -x face, 2: the row on the -y face, 4: on the +y face
+};
+
+__device__ __forceinline__ CgEdge cg_edge(const CgCoef& c, int gx, int gy) {
+    CgEdge e;
+    const int nx = c.n[0], ny = c.n[1];
+    e.ih = (!c.periodic[0] && gx <= nx - 1 && nx - 1 - gx < 4) ? nx - 1 - gx : 4;
+    e.bits = ((!c.periodic[0] && gx == 0) ? 1u : 0u) | ((!c.periodic[1] && gy == 0) ? 2u : 0u) |
+             ((!c.periodic[1] && gy == ny - 1) ? 4u : 0u);
+    return e;
+}
+
+// ghost value across face f of a cell holding v: -v (Dirichlet face) or v
+__device__ __forceinline__ float ghost(const CgCoef& c, int f, float v) { return c.dface[f] ? -v : v; }
+
+// q = A p for the 4 cells of a thread at plane z, and their p.q (cells inside
+// the domain). EDGE (chosen warp-uniformly) puts ghost values across
+// boundary faces and masks held cells and cells beyond the x end; without
+// it every neighbour is inside the domain or across a periodic face. Both
+// evaluate the same expression, so an interior cell gets the same bits
+// either way.
+template <bool KVAR, bool EDGE>
+__device__ __forceinline__ float cg_q4(const CgCoef& c, const CgEdge& e, int gx, int gy, int z, const float pc[4],
                                        const float pm[4], const float pp[4], const float ym[4], const float yp[4],
                                        float xm, float xp, const float kc[4], const float km[4], const float kp[4],
                                        const float kym[4], const float kyp[4], float kxm, float kxp, float q[4]) {
     float psum = 0.0f;
-    if (fast) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float pw = i == 0 ? xm : pc[i - 1], pe = i == 3 ? xp : pc[i + 1];
-            if (KVAR) {
-                const float kw = i == 0 ? kxm : kc[i - 1], ke = i == 3 ? kxp : kc[i + 1];
-                const float r0 = kc[i];
-                float acc = __fmul_rn(face_r(r0, kw, c.tcd[0]), __fsub_rn(pc[i], pw));
-                acc = __fmaf_rn(face_r(r0, ke, c.tcd[0]), __fsub_rn(pc[i], pe), acc);
-                acc = __fmaf_rn(face_r(r0, kym[i], c.tcd[1]), __fsub_rn(pc[i], ym[i]), acc);
-                acc = __fmaf_rn(face_r(r0, kyp[i], c.tcd[1]), __fsub_rn(pc[i], yp[i]), acc);
-                acc = __fmaf_rn(face_r(r0, km[i], c.tcd[2]), __fsub_rn(pc[i], pm[i]), acc);
-                acc = __fmaf_rn(face_r(r0, kp[i], c.tcd[2]), __fsub_rn(pc[i], pp[i]), acc);
-                q[i] = __fadd_rn(pc[i], acc);
-            } else {
-                float acc = __fmul_rn(c.du, pc[i]);
-                acc = __fmaf_rn(-c.cu[0], __fadd_rn(pw, pe), acc);
-                acc = __fmaf_rn(-c.cu[1], __fadd_rn(ym[i], yp[i]), acc);
-                q[i] = __fmaf_rn(-c.cu[2], __fadd_rn(pm[i], pp[i]), acc);
-            }
-            psum = __fmaf_rn(pc[i], q[i], psum);
-        }
-        return psum;
-    }
-    const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
-    const bool perx = c.periodic[0], pery = c.periodic[1], perz = c.periodic[2];
+    const bool zlo = EDGE && !c.periodic[2] && z == 0, zhi = EDGE && !c.periodic[2] && z == c.n[2] - 1;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const int xi = gx + i;
-        const float pw = i == 0 ? xm : pc[i - 1], pe = i == 3 ? xp : pc[i + 1];
-        const float nbv[6] = {pw, pe, ym[i], yp[i], pm[i], pp[i]};
-        float nbk[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        float pw = i == 0 ? xm : pc[i - 1], pe = i == 3 ? xp : pc[i + 1];
+        float y0 = ym[i], y1 = yp[i], z0 = pm[i], z1 = pp[i];
+        float kw = 0.0f, ke = 0.0f, ky0 = 0.0f, ky1 = 0.0f, kz0 = 0.0f, kz1 = 0.0f;
         if (KVAR) {
-            nbk[0] = i == 0 ? kxm : kc[i - 1];
-            nbk[1] = i == 3 ? kxp : kc[i + 1];
-            nbk[2] = kym[i];
-            nbk[3] = kyp[i];
-            nbk[4] = km[i];
-            nbk[5] = kp[i];
+            kw = i == 0 ? kxm : kc[i - 1];
+            ke = i == 3 ? kxp : kc[i + 1];
+            ky0 = kym[i];
+            ky1 = kyp[i];
+            kz0 = km[i];
+            kz1 = kp[i];
         }
-        const bool nbin[6] = {perx || xi > 0, perx || xi < nx - 1, pery || gy > 0, pery || gy < ny - 1,
-                              perz || z > 0, perz || z < nz - 1};
-        float acc = 0.0f;
-#pragma unroll
-        for (int f = 0; f < 6; ++f) {
-            const int ax = f >> 1;
-            const float cf = KVAR ? face_r(kc[i], nbk[f], c.tcd[ax]) : c.cu[ax];
-            const float df = KVAR ? dirichlet_r(kc[i], c.tcd[ax]) : 2.0f * c.cu[ax];
-            const float t = nbin[f] ? __fmul_rn(cf, __fsub_rn(pc[i], nbv[f]))
-                                    : (c.dface[f] ? __fmul_rn(df, pc[i]) : 0.0f);
-            acc = __fadd_rn(acc, t);
+        if (EDGE) {
+            if (i == 0 && (e.bits & 1u)) { pw = ghost(c, 0, pc[i]); kw = kc[i]; }
+            if (i == e.ih) { pe = ghost(c, 1, pc[i]); ke = kc[i]; }
+            if (e.bits & 2u) { y0 = ghost(c, 2, pc[i]); ky0 = kc[i]; }
+            if (e.bits & 4u) { y1 = ghost(c, 3, pc[i]); ky1 = kc[i]; }
+            if (zlo) { z0 = ghost(c, 4, pc[i]); kz0 = kc[i]; }
+            if (zhi) { z1 = ghost(c, 5, pc[i]); kz1 = kc[i]; }
         }
-        const bool isfree = xi < nx && gy < ny && !cg_held(c, xi, gy, z);
-        q[i] = isfree ? __fadd_rn(pc[i], acc) : 0.0f;
-        psum = isfree ? __fmaf_rn(pc[i], q[i], psum) : psum;
+        float qi;
+        if (KVAR) {
+            const float r0 = kc[i];
+            float acc = __fmul_rn(face_r(r0, kw, c.tcd[0]), __fsub_rn(pc[i], pw));
+            acc = __fmaf_rn(face_r(r0, ke, c.tcd[0]), __fsub_rn(pc[i], pe), acc);
+            acc = __fmaf_rn(face_r(r0, ky0, c.tcd[1]), __fsub_rn(pc[i], y0), acc);
+            acc = __fmaf_rn(face_r(r0, ky1, c.tcd[1]), __fsub_rn(pc[i], y1), acc);
+            acc = __fmaf_rn(face_r(r0, kz0, c.tcd[2]), __fsub_rn(pc[i], z0), acc);
+            acc = __fmaf_rn(face_r(r0, kz1, c.tcd[2]), __fsub_rn(pc[i], z1), acc);
+            qi = __fadd_rn(pc[i], acc);
+        } else {
+            float acc = __fmul_rn(c.du, pc[i]);
+            acc = __fmaf_rn(-c.cu[0], __fadd_rn(pw, pe), acc);
+            acc = __fmaf_rn(-c.cu[1], __fadd_rn(y0, y1), acc);
+            qi = __fmaf_rn(-c.cu[2], __fadd_rn(z0, z1), acc);
+        }
+        if (EDGE) {
+            const bool isfree = gx + i < c.n[0] && gy < c.n[1] && !cg_held(c, gx + i, gy, z);
+            qi = isfree ? qi : 0.0f;
+            psum = isfree ? __fmaf_rn(pc[i], qi, psum) : psum;
+        } else {
+            psum = __fmaf_rn(pc[i], qi, psum);
+        }
+        q[i] = qi;
     }
     return psum;
 }
@@ -470,6 +484,7 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv(co
         const long long sy = c.sy, sz = c.sz;
         const long long row = cg_at(c, gx, gy, 0);
         const bool inner_xy = gx + 3 < nx && (perx || (gx > 0 && gx + 4 < nx)) && (pery || (gy > 0 && gy < ny - 1));
+        const CgEdge edge = cg_edge(c, gx, gy);
         float pm[4], pc[4], km[4], kc[4];
         pnew4(P, row + (long long)(z0 - 1) * sz, pm);
         pnew4(P, row + (long long)z0 * sz, pc);
@@ -498,8 +513,11 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv(co
             }
             float q[4];
             const bool fast = inner_xy && (perz || (z > 0 && z < nz - 1));
-            const float psum = cg_q4<KVAR>(c, gx, gy, z, __all_sync(__activemask(), fast), pc, pm, pp, ym, yp, xm, xp,
-                                           kc, km, kp, kym, kyp, kxm, kxp, q);
+            const float psum = __all_sync(__activemask(), fast)
+                                   ? cg_q4<KVAR, false>(c, edge, gx, gy, z, pc, pm, pp, ym, yp, xm, xp, kc, km, kp, kym,
+                                                        kyp, kxm, kxp, q)
+                                   : cg_q4<KVAR, true>(c, edge, gx, gy, z, pc, pm, pp, ym, yp, xm, xp, kc, km, kp, kym,
+                                                       kyp, kxm, kxp, q);
             dot.add(psum);
             st4_twins(pn, c, gx, gy, z, pc);
             if (gx + 3 < nx) {
@@ -581,6 +599,7 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv_sm
     const int yrow = ty == 0 ? 0 : CG_TY + 1, xcol = tx == 0 ? 3 : 4 + 64;
     const long long own_o = cg_at(c, gx, gy, 0), yr_o = cg_at(c, gx, ry, 0), xr_o = cg_at(c, rx, gy, 0);
     const bool inner_xy = own && gx + 3 < nx && (perx || (gx > 0 && gx + 4 < nx)) && (pery || (gy > 0 && gy < ny - 1));
+    const CgEdge edge = cg_edge(c, gx, gy);
 
     // shared planes start at 0: cells no thread writes (outside the ring of
     // the domain) stay finite
@@ -659,8 +678,11 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv_sm
         // threads without own cells do not hold the warp back from the
         // interior formula (as in cg_spmv, where they do not take part)
         const bool fast = !own || (inner_xy && (perz || (z > 0 && z < nz - 1)));
-        const float psum = cg_q4<KVAR>(c, gx, gy, z, __all_sync(__activemask(), fast), pc, pm, pp, ym, yp, xm, xp,
-                                       kc, km, kp, kym, kyp, kxm, kxp, q);
+        const float psum = __all_sync(__activemask(), fast)
+                               ? cg_q4<KVAR, false>(c, edge, gx, gy, z, pc, pm, pp, ym, yp, xm, xp, kc, km, kp, kym, kyp,
+                                                    kxm, kxp, q)
+                               : cg_q4<KVAR, true>(c, edge, gx, gy, z, pc, pm, pp, ym, yp, xm, xp, kc, km, kp, kym, kyp,
+                                                   kxm, kxp, q);
         if (own) {
             dot.add(psum);
             st4_twins(pn, c, gx, gy, z, pc);
