@@ -202,6 +202,99 @@ struct CgOcc {
     static constexpr int blocks = KVAR ? 3 : 4;
 };
 
+// Boundary faces a thread's cells touch (non-periodic axes only). A face is
+// taken as a ghost neighbour that makes the interior formula exact: across a
+// Dirichlet face (value 0 in A) p_ghost = -p_C, across a zero-flux face
+// p_ghost = p_C, with the ghost's conductivity that of the cell (so the face
+// coefficient is tcd / (2 r_C): twice it is the Dirichlet coefficient
+// 2 k_C dt / h^2). Held cells are masked (q = 0).
+struct CgEdge {
+    int ih;            // index 0..3 of the thread's cell on the +x face (4: none)
+    unsigned bits;     // 1: cell 0 on the -x face, 2: the row on the -y face, 4: on the +y face
+};
+
+__device__ __forceinline__ CgEdge cg_edge(const CgCoef& c, int gx, int gy) {
+    CgEdge e;
+    const int nx = c.n[0], ny = c.n[1];
+    e.ih = (!c.periodic[0] && gx <= nx - 1 && nx - 1 - gx < 4) ? nx - 1 - gx : 4;
+    e.bits = ((!c.periodic[0] && gx == 0) ? 1u : 0u) | ((!c.periodic[1] && gy == 0) ? 2u : 0u) |
+             ((!c.periodic[1] && gy == ny - 1) ? 4u : 0u);
+    return e;
+}
+
+// ghost value across face f of a cell holding v: -v (Dirichlet face) or v
+__device__ __forceinline__ float ghost(const CgCoef& c, int f, float v) { return c.dface[f] ? -v : v; }
+
+// r = dt acc(T) and the b terms of the 4 cells of a thread at plane z. EDGE
+// (warp-uniform) puts ghost values across boundary faces (2 Tb - T_C across a
+// Dirichlet face, T_C across a zero-flux face, the cell's own 1/k), adds the
+// known values to b (Dirichlet faces: d_f Tb; held neighbours: c_f T_D) and
+// masks held cells and cells beyond the x end; without it every neighbour
+// is a free cell inside the domain or across a periodic face.
+template <bool KVAR, bool EDGE>
+__device__ __forceinline__ void cg_r4(const CgCoef& c, const CgEdge& e, int gx, int gy, int z, const float tc[4],
+                                      const float tm[4], const float tp[4], const float ym[4], const float yp[4],
+                                      float xm, float xp, const float kc[4], const float km[4], const float kp[4],
+                                      const float kym[4], const float kyp[4], float kxm, float kxp, float rv[4],
+                                      float& sr, float& sb) {
+    const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
+    const bool zlo = EDGE && !c.periodic[2] && z == 0, zhi = EDGE && !c.periodic[2] && z == nz - 1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float t[6] = {i == 0 ? xm : tc[i - 1], i == 3 ? xp : tc[i + 1], ym[i], yp[i], tm[i], tp[i]};
+        float k[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (KVAR) {
+            k[0] = i == 0 ? kxm : kc[i - 1];
+            k[1] = i == 3 ? kxp : kc[i + 1];
+            k[2] = kym[i];
+            k[3] = kyp[i];
+            k[4] = km[i];
+            k[5] = kp[i];
+        }
+        float bs = tc[i];
+        if (EDGE) {
+            const int xi = gx + i;
+            const bool bd[6] = {i == 0 && (e.bits & 1u) != 0, i == e.ih, (e.bits & 2u) != 0, (e.bits & 4u) != 0, zlo, zhi};
+            // a neighbour inside the domain is held only through its own axis's face
+            const bool hn[6] = {c.held[0] && xi == 1, c.held[1] && xi == nx - 2, c.held[2] && gy == 1,
+                                c.held[3] && gy == ny - 2, c.held[4] && z == 1, c.held[5] && z == nz - 2};
+#pragma unroll
+            for (int f = 0; f < 6; ++f) {
+                const float cf = KVAR ? face_r(kc[i], bd[f] ? kc[i] : k[f], c.tcd[f >> 1]) : c.cu[f >> 1];
+                if (hn[f]) bs = __fmaf_rn(cf, t[f], bs);
+                if (bd[f]) {
+                    if (c.dface[f]) bs = __fmaf_rn(__fmul_rn(2.0f, cf), c.tb[f], bs);
+                    t[f] = c.dface[f] ? __fsub_rn(__fmul_rn(2.0f, c.tb[f]), tc[i]) : tc[i];
+                    k[f] = kc[i];
+                }
+            }
+        }
+        float acc;
+        if (KVAR) {
+            acc = __fmul_rn(face_r(kc[i], k[0], c.tcd[0]), __fsub_rn(t[0], tc[i]));
+            acc = __fmaf_rn(face_r(kc[i], k[1], c.tcd[0]), __fsub_rn(t[1], tc[i]), acc);
+            acc = __fmaf_rn(face_r(kc[i], k[2], c.tcd[1]), __fsub_rn(t[2], tc[i]), acc);
+            acc = __fmaf_rn(face_r(kc[i], k[3], c.tcd[1]), __fsub_rn(t[3], tc[i]), acc);
+            acc = __fmaf_rn(face_r(kc[i], k[4], c.tcd[2]), __fsub_rn(t[4], tc[i]), acc);
+            acc = __fmaf_rn(face_r(kc[i], k[5], c.tcd[2]), __fsub_rn(t[5], tc[i]), acc);
+        } else {
+            acc = __fmul_rn(c.cu[0], __fadd_rn(__fsub_rn(t[0], tc[i]), __fsub_rn(t[1], tc[i])));
+            acc = __fmaf_rn(c.cu[1], __fadd_rn(__fsub_rn(t[2], tc[i]), __fsub_rn(t[3], tc[i])), acc);
+            acc = __fmaf_rn(c.cu[2], __fadd_rn(__fsub_rn(t[4], tc[i]), __fsub_rn(t[5], tc[i])), acc);
+        }
+        if (EDGE) {
+            const bool isfree = gx + i < nx && gy < ny && !cg_held(c, gx + i, gy, z);
+            rv[i] = isfree ? acc : 0.0f;
+            sr = __fmaf_rn(rv[i], rv[i], sr);
+            if (isfree) sb = __fmaf_rn(bs, bs, sb);
+        } else {
+            rv[i] = acc;
+            sr = __fmaf_rn(acc, acc, sr);
+            sb = __fmaf_rn(bs, bs, sb);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- cg_init --
 // r = b - A T (dt times the explicit step's accumulation), b.b and r.r, on
 // the column-march layout of cg_spmv (4 x cells a thread, z queue). The
@@ -228,6 +321,7 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_init(co
         // fast cells: no boundary face and no held neighbour (two cells from
         // every non-periodic face)
         const bool inner_xy = gx + 3 < nx && (perx || (gx > 1 && gx + 5 < nx)) && (pery || (gy > 1 && gy < ny - 2));
+        const CgEdge edge = cg_edge(c, gx, gy);
         float tm[4], tc[4], km[4], kc[4];
         ld4(xv + row + (long long)(z0 - 1) * sz, tm);
         ld4(xv + row + (long long)z0 * sz, tc);
@@ -254,67 +348,12 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_init(co
             float rv[4];
             float sr = 0.0f, sb = 0.0f;
             const bool fast = inner_xy && (perz || (z > 1 && z < nz - 2));
-            if (__all_sync(__activemask(), fast)) {   // warp-uniform choice, as in cg_spmv
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float tw = i == 0 ? xm : tc[i - 1], te = i == 3 ? xp : tc[i + 1];
-                    float acc;
-                    if (KVAR) {
-                        const float kw = i == 0 ? kxm : kc[i - 1], ke = i == 3 ? kxp : kc[i + 1];
-                        acc = __fmul_rn(face_r(kc[i], kw, c.tcd[0]), __fsub_rn(tw, tc[i]));
-                        acc = __fmaf_rn(face_r(kc[i], ke, c.tcd[0]), __fsub_rn(te, tc[i]), acc);
-                        acc = __fmaf_rn(face_r(kc[i], kym[i], c.tcd[1]), __fsub_rn(ym[i], tc[i]), acc);
-                        acc = __fmaf_rn(face_r(kc[i], kyp[i], c.tcd[1]), __fsub_rn(yp[i], tc[i]), acc);
-                        acc = __fmaf_rn(face_r(kc[i], km[i], c.tcd[2]), __fsub_rn(tm[i], tc[i]), acc);
-                        acc = __fmaf_rn(face_r(kc[i], kp[i], c.tcd[2]), __fsub_rn(tp[i], tc[i]), acc);
-                    } else {
-                        acc = __fmul_rn(c.cu[0], __fadd_rn(__fsub_rn(tw, tc[i]), __fsub_rn(te, tc[i])));
-                        acc = __fmaf_rn(c.cu[1], __fadd_rn(__fsub_rn(ym[i], tc[i]), __fsub_rn(yp[i], tc[i])), acc);
-                        acc = __fmaf_rn(c.cu[2], __fadd_rn(__fsub_rn(tm[i], tc[i]), __fsub_rn(tp[i], tc[i])), acc);
-                    }
-                    rv[i] = acc;
-                    sr = __fmaf_rn(acc, acc, sr);
-                    sb = __fmaf_rn(tc[i], tc[i], sb);
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int xi = gx + i;
-                    const float tv[6] = {i == 0 ? xm : tc[i - 1], i == 3 ? xp : tc[i + 1], ym[i], yp[i], tm[i], tp[i]};
-                    float kv[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-                    if (KVAR) {
-                        kv[0] = i == 0 ? kxm : kc[i - 1];
-                        kv[1] = i == 3 ? kxp : kc[i + 1];
-                        kv[2] = kym[i];
-                        kv[3] = kyp[i];
-                        kv[4] = km[i];
-                        kv[5] = kp[i];
-                    }
-                    const bool nbin[6] = {perx || xi > 0, perx || xi < nx - 1, pery || gy > 0, pery || gy < ny - 1,
-                                          perz || z > 0, perz || z < nz - 1};
-                    // a neighbour inside the domain is held only through its own axis's face
-                    const bool nbheld[6] = {c.held[0] && xi == 1, c.held[1] && xi == nx - 2, c.held[2] && gy == 1,
-                                            c.held[3] && gy == ny - 2, c.held[4] && z == 1, c.held[5] && z == nz - 2};
-                    float acc = 0.0f, bs = tc[i];
-#pragma unroll
-                    for (int f = 0; f < 6; ++f) {
-                        const int ax = f >> 1;
-                        if (nbin[f]) {
-                            const float cf = KVAR ? face_r(kc[i], kv[f], c.tcd[ax]) : c.cu[ax];
-                            acc = __fmaf_rn(cf, __fsub_rn(tv[f], tc[i]), acc);
-                            if (nbheld[f]) bs = __fmaf_rn(cf, tv[f], bs);
-                        } else if (c.dface[f]) {
-                            const float df = KVAR ? dirichlet_r(kc[i], c.tcd[ax]) : 2.0f * c.cu[ax];
-                            acc = __fmaf_rn(df, __fsub_rn(c.tb[f], tc[i]), acc);
-                            bs = __fmaf_rn(df, c.tb[f], bs);
-                        }
-                    }
-                    const bool isfree = xi < nx && !cg_held(c, xi, gy, z);
-                    rv[i] = isfree ? acc : 0.0f;
-                    sr = __fmaf_rn(rv[i], rv[i], sr);
-                    if (isfree) sb = __fmaf_rn(bs, bs, sb);
-                }
-            }
+            if (__all_sync(__activemask(), fast))   // warp-uniform choice, as in cg_spmv
+                cg_r4<KVAR, false>(c, edge, gx, gy, z, tc, tm, tp, ym, yp, xm, xp, kc, km, kp, kym, kyp, kxm, kxp, rv,
+                                   sr, sb);
+            else
+                cg_r4<KVAR, true>(c, edge, gx, gy, z, tc, tm, tp, ym, yp, xm, xp, kc, km, kp, kym, kyp, kxm, kxp, rv,
+                                  sr, sb);
             st4_twins(a.r, c, gx, gy, z, rv);
             rr.add(sr);
             bb.add(sb);
@@ -373,29 +412,6 @@ __device__ __forceinline__ float pnew1(const PNew& P, long long o) {
     const float v = __ldg(P.r + o);
     return P.first ? v : __fmaf_rn(P.beta, __ldg(P.po + o), v);
 }
-
-// Boundary faces a thread's cells touch (non-periodic axes only). A face is
-// taken as a ghost neighbour that makes the interior formula exact: across a
-// Dirichlet face (value 0 in A) p_ghost = -p_C, across a zero-flux face
-// p_ghost = p_C, with the ghost's conductivity that of the cell (so the face
-// coefficient is tcd / (2 r_C): twice it is the Dirichlet coefficient
-// 2 k_C dt / h^2). Held cells are masked (q = 0).
-struct CgEdge {
-    int ih;            // index 0..3 of the thread's cell on the +x face (4: none)
-    unsigned bits;     // 1: cell 0 on the -x face, 2: the row on the -y face, 4: on the +y face
-};
-
-__device__ __forceinline__ CgEdge cg_edge(const CgCoef& c, int gx, int gy) {
-    CgEdge e;
-    const int nx = c.n[0], ny = c.n[1];
-    e.ih = (!c.periodic[0] && gx <= nx - 1 && nx - 1 - gx < 4) ? nx - 1 - gx : 4;
-    e.bits = ((!c.periodic[0] && gx == 0) ? 1u : 0u) | ((!c.periodic[1] && gy == 0) ? 2u : 0u) |
-             ((!c.periodic[1] && gy == ny - 1) ? 4u : 0u);
-    return e;
-}
-
-// ghost value across face f of a cell holding v: -v (Dirichlet face) or v
-__device__ __forceinline__ float ghost(const CgCoef& c, int f, float v) { return c.dface[f] ? -v : v; }
 
 // q = A p for the 4 cells of a thread at plane z, and their p.q (cells inside
 // the domain). EDGE (chosen warp-uniformly) puts ghost values across
@@ -736,11 +752,16 @@ __global__ void __launch_bounds__(CG_THREADS) cg_update(const __grid_constant__ 
     const int xg = (nx + 3) / 4;
     const long long items = (long long)xg * ny * nz;
     KahanF rr;
-    for (long long it = blockIdx.x * (long long)CG_THREADS + threadIdx.x; it < items;
-         it += (long long)gridDim.x * CG_THREADS) {
-        const long long rowi = it / xg;
-        const int gx = 4 * (int)(it - rowi * xg);
-        const int y = (int)(rowi % ny), z = (int)(rowi / ny);
+    // item it = (x group, y, z); one division at the start, then the stride
+    // is added digit by digit (no 64-bit division in the loop)
+    const long long it0 = blockIdx.x * (long long)CG_THREADS + threadIdx.x;
+    const long long stride = (long long)gridDim.x * CG_THREADS;
+    const int dxg = (int)(stride % xg);
+    const long long drow = stride / xg;
+    const int dy = (int)(drow % ny), dz = (int)(drow / ny);
+    int ixg = (int)(it0 % xg), y = (int)((it0 / xg) % ny), z = (int)(it0 / xg / ny);
+    for (long long it = it0; it < items; it += stride) {
+        const int gx = 4 * ixg;
         const long long o = cg_at(c, gx, y, z);
         float xv[4], pv[4], qv[4], rv[4];
         ld4(a.x + o, xv);
@@ -757,6 +778,17 @@ __global__ void __launch_bounds__(CG_THREADS) cg_update(const __grid_constant__ 
         rr.add(s);
         st4_twins(a.x, c, gx, y, z, xv);   // the field's twins feed the next step's cg_init
         st4_twins(a.r, c, gx, y, z, rv);
+        ixg += dxg;
+        y += dy;
+        z += dz;
+        if (ixg >= xg) {
+            ixg -= xg;
+            ++y;
+        }
+        if (y >= ny) {
+            y -= ny;
+            ++z;
+        }
     }
     const double bsum = block_sum(rr.value(), red);
     if (!publish(a, a.part + blockIdx.x, bsum, &last)) return;
