@@ -1008,12 +1008,16 @@ int wfa_implicit_step(wfa_grid g, double dt, long long n, double rtol, int max_i
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (nsm <= 0) nsm = 1;
-    {   // cg_spmv grid: 64 x 16 columns, z chunks of >= 8 planes filling two waves
+    {   // cg_spmv / cg_init grid: 64 x 16 columns, z chunks of about 16 planes,
+        // many waves of blocks so the last wave's tail is short; chunks down to
+        // 2 planes only where 16 would leave SMs idle (small grids)
         const int gxb = (g->n[0] + 63) / 64, gyb = (g->n[1] + CG_TY - 1) / CG_TY;
         const long long cols = (long long)gxb * gyb;
-        const long long want = 2LL * nsm * (kvar ? CgOcc<true>::blocks : CgOcc<false>::blocks);
-        long long nch = std::max<long long>(1, (want + cols - 1) / cols);
-        nch = std::min<long long>(nch, std::max(1, g->n[2] / 8));
+        const long long resident = (long long)nsm * (kvar ? CgOcc<true>::blocks : CgOcc<false>::blocks);
+        long long nch = std::max<long long>(1, resident * 16 / cols);
+        long long cap = std::max(1, g->n[2] / 16);
+        if (cols * cap < resident) cap = std::max(1, g->n[2] / 2);
+        nch = std::min(nch, cap);
         nch = std::min<long long>(nch, std::max<long long>(1, CG_MAX_PART / cols));
         base.zchunk = (int)((g->n[2] + nch - 1) / nch);
         nch = (g->n[2] + base.zchunk - 1) / base.zchunk;
