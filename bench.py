@@ -75,11 +75,20 @@ def job_rate(world, updates_per_rank, seconds):
     return world * updates_per_rank / seconds / 1e9
 
 
+DEVICE_MATH_MARK = b"// ----------------------------------------------------------- device math --"
+
+
 def kernel_hash():
+    """Hash of the sweep kernels' device code: their own headers, plus the
+    device-math part of wfa_internal.cuh (its host declarations above the
+    marker do not change the kernels)."""
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES:
         with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+            text = f.read()
+        if rel.endswith("wfa_internal.cuh") and DEVICE_MATH_MARK in text:
+            text = text[text.index(DEVICE_MATH_MARK):]
+        h.update(text)
     return h.hexdigest()[:16]
 
 
