@@ -354,6 +354,17 @@ def batch_bench(args):
     print(json.dumps(line), flush=True)
 
 
+CG_SOURCES = ["paper_2209_13768_gb300/csrc/wfa_implicit.cu"]
+
+
+def cg_kernel_hash():
+    h = hashlib.sha256()
+    for rel in CG_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def cg_bytes_per_cell(kvar):
     """Algorithmic HBM bytes per cell per CG iteration: cg_spmv reads r and
     p_old and writes p and q (16 B, + 4 B of 1/k for per-cell k); cg_update
@@ -411,6 +422,14 @@ def implicit_bench(args, rank, world, dist):
     except OSError:
         pass
     peak = peaks.get("hbm_gbs", 6800.0)
+    traffic = None   # DRAM bytes of one CG iteration (cg_spmv + cg_update) from ncu, if current
+    try:
+        with open(TRAFFIC_FILE) as f:
+            ent = json.load(f).get(f"implicit:{'k' if kvar else 'u'}:cg_iteration")
+        if ent and ent.get("kernel_hash") == cg_kernel_hash() and shape == W.IMPLICIT_SHAPE:
+            traffic = ent["bytes_per_iteration"]
+    except (OSError, ValueError):
+        pass
     e2e = None
     if not args.no_e2e:
         T0h = torch.from_numpy(np.ascontiguousarray(p.T0)).pin_memory()
@@ -456,7 +475,7 @@ def implicit_bench(args, rank, world, dist):
                            "l2": "inputs larger than L2 (six 512 MiB vectors)", "parallelism": f"replicas x{world}"},
                 "cg_iterations_per_s": world * iters / total_s,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": None,
+                             "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per CG iteration",
                              "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                              "bytes_per_cell_per_iteration": bpc,
                              "scope": "every kernel of the timed steps (cg_init, cg_spmv, cg_update) and the "
