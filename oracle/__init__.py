@@ -9,7 +9,8 @@ Functions
 ---------
 run(T0, n_steps, **problem)      -> field after n_steps (Eq. expl_form, face-flux form)
 implicit(T0, n_steps, **problem) -> (field, CG iterations, relative residual) after
-                                    n_steps backward-Euler steps (Eq. impl_form, classic CG)
+                                    n_steps backward-Euler steps (Eq. impl_form, classic CG;
+                                    method="cgcg": Chronopoulos-Gear CG)
 dt_max(**problem)                -> positivity limit of the explicit step (Sec. 1.1.1)
 total_heat(T, h)                 -> sum of T times the cell volume
 round_to(x, mode)                -> fp32 / bf16 nearest-even rounding used by ``run``
@@ -72,6 +73,9 @@ def _bind(path):
         lib.wfa_oracle_implicit.argtypes = [i64p, dp, ctypes.c_double, dp, ip, dp, ctypes.c_double, dp,
                                             ctypes.c_int64, ctypes.c_double, ctypes.c_int64, i64p, dp, ctypes.c_int]
         lib.wfa_oracle_implicit.restype = ctypes.c_int
+    if hasattr(lib, "wfa_oracle_implicit_cgcg"):
+        lib.wfa_oracle_implicit_cgcg.argtypes = lib.wfa_oracle_implicit.argtypes
+        lib.wfa_oracle_implicit_cgcg.restype = ctypes.c_int
     return lib
 
 
@@ -129,13 +133,15 @@ def run(T0, n_steps, *, shape, h=(1.0, 1.0, 1.0), k=1.0, u=(0.0, 0.0, 0.0), bc, 
 
 
 def implicit(T0, n_steps, *, shape, h=(1.0, 1.0, 1.0), k=1.0, bc, dt, rtol=1e-12, max_iter=10000,
-             threads=0, lib=None):
+             threads=0, lib=None, method="classic"):
     """Advance T0 by n_steps backward-Euler steps, each solved by classic CG
     in fp64 (Sec. 1.1.2, Eq. impl_form, face-flux form, no advection).
 
     Returns (T, iterations of all steps, last step's relative residual
     sqrt(r.r / b.b)). rtol = 0 runs exactly max_iter iterations per step
-    (fewer only if the residual becomes exactly zero)."""
+    (fewer only if the residual becomes exactly zero). method="cgcg" runs
+    Chronopoulos and Gear's single-synchronisation CG instead (the same
+    iterates in exact arithmetic)."""
     lib = lib or _load()
     n, hh, _, k_uniform, karr, kinds, vals = _common(shape, h, (0.0, 0.0, 0.0), k, bc)
     T = np.array(T0, dtype=np.float64, order="C", copy=True)
@@ -144,8 +150,9 @@ def implicit(T0, n_steps, *, shape, h=(1.0, 1.0, 1.0), k=1.0, bc, dt, rtol=1e-12
         raise ValueError(f"T0 has shape {T.shape}, expected {(nz, ny, nx)}")
     iters = ctypes.c_int64()
     res = ctypes.c_double()
-    rc = lib.wfa_oracle_implicit(n, hh, k_uniform, _ptr(karr), kinds, vals, float(dt), _ptr(T), int(n_steps),
-                                 float(rtol), int(max_iter), ctypes.byref(iters), ctypes.byref(res), int(threads))
+    fn = {"classic": lib.wfa_oracle_implicit, "cgcg": lib.wfa_oracle_implicit_cgcg}[method]
+    rc = fn(n, hh, k_uniform, _ptr(karr), kinds, vals, float(dt), _ptr(T), int(n_steps),
+            float(rtol), int(max_iter), ctypes.byref(iters), ctypes.byref(res), int(threads))
     if rc != 0:
         raise ValueError(f"oracle rejected the problem (code {rc})")
     return T, iters.value, res.value

@@ -410,3 +410,101 @@ int wfa_oracle_implicit(const int64_t n[3], const double h[3], double k_uniform,
     free(buf);
     return 0;
 }
+
+/*
+ * The same backward-Euler steps solved by Chronopoulos and Gear's CG: one
+ * synchronisation per iteration, both inner products taken together (the
+ * reduction-limited Krylov variants Sec. 1.1.2 and Sec. 4.2 point to). In
+ * exact arithmetic its iterates are those of classic CG; it carries w = A r
+ * and s = A p by recurrence instead of applying A to p:
+ *   x = T^n on free cells;  r = b - A x;  w = A r
+ *   gamma = r.r;  delta = w.r;  alpha = gamma / delta;  beta = 0
+ *   while gamma > rtol^2 bb and it < max_iter:
+ *     p = r + beta p;  s = w + beta s
+ *     x += alpha p;  r -= alpha s;  w = A r
+ *     gamma' = r.r;  delta = w.r
+ *     beta = gamma' / gamma;  alpha = gamma' / (delta - beta gamma' / alpha)
+ *     gamma = gamma';  ++it
+ * Arguments and results as wfa_oracle_implicit.
+ */
+int wfa_oracle_implicit_cgcg(const int64_t n[3], const double h[3], double k_uniform, const double* k,
+                             const int kind[6], const double value[6], double dt, double* T, int64_t nsteps,
+                             double rtol, int64_t max_iter, int64_t* iters, double* rel_res, int nthreads) {
+    prob_t p, p0;
+    memcpy(p.n, n, sizeof p.n);
+    memcpy(p.h, h, sizeof p.h);
+    for (int a = 0; a < 3; ++a) p.u[a] = 0.0;
+    p.k_uniform = k_uniform;
+    p.k = k;
+    memcpy(p.kind, kind, sizeof p.kind);
+    memcpy(p.value, value, sizeof p.value);
+    p.dt = dt;
+    int rc = check(&p);
+    if (rc) return rc;
+    if (!(dt >= 0.0) || !(rtol >= 0.0) || max_iter < 0) return -1;
+    p0 = p;
+    for (int f = 0; f < 6; ++f) p0.value[f] = 0.0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    const int64_t N = n[0] * n[1] * n[2];
+    unsigned char* held = held_mask(&p);
+    double* buf = (double*)malloc((size_t)N * 7 * sizeof(double));
+    if (!held || !buf) {
+        free(held);
+        free(buf);
+        return -2;
+    }
+    double *z = buf, *x = buf + N, *r = buf + 2 * N, *w = buf + 3 * N, *pv = buf + 4 * N, *sv = buf + 5 * N,
+           *acc = buf + 6 * N;
+    int64_t total = 0;
+    double last = 0.0;
+    for (int64_t c = 0; c < N; ++c) {
+        z[c] = held[c] ? value[held[c] - 1] : 0.0;
+        if (held[c]) T[c] = z[c];
+    }
+    for (int64_t st = 0; st < nsteps; ++st) {
+        memset(acc, 0, (size_t)N * sizeof(double));
+        for (int a = 0; a < 3; ++a) face_pass(&p, z, acc, a);
+        for (int64_t c = 0; c < N; ++c) {
+            r[c] = held[c] ? 0.0 : T[c] + dt * acc[c];   /* b, for now */
+            x[c] = held[c] ? 0.0 : T[c];
+            pv[c] = sv[c] = 0.0;
+        }
+        const double bb = dot_free(held, r, r, N);
+        apply_A(&p0, held, x, w, acc);
+        for (int64_t c = 0; c < N; ++c) r[c] -= w[c];
+        apply_A(&p0, held, r, w, acc);
+        double gamma = dot_free(held, r, r, N);
+        double delta = dot_free(held, w, r, N);
+        double alpha = delta > 0.0 ? gamma / delta : 0.0, beta = 0.0;
+        int64_t it = 0;
+        while (gamma > rtol * rtol * bb && it < max_iter && alpha > 0.0) {
+            for (int64_t c = 0; c < N; ++c) {
+                pv[c] = r[c] + beta * pv[c];
+                sv[c] = w[c] + beta * sv[c];
+                x[c] += alpha * pv[c];
+                r[c] -= alpha * sv[c];
+            }
+            apply_A(&p0, held, r, w, acc);
+            const double g1 = dot_free(held, r, r, N);
+            delta = dot_free(held, w, r, N);
+            beta = g1 / gamma;
+            const double den = delta - beta * g1 / alpha;
+            alpha = den > 0.0 ? g1 / den : 0.0;   /* 0: breakdown or exact solution, the loop ends */
+            gamma = g1;
+            ++it;
+        }
+        for (int64_t c = 0; c < N; ++c)
+            if (!held[c]) T[c] = x[c];
+        total += it;
+        last = bb > 0.0 ? sqrt(gamma / bb) : sqrt(gamma);
+    }
+    if (iters) *iters = total;
+    if (rel_res) *rel_res = last;
+    free(held);
+    free(buf);
+    return 0;
+}

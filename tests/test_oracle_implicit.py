@@ -185,3 +185,36 @@ def test_implicit_zero_steps_and_rejects():
         oracle.implicit(T0, 1, shape=(5, 4, 3), k=1.0, bc=_bc([P, D, ZF, ZF, P, P]), dt=1.0)
     with pytest.raises(ValueError):
         oracle.implicit(T0, 1, shape=(5, 4, 3), k=1.0, bc=bc, dt=-1.0)
+
+
+@pytest.mark.parametrize("mix", [0, 3, 4, 5, 6])
+def test_cgcg_iterates_equal_classic_cg(mix):
+    # Chronopoulos-Gear CG carries A r and A p by recurrence; in exact
+    # arithmetic its iterates are classic CG's, so every fixed iteration count
+    # must agree to rounding
+    rng = np.random.default_rng(300 + mix)
+    shape = (7, 5, 6)
+    nx, ny, nz = shape
+    k = np.exp(0.5 * rng.standard_normal((nz, ny, nx)))
+    bc = _bc(BC_MIXES[mix], list(rng.uniform(-1, 2, 6)))
+    T0 = rng.uniform(0, 1, (nz, ny, nx))
+    for m in (1, 2, 4, 8, 15):
+        a, ia, _ = oracle.implicit(T0, 1, shape=shape, k=k, bc=bc, dt=2.0, rtol=0.0, max_iter=m)
+        b, ib, _ = oracle.implicit(T0, 1, shape=shape, k=k, bc=bc, dt=2.0, rtol=0.0, max_iter=m, method="cgcg")
+        assert ia == ib == m
+        np.testing.assert_allclose(b, a, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("mix", [1, 2, 4])
+def test_cgcg_matches_dense_solve(mix):
+    rng = np.random.default_rng(310 + mix)
+    shape = (5, 4, 6)
+    nx, ny, nz = shape
+    k = np.exp(0.5 * rng.standard_normal((nz, ny, nx)))
+    bc = _bc(BC_MIXES[mix], list(rng.uniform(-1, 2, 6)))
+    T0 = rng.uniform(0, 1, (nz, ny, nx))
+    ref, _, _ = dense_implicit(T0, 2, shape, (1.1, 0.8, 1.3), k, bc, 0.7)
+    T, _, res = oracle.implicit(T0, 2, shape=shape, h=(1.1, 0.8, 1.3), k=k, bc=bc, dt=0.7, rtol=1e-14,
+                                method="cgcg")
+    assert res <= 1e-14
+    np.testing.assert_allclose(T, ref, rtol=0, atol=1e-12)

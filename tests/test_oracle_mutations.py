@@ -29,12 +29,16 @@ MUTANTS = {
                                               "D += kc(&p, C) * inv_h2;"),
     "dt limit without advection": ("if (side == 1 && u[a] > 0.0) D += u[a] / h[a];", ""),
     "CG without beta (steepest descent)": ("const double beta = rr_new / rr;", "const double beta = 0.0;"),
-    "implicit right-hand side without boundary terms": ("r[c] = held[c] ? 0.0 : T[c] + dt * acc[c];",
-                                                        "r[c] = held[c] ? 0.0 : T[c];"),
+    "implicit right-hand side without boundary terms": ("r[c] = held[c] ? 0.0 : T[c] + dt * acc[c];\n            x[c]",
+                                                        "r[c] = held[c] ? 0.0 : T[c];\n            x[c]"),
     "implicit operator sign": ("out[c] = held[c] ? 0.0 : y[c] - p0->dt * acc[c];",
                                "out[c] = held[c] ? 0.0 : y[c] + p0->dt * acc[c];"),
     "CG residual update sign": ("r[c] -= alpha * q[c];", "r[c] += alpha * q[c];"),
-    "Dirichlet values left in the linear part": ("for (int f = 0; f < 6; ++f) p0.value[f] = 0.0;", "(void)0;"),
+    "Dirichlet values left in the linear part": ("for (int f = 0; f < 6; ++f) p0.value[f] = 0.0;\n#ifdef _OPENMP\n    if (nthreads > 0) omp_set_num_threads(nthreads);\n#else\n    (void)nthreads;\n#endif\n    const int64_t N = n[0] * n[1] * n[2];\n    unsigned char* held = held_mask(&p);\n    double* buf = (double*)malloc((size_t)N * 6",
+                                                 "(void)0;\n#ifdef _OPENMP\n    if (nthreads > 0) omp_set_num_threads(nthreads);\n#else\n    (void)nthreads;\n#endif\n    const int64_t N = n[0] * n[1] * n[2];\n    unsigned char* held = held_mask(&p);\n    double* buf = (double*)malloc((size_t)N * 6"),
+    "CG-CG step length without its beta correction": ("const double den = delta - beta * g1 / alpha;",
+                                                      "const double den = delta;"),
+    "CG-CG A p recurrence without beta": ("sv[c] = w[c] + beta * sv[c];", "sv[c] = w[c];"),
 }
 
 
@@ -100,6 +104,22 @@ def battery(lib):
     _, iters, res = oracle.implicit(T0, 1, shape=shape, k=1.0, bc=bc, dt=0.9, rtol=1e-12, max_iter=2000, lib=lib)
     if iters > 15 or res > 1e-12:   # 15 distinct eigenvalues
         failed.append("implicit iterations")
+    # Chronopoulos-Gear CG: the iterates of classic CG
+    rng = np.random.default_rng(103)
+    shape = (7, 5, 6)
+    k = np.exp(0.5 * rng.standard_normal(shape[::-1]))
+    bc = _bc(BC_MIXES[4], list(rng.uniform(-1, 2, 6)))
+    T0 = rng.uniform(0, 1, shape[::-1])
+    try:
+        for m in (2, 5, 9):
+            a, _, _ = oracle.implicit(T0, 1, shape=shape, k=k, bc=bc, dt=2.0, rtol=0.0, max_iter=m, lib=lib)
+            b, _, _ = oracle.implicit(T0, 1, shape=shape, k=k, bc=bc, dt=2.0, rtol=0.0, max_iter=m, lib=lib,
+                                      method="cgcg")
+            if not np.allclose(a, b, rtol=0, atol=1e-12):
+                failed.append("cgcg iterates")
+                break
+    except ValueError:
+        failed.append("cgcg rejected")
     return failed
 
 
