@@ -47,6 +47,8 @@ def parse():
                                            "implicit", "implicit_lognormal"],
                     default="lognormal")
     ap.add_argument("--rtol", type=float, default=1e-6, help="implicit: CG tolerance ||r|| <= rtol ||b||")
+    ap.add_argument("--cg", choices=["classic", "pipelined"], default="classic",
+                    help="implicit: classic CG or Chronopoulos-Gear (one reduction an iteration)")
     ap.add_argument("--serve-requests", type=int, default=400,
                     help="requests in the serving sample added to the line (0: none)")
     ap.add_argument("--solve-steps", type=int, default=0, help="time steps per benchmark step (0: workload default)")
@@ -368,7 +370,8 @@ def cg_kernel_hash():
 def cg_bytes_per_cell(kvar):
     """Algorithmic HBM bytes per cell per CG iteration: cg_spmv reads r and
     p_old and writes p and q (16 B, + 4 B of 1/k for per-cell k); cg_update
-    reads x, p, q, r and writes x, r (24 B)."""
+    reads x, p, q, r and writes x, r (24 B). The pipelined kernel moves the
+    same 40 B (+4): reads r, w, s, p, x, writes them."""
     return 40 + (4 if kvar else 0)
 
 
@@ -390,6 +393,7 @@ def implicit_bench(args, rank, world, dist):
     g.set_bcs(p.bc)
     g.set_coeffs(p.k)
     g.set_field(p.T0)
+    g.set_cg_method(args.cg)
     max_iter = 1000
     for _ in range(args.warmup):
         g.implicit_step(p.dt, p.steps, rtol=args.rtol, max_iter=max_iter)
@@ -426,7 +430,7 @@ def implicit_bench(args, rank, world, dist):
     try:
         with open(TRAFFIC_FILE) as f:
             ent = json.load(f).get(f"implicit:{'k' if kvar else 'u'}:cg_iteration")
-        if ent and ent.get("kernel_hash") == cg_kernel_hash() and shape == W.IMPLICIT_SHAPE:
+        if ent and ent.get("kernel_hash") == cg_kernel_hash() and shape == W.IMPLICIT_SHAPE and args.cg == "classic":
             traffic = ent["bytes_per_iteration"]
     except (OSError, ValueError):
         pass
@@ -469,7 +473,7 @@ def implicit_bench(args, rank, world, dist):
                 "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": p.name, "cells": cells, "time_steps_per_step": p.steps, "dt": p.dt,
-                           "omega": p.dt, "rtol": args.rtol, "cg_iterations": iters,
+                           "omega": p.dt, "rtol": args.rtol, "cg": args.cg, "cg_iterations": iters,
                            "cg_iterations_per_time_step": iters / (p.steps * args.steps), "last_rel_residual": res,
                            "conductivity": "per-cell lognormal(0,0.5)" if kvar else "uniform 1",
                            "l2": "inputs larger than L2 (six 512 MiB vectors)", "parallelism": f"replicas x{world}"},
@@ -478,8 +482,9 @@ def implicit_bench(args, rank, world, dist):
                              "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per CG iteration",
                              "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                              "bytes_per_cell_per_iteration": bpc,
-                             "scope": "every kernel of the timed steps (cg_init, cg_spmv, cg_update) and the "
-                                      "host's flag checks between graph runs"},
+                             "scope": "every kernel of the timed steps (cg_init, cg_spmv, cg_update; pipelined: "
+                                      "cg_init, cg_spmv once a step, cg_pipe) and the host's flag checks between "
+                                      "graph runs"},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clocks}
         print(json.dumps(line), flush=True)
 

@@ -192,6 +192,18 @@ int wfa_sum_f32_noalloc(const float* d_x, long long n, double scale, double* d_o
 int wfa_implicit_step(wfa_grid g, double dt, long long n, double rtol, int max_iter, long long* iters,
                       double* rel_res);
 
+/* CG variant of wfa_implicit_step (the iterates are the same in exact
+ * arithmetic; the default is WFA_CG_CLASSIC):
+ *   WFA_CG_CLASSIC    classic CG, two inner products and two kernels an
+ *                     iteration (Sec. 1.1.2);
+ *   WFA_CG_PIPELINED  Chronopoulos and Gear's CG, both inner products in one
+ *                     reduction and one kernel an iteration (the
+ *                     reduction-limited variant Sec. 4.2 points to); w = A r
+ *                     and s = A p by recurrence, three more fp32 work fields.
+ * Errors: WFA_ERR_ARG for a NULL grid or another value. */
+enum { WFA_CG_CLASSIC = 0, WFA_CG_PIPELINED = 1 };
+int wfa_set_cg_method(wfa_grid g, int method);
+
 /* Heat that one time step from the current field brings in through the
  * Dirichlet faces (Sec. 3's reduction, applied to the boundary), in fp64:
  * dt * hx*hy*hz * sum over the cells on Dirichlet faces of

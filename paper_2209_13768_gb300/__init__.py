@@ -22,6 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libwfa.so")
 
 F32, BF16 = 0, 1
+CG_CLASSIC, CG_PIPELINED = 0, 1
 DIRICHLET, ZEROFLUX, PERIODIC, DIRICHLET_CELL = 0, 1, 2, 3
 BC_KINDS = {"dirichlet": DIRICHLET, "zeroflux": ZEROFLUX, "periodic": PERIODIC,
             "dirichlet_cell": DIRICHLET_CELL}
@@ -75,6 +76,7 @@ SIGNATURES = {
     "wfa_last_error": (ctypes.c_char_p, []),
     "wfa_inject_alloc_failure": (_i, [_i]),
     "wfa_implicit_step": (_i, [_vp, _d, _ll, _d, _i, _llp, _dp]),
+    "wfa_set_cg_method": (_i, [_vp, _i]),
     "wfa_batch_run": (_i, [ctypes.POINTER(_vp), _llp, _i]),
     "wfa_server_create": (_i, [_sz, _i, _ll, ctypes.POINTER(_vp)]),
     "wfa_server_submit": (_i, [_vp, ctypes.POINTER(Request), _llp]),
@@ -258,6 +260,12 @@ class Grid:
         n = ctypes.c_longlong()
         check(lib().wfa_launch_count(self.handle, ctypes.byref(n)), "wfa_launch_count")
         return n.value
+
+    def set_cg_method(self, method):
+        """"classic" (two kernels and two reductions an iteration) or
+        "pipelined" (Chronopoulos-Gear: one of each); see wfa_set_cg_method."""
+        m = {"classic": CG_CLASSIC, "pipelined": CG_PIPELINED}.get(method, method)
+        check(lib().wfa_set_cg_method(self.handle, int(m)), "wfa_set_cg_method")
 
     def implicit_step(self, dt, n=1, rtol=1e-6, max_iter=1000):
         """n backward-Euler steps of size dt, each solved by classic CG to

@@ -88,8 +88,12 @@ struct CgArgs {
     float* q;
     double* part;      // per-block partials (two arrays of CG_MAX_PART for cg_init)
     CgState* s;
+    float* r2;         // pipelined CG: second r, w and s buffers (r, w and s ping-pong, read at
+    float* w2;         // neighbours: r in r / r2, w in q / w2, s in p1 / s2; p in p0)
+    float* s2;
     int zchunk;        // cg_spmv planes per block
     int nblk;          // blocks of this launch
+    int q_twins;       // cg_spmv also writes q's periodic twins (q is the pipelined solver's first w)
 };
 
 __device__ __forceinline__ long long cg_at(const CgCoef& c, int x, int y, int z) {
@@ -536,7 +540,9 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv(co
                                                        kyp, kxm, kxp, q);
             dot.add(psum);
             st4_twins(pn, c, gx, gy, z, pc);
-            if (gx + 3 < nx) {
+            if (a.q_twins) {
+                st4_twins(qv, c, gx, gy, z, q);
+            } else if (gx + 3 < nx) {
                 *reinterpret_cast<float4*>(qv + o) = make_float4(q[0], q[1], q[2], q[3]);
             } else {
 #pragma unroll
@@ -737,6 +743,177 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv_sm
     }
 }
 
+// ---------------------------------------------------------------- cg_pipe --
+// One iteration of Chronopoulos and Gear's CG in one kernel and one
+// reduction (the reduction-limited variant Sec. 4.2 points to): with alpha,
+// beta of this iteration,
+//   s = w + beta s,  p = r + beta p,  x += alpha p,  r' = r - alpha s,
+//   w' = A r',  gamma' = r'.r',  delta' = w'.r'
+// and the last block forms beta' = gamma' / gamma and
+// alpha' = gamma' / (delta' - beta' gamma' / alpha). r' is needed at the
+// neighbours of each cell, so it is formed there from r, w and s (three
+// arrays with their x / y halo); r, w and s ping-pong between two buffers, p
+// is read and written only at its own cell.
+template <bool KVAR>
+struct PipeOcc {
+    static constexpr int blocks = KVAR ? 2 : 3;
+};
+
+struct RNew {
+    const float* r;
+    const float* w;
+    const float* s;
+    float alpha, beta;
+    bool first;   // beta = 0: s = w (s is not read)
+};
+
+// r' and s at 4 cells of one row
+__device__ __forceinline__ void rnew4(const RNew& R, long long o, float rn[4], float sn[4], float rv[4]) {
+    ld4(R.r + o, rv);
+    ld4(R.w + o, sn);
+    if (!R.first) {
+        float so[4];
+        ld4(R.s + o, so);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) sn[i] = __fmaf_rn(R.beta, so[i], sn[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) rn[i] = __fmaf_rn(-R.alpha, sn[i], rv[i]);
+}
+__device__ __forceinline__ float rnew1(const RNew& R, long long o) {
+    float sv = __ldg(R.w + o);
+    if (!R.first) sv = __fmaf_rn(R.beta, __ldg(R.s + o), sv);
+    return __fmaf_rn(-R.alpha, sv, __ldg(R.r + o));
+}
+
+template <bool KVAR>
+__global__ void __launch_bounds__(CG_TX * CG_TY, PipeOcc<KVAR>::blocks) cg_pipe(const __grid_constant__ CgArgs a) {
+    __shared__ double red[CG_TX * CG_TY / 32];
+    __shared__ bool last;
+    const CgCoef& c = a.c;
+    if (a.s->done) return;
+    const int par = a.s->iter & 1;   // iteration i reads r, w [i mod 2], writes [(i + 1) mod 2]
+    RNew R;
+    R.r = par ? a.r2 : a.r;
+    R.w = par ? a.w2 : a.q;
+    R.s = par ? a.s2 : a.p1;
+    R.alpha = (float)a.s->alpha;
+    R.beta = (float)a.s->beta;
+    R.first = a.s->iter == 0;
+    float* __restrict__ r_out = par ? a.r : a.r2;
+    float* __restrict__ w_out = par ? a.q : a.w2;
+    float* __restrict__ pv = a.p0;
+    float* __restrict__ sv = par ? a.p1 : a.s2;
+    float* __restrict__ xv = a.x;
+    const float* __restrict__ rk = a.rk;
+    const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int gx = blockIdx.x * 64 + 4 * tx, gy = blockIdx.y * CG_TY + ty;
+    const int z0 = blockIdx.z * a.zchunk, z1 = min(z0 + a.zchunk, nz);
+    const bool perx = c.periodic[0], pery = c.periodic[1], perz = c.periodic[2];
+    KahanF gam, del;
+    if (gx < nx && gy < ny) {
+        const long long sy = c.sy, sz = c.sz;
+        const long long row = cg_at(c, gx, gy, 0);
+        const bool inner_xy = gx + 3 < nx && (perx || (gx > 0 && gx + 4 < nx)) && (pery || (gy > 0 && gy < ny - 1));
+        const CgEdge edge = cg_edge(c, gx, gy);
+        float rm[4], rc[4], sc[4], rvc[4], km[4], kc[4], tmp[4];
+        rnew4(R, row + (long long)(z0 - 1) * sz, rm, tmp, rvc);
+        rnew4(R, row + (long long)z0 * sz, rc, sc, rvc);
+        if (KVAR) {
+            ld4(rk + row + (long long)(z0 - 1) * sz, km);
+            ld4(rk + row + (long long)z0 * sz, kc);
+        }
+        for (int z = z0; z < z1; ++z) {
+            const long long o = row + (long long)z * sz;
+            if ((tx & 7) == 0) {   // one thread per 128-byte line asks L2 for plane z + 3
+                prefetch_l2(R.r + o + 3 * sz);
+                prefetch_l2(R.w + o + 3 * sz);
+                if (!R.first) prefetch_l2(R.s + o + 3 * sz);
+            }
+            float rp[4], sp_[4], rvp[4], ym[4], yp[4], t4[4], t5[4];
+            rnew4(R, o + sz, rp, sp_, rvp);
+            rnew4(R, o - sy, ym, t4, t5);
+            rnew4(R, o + sy, yp, t4, t5);
+            const float xm = rnew1(R, o - 1), xp = rnew1(R, o + 4);
+            float kp[4], kym[4], kyp[4], kxm = 0.0f, kxp = 0.0f;
+            if (KVAR) {
+                ld4(rk + o + sz, kp);
+                ld4(rk + o - sy, kym);
+                ld4(rk + o + sy, kyp);
+                kxm = __ldg(rk + o - 1);
+                kxp = __ldg(rk + o + 4);
+            }
+            float wn[4];
+            const bool fast = inner_xy && (perz || (z > 0 && z < nz - 1));
+            const bool interior = __all_sync(__activemask(), fast);
+            const float dsum = interior
+                                   ? cg_q4<KVAR, false>(c, edge, gx, gy, z, rc, rm, rp, ym, yp, xm, xp, kc, km, kp, kym,
+                                                        kyp, kxm, kxp, wn)
+                                   : cg_q4<KVAR, true>(c, edge, gx, gy, z, rc, rm, rp, ym, yp, xm, xp, kc, km, kp, kym,
+                                                       kyp, kxm, kxp, wn);
+            float gsum = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                gsum = (interior || gx + i < nx) ? __fmaf_rn(rc[i], rc[i], gsum) : gsum;   // held cells: r' = 0
+            gam.add(gsum);
+            del.add(dsum);
+            // own cells at plane z: p, x, and the new s, r, w
+            float pn[4], xn[4];
+            ld4(xv + o, xn);
+            if (R.first) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) pn[i] = rvc[i];
+            } else {
+                ld4(pv + o, pn);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) pn[i] = __fmaf_rn(R.beta, pn[i], rvc[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) xn[i] = __fmaf_rn(R.alpha, pn[i], xn[i]);
+            st4_row(pv + o, gx, nx, pn);
+            st4_twins(sv, c, gx, gy, z, sc);
+            st4_twins(xv, c, gx, gy, z, xn);
+            st4_twins(r_out, c, gx, gy, z, rc);
+            st4_twins(w_out, c, gx, gy, z, wn);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                rm[i] = rc[i];
+                rc[i] = rp[i];
+                sc[i] = sp_[i];
+                rvc[i] = rvp[i];
+                if (KVAR) {
+                    km[i] = kc[i];
+                    kc[i] = kp[i];
+                }
+            }
+        }
+    }
+    const double gs = block_sum(gam.value(), red);
+    const double ds = block_sum(del.value(), red);
+    const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    if (threadIdx.x == 0 && threadIdx.y == 0) a.part[CG_MAX_PART + blk] = ds;
+    if (!publish(a, a.part + blk, gs, &last)) return;
+    const double G = sum_partials(a.part, a.nblk, red);
+    const double Dl = sum_partials(a.part + CG_MAX_PART, a.nblk, red);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        CgState* st = a.s;
+        const double beta = st->rr > 0.0 ? G / st->rr : 0.0;
+        const double den = st->alpha > 0.0 ? Dl - beta * G / st->alpha : 0.0;
+        st->iter += 1;
+        st->beta = beta;
+        st->rr = G;
+        if (den > 0.0 && den < INFINITY) {
+            st->alpha = G / den;
+        } else {
+            st->alpha = 0.0;
+            st->done = 1;   // r' = 0 (exact solution) or a breakdown
+        }
+        if (G <= st->tol2 * st->bb || st->iter >= st->max_iter || !(G == G)) st->done = 1;
+        st->ticket = 0;
+    }
+}
+
 // -------------------------------------------------------------- cg_update --
 // x += alpha p, r -= alpha q over the domain cells (4 along x per item),
 // r.r partials; then beta and the convergence test.
@@ -812,10 +989,12 @@ struct CgWork {
     CgState* s = nullptr;
     CgState* h[2] = {nullptr, nullptr};   // pinned read-back slots
     cudaEvent_t ev[2] = {nullptr, nullptr};
+    float* extra[3] = {nullptr, nullptr, nullptr};   // pipelined CG: r2, w2, s2 (allocated on first use)
     cudaGraphExec_t exec[CG_NRUN] = {nullptr, nullptr, nullptr, nullptr};
     cudaStream_t cap = nullptr;   // capture stream (the grid's own may be the legacy default stream)
     CgArgs key;        // arguments the graph was captured with
     int kvar = -1;
+    int method = -1;   // WFA_CG_CLASSIC / WFA_CG_PIPELINED of the captured graphs
     int spmv_grid[3] = {0, 0, 0};
     int upd_blocks = 0;
     long long prev_iters = 0;   // iterations the last step needed (sizes the first run of the next)
@@ -833,6 +1012,7 @@ void free_cg(wfa_grid_s* g) {
         pinned_release(w->h[b]);
         dev_free(w->p[b], g->stream);
     }
+    for (float* e : w->extra) dev_free(e, g->stream);
     dev_free(w->r, g->stream);
     dev_free(w->q, g->stream);
     dev_free(w->part, g->stream);
@@ -895,8 +1075,9 @@ static void cg_coef(const wfa_grid_s* g, double dt, CgCoef* c) {
     c->sz = g->px * g->py;
 }
 
-static int cg_capture(wfa_grid_s* g, CgWork* w, const CgArgs& base, bool kvar) {
-    if (w->exec[0] && w->kvar == (int)kvar && memcmp(&w->key, &base, sizeof base) == 0) return WFA_OK;
+static int cg_capture(wfa_grid_s* g, CgWork* w, const CgArgs& base, bool kvar, int method) {
+    if (w->exec[0] && w->kvar == (int)kvar && w->method == method && memcmp(&w->key, &base, sizeof base) == 0)
+        return WFA_OK;
     for (cudaGraphExec_t& e : w->exec)
         if (e) {
             cudaGraphExecDestroy(e);
@@ -916,6 +1097,14 @@ static int cg_capture(wfa_grid_s* g, CgWork* w, const CgArgs& base, bool kvar) {
         WFA_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaSuccess;
         for (int it = 0; it < CG_RUN_LEN[k] && e == cudaSuccess; ++it) {
+            if (method == WFA_CG_PIPELINED) {   // one kernel, one reduction an iteration
+                if (kvar)
+                    cg_pipe<true><<<sgrid, sblock, 0, st>>>(sp);
+                else
+                    cg_pipe<false><<<sgrid, sblock, 0, st>>>(sp);
+                e = cudaGetLastError();
+                continue;
+            }
             if (kvar && use_sm)
                 cg_spmv_sm<true><<<sgrid, sblock, 0, st>>>(sp);
             else if (kvar)
@@ -942,6 +1131,7 @@ static int cg_capture(wfa_grid_s* g, CgWork* w, const CgArgs& base, bool kvar) {
     }
     w->key = base;
     w->kvar = kvar;
+    w->method = method;
     return WFA_OK;
 }
 
@@ -1031,12 +1221,26 @@ int wfa_implicit_step(wfa_grid g, double dt, long long n, double rtol, int max_i
         const long long items = (long long)((g->n[0] + 3) / 4) * g->n[1] * g->n[2];
         w->upd_blocks = (int)std::max<long long>(1, std::min<long long>((items + CG_THREADS - 1) / CG_THREADS, nsm * 8LL));
     }
-    rc = cg_capture(g, w, base, kvar);
+    const int method = g->cg_method;
+    if (method == WFA_CG_PIPELINED) {   // three more work vectors: r, w and s ping-pong
+        const size_t fb = field_elems(g) * sizeof(float);
+        for (float*& e : w->extra)
+            if (!e) {
+                WFA_CUDA(dev_alloc((void**)&e, fb, g->stream));
+                WFA_CUDA(cudaMemsetAsync(e, 0, fb, g->stream));
+            }
+        base.r2 = w->extra[0] + off;
+        base.w2 = w->extra[1] + off;
+        base.s2 = w->extra[2] + off;
+        base.q_twins = 1;
+    }
+    rc = cg_capture(g, w, base, kvar, method);
     if (rc) return rc;
 
     CgArgs ia = base;
     ia.nblk = w->spmv_grid[0] * w->spmv_grid[1] * w->spmv_grid[2];
     const dim3 sgrid(w->spmv_grid[0], w->spmv_grid[1], w->spmv_grid[2]), sblock(CG_TX, CG_TY);
+    const int per_iter = method == WFA_CG_PIPELINED ? 1 : 2;   // kernels an iteration
     long long total = 0;
     double last_rel = 0.0;
     for (long long step = 0; step < n; ++step) {
@@ -1046,6 +1250,16 @@ int wfa_implicit_step(wfa_grid g, double dt, long long n, double rtol, int max_i
             cg_init<false><<<sgrid, sblock, 0, g->stream>>>(ia, rtol * rtol, max_iter);
         WFA_CUDA(cudaGetLastError());
         g->launches += 1;
+        if (method == WFA_CG_PIPELINED) {
+            // w = A r, delta = w.r and alpha = r.r / delta: the first half of a
+            // classic iteration (q = A p with p = r), q keeping its twins
+            if (kvar)
+                cg_spmv<true><<<sgrid, sblock, 0, g->stream>>>(ia);
+            else
+                cg_spmv<false><<<sgrid, sblock, 0, g->stream>>>(ia);
+            WFA_CUDA(cudaGetLastError());
+            g->launches += 1;
+        }
         // Runs of captured iterations with one run queued ahead of the flag
         // check, so the GPU does not wait for the host: the first run as long
         // as the last step needed (rounded up to 1, 2, 4 or 8), then 2, then 8s.
@@ -1063,7 +1277,7 @@ int wfa_implicit_step(wfa_grid g, double dt, long long n, double rtol, int max_i
             WFA_CUDA(cudaGraphLaunch(w->exec[k], g->stream));
             WFA_CUDA(cudaMemcpyAsync(w->h[launched & 1], w->s, sizeof(CgState), cudaMemcpyDeviceToHost, g->stream));
             WFA_CUDA(cudaEventRecord(w->ev[launched & 1], g->stream));
-            g->launches += 2 * CG_RUN_LEN[k];
+            g->launches += per_iter * CG_RUN_LEN[k];
             queued += CG_RUN_LEN[k];
             ++launched;
             return WFA_OK;
@@ -1094,5 +1308,14 @@ int wfa_implicit_step(wfa_grid g, double dt, long long n, double rtol, int max_i
     g->steps_done += n;
     if (iters) *iters = total;
     if (rel_res) *rel_res = last_rel;
+    return WFA_OK;
+}
+
+int wfa_set_cg_method(wfa_grid g, int method) {
+    if (!g || (method != WFA_CG_CLASSIC && method != WFA_CG_PIPELINED)) {
+        set_error("wfa_set_cg_method: NULL grid or unknown method %d", method);
+        return WFA_ERR_ARG;
+    }
+    g->cg_method = method;
     return WFA_OK;
 }

@@ -134,6 +134,7 @@ struct wfa_grid_s {
     void* timing;         // wfa::KernelTiming (recorded event pairs)
     void* graphs;         // wfa::StepGraphs (captured runs of passes for small grids)
     void* cg;             // wfa::CgWork (work vectors and graph of the implicit solver)
+    int cg_method;        // WFA_CG_CLASSIC / WFA_CG_PIPELINED (wfa_set_cg_method)
 };
 
 namespace wfa {

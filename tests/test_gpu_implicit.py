@@ -264,3 +264,91 @@ def test_implicit_shared_memory_spmv_is_bitwise_equal(kvar):
                     os.environ.pop("WFA_CG_SPMV", None)
             assert out["l1"][0] == out["sm"][0], (mix, shape)
             np.testing.assert_array_equal(out["l1"][1], out["sm"][1], err_msg=f"{mix} {shape}")
+
+
+# ---------------------------------------------------------------------------
+# pipelined (Chronopoulos-Gear) CG: one kernel and one reduction an iteration
+# ---------------------------------------------------------------------------
+def _pgrid(p):
+    g = _grid(p)
+    g.set_cg_method("pipelined")
+    return g
+
+
+@pytest.mark.parametrize("kvar", [False, True])
+@pytest.mark.parametrize("mix", range(len(MIXES)))
+def test_pipelined_matches_oracle(mix, kvar):
+    p = _problem(mix, kvar=kvar, seed=80 + mix)
+    dt = _dt(p)
+    ref, _, _ = _oracle(p, 3, dt)
+    with _pgrid(p) as g:
+        iters, res = g.implicit_step(dt, 3, rtol=1e-7, max_iter=500)
+        T = g.read_field()
+        assert g.steps_done() == 3
+    assert 0 < iters < 1500 and res <= 1e-7
+    assert rel_linf(T, ref) <= TOL
+
+
+@pytest.mark.parametrize("kvar", [False, True])
+@pytest.mark.parametrize("mix", [0, 2, 4, 5])
+def test_pipelined_fixed_iterations_match_oracle_iterates(mix, kvar):
+    # the pipelined iterates are classic CG's in exact arithmetic: compare
+    # them with the oracle's Chronopoulos-Gear and classic iterates
+    p = _problem(mix, kvar=kvar, seed=90 + mix)
+    dt = _dt(p, 3.0)
+    for m in (1, 2, 5, 9):
+        ref, it_ref, _ = _oracle(p, 1, dt, rtol=0.0, max_iter=m)
+        kk = p.k if np.isscalar(p.k) else np.asarray(p.k, dtype=np.float64)
+        ref2, _, _ = oracle.implicit(p.T0, 1, shape=p.shape, h=p.h, k=kk, bc=p.bc, dt=dt, rtol=0.0, max_iter=m,
+                                     method="cgcg")
+        with _pgrid(p) as g:
+            iters, _ = g.implicit_step(dt, 1, rtol=0.0, max_iter=m)
+            T = g.read_field()
+        assert iters == it_ref == m
+        assert rel_linf(T, ref) <= 1e-5, m
+        assert rel_linf(T, ref2) <= 1e-5, m
+
+
+@pytest.mark.parametrize("shape", [(2, 2, 2), (3, 5, 7), (65, 17, 9), (130, 33, 20)])
+def test_pipelined_small_and_ragged_shapes(shape):
+    for mix in (0, 2, 4, 5, 6):
+        if any(kind == DC and shape[f // 2] < 3 for f, (kind, _) in enumerate(MIXES[mix])):
+            continue
+        for kvar in (False, True):
+            p = _problem(mix, shape=shape, kvar=kvar, seed=mix + shape[1])
+            dt = _dt(p, 4.0)
+            ref, _, _ = _oracle(p, 2, dt)
+            with _pgrid(p) as g:
+                g.implicit_step(dt, 2, rtol=1e-7, max_iter=400)
+                T = g.read_field()
+            assert rel_linf(T, ref) <= TOL, (shape, mix, kvar)
+
+
+def test_pipelined_iteration_counts_and_switching():
+    p = _problem(4, kvar=True, seed=95)
+    dt = _dt(p)
+    kk = np.asarray(p.k, dtype=np.float64)
+    _, it_ref, _ = oracle.implicit(p.T0, 1, shape=p.shape, h=p.h, k=kk, bc=p.bc, dt=dt, rtol=1e-4, method="cgcg")
+    with _grid(p) as g:
+        g.set_cg_method("pipelined")
+        it_p, res = g.implicit_step(dt, 1, rtol=1e-4)
+        assert abs(it_p - it_ref) <= 1 and res <= 1e-4
+        g.set_cg_method("classic")   # switching back and forth on one grid
+        g.implicit_step(dt, 1, rtol=1e-7)
+        g.set_cg_method("pipelined")
+        g.implicit_step(dt, 1, rtol=1e-7)
+        T = g.read_field()
+        with pytest.raises(wfa.WfaError) as e:
+            g.set_cg_method(7)
+        assert e.value.code == -1
+    ref, _, _ = _oracle(p, 3, dt)
+    assert rel_linf(T, ref) <= TOL
+
+
+def test_pipelined_conserves_heat():
+    p = _problem(2, shape=(70, 45, 33), kvar=True, seed=96)
+    with _pgrid(p) as g:
+        E0 = g.total_heat()
+        g.implicit_step(_dt(p, 20.0), 5, rtol=1e-7)
+        E1 = g.total_heat()
+    assert abs(E1 - E0) <= 2e-6 * abs(E0)
