@@ -329,10 +329,11 @@ def test_pipelined_iteration_counts_and_switching():
     dt = _dt(p)
     kk = np.asarray(p.k, dtype=np.float64)
     _, it_ref, _ = oracle.implicit(p.T0, 1, shape=p.shape, h=p.h, k=kk, bc=p.bc, dt=dt, rtol=1e-4, method="cgcg")
-    with _grid(p) as g:
-        g.set_cg_method("pipelined")
+    with _pgrid(p) as g:
         it_p, res = g.implicit_step(dt, 1, rtol=1e-4)
         assert abs(it_p - it_ref) <= 1 and res <= 1e-4
+    with _pgrid(p) as g:
+        g.implicit_step(dt, 1, rtol=1e-7)
         g.set_cg_method("classic")   # switching back and forth on one grid
         g.implicit_step(dt, 1, rtol=1e-7)
         g.set_cg_method("pipelined")
