@@ -980,6 +980,48 @@ __global__ void __launch_bounds__(CG_THREADS) cg_update(const __grid_constant__ 
     }
 }
 
+// ---------------------------------------------------------- device loops --
+// The whole call as one graph launch: an outer conditional WHILE node over the
+// time steps, an inner one over the CG iterations of a step. One thread of a
+// control kernel sets each loop's condition; both loops also stop on their
+// own counters (max_iter + 2 iterations, n steps), whatever the solver
+// scalars say, so neither can run on without bound.
+struct CgLoop {
+    long long steps_left;    // time steps still to take
+    long long steps_limit;   // n: the outer loop's own bound
+    long long steps_done;
+    long long total_iters;   // CG iterations of all steps
+    double last_rr, last_bb; // the last step's r.r and b.b
+    unsigned inner_count;    // iterations run in the current step (the inner loop's own bound)
+    unsigned pad;
+};
+static_assert(sizeof(CgLoop) <= 64, "CgLoop is read back into a 64-byte pinned word");
+
+__global__ void cg_ctl_start(CgState* s, CgLoop* L, cudaGraphConditionalHandle inner) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        L->inner_count = 0;
+        cudaGraphSetConditional(inner, s->done ? 0u : 1u);
+    }
+}
+
+__global__ void cg_ctl_iter(CgState* s, CgLoop* L, cudaGraphConditionalHandle inner, int max_iter) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const unsigned k = ++L->inner_count;
+        cudaGraphSetConditional(inner, (!s->done && k < (unsigned)max_iter + 2u) ? 1u : 0u);
+    }
+}
+
+__global__ void cg_ctl_step(CgState* s, CgLoop* L, cudaGraphConditionalHandle outer) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        L->total_iters += s->iter;
+        L->last_rr = s->rr;
+        L->last_bb = s->bb;
+        L->steps_left -= 1;
+        L->steps_done += 1;
+        cudaGraphSetConditional(outer, (L->steps_left > 0 && L->steps_done < L->steps_limit) ? 1u : 0u);
+    }
+}
+
 // ------------------------------------------------------------------ host --
 struct CgWork {
     float* r = nullptr;
@@ -990,6 +1032,12 @@ struct CgWork {
     CgState* h[2] = {nullptr, nullptr};   // pinned read-back slots
     cudaEvent_t ev[2] = {nullptr, nullptr};
     float* extra[3] = {nullptr, nullptr, nullptr};   // pipelined CG: r2, w2, s2 (allocated on first use)
+    CgLoop* loop = nullptr;            // device loop counters
+    cudaGraphExec_t loop_exec = nullptr;   // the whole call as one graph (device loops)
+    CgArgs loop_key;
+    int loop_kvar = -1, loop_method = -1, loop_max_iter = -1;
+    double loop_tol2 = -1.0;
+    bool loop_broken = false;          // building it failed once: host loop from then on
     cudaGraphExec_t exec[CG_NRUN] = {nullptr, nullptr, nullptr, nullptr};
     cudaStream_t cap = nullptr;   // capture stream (the grid's own may be the legacy default stream)
     CgArgs key;        // arguments the graph was captured with
@@ -1012,6 +1060,8 @@ void free_cg(wfa_grid_s* g) {
         pinned_release(w->h[b]);
         dev_free(w->p[b], g->stream);
     }
+    if (w->loop_exec) cudaGraphExecDestroy(w->loop_exec);
+    dev_free(w->loop, g->stream);
     for (float* e : w->extra) dev_free(e, g->stream);
     dev_free(w->r, g->stream);
     dev_free(w->q, g->stream);
@@ -1135,6 +1185,90 @@ static int cg_capture(wfa_grid_s* g, CgWork* w, const CgArgs& base, bool kvar, i
     return WFA_OK;
 }
 
+// Kernel node of `fn` with the given arguments, depending on `dep` (if any).
+static cudaError_t add_kernel(cudaGraph_t gr, cudaGraphNode_t* node, cudaGraphNode_t dep, const void* fn, dim3 grid,
+                              dim3 block, void** args) {
+    cudaKernelNodeParams kp;
+    memset(&kp, 0, sizeof kp);
+    kp.func = const_cast<void*>(fn);
+    kp.gridDim = grid;
+    kp.blockDim = block;
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    return cudaGraphAddKernelNode(node, gr, dep ? &dep : nullptr, dep ? 1 : 0, &kp);
+}
+
+// Conditional WHILE node depending on `dep`; its body graph is returned.
+static cudaError_t add_while(cudaGraph_t gr, cudaGraphNode_t* node, cudaGraphNode_t dep, cudaGraphConditionalHandle h,
+                             cudaGraph_t* body) {
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaError_t e = cudaGraphAddNode(node, gr, dep ? &dep : nullptr, nullptr, dep ? 1 : 0, &np);
+    if (e == cudaSuccess) *body = np.conditional.phGraph_out[0];
+    return e;
+}
+
+// outer WHILE (steps) { cg_init; [pipelined: cg_spmv]; cg_ctl_start;
+//   inner WHILE (iterations) { classic: cg_spmv, cg_update | pipelined: cg_pipe; cg_ctl_iter }; cg_ctl_step }
+static cudaError_t build_loop_graph(wfa_grid_s* g, CgWork* w, const CgArgs& base, bool kvar, int method, double tol2,
+                                    int max_iter, cudaGraphExec_t* out) {
+    cudaGraph_t top = nullptr;
+    cudaError_t e = cudaGraphCreate(&top, 0);
+    if (e != cudaSuccess) return e;
+    cudaGraphConditionalHandle ho = 0, hi = 0;
+    cudaGraph_t outer = nullptr, inner = nullptr;
+    cudaGraphNode_t n_outer = nullptr, n = nullptr, prev = nullptr;
+    CgArgs ia = base, sp = base, up = base;
+    ia.nblk = sp.nblk = w->spmv_grid[0] * w->spmv_grid[1] * w->spmv_grid[2];
+    up.nblk = w->upd_blocks;
+    const dim3 sgrid(w->spmv_grid[0], w->spmv_grid[1], w->spmv_grid[2]), sblock(CG_TX, CG_TY);
+    CgState* st = w->s;
+    CgLoop* L = w->loop;
+    void* a_init[] = {&ia, &tol2, &max_iter};
+    void* a_sp[] = {&sp};
+    void* a_up[] = {&up};
+    void* a_start[] = {&st, &L, &hi};
+    void* a_iter[] = {&st, &L, &hi, &max_iter};
+    void* a_step[] = {&st, &L, &ho};
+    e = cudaGraphConditionalHandleCreate(&ho, top, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) e = add_while(top, &n_outer, nullptr, ho, &outer);
+    if (e == cudaSuccess)
+        e = add_kernel(outer, &n, nullptr, kvar ? (const void*)cg_init<true> : (const void*)cg_init<false>, sgrid,
+                       sblock, a_init);
+    prev = n;
+    if (e == cudaSuccess && method == WFA_CG_PIPELINED) {
+        e = add_kernel(outer, &n, prev, kvar ? (const void*)cg_spmv<true> : (const void*)cg_spmv<false>, sgrid, sblock,
+                       a_sp);
+        prev = n;
+    }
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hi, outer, 0, 0);
+    if (e == cudaSuccess) e = add_kernel(outer, &n, prev, (const void*)cg_ctl_start, dim3(1), dim3(32), a_start);
+    prev = n;
+    cudaGraphNode_t n_inner = nullptr;
+    if (e == cudaSuccess) e = add_while(outer, &n_inner, prev, hi, &inner);
+    if (e == cudaSuccess) {
+        cudaGraphNode_t ip = nullptr;
+        if (method == WFA_CG_PIPELINED) {
+            e = add_kernel(inner, &ip, nullptr, kvar ? (const void*)cg_pipe<true> : (const void*)cg_pipe<false>, sgrid,
+                           sblock, a_sp);
+        } else {
+            e = add_kernel(inner, &ip, nullptr, kvar ? (const void*)cg_spmv<true> : (const void*)cg_spmv<false>, sgrid,
+                           sblock, a_sp);
+            if (e == cudaSuccess)
+                e = add_kernel(inner, &ip, ip, (const void*)cg_update, dim3(w->upd_blocks), dim3(CG_THREADS), a_up);
+        }
+        if (e == cudaSuccess) e = add_kernel(inner, &ip, ip, (const void*)cg_ctl_iter, dim3(1), dim3(32), a_iter);
+    }
+    if (e == cudaSuccess) e = add_kernel(outer, &n, n_inner, (const void*)cg_ctl_step, dim3(1), dim3(32), a_step);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, top, 0);
+    cudaGraphDestroy(top);
+    (void)g;
+    return e;
+}
+
 }  // namespace wfa
 
 using namespace wfa;
@@ -1237,10 +1371,64 @@ int wfa_implicit_step(wfa_grid g, double dt, long long n, double rtol, int max_i
     rc = cg_capture(g, w, base, kvar, method);
     if (rc) return rc;
 
+    const int per_iter = method == WFA_CG_PIPELINED ? 1 : 2;   // kernels an iteration
+
+    // The device-loop graph: every step and iteration without a host round
+    // trip (WFA_CG_LOOP=host keeps the host-checked runs below).
+    const char* loop_pick = getenv("WFA_CG_LOOP");
+    if (!(loop_pick && strcmp(loop_pick, "host") == 0) && !w->loop_broken) {
+        const double tol2 = rtol * rtol;
+        if (!w->loop) {
+            WFA_CUDA(dev_alloc((void**)&w->loop, sizeof(CgLoop), g->stream));
+        }
+        if (!w->loop_exec || w->loop_kvar != (int)kvar || w->loop_method != method || w->loop_max_iter != max_iter ||
+            w->loop_tol2 != tol2 || memcmp(&w->loop_key, &base, sizeof base) != 0) {
+            if (w->loop_exec) cudaGraphExecDestroy(w->loop_exec);
+            w->loop_exec = nullptr;
+            const cudaError_t e = build_loop_graph(g, w, base, kvar, method, tol2, max_iter, &w->loop_exec);
+            if (e != cudaSuccess) {   // no conditional nodes here: host-checked runs from now on
+                cudaGetLastError();
+                w->loop_exec = nullptr;
+                w->loop_broken = true;
+            } else {
+                w->loop_key = base;
+                w->loop_kvar = kvar;
+                w->loop_method = method;
+                w->loop_max_iter = max_iter;
+                w->loop_tol2 = tol2;
+            }
+        }
+        if (w->loop_exec) {
+            CgLoop L0;
+            memset(&L0, 0, sizeof L0);
+            L0.steps_left = n;
+            L0.steps_limit = n;
+            CgLoop* h = reinterpret_cast<CgLoop*>(w->h[0]);
+            memcpy(h, &L0, sizeof L0);
+            WFA_CUDA(cudaMemcpyAsync(w->loop, h, sizeof(CgLoop), cudaMemcpyHostToDevice, g->stream));
+            WFA_CUDA(cudaGraphLaunch(w->loop_exec, g->stream));
+            WFA_CUDA(cudaMemcpyAsync(h, w->loop, sizeof(CgLoop), cudaMemcpyDeviceToHost, g->stream));
+            WFA_CUDA(cudaStreamSynchronize(g->stream));
+            CgLoop Lr;
+            memcpy(&Lr, h, sizeof Lr);
+            if (Lr.steps_done != n) {
+                set_error("wfa_implicit_step: the device loop ran %lld of %lld steps", Lr.steps_done, n);
+                return WFA_ERR_STATE;
+            }
+            const int extra_per_step = method == WFA_CG_PIPELINED ? 4 : 3;   // init, [spmv], start, step
+            g->launches += extra_per_step * n + (long long)(per_iter + 1) * Lr.total_iters;
+            w->prev_iters = n > 0 ? Lr.total_iters / n : 0;
+            g->halo_dirty = true;
+            g->steps_done += n;
+            if (iters) *iters = Lr.total_iters;
+            if (rel_res) *rel_res = Lr.last_bb > 0.0 ? sqrt(Lr.last_rr / Lr.last_bb) : sqrt(Lr.last_rr);
+            return WFA_OK;
+        }
+    }
+
     CgArgs ia = base;
     ia.nblk = w->spmv_grid[0] * w->spmv_grid[1] * w->spmv_grid[2];
     const dim3 sgrid(w->spmv_grid[0], w->spmv_grid[1], w->spmv_grid[2]), sblock(CG_TX, CG_TY);
-    const int per_iter = method == WFA_CG_PIPELINED ? 1 : 2;   // kernels an iteration
     long long total = 0;
     double last_rel = 0.0;
     for (long long step = 0; step < n; ++step) {

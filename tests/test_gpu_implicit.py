@@ -353,3 +353,28 @@ def test_pipelined_conserves_heat():
         g.implicit_step(_dt(p, 20.0), 5, rtol=1e-7)
         E1 = g.total_heat()
     assert abs(E1 - E0) <= 2e-6 * abs(E0)
+
+
+@pytest.mark.parametrize("method", ["classic", "pipelined"])
+def test_device_loop_equals_host_loop(method):
+    # the whole call as one graph (conditional loops over steps and
+    # iterations) runs the same kernels in the same order as the host-checked
+    # runs: identical fields and iteration counts
+    for mix, kvar, shape in [(4, True, (37, 29, 23)), (2, False, (65, 17, 9)), (5, True, (3, 5, 7))]:
+        p = _problem(mix, shape=shape, kvar=kvar, seed=120 + mix)
+        dt = _dt(p, 4.0)
+        out = {}
+        for loop in ("host", "device"):
+            if loop == "host":
+                os.environ["WFA_CG_LOOP"] = "host"
+            try:
+                with _grid(p) as g:
+                    g.set_cg_method(method)
+                    it, res = g.implicit_step(dt, 3, rtol=1e-7, max_iter=300)
+                    it2, _ = g.implicit_step(dt, 2, rtol=1e-6, max_iter=7)   # new parameters: rebuilt
+                    out[loop] = (it, it2, res, g.read_field(), g.steps_done())
+            finally:
+                os.environ.pop("WFA_CG_LOOP", None)
+        assert out["host"][:3] == out["device"][:3], (mix, shape)
+        assert out["device"][4] == 5
+        np.testing.assert_array_equal(out["host"][3], out["device"][3])
