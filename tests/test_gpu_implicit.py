@@ -370,11 +370,18 @@ def test_device_loop_equals_host_loop(method):
             try:
                 with _grid(p) as g:
                     g.set_cg_method(method)
+                    n0 = g.launch_count()
                     it, res = g.implicit_step(dt, 3, rtol=1e-7, max_iter=300)
                     it2, _ = g.implicit_step(dt, 2, rtol=1e-6, max_iter=7)   # new parameters: rebuilt
-                    out[loop] = (it, it2, res, g.read_field(), g.steps_done())
+                    out[loop] = (it, it2, res, g.read_field(), g.steps_done(), g.launch_count() - n0)
             finally:
                 os.environ.pop("WFA_CG_LOOP", None)
         assert out["host"][:3] == out["device"][:3], (mix, shape)
         assert out["device"][4] == 5
         np.testing.assert_array_equal(out["host"][3], out["device"][3])
+        # the device loop ran (its launch count has no converged no-op runs):
+        # per step cg_init, [cg_spmv,] two control kernels; per iteration the
+        # solver kernels and one control kernel
+        its = out["device"][0] + out["device"][1]
+        expect = 5 * 3 + 3 * its if method == "classic" else 5 * 4 + 2 * its
+        assert out["device"][5] == expect, (out["device"][5], expect)
