@@ -1213,7 +1213,7 @@ static cudaError_t add_while(cudaGraph_t gr, cudaGraphNode_t* node, cudaGraphNod
 
 // outer WHILE (steps) { cg_init; [pipelined: cg_spmv]; cg_ctl_start;
 //   inner WHILE (iterations) { classic: cg_spmv, cg_update | pipelined: cg_pipe; cg_ctl_iter }; cg_ctl_step }
-static cudaError_t build_loop_graph(wfa_grid_s* g, CgWork* w, const CgArgs& base, bool kvar, int method, double tol2,
+static cudaError_t build_loop_graph(CgWork* w, const CgArgs& base, bool kvar, int method, double tol2,
                                     int max_iter, cudaGraphExec_t* out) {
     cudaGraph_t top = nullptr;
     cudaError_t e = cudaGraphCreate(&top, 0);
@@ -1265,7 +1265,6 @@ static cudaError_t build_loop_graph(wfa_grid_s* g, CgWork* w, const CgArgs& base
     if (e == cudaSuccess) e = add_kernel(outer, &n, n_inner, (const void*)cg_ctl_step, dim3(1), dim3(32), a_step);
     if (e == cudaSuccess) e = cudaGraphInstantiate(out, top, 0);
     cudaGraphDestroy(top);
-    (void)g;
     return e;
 }
 
@@ -1385,7 +1384,7 @@ int wfa_implicit_step(wfa_grid g, double dt, long long n, double rtol, int max_i
             w->loop_tol2 != tol2 || memcmp(&w->loop_key, &base, sizeof base) != 0) {
             if (w->loop_exec) cudaGraphExecDestroy(w->loop_exec);
             w->loop_exec = nullptr;
-            const cudaError_t e = build_loop_graph(g, w, base, kvar, method, tol2, max_iter, &w->loop_exec);
+            const cudaError_t e = build_loop_graph(w, base, kvar, method, tol2, max_iter, &w->loop_exec);
             if (e != cudaSuccess) {   // no conditional nodes here: host-checked runs from now on
                 cudaGetLastError();
                 w->loop_exec = nullptr;
