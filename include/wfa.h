@@ -181,8 +181,10 @@ int wfa_sum_f32_noalloc(const float* d_x, long long n, double scale, double* d_o
  * iteration, started from T. Uniform k = k0, h = 1 and held layers on every
  * face give Eq. impl_form with omega = k0 dt. A step stops when
  * ||r|| <= rtol ||b|| (the recursively updated residual; rtol = 0 runs
- * max_iter iterations) or after max_iter iterations. Work vectors (four fp32
- * fields) are allocated on the first call and kept with the grid.
+ * max_iter iterations) or after max_iter iterations. A call is one graph
+ * launch (device-side loops over the steps and iterations) and one wait.
+ * Work vectors (four fp32 fields, seven for WFA_CG_PIPELINED) are allocated
+ * on the first call and kept with the grid.
  * *iters (may be NULL) receives the CG iterations of all n steps,
  * *rel_res (may be NULL) the last step's ||r|| / ||b||. Synchronises the
  * stream. Needs fp32 storage and no advection (with u != 0 the system is not

@@ -25,11 +25,16 @@
 // The last block of each kernel to finish (an atomic ticket, no waiting) sums
 // the partials in a fixed order and computes alpha (resp. beta and the
 // convergence test) on the device, so no host round trip sits between
-// iterations: runs of iterations are captured once as a CUDA graph and
-// replayed, the host reading the convergence flag between runs, one run ahead.
+// iterations: a whole call is one graph launch whose conditional WHILE nodes
+// loop over the time steps and the iterations (device loops, below); where
+// those cannot be built, captured runs of iterations are replayed with the
+// host reading the convergence flag between runs, one run ahead.
 // Periodic axes read the neighbour across the boundary from a twin copy
 // that every writer of a boundary cell also stores one cell beyond the
-// opposite face; non-periodic boundary faces are taken by select.
+// opposite face; non-periodic boundary faces take a ghost value that makes
+// the interior expression exact, only in warps that hold a boundary cell.
+// cg_pipe is the pipelined alternative (Chronopoulos and Gear): one kernel
+// and one reduction an iteration.
 // Inner products: fp32 products summed per plane, a compensated fp32 sum over
 // a thread's planes, fp64 above that (the block, the fixed-order sum over
 // blocks); the GPU's fp64 rate is low, so no fp64 arithmetic sits in the
