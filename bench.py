@@ -482,9 +482,9 @@ def implicit_bench(args, rank, world, dist):
                              "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per CG iteration",
                              "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                              "bytes_per_cell_per_iteration": bpc,
-                             "scope": "every kernel of the timed steps (cg_init, cg_spmv, cg_update; pipelined: "
-                                      "cg_init, cg_spmv once a step, cg_pipe) and the host's flag checks between "
-                                      "graph runs"},
+                             "scope": "the whole solve: every kernel of the timed steps (cg_init, cg_spmv, "
+                                      "cg_update and the loop-control kernels; pipelined: cg_init, cg_spmv once a "
+                                      "step, cg_pipe), one graph launch a call"},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clocks}
         print(json.dumps(line), flush=True)
 
