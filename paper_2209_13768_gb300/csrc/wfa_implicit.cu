@@ -323,7 +323,6 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_init(co
     const int gx = blockIdx.x * 64 + 4 * tx, gy = blockIdx.y * CG_TY + ty;
     const int z0 = blockIdx.z * a.zchunk, z1 = min(z0 + a.zchunk, nz);
     const bool perx = c.periodic[0], pery = c.periodic[1], perz = c.periodic[2];
-    const unsigned act = __ballot_sync(0xffffffffu, gx < nx && gy < ny);   // lanes with cells, as in cg_spmv
     KahanF rr, bb;
     if (gx < nx && gy < ny) {
         const long long sy = c.sy, sz = c.sz;
@@ -346,17 +345,14 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_init(co
             ld4(xv + o + sz, tp);
             ld4(xv + o - sy, ym);
             ld4(xv + o + sy, yp);
-            const bool from_m = tx > 0, from_p = tx < CG_TX - 1 && gx + 4 < nx;   // x neighbours from lanes
-            const float sm_ = __shfl_up_sync(act, tc[3], 1, CG_TX), sp_ = __shfl_down_sync(act, tc[0], 1, CG_TX);
-            const float xm = from_m ? sm_ : __ldg(xv + o - 1), xp = from_p ? sp_ : __ldg(xv + o + 4);
+            const float xm = __ldg(xv + o - 1), xp = __ldg(xv + o + 4);
             float kp[4], kym[4], kyp[4], kxm = 0.0f, kxp = 0.0f;
             if (KVAR) {
                 ld4(rk + o + sz, kp);
                 ld4(rk + o - sy, kym);
                 ld4(rk + o + sy, kyp);
-                const float km_ = __shfl_up_sync(act, kc[3], 1, CG_TX), kp_ = __shfl_down_sync(act, kc[0], 1, CG_TX);
-                kxm = from_m ? km_ : __ldg(rk + o - 1);
-                kxp = from_p ? kp_ : __ldg(rk + o + 4);
+                kxm = __ldg(rk + o - 1);
+                kxp = __ldg(rk + o + 4);
             }
             float rv[4];
             float sr = 0.0f, sb = 0.0f;
@@ -508,10 +504,6 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv(co
     const int gx = blockIdx.x * 64 + 4 * tx, gy = blockIdx.y * CG_TY + ty;
     const int z0 = blockIdx.z * a.zchunk, z1 = min(z0 + a.zchunk, nz);
     const bool perx = c.periodic[0], pery = c.periodic[1], perz = c.periodic[2];
-    // lanes with cells (all of the warp is converged here): a row of 16
-    // threads holds 64 consecutive cells, so a thread's x neighbours are the
-    // next and previous lanes' own cells
-    const unsigned act = __ballot_sync(0xffffffffu, gx < nx && gy < ny);
     KahanF dot;
     if (gx < nx && gy < ny) {
         const long long sy = c.sy, sz = c.sz;
@@ -535,19 +527,14 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv(co
             pnew4(P, o + sz, pp);
             pnew4(P, o - sy, ym);
             pnew4(P, o + sy, yp);
-            // x neighbours from the adjacent lanes; from memory at the
-            // block's x ends and where the next lane has no cells
-            const bool from_m = tx > 0, from_p = tx < CG_TX - 1 && gx + 4 < nx;
-            const float sm_ = __shfl_up_sync(act, pc[3], 1, CG_TX), sp_ = __shfl_down_sync(act, pc[0], 1, CG_TX);
-            const float xm = from_m ? sm_ : pnew1(P, o - 1), xp = from_p ? sp_ : pnew1(P, o + 4);
+            const float xm = pnew1(P, o - 1), xp = pnew1(P, o + 4);
             float kp[4], kym[4], kyp[4], kxm = 0.0f, kxp = 0.0f;
             if (KVAR) {
                 ld4(rk + o + sz, kp);
                 ld4(rk + o - sy, kym);
                 ld4(rk + o + sy, kyp);
-                const float km_ = __shfl_up_sync(act, kc[3], 1, CG_TX), kp_ = __shfl_down_sync(act, kc[0], 1, CG_TX);
-                kxm = from_m ? km_ : __ldg(rk + o - 1);
-                kxp = from_p ? kp_ : __ldg(rk + o + 4);
+                kxm = __ldg(rk + o - 1);
+                kxp = __ldg(rk + o + 4);
             }
             float q[4];
             const bool fast = inner_xy && (perz || (z > 0 && z < nz - 1));
@@ -829,7 +816,6 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, PipeOcc<KVAR>::blocks) cg_pipe(
     const int gx = blockIdx.x * 64 + 4 * tx, gy = blockIdx.y * CG_TY + ty;
     const int z0 = blockIdx.z * a.zchunk, z1 = min(z0 + a.zchunk, nz);
     const bool perx = c.periodic[0], pery = c.periodic[1], perz = c.periodic[2];
-    const unsigned act = __ballot_sync(0xffffffffu, gx < nx && gy < ny);   // lanes with cells, as in cg_spmv
     KahanF gam, del;
     if (gx < nx && gy < ny) {
         const long long sy = c.sy, sz = c.sz;
@@ -854,17 +840,14 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, PipeOcc<KVAR>::blocks) cg_pipe(
             rnew4(R, o + sz, rp, sp_, rvp);
             rnew4(R, o - sy, ym, t4, t5);
             rnew4(R, o + sy, yp, t4, t5);
-            const bool from_m = tx > 0, from_p = tx < CG_TX - 1 && gx + 4 < nx;   // x neighbours from lanes
-            const float sm_ = __shfl_up_sync(act, rc[3], 1, CG_TX), sp2 = __shfl_down_sync(act, rc[0], 1, CG_TX);
-            const float xm = from_m ? sm_ : rnew1(R, o - 1), xp = from_p ? sp2 : rnew1(R, o + 4);
+            const float xm = rnew1(R, o - 1), xp = rnew1(R, o + 4);
             float kp[4], kym[4], kyp[4], kxm = 0.0f, kxp = 0.0f;
             if (KVAR) {
                 ld4(rk + o + sz, kp);
                 ld4(rk + o - sy, kym);
                 ld4(rk + o + sy, kyp);
-                const float km_ = __shfl_up_sync(act, kc[3], 1, CG_TX), kp_ = __shfl_down_sync(act, kc[0], 1, CG_TX);
-                kxm = from_m ? km_ : __ldg(rk + o - 1);
-                kxp = from_p ? kp_ : __ldg(rk + o + 4);
+                kxm = __ldg(rk + o - 1);
+                kxp = __ldg(rk + o + 4);
             }
             float wn[4];
             const bool fast = inner_xy && (perz || (z > 0 && z < nz - 1));
@@ -1210,7 +1193,8 @@ static int cg_capture(wfa_grid_s* g, CgWork* w, const CgArgs& base, bool kvar, i
 // Kernel node of `fn` with the given arguments, depending on `dep` (if any).
 static cudaError_t add_kernel(cudaGraph_t gr, cudaGraphNode_t* node, cudaGraphNode_t dep, const void* fn, dim3 grid,
                               dim3 block, void** args) {
-    cudaKernelNodeParams kp = {};
+    cudaKernelNodeParams kp;
+    memset(&kp, 0, sizeof kp);
     kp.func = const_cast<void*>(fn);
     kp.gridDim = grid;
     kp.blockDim = block;
