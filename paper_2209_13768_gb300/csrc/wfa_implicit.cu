@@ -1193,8 +1193,7 @@ static int cg_capture(wfa_grid_s* g, CgWork* w, const CgArgs& base, bool kvar, i
 // Kernel node of `fn` with the given arguments, depending on `dep` (if any).
 static cudaError_t add_kernel(cudaGraph_t gr, cudaGraphNode_t* node, cudaGraphNode_t dep, const void* fn, dim3 grid,
                               dim3 block, void** args) {
-    cudaKernelNodeParams kp;
-    memset(&kp, 0, sizeof kp);
+    cudaKernelNodeParams kp = {};
     kp.func = const_cast<void*>(fn);
     kp.gridDim = grid;
     kp.blockDim = block;
