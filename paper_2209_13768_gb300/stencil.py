@@ -147,6 +147,11 @@ def _check_name(name):
         raise ValueError(f"bad name {name!r}: an identifier not starting with '_'")
 
 
+def _wname(field, dz):
+    """Register of a z window: field value at plane z + dz of the own column."""
+    return f"zw_{field}_{'m' if dz < 0 else 'p'}{abs(dz)}"
+
+
 def _walk(e):
     yield e
     for c in e.children():
@@ -184,6 +189,15 @@ class Program:
             raise ValueError("a field is updated twice")
         self.params = sorted(params)
         self.radius = radius   # 0: a pointwise update of every cell
+        # z windows: a field read at several dz of the cell's own column keeps
+        # those values in registers while the thread marches z (one new load
+        # a plane instead of one a reference)
+        col = {}
+        for _, e in self.updates:
+            for n in _walk(e):
+                if isinstance(n, Ref) and n.offset[0] == 0 and n.offset[1] == 0:
+                    col.setdefault(n.field.name, set()).add(n.offset[2])
+        self.windows = {f: (min(d), max(d)) for f, d in col.items() if len(d) >= 2}
         self.source = self._source()
         self.key = hashlib.sha256(self.source.encode()).hexdigest()[:16]
 
@@ -194,6 +208,8 @@ class Program:
             return f"p_{e.name}"
         if isinstance(e, Ref):
             dx, dy, dz = e.offset
+            if dx == 0 and dy == 0 and e.field.name in getattr(self, "windows", {}):
+                return _wname(e.field.name, dz)
             return f"__ldg(in_{e.field.name} + o + ({dx}) + ({dy}) * sy + ({dz}) * sz)"
         if isinstance(e, Neg):
             return f"(-{self._expr(e.a)})"
@@ -213,6 +229,13 @@ class Program:
         call_p = ", ".join(f"params[{i}]" for i in range(len(self.params)))
         call = ", ".join(x for x in (call_in, call_out, call_p) if x)
         R = self.radius
+        pre, top, shift = [], [], []
+        for f, (lo, hi) in sorted(self.windows.items()):
+            for dz in range(lo, hi):
+                pre.append(f"    float {_wname(f, dz)} = __ldg(in_{f} + o0 + ({dz}) * sz);")
+            top.append(f"        const float {_wname(f, hi)} = __ldg(in_{f} + o + ({hi}) * sz);")
+            shift.extend(f"        {_wname(f, dz)} = {_wname(f, dz + 1)};" for dz in range(lo, hi))
+        pre_s, top_s, shift_s = "\n".join(pre), "\n".join(top), "\n".join(shift)
         return f"""// generated by paper_2209_13768_gb300.stencil: one explicit step, every update fused
 #include <cuda_runtime.h>
 // one thread per (x, y) column of interior cells and z chunk, marching z;
@@ -224,9 +247,13 @@ __global__ void __launch_bounds__(256) step_kernel({sig}, int nx, int ny, int nz
     const int z0 = {R} + blockIdx.z * zchunk;
     const int z1 = min(z0 + zchunk, nz - {R});
     const long long sy = nx, sz = (long long)nx * ny;
+    const long long o0 = x + y * sy + z0 * sz;
+{pre_s}
     for (int z = z0; z < z1; ++z) {{
         const long long o = x + y * sy + z * sz;
+{top_s}
 {body}
+{shift_s}
     }}
 }}
 

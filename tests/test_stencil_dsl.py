@@ -22,7 +22,9 @@ def test_program_analysis():
     q = S.Program({T: T + K[0, 0, 2] * (T[0, 0, 1] - T)})
     assert q.fields == ["K", "T"] and q.written == ["T"] and q.params == [] and q.radius == 2
     assert S.Program({T: 2 * T}).radius == 0
-    assert "__ldg(in_T + o + (0) + (0) * sy + (-1) * sz)" in p.source
+    # the own column's z neighbours ride in a register window; x / y ones load
+    assert p.windows == {"T": (-1, 1)} and q.windows == {"T": (0, 1)}
+    assert "zw_T_m1 = zw_T_p0;" in p.source and "__ldg(in_T + o + (1) + (0) * sy + (0) * sz)" in p.source
     assert p.key != q.key
 
 
