@@ -60,6 +60,11 @@ def test_argument_errors_need_no_gpu(libpath):
     assert L.wfa_create_grid(4, 4, 4, 1.0, 1.0, 1.0, 7, None, ctypes.byref(out)) == -1
     assert L.wfa_step(None, 1) == -1
     assert L.wfa_destroy_grid(None) == 0
+    it, res = ctypes.c_longlong(), ctypes.c_double()
+    assert L.wfa_implicit_step(None, 0.1, 1, 1e-6, 10, ctypes.byref(it), ctypes.byref(res)) == -1
+    assert L.wfa_set_cg_method(None, 0) == -1
+    assert L.wfa_inject_alloc_failure(-1) == 0   # disarm: nothing to inject
+    assert L.wfa_batch_run(None, None, -1) == -1
 
 
 def test_product_path_does_not_use_the_oracle():
