@@ -146,3 +146,23 @@ def test_run_argument_errors():
     with pytest.raises(ValueError):
         step.run({"T": t}, steps=-1, w=0.1)
     step.run({"T": t}, steps=0, w=0.1)            # no-op
+
+
+@pytest.mark.parametrize("case", ["pointwise", "coupled", "radius3"])
+def test_more_programs_cross_compile(case):
+    # code generation for a pointwise update (radius 0), two coupled fields
+    # with a read-only third, and a radius-3 stencil with every operator
+    A, B, K = S.Field("A"), S.Field("B"), S.Field("K")
+    a, b = S.Param("a"), S.Param("b")
+    if case == "pointwise":
+        prog = S.Program({A: a * A * A - b / (1.0 + A)})
+        assert prog.radius == 0 and prog.windows == {}
+    elif case == "coupled":
+        prog = S.Program({A: A + a * K * (B[1, 0, 0] - A), B: B - a * K[0, -1, 0] * (A[0, 0, 1] - B)})
+        assert prog.written == ["A", "B"] and prog.fields == ["A", "B", "K"] and prog.params == ["a"]
+    else:
+        prog = S.Program({A: A + a * (A[3, 0, 0] - A[-3, 0, 0]) / 6.0 - (-A[0, 0, -3] + A[0, 0, 3]) * b
+                          + A[0, 2, 1] * A[0, -2, -1]})
+        assert prog.radius == 3 and prog.windows == {"A": (-3, 3)}
+        assert "zw_A_m3" in prog.source and "zw_A_p3" in prog.source
+    assert S.build(prog).endswith(".so")
