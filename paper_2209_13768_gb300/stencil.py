@@ -29,6 +29,7 @@ from __future__ import annotations
 import ctypes
 import hashlib
 import os
+import platform
 import shutil
 import subprocess
 import threading
@@ -281,7 +282,7 @@ def build(program: Program) -> str:
     """Compile the program's kernel into _dsl_cache/ (once per source)."""
     with _lock:
         os.makedirs(CACHE, exist_ok=True)
-        so = os.path.join(CACHE, f"stencil_{program.key}.so")
+        so = os.path.join(CACHE, f"stencil_{program.key}_{platform.machine()}.so")   # per host architecture
         if os.path.exists(so):
             return so
         src = os.path.join(CACHE, f"stencil_{program.key}.cu")
