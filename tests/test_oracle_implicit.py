@@ -9,6 +9,8 @@ cells, conservation, the maximum principle, and two properties of CG itself:
 a single eigenmode converges in one iteration, and a system with m distinct
 eigenvalues in at most m.
 """
+import os
+
 import numpy as np
 import pytest
 import scipy.ndimage as ndi
@@ -218,3 +220,19 @@ def test_cgcg_matches_dense_solve(mix):
                                 method="cgcg")
     assert res <= 1e-14
     np.testing.assert_allclose(T, ref, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("method", ["classic", "cgcg"])
+def test_implicit_thread_count_does_not_change_results(method):
+    # the face passes run in parallel over lines (no shared accumulator) and
+    # the inner products are sequential: any thread count, the same bits
+    rng = np.random.default_rng(17)
+    shape = (23, 17, 11)
+    k = np.exp(0.5 * rng.standard_normal(shape[::-1]))
+    bc = _bc(BC_MIXES[4], list(rng.uniform(0, 1, 6)))
+    T0 = rng.uniform(0, 1, shape[::-1])
+    a = oracle.implicit(T0, 2, shape=shape, k=k, bc=bc, dt=1.5, rtol=1e-10, threads=1, method=method)
+    b = oracle.implicit(T0, 2, shape=shape, k=k, bc=bc, dt=1.5, rtol=1e-10, threads=4, method=method)
+    oracle.implicit(T0, 0, shape=shape, k=k, bc=bc, dt=1.5, threads=os.cpu_count() or 1)   # restore
+    assert a[1] == b[1]
+    np.testing.assert_array_equal(a[0], b[0])

@@ -36,6 +36,8 @@ MUTANTS = {
     "CG residual update sign": ("r[c] -= alpha * q[c];", "r[c] += alpha * q[c];"),
     "Dirichlet values left in the linear part": ("for (int f = 0; f < 6; ++f) p0.value[f] = 0.0;\n#ifdef _OPENMP\n    if (nthreads > 0) omp_set_num_threads(nthreads);\n#else\n    (void)nthreads;\n#endif\n    const int64_t N = n[0] * n[1] * n[2];\n    unsigned char* held = held_mask(&p);\n    double* buf = (double*)malloc((size_t)N * 6",
                                                  "(void)0;\n#ifdef _OPENMP\n    if (nthreads > 0) omp_set_num_threads(nthreads);\n#else\n    (void)nthreads;\n#endif\n    const int64_t N = n[0] * n[1] * n[2];\n    unsigned char* held = held_mask(&p);\n    double* buf = (double*)malloc((size_t)N * 6"),
+    "implicit held cells overwritten": ("if (!held[c]) T[c] = x[c];\n        total += it;\n        last = bb > 0.0 ? sqrt(rr / bb)",
+                                        "T[c] = x[c];\n        total += it;\n        last = bb > 0.0 ? sqrt(rr / bb)"),
     "CG-CG step length without its beta correction": ("const double den = delta - beta * g1 / alpha;",
                                                       "const double den = delta;"),
     "CG-CG A p recurrence without beta": ("sv[c] = w[c] + beta * sv[c];", "sv[c] = w[c];"),
