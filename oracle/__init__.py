@@ -69,6 +69,9 @@ def _bind(path):
     lib.wfa_oracle_total_heat.restype = ctypes.c_double
     lib.wfa_oracle_round.argtypes = [ctypes.c_double, ctypes.c_int]
     lib.wfa_oracle_round.restype = ctypes.c_double
+    if hasattr(lib, "wfa_oracle_round_array"):
+        lib.wfa_oracle_round_array.argtypes = [dp, ctypes.c_int64, ctypes.c_int]
+        lib.wfa_oracle_round_array.restype = None
     if hasattr(lib, "wfa_oracle_implicit"):
         lib.wfa_oracle_implicit.argtypes = [i64p, dp, ctypes.c_double, dp, ip, dp, ctypes.c_double, dp,
                                             ctypes.c_int64, ctypes.c_double, ctypes.c_int64, i64p, dp, ctypes.c_int]
@@ -177,5 +180,6 @@ def total_heat(T, h=(1.0, 1.0, 1.0)):
 
 def round_to(x, mode):
     lib = _load()
-    f = np.vectorize(lambda v: lib.wfa_oracle_round(float(v), ROUND[mode]))
-    return f(np.asarray(x, dtype=np.float64))
+    a = np.array(x, dtype=np.float64, order="C", copy=True)
+    lib.wfa_oracle_round_array(_ptr(a), a.size, ROUND[mode])
+    return a

@@ -95,6 +95,11 @@ double wfa_oracle_round(double v, int mode) {
     return v;
 }
 
+/* wfa_oracle_round applied to n values in place. */
+void wfa_oracle_round_array(double* x, int64_t n, int mode) {
+    for (int64_t i = 0; i < n; ++i) x[i] = wfa_oracle_round(x[i], mode);
+}
+
 /* Face-flux accumulation along axis a (one pass). */
 static void face_pass(const prob_t* p, const double* T, double* acc, int a) {
     const int64_t nx = p->n[0], ny = p->n[1];
