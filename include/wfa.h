@@ -75,7 +75,10 @@ enum wfa_face { WFA_XLO = 0, WFA_XHI = 1, WFA_YLO = 2, WFA_YHI = 3, WFA_ZLO = 4,
 int wfa_create_grid(int nx, int ny, int nz, double hx, double hy, double hz, int storage,
                     void* cuda_stream, wfa_grid* out);
 
-/* Free the handle and its device memory (synchronises its stream). NULL is a no-op. */
+/* Free the handle and its device memory (synchronises its stream). NULL is a
+ * no-op. The handle is this library's counterpart of a WSE_Array (Sec. 3,
+ * Example Code): the field and its coefficients resident on the device for
+ * the whole solve, released here. */
 int wfa_destroy_grid(wfa_grid g);
 
 /* Copy a dense host field (nx*ny*nz floats) in (Sec. 2.1: T_init -> WSE_Array).
@@ -123,7 +126,22 @@ int wfa_set_dt(wfa_grid g, double dt);
  * per-cell expression, so fields are bit-identical. */
 int wfa_set_tuning(wfa_grid g, int depth, int variant);
 
-/* Time the compiled kernel configurations (the column-march kernels 3, 4, 5;
+/* Planes per z chunk of the column-march kernels (variants 3 and 5): each
+ * block of those kernels marches one chunk of the z extent, neighbouring
+ * chunks in opposite directions. planes = 0 (the default) lets the tuned or
+ * automatic choice stand. A tuning aid with no counterpart in the paper:
+ * results do not depend on it (fields are bit-identical).
+ * Errors: WFA_ERR_ARG for a NULL grid or planes < 0. */
+int wfa_set_zchunk(wfa_grid g, int planes);
+
+/* The kernel configuration the next wfa_step of this grid uses (after
+ * wfa_set_tuning, wfa_set_zchunk and wfa_autotune): fused depth, variant
+ * (as in wfa_set_tuning) and planes per z chunk (0 = automatic). Any output
+ * pointer may be NULL. Errors: WFA_ERR_ARG for a NULL grid. */
+int wfa_get_tuning(wfa_grid g, int* depth, int* variant, int* zchunk);
+
+/* Time the compiled kernel configurations (the column-march kernels 3, 4, 5,
+ * kernel 3 also with z chunks of 32, 64, 128 planes and of half the z extent;
  * the tiled TMA kernel at depths 1..8 and two tile shapes) on this grid and
  * use the fastest from now
  * on. The trials run on a scratch copy of the field: the field and the step
@@ -136,15 +154,23 @@ int wfa_set_tuning(wfa_grid g, int depth, int variant);
  * runs. *depth / *variant (may be NULL) receive the choice. */
 int wfa_autotune(wfa_grid g, int* depth, int* variant);
 
-/* Advance n >= 0 time steps (asynchronous on the grid's stream).
+/* Advance n >= 0 time steps (asynchronous on the grid's stream): n
+ * applications of Eq. expl_form (Sec. 1.1.1, the explicit time step, T^n ->
+ * T^{n+1} for every cell from the values of step n), in the face-flux form
+ * given at the top of this file. The paper's fused kernel runs one step per
+ * RPC (Sec. 3, Example Code); here a step is one pass of a kernel over the
+ * grid, or several steps per pass with temporal blocking.
  * Errors: WFA_ERR_STATE before the field, coefficients and dt are set,
  * WFA_ERR_BC for an unpaired periodic face, WFA_ERR_CUDA. */
 int wfa_step(wfa_grid g, long long n);
 
-/* Number of steps taken since the last wfa_set_field. */
+/* Number of steps taken since the last wfa_set_field: the time index n of
+ * T^n in Eq. expl_form, counted from the field that was set. */
 int wfa_steps_done(wfa_grid g, long long* n);
 
-/* Copy the field out as dense fp32 (nx*ny*nz floats). Synchronises the stream. */
+/* Copy the field out as dense fp32 (nx*ny*nz floats). Synchronises the
+ * stream. The counterpart of reading a WSE_Array back into a NumPy array
+ * (Sec. 3, Example Code), where the WFA's validation mode compares results. */
 int wfa_read_field(wfa_grid g, float* host_dense);
 
 /* Total heat E = sum_C T_C hx hy hz, summed on the device in fp64 in a fixed
@@ -233,7 +259,9 @@ int wfa_grid_buffer_bytes(wfa_grid g, size_t* field_bytes, size_t* k_bytes);
  * Synchronises the stream. Errors: WFA_ERR_ARG, WFA_ERR_CUDA. */
 int wfa_grid_attach_buffers(wfa_grid g, void* d_Ta, void* d_Tb, float* d_k, float* d_r);
 
-/* Wait for the grid's queued work; reports a device-side error. */
+/* Wait for the grid's queued work; reports a device-side error. The host
+ * side of Sec. 2's control flow: the program runs on the device without host
+ * interaction until the host collects the result. */
 int wfa_sync(wfa_grid g);
 
 /* Kernel timing, a profiling aid with no counterpart in the paper.
@@ -255,10 +283,13 @@ int wfa_launch_count(wfa_grid g, long long* n);
 
 /* Synchronise the stream, then give the summed duration in milliseconds and
  * the number of the sampled kernel launches since the last call (0 and 0 when
- * timing is off), and start counting afresh. */
+ * timing is off), and start counting afresh. A profiling aid with no
+ * counterpart in the paper (it feeds the bandwidth model of Sec. 4.1.3,
+ * Eqs. A_eff and t_it_min, with measured kernel times). */
 int wfa_kernel_time(wfa_grid g, double* ms, long long* launches);
 
-/* Message of the last failed call on this thread ("" if none). */
+/* Message of the last failed call on this thread ("" if none). Error
+ * reporting of this C ABI; no counterpart in the paper. */
 const char* wfa_last_error(void);
 
 /* Host-side fault injection for testing the out-of-memory paths, with no
@@ -294,6 +325,14 @@ int wfa_inject_alloc_failure(int n);
 int wfa_batch_run(wfa_grid* gs, const long long* steps, int count);
 
 /* ------------------------------------------------------------- serving -- */
+/* Serving has no counterpart call in the paper. It applies Sec. 4.1.2's
+ * point about small workloads per processor (the explicit step keeps its rate
+ * down to about 50 cells per WSE tile, where a distributed code needs
+ * thousands) to a stream of independent small solves: many grids resident on
+ * the device at once, advanced together by the batched sweep. A request
+ * carries its own inputs (not a wfa_grid) because the server owns the device
+ * memory of resident requests: it allocates a grid only when the request fits
+ * the HBM budget, and frees it when the result is back on the host. */
 
 typedef struct wfa_server_s* wfa_server;
 
@@ -341,19 +380,28 @@ typedef struct {
 int wfa_server_create(size_t hbm_budget_bytes, int max_resident, long long quantum,
                       wfa_server* out);
 
-/* Queue a request; *ticket identifies it. WFA_ERR_BUDGET if it can never fit. */
+/* Queue a request (one transient solve: Eq. expl_form for r->steps steps on
+ * its own grid; see the serving note above); *ticket identifies it.
+ * WFA_ERR_BUDGET if it can never fit. */
 int wfa_server_submit(wfa_server s, const wfa_request* r, long long* ticket);
 
 /* *done = 1 once out_host holds the result (0 while queued or running;
- * -1 if the request failed, with the reason in wfa_last_error()). */
+ * -1 if the request failed, with the reason in wfa_last_error()). Serving
+ * (see the note above); no counterpart call in the paper. */
 int wfa_server_poll(wfa_server s, long long ticket, int* done);
 
-/* Block until the ticket is done or timeout_s passes (WFA_ERR_TIMEOUT). */
+/* Block until the ticket is done or timeout_s passes (WFA_ERR_TIMEOUT).
+ * Serving (see the note above); no counterpart call in the paper. */
 int wfa_server_wait(wfa_server s, long long ticket, double timeout_s);
 
+/* Counters and latency percentiles of the server so far (see
+ * wfa_server_stats). Serving (see the note above); the iteration-rate and
+ * latency figures the paper reports for single solves (Sec. 4) become
+ * throughput and p50 / p99 latency of a request stream here. */
 int wfa_server_stats_get(wfa_server s, wfa_server_stats* st);
 
-/* Stop the scheduler (finishing resident work first) and free everything. */
+/* Stop the scheduler (finishing resident work first) and free everything.
+ * Serving (see the note above); no counterpart call in the paper. */
 int wfa_server_destroy(wfa_server s);
 
 #ifdef __cplusplus

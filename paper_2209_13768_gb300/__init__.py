@@ -60,6 +60,8 @@ SIGNATURES = {
     "wfa_stability_dt": (_i, [_vp, _dp]),
     "wfa_set_dt": (_i, [_vp, _d]),
     "wfa_set_tuning": (_i, [_vp, _i, _i]),
+    "wfa_set_zchunk": (_i, [_vp, _i]),
+    "wfa_get_tuning": (_i, [_vp, _ip, _ip, _ip]),
     "wfa_autotune": (_i, [_vp, _ip, _ip]),
     "wfa_step": (_i, [_vp, _ll]),
     "wfa_steps_done": (_i, [_vp, _llp]),
@@ -202,6 +204,16 @@ class Grid:
 
     def set_tuning(self, depth=0, variant=0):
         check(lib().wfa_set_tuning(self.handle, int(depth), int(variant)), "wfa_set_tuning")
+
+    def set_zchunk(self, planes=0):
+        """Planes per z chunk of the column-march kernels (0: automatic; see wfa_set_zchunk)."""
+        check(lib().wfa_set_zchunk(self.handle, int(planes)), "wfa_set_zchunk")
+
+    def tuning(self):
+        """(depth, variant, z-chunk planes) the next step uses (see wfa_get_tuning)."""
+        d, v, z = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(lib().wfa_get_tuning(self.handle, ctypes.byref(d), ctypes.byref(v), ctypes.byref(z)), "wfa_get_tuning")
+        return d.value, v.value, z.value
 
     def autotune(self):
         """Pick the fastest kernel configuration for this grid; returns (depth, variant)."""

@@ -1102,6 +1102,13 @@ int wfa_set_tuning(wfa_grid g, int depth, int variant) {
     return WFA_OK;
 }
 
+int wfa_set_zchunk(wfa_grid g, int planes) {
+    if (!g) return fail(WFA_ERR_ARG, "NULL grid");
+    if (planes < 0) return fail(WFA_ERR_ARG, "planes must be >= 0");
+    g->force_zchunk = planes;
+    return WFA_OK;
+}
+
 int wfa_step(wfa_grid g, long long n) {
     NvtxRange nvtx_("wfa_step");
     if (!g) return fail(WFA_ERR_ARG, "NULL grid");

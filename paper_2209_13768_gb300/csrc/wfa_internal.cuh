@@ -118,6 +118,7 @@ struct wfa_grid_s {
     bool k_halo_dirty;    // k twins / ghost layers and 1/k must be rebuilt before use
     long long steps_done;
     int force_depth, force_variant;   // wfa_set_tuning (0 = automatic)
+    int force_zchunk;                 // wfa_set_zchunk: planes per z chunk of the column kernels (0 = automatic)
     double* d_partials;   // fp64 reduction partials (scratch)
     double* h_result;     // pinned host word for reduction results
     float* d_stage;       // dense fp32 staging buffer for set/read (scratch)
@@ -125,6 +126,7 @@ struct wfa_grid_s {
     int* h_status;        // pinned host copy
     void* tmaps;          // wfa::TmapCache (TMA descriptors for the current tile box)
     int tuned_depth, tuned_variant;   // configuration picked by the autotuner (0 = none)
+    int tuned_zchunk;                 // its z chunk length (0 = automatic)
     bool own_T, own_k;    // the library allocated T[] / k and r (else the caller attached them)
     float* ext_k;         // caller buffers for k and 1/k, used when per-cell k is set
     float* ext_r;

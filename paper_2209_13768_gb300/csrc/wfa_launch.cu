@@ -160,6 +160,7 @@ static int num_sms() {
 // and depth.
 struct Choice {
     int variant, depth;
+    int zc = 0;   // column kernels: planes per z chunk (0 = automatic)
 };
 
 // Autotuned choices, per size class, shared by every grid of the process and
@@ -204,8 +205,11 @@ static void tune_load_locked() {
     FILE* f = fopen(path, "r");
     if (!f) return;
     char key[128];
-    int v, d;
-    while (fscanf(f, "%127s %d %d", key, &v, &d) == 3) g_tune[key] = Choice{v, d};
+    char line[256];
+    while (fgets(line, sizeof line, f)) {   // "key variant depth [zchunk]"
+        int v, d, z = 0;
+        if (sscanf(line, "%127s %d %d %d", key, &v, &d, &z) >= 3) g_tune[key] = Choice{v, d, z};
+    }
     fclose(f);
 }
 
@@ -214,14 +218,15 @@ static void tune_save_locked() {
     if (!path) return;
     FILE* f = fopen(path, "w");
     if (!f) return;
-    for (const auto& kv : g_tune) fprintf(f, "%s %d %d\n", kv.first.c_str(), kv.second.variant, kv.second.depth);
+    for (const auto& kv : g_tune)
+        fprintf(f, "%s %d %d %d\n", kv.first.c_str(), kv.second.variant, kv.second.depth, kv.second.zc);
     fclose(f);
 }
 
 static Choice choose(const wfa_grid_s* g) {
     Choice ch{COL_VARIANT, 1};   // untuned default: the column-march kernel, one step per pass
     if (g->tuned_variant) {
-        ch = Choice{g->tuned_variant, g->tuned_depth};
+        ch = Choice{g->tuned_variant, g->tuned_depth, g->tuned_zchunk};
     } else {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         tune_load_locked();
@@ -233,6 +238,7 @@ static Choice choose(const wfa_grid_s* g) {
         int d = g->force_depth ? g->force_depth : (v == COL_VARIANT || v < 0 ? 1 : 2);
         ch = Choice{v, d};
     }
+    if (g->force_zchunk) ch.zc = g->force_zchunk;
     if (ch.variant < 0 || ch.variant == COL_VARIANT || ch.variant == INPLACE_VARIANT) ch.depth = 1;
     if (ch.variant == FUSED_VARIANT) ch.depth = g->k ? 1 : 2;   // per-cell k: the one-step column kernel
     return ch;
@@ -266,9 +272,10 @@ static void choose_chunks(int nz, int depth, long long tiles, long long resident
     *nchunk = bn;
 }
 
-static SweepArgs base_args(wfa_grid_s* g, const SweepCoef& c, int in_buf) {
+static SweepArgs base_args(wfa_grid_s* g, const SweepCoef& c, int in_buf, int zc = 0) {
     SweepArgs a;
     memset(&a, 0, sizeof a);
+    a.zchunk = zc;
     a.c = c;
     const long long off = domain_offset(g);
     a.tin = (const char*)g->T[in_buf] + off * g->esize;
@@ -288,10 +295,11 @@ static int pass_launches(const wfa_grid_s* g, const SweepCoef& c, int depth, int
     return 1;
 }
 
-// One pass of `depth` fused steps from buffer g->cur into the other buffer.
-static int one_pass(wfa_grid_s* g, const SweepCoef& c, int depth, int variant) {
+// One pass of `depth` fused steps from buffer g->cur into the other buffer
+// (zc: planes per z chunk of the column kernels, 0 = automatic).
+static int one_pass(wfa_grid_s* g, const SweepCoef& c, int depth, int variant, int zc = 0) {
     g->launches += pass_launches(g, c, depth, variant);
-    SweepArgs a = base_args(g, c, g->cur);
+    SweepArgs a = base_args(g, c, g->cur, zc);
     const cudaEvent_t* ev = timing_slot(g);
     if (variant < 0) {   // one-column reference kernel, one step
         cudaError_t e;
@@ -360,7 +368,7 @@ struct StepGraph {
     SweepCoef c;
     const void* T[2];
     const float* r;
-    int variant = 0, depth = 0;
+    int variant = 0, depth = 0, zc = 0;
     cudaGraphExec_t exec = nullptr;
 };
 struct StepGraphs {
@@ -389,7 +397,7 @@ static int run_graph(wfa_grid_s* g, const SweepCoef& c, const Choice& ch, cudaGr
     }
     StepGraph& sl = gs->slot[g->cur];
     const bool same = sl.exec && !memcmp(&sl.c, &c, sizeof c) && sl.T[0] == g->T[0] && sl.T[1] == g->T[1] &&
-                      sl.r == g->r && sl.variant == ch.variant && sl.depth == ch.depth;
+                      sl.r == g->r && sl.variant == ch.variant && sl.depth == ch.depth && sl.zc == ch.zc;
     if (!same) {
         if (sl.exec) cudaGraphExecDestroy(sl.exec);
         sl.exec = nullptr;
@@ -402,7 +410,8 @@ static int run_graph(wfa_grid_s* g, const SweepCoef& c, const Choice& ch, cudaGr
         g->stream = gs->stream;
         cudaError_t e = cudaStreamBeginCapture(gs->stream, cudaStreamCaptureModeThreadLocal);
         int rc = WFA_OK;
-        for (int k = 0; k < GRAPH_PASSES && e == cudaSuccess && !rc; ++k) rc = one_pass(g, c, ch.depth, ch.variant);
+        for (int k = 0; k < GRAPH_PASSES && e == cudaSuccess && !rc; ++k)
+            rc = one_pass(g, c, ch.depth, ch.variant, ch.zc);
         cudaGraph_t graph = nullptr;
         const cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(gs->stream, &graph) : e;
         g->stream = user;
@@ -419,6 +428,7 @@ static int run_graph(wfa_grid_s* g, const SweepCoef& c, const Choice& ch, cudaGr
         sl.r = g->r;
         sl.variant = ch.variant;
         sl.depth = ch.depth;
+        sl.zc = ch.zc;
     }
     *out = sl.exec;
     return WFA_OK;
@@ -450,7 +460,7 @@ int launch_sweep(wfa_grid_s* g, long long nsteps) {
     }
     while (nsteps > 0) {
         const int d = (int)std::min<long long>(ch.depth, nsteps);
-        rc = one_pass(g, c, d, ch.variant);
+        rc = one_pass(g, c, d, ch.variant, ch.zc);
         if (rc) return rc;
         nsteps -= d;
     }
@@ -470,8 +480,15 @@ int autotune(wfa_grid_s* g, int* depth_out, int* variant_out) {
         ~Pause() { g->timing_every = every; }
     } pause{g, g->timing_every};
     g->timing_every = 0;
-    static const Choice cands[] = {{COL_VARIANT, 1}, {INPLACE_VARIANT, 1}, {FUSED_VARIANT, 2}, {1, 1}, {2, 1},
-                                   {1, 2}, {2, 2}, {1, 3}, {2, 3}, {1, 4}, {2, 4}, {1, 6}, {1, 8}};
+    std::vector<Choice> cands = {{COL_VARIANT, 1}, {INPLACE_VARIANT, 1}, {FUSED_VARIANT, 2}, {1, 1}, {2, 1},
+                                 {1, 2}, {2, 2}, {1, 3}, {2, 3}, {1, 4}, {2, 4}, {1, 6}, {1, 8}};
+    // the column kernel with longer z chunks: fewer boundary planes read
+    // twice, fewer and longer-lived blocks; down to two chunks (one wave on
+    // large grids)
+    const int half = (c.n[2] + 1) / 2;
+    for (int zc : {32, 64, 128})
+        if (zc < half) cands.push_back(Choice{COL_VARIANT, 1, zc});
+    if (half >= 32) cands.push_back(Choice{COL_VARIANT, 1, half});
     const size_t bytes = field_elems(g) * g->esize;
     void* save = nullptr;
     WFA_CUDA(dev_alloc(&save, bytes, g->stream));
@@ -488,10 +505,10 @@ int autotune(wfa_grid_s* g, int* depth_out, int* variant_out) {
         if (e != cudaSuccess) break;
         if (ch.variant == FUSED_VARIANT && g->k) continue;   // uniform k only
         // one warm-up pass, then the timed passes
-        rc = one_pass(g, c, ch.depth, ch.variant);
+        rc = one_pass(g, c, ch.depth, ch.variant, ch.zc);
         if (rc) break;
         cudaEventRecord(e0, g->stream);
-        for (int s = 0; s < steps && !rc; s += ch.depth) rc = one_pass(g, c, ch.depth, ch.variant);
+        for (int s = 0; s < steps && !rc; s += ch.depth) rc = one_pass(g, c, ch.depth, ch.variant, ch.zc);
         cudaEventRecord(e1, g->stream);
         if (rc) break;
         e = cudaEventSynchronize(e1);
@@ -514,6 +531,7 @@ int autotune(wfa_grid_s* g, int* depth_out, int* variant_out) {
     if (e != cudaSuccess) return cuda_fail(e, "autotune");
     g->tuned_variant = best.variant;
     g->tuned_depth = best.depth;
+    g->tuned_zchunk = best.zc;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         tune_load_locked();
@@ -569,6 +587,18 @@ int wfa_kernel_time(wfa_grid g, double* ms, long long* launches) {
 }
 
 }  // extern "C"
+
+extern "C" int wfa_get_tuning(wfa_grid g, int* depth, int* variant, int* zchunk) {
+    if (!g) {
+        wfa::set_error("NULL grid");
+        return WFA_ERR_ARG;
+    }
+    const wfa::Choice ch = wfa::choose(g);
+    if (depth) *depth = ch.depth;
+    if (variant) *variant = ch.variant;
+    if (zchunk) *zchunk = ch.zc;
+    return WFA_OK;
+}
 
 extern "C" int wfa_launch_count(wfa_grid g, long long* n) {
     if (!g || !n) {

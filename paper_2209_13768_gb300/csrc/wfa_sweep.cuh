@@ -32,7 +32,8 @@ struct SweepArgs {
     const void* tin;    // input field, domain origin
     void* tout;         // output field, domain origin
     const float* rk;    // reciprocal conductivity 1/k, domain origin (nullptr for uniform k)
-    int tiles_x, tiles_y, zchunk, nzchunk, items;
+    int tiles_x, tiles_y, zchunk, nzchunk, items;   // column kernels: zchunk > 0 on entry asks for
+                                                     // chunks of that many planes (0: automatic)
     int* status;
 };
 

@@ -155,7 +155,15 @@ template <bool KVAR, bool INL = false, int ES = 4> struct ColOcc {
 // FIX = false: boundary cells (unless the ghost layers encode the boundary
 // conditions) and halo copies are handled in place. GHOST: the caller
 // guarantees c.halo_bc, so the boundary path is not compiled at all.
-template <typename S, bool KVAR, bool ADV, bool COH, int UNROLL, bool FIX, bool PF = false, bool GHOST = false>
+// DIR = +1 marches planes z0 .. z1-1 upwards, DIR = -1 marches z1-1 .. z0
+// downwards. The single-grid kernel alternates the direction between
+// neighbouring z chunks, so that the two chunks that share a boundary plane
+// read it at about the same time (both at their start, or both at their end)
+// and the second read hits L2 instead of DRAM. The march direction does not
+// change a cell's value: the z faces are symmetric bit for bit and every
+// cell takes the same operands in the same order.
+template <typename S, bool KVAR, bool ADV, bool COH, int UNROLL, bool FIX, bool PF = false, bool GHOST = false,
+          int DIR = 1>
 __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict__ tin, S* __restrict__ tout,
                                         const float* __restrict__ rk, int* status, int gx, int gy, int z0, int z1) {
     const long long sy = c.sy, sz = c.sz;
@@ -171,28 +179,37 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
     const bool plain_xy = gx + 3 < c.n[0] && !(perx && (gx < HALO || gx + 3 >= c.n[0] - HALO)) &&
                           !(pery && (gy < HALO || gy >= c.n[1] - HALO));
 
+    // register queue: tm = the plane already passed (z - DIR), tc = plane z,
+    // tz = the plane ahead (z + DIR), loaded at plane z; gzm = the face
+    // between the passed plane and plane z (per-cell k)
+    const int zs = DIR > 0 ? z0 : z1 - 1;          // first plane of the march
+    const long long dsz = DIR > 0 ? sz : -sz;      // one plane ahead
     float tm[4], tc[4], rc[4], gzm[4];
-    ldg4<S, COH>(tcol + (long long)(z0 - 1) * sz, tm);
-    ldg4<S, COH>(tcol + (long long)z0 * sz, tc);
+    ldg4<S, COH>(tcol + (long long)(zs - DIR) * sz, tm);
+    ldg4<S, COH>(tcol + (long long)zs * sz, tc);
     if (KVAR) {
         float rb[4];
-        ldg4<float, false>(rcol + (long long)(z0 - 1) * sz, rb);
-        ldg4<float, false>(rcol + (long long)z0 * sz, rc);
+        ldg4<float, false>(rcol + (long long)(zs - DIR) * sz, rb);
+        ldg4<float, false>(rcol + (long long)zs * sz, rc);
 #pragma unroll
         for (int i = 0; i < 4; ++i) gzm[i] = face_r(rb[i], rc[i], c.tcd[2]);
     }
 
 #pragma unroll(UNROLL)
-    for (int z = z0; z < z1; ++z) {
+    for (int s = 0; s < z1 - z0; ++s) {
+        const int z = DIR > 0 ? z0 + s : z1 - 1 - s;
         const S* tp = tcol + (long long)z * sz;
         const float* rp = KVAR ? rcol + (long long)z * sz : nullptr;
         float tz[4], rz[4];
-        ldg4<S, COH>(tp + sz, tz);                       // own cells, plane z + 1
-        if (PF && (threadIdx.x & 7) == 0) {              // one thread per 128-byte line
-            prefetch_l2(tp + 3 * sz);                    // plane z + 3 <= nz + 2 stays inside the halo
-            if (KVAR) prefetch_l2(rp + 3 * sz);
+        ldg4<S, COH>(tp + dsz, tz);                      // own cells, plane z + DIR
+        // one thread per 128-byte line asks L2 for plane z + 3 DIR, as long as
+        // the chunk still needs it (the last plane read is z1 going up, z0 - 1
+        // going down); the plane after that belongs to the next chunk
+        if (PF && (threadIdx.x & 7) == 0 && s + 3 <= z1 - z0) {
+            prefetch_l2(tp + 3 * dsz);
+            if (KVAR) prefetch_l2(rp + 3 * dsz);
         }
-        if (KVAR) ldg4<float, false>(rp + sz, rz);
+        if (KVAR) ldg4<float, false>(rp + dsz, rz);
         ColNb<S, KVAR, COH> nb;                          // x / y neighbours, plane z
         nb.load(tp, rp, sy);
 
@@ -217,8 +234,8 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
                 w[i][1] = xf[i + 1];
                 w[i][2] = face_r(nb.ry_m[i], rc[i], c.tcd[1]);
                 w[i][3] = face_r(rc[i], nb.ry_p[i], c.tcd[1]);
-                w[i][4] = gzm[i];
-                w[i][5] = gzp[i];
+                w[i][4] = DIR > 0 ? gzm[i] : gzp[i];   // the -z face
+                w[i][5] = DIR > 0 ? gzp[i] : gzm[i];   // the +z face
                 if (ADV) {
 #pragma unroll
                     for (int f = 0; f < 6; ++f) w[i][f] = __fadd_rn(w[i][f], c.adv[f]);
@@ -234,24 +251,26 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
             for (int i = 0; i < 4; ++i) {
                 const float txm = i == 0 ? nb.tx_m : tc[i - 1];
                 const float txp = i == 3 ? nb.tx_p : tc[i + 1];
-                out[i] = storage_round<S>(__fadd_rn(tc[i], flux_sum(tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i], tm[i],
-                                                                    tz[i], w[i][0], w[i][1], w[i][2], w[i][3],
-                                                                    w[i][4], w[i][5])));
+                out[i] = storage_round<S>(__fadd_rn(tc[i], flux_sum(tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i],
+                                                                    DIR > 0 ? tm[i] : tz[i], DIR > 0 ? tz[i] : tm[i],
+                                                                    w[i][0], w[i][1], w[i][2], w[i][3], w[i][4],
+                                                                    w[i][5])));
             }
         } else {
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const float txm = i == 0 ? nb.tx_m : tc[i - 1];
                 const float txp = i == 3 ? nb.tx_p : tc[i + 1];
+                const float tzm = DIR > 0 ? tm[i] : tz[i], tzp = DIR > 0 ? tz[i] : tm[i];
                 const bool edge_cell = bym || byp || bzm || bzp || (!perx && (gx + i == 0 || gx + i == c.n[0] - 1));
                 float v;
                 if (!KVAR) {   // uniform k: the boundary formula by select, inline
-                    v = uniform_cell(c, tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i], tm[i], tz[i], gx + i, gy, z);
+                    v = uniform_cell(c, tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i], tzm, tzp, gx + i, gy, z);
                 } else if (!edge_cell) {
-                    v = __fadd_rn(tc[i], flux_sum(tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i], tm[i], tz[i], w[i][0],
+                    v = __fadd_rn(tc[i], flux_sum(tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i], tzm, tzp, w[i][0],
                                                   w[i][1], w[i][2], w[i][3], w[i][4], w[i][5]));
                 } else {
-                    v = boundary_update<KVAR>(&c, tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i], tm[i], tz[i], w[i][0],
+                    v = boundary_update<KVAR>(&c, tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i], tzm, tzp, w[i][0],
                                               w[i][1], w[i][2], w[i][3], w[i][4], w[i][5], KVAR ? rc[i] : 0.0f,
                                               gx + i, gy, z);
                 }
@@ -298,8 +317,13 @@ __global__ void __launch_bounds__(256, (ColOcc<KVAR, INL, sizeof(S)>::blocks)) s
     if (gx >= c.n[0] || gy >= c.n[1]) return;
     const int z0 = blockIdx.z * a.zchunk;
     const int z1 = min(z0 + a.zchunk, c.n[2]);
-    col_run<S, KVAR, ADV, false, ColOcc<KVAR, INL, sizeof(S)>::unroll, !INL, true>(c, (const S*)a.tin, (S*)a.tout, a.rk,
-                                                                         a.status, gx, gy, z0, z1);
+    constexpr int U = ColOcc<KVAR, INL, sizeof(S)>::unroll;
+    if (blockIdx.z & 1)   // odd chunks march down: see col_run
+        col_run<S, KVAR, ADV, false, U, !INL, true, false, -1>(c, (const S*)a.tin, (S*)a.tout, a.rk, a.status, gx,
+                                                              gy, z0, z1);
+    else
+        col_run<S, KVAR, ADV, false, U, !INL, true, false, 1>(c, (const S*)a.tin, (S*)a.tout, a.rk, a.status, gx,
+                                                             gy, z0, z1);
 }
 
 // Boundary cells (the outer layer on every non-periodic face): recomputed
@@ -408,6 +432,8 @@ cudaError_t col_launch(const SweepArgs& a_in, cudaStream_t st, int nsm, const cu
     int cap = std::max(1, a.c.n[2] / 16);
     if (cols * cap < resident) cap = std::max(1, a.c.n[2] / 2);
     nch = std::min(nch, cap);
+    // a chunk length asked for by the caller (the autotuner's trials)
+    if (a_in.zchunk > 0) nch = (a.c.n[2] + a_in.zchunk - 1) / a_in.zchunk;
     a.zchunk = (a.c.n[2] + nch - 1) / nch;
     nch = (a.c.n[2] + a.zchunk - 1) / a.zchunk;
     dim3 grid(gxb, gyb, nch);

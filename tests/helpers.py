@@ -29,7 +29,7 @@ def run_oracle(p, steps=None, dt=None, round_to=None, T0=None):
                       bc=p.bc, dt=dt, round_to=round_to)
 
 
-def make_grid(p, storage=wfa.F32, depth=0, variant=0, dt=None):
+def make_grid(p, storage=wfa.F32, depth=0, variant=0, dt=None, zchunk=0):
     g = wfa.Grid(p.shape, h=p.h, storage=storage)
     g.set_bcs(p.bc)
     g.set_coeffs(p.k, p.u)
@@ -38,11 +38,12 @@ def make_grid(p, storage=wfa.F32, depth=0, variant=0, dt=None):
         dt = p.dt if p.dt else p.dt_factor * g.stability_dt()
     g.set_dt(dt)
     g.set_tuning(depth, variant)
+    g.set_zchunk(zchunk)
     return g
 
 
-def run_gpu(p, steps=None, storage=wfa.F32, depth=0, variant=0, dt=None):
+def run_gpu(p, steps=None, storage=wfa.F32, depth=0, variant=0, dt=None, zchunk=0):
     steps = p.steps if steps is None else steps
-    with make_grid(p, storage, depth, variant, dt) as g:
+    with make_grid(p, storage, depth, variant, dt, zchunk) as g:
         g.step(steps)
         return g.read_field()

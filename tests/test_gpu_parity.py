@@ -100,6 +100,24 @@ def test_boundary_mixes_all_kernels(mix, kvar, adv):
                                   run_gpu(p, steps=p.steps - 1, variant=-1), err_msg="two-step, odd count")
 
 
+@pytest.mark.parametrize("kvar,adv", [(True, True), (False, True), (True, False)])
+@pytest.mark.parametrize("mix", range(len(MIXES)))
+def test_column_kernel_z_chunks(mix, kvar, adv):
+    """The column kernels march z chunks of any length, neighbouring chunks
+    in opposite directions: the field is bitwise the same for every chunk
+    length (one plane, odd lengths, a ragged last chunk, one chunk)."""
+    p = _mixed_problem(mix, kvar=kvar, adv=adv, seed=50 + mix)
+    base = run_gpu(p, variant=-1)
+    for zc in (1, 2, 3, 5, 8, 12, 22, 23, 64):
+        np.testing.assert_array_equal(run_gpu(p, variant=3, zchunk=zc), base, err_msg=f"variant 3, zchunk {zc}")
+        np.testing.assert_array_equal(run_gpu(p, variant=5, zchunk=zc), base, err_msg=f"variant 5, zchunk {zc}")
+    for storage in (wfa.BF16,):
+        ref = run_gpu(p, storage=storage, variant=-1)
+        for zc in (3, 8, 12):
+            np.testing.assert_array_equal(run_gpu(p, storage=storage, variant=3, zchunk=zc), ref,
+                                          err_msg=f"bf16 zchunk {zc}")
+
+
 @pytest.mark.parametrize("shape", [(2, 2, 2), (3, 2, 5), (5, 7, 3), (64, 3, 9), (131, 67, 4), (70, 35, 40)])
 def test_small_and_ragged_shapes(shape):
     for mix in (0, 2, 4):
