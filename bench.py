@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-solo", action="store_true", help="batch: skip the one-grid-per-launch comparison")
+    ap.add_argument("--zchunk", type=int, default=0, help="planes per z chunk of the column kernels (0: tuned)")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the oracle comparison of the bench line")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default line: skip the advection-diffusion and batch configurations")
     return ap.parse_args()
 
 
@@ -313,7 +317,7 @@ def serving_sample(n_requests, rate=200.0, seed=5, pool=24, quantum=64):
             "inputs": f"pool of {pool} request shapes from the serving request stream"}
 
 
-def batch_bench(args):
+def batch_bench(args, emit=True):
     """256 grids, edges log-uniform in [16,128], k lognormal(0,0.5), steps
     U{50..500}: one persistent CUDA-graph launch vs one grid at a
     time through wfa_step."""
@@ -332,17 +336,27 @@ def batch_bench(args):
         g.set_dt(0.9 * g.stability_dt())
         grids.append(g)
     steps = [p.steps for p in probs]
-    updates = sum(p.shape[0] * p.shape[1] * p.shape[2] * n for p, n in zip(probs, steps))
+    cells = [p.shape[0] * p.shape[1] * p.shape[2] for p in probs]
+    updates = sum(c * n for c, n in zip(cells, steps))
     wfa.batch_run(grids, [1] * len(grids))   # builds the graph
-    times = []
-    for _ in range(args.warmup + args.steps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+    for _ in range(args.warmup):
         wfa.batch_run(grids, steps)
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.synchronize()
+    sampler.start()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        wfa.batch_run(grids, steps)   # returns when the work is done
         times.append(time.perf_counter() - t0)
-    t_batch = sum(times[args.warmup:]) / args.steps
+    clocks = sampler.stop()
+    t_batch = sum(times) / args.steps
     t_solo = float("nan")
     if not args.no_solo:
+        for g, n in zip(grids, steps):   # warm-up: graphs of the small grids, tuned kernels
+            g.step(n)
+        for g in grids:
+            g.sync()
         t0 = time.perf_counter()
         for g, n in zip(grids, steps):
             g.step(n)
@@ -351,14 +365,30 @@ def batch_bench(args):
         t_solo = time.perf_counter() - t0
     for g in grids:
         g.close()
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = bytes_per_cell(False, True) * updates / t_batch / 1e9
     line = {"metric": METRIC, "value": updates / t_batch / 1e9, "unit": "GLUPS", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_batch, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "256 grids, edges log-uniform [16,128], k lognormal(0,0.5), steps U{50..500}",
-                       "cell_updates_per_step": updates},
+                       "grids": len(probs), "cells": sum(cells), "cell_updates_per_step": updates,
+                       "timing": "host wall clock around wfa_batch_run (one graph launch, waits for the work)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "bytes_per_cell_update": 12,
+                         "scope": "the whole batched call (every kernel of every round, the graph launch)"},
             "one_grid_per_launch": None if args.no_solo else
-            {"value": updates / t_solo / 1e9, "unit": "GLUPS", "ms_per_step": 1e3 * t_solo}}
-    print(json.dumps(line), flush=True)
+            {"value": updates / t_solo / 1e9, "unit": "GLUPS", "ms_per_step": 1e3 * t_solo,
+             "form": "wfa_step on each grid in turn (its own tuned kernels and step graphs), one stream"},
+            "gpu_launches": None, "clocks": clocks}
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 CG_SOURCES = ["paper_2209_13768_gb300/csrc/wfa_implicit.cu"]
@@ -602,6 +632,102 @@ def main():
 
     p = workload(args.workload, args.solve_steps, args.shape)
     storage = wfa.BF16 if args.workload == "advdiff_bf16" else wfa.F32
+    r = grid_bench(args, p, storage, world, rank, dist, local, e2e=not args.no_e2e,
+                   accuracy=not args.no_accuracy)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_rate(p, args.cpu_seconds)
+    default = args.workload == "lognormal" and not args.shape and not args.solve_steps
+    serving = None
+    if rank == 0 and world == 1 and args.serve_requests and default:
+        serving = serving_sample(args.serve_requests)
+    extras = {}
+    if rank == 0 and world == 1 and default and not args.no_extras:
+        # the other single-GPU configurations, driver-recorded beside the
+        # headline: advection-diffusion 1024x1024x512 (fp32 and bf16 storage)
+        # and the 256-grid batch against one grid per launch
+        for name, st in (("advdiff_1024x1024x512_f32", wfa.F32), ("advdiff_1024x1024x512_bf16", wfa.BF16)):
+            sub = grid_bench(args, workload("advdiff", 0), st, 1, 0, None, local, e2e=False,
+                             accuracy=not args.no_accuracy)
+            extras[name] = {k: sub[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup", "config",
+                                                "roofline", "accuracy", "gpu_launches", "clocks")}
+        extras["batch_256_grids"] = batch_bench(args, emit=False)
+    if rank == 0:
+        line = {"metric": METRIC, "value": r["value"], "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": r["config"], "roofline": r["roofline"], "linf_rel_err": r["accuracy"] and
+                r["accuracy"]["linf_rel_err"], "accuracy": r["accuracy"], "cpu_baseline": cpu, "e2e": r["e2e"],
+                "serving": serving, "gpu_launches": r["gpu_launches"], "clocks": r["clocks"]}
+        if extras:
+            line["other_configs"] = extras
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+KERNEL_NAMES = {3: "sweep_col", 4: "sweep_col2 (two steps per pass)", 5: "sweep_col (boundaries in place)",
+                -1: "sweep_simple"}
+
+
+def accuracy_boxes(p, edge=16):
+    """Target boxes for the oracle comparison: the corners where the most
+    faces meet, the middle of a face of every axis, and the grid's centre
+    (where the advection-diffusion blob has its maximum)."""
+    nx, ny, nz = p.shape
+    e = [min(edge, n) for n in p.shape]
+    mid = lambda n, w: (n - w) // 2
+    corners = [(0, 0, 0), (nx - e[0], ny - e[1], nz - e[2]), (0, ny - e[1], nz - e[2]), (nx - e[0], 0, 0)]
+    faces = [(0, mid(ny, e[1]), mid(nz, e[2])), (mid(nx, e[0]), 0, mid(nz, e[2])),
+             (mid(nx, e[0]), mid(ny, e[1]), nz - e[2])]
+    centre = [(mid(nx, e[0]), mid(ny, e[1]), mid(nz, e[2]))]
+    return [(lo, (lo[0] + e[0], lo[1] + e[1], lo[2] + e[2])) for lo in corners + faces + centre]
+
+
+def accuracy_sample(g, p, dt, storage, n):
+    """L-inf error of the GPU field after an n-step prefix of the workload,
+    relative to max |T| of the FP64 oracle, on sampled boxes (outside every
+    timed region). The oracle steps each box widened by n cells (the
+    stencil's domain of dependence, oracle/lightcone.py), so its values there
+    are the whole-grid oracle's."""
+    import numpy as np
+
+    from oracle import lightcone
+    kvar = not np.isscalar(p.k)
+    t0 = time.perf_counter()
+    g.set_field(p.T0)
+    g.set_dt(dt)
+    g.step(n)
+    T = g.read_field()
+    err, scale, cells = 0.0, 0.0, 0
+    k = np.asarray(p.k) if kvar else float(p.k)
+    for lo, hi in accuracy_boxes(p):
+        ref = lightcone.run_box(p.T0, n, shape=p.shape, lo=lo, hi=hi, h=p.h, k=k, u=p.u, bc=p.bc, dt=dt)
+        got = T[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]].astype(np.float64)
+        err = max(err, float(np.abs(got - ref).max()))
+        scale = max(scale, float(np.abs(ref).max()))
+        cells += ref.size
+    rel = err / scale if scale > 0 else err
+    bf16 = storage == 1
+    bound = (n + 1) * 2.0 ** -9 if bf16 else 1e-5
+    return {"linf_rel_err": rel, "bound": bound, "within_bound": rel <= bound, "steps": n,
+            "reference": "FP64 oracle (oracle.run on each box widened by n cells)",
+            "sample": f"{cells} cells in {len(accuracy_boxes(p))} boxes of up to 16^3 (corners, face middles, "
+                      f"centre) after the first {n} time steps of the workload",
+            "bound_reason": "(n+1) 2^-9 relative: bf16 storage rounds once at set-up and once a step, "
+                            "the update is non-expansive" if bf16 else
+                            "1e-5 after 100 steps (fp32 arithmetic, the update is non-expansive)",
+            "seconds": time.perf_counter() - t0}
+
+
+def grid_bench(args, p, storage, world, rank, dist, local, e2e=True, accuracy=True):
+    """Time one single-grid workload (a benchmark step = p.steps time steps)
+    and return its numbers: rate, roofline of the main sweep kernel, e2e
+    through the C ABI from pinned host buffers, accuracy against the oracle."""
+    import numpy as np
+    import torch
+
+    import paper_2209_13768_gb300 as wfa
     kvar = not np.isscalar(p.k)
     cells = p.shape[0] * p.shape[1] * p.shape[2]
     stream = torch.cuda.Stream()
@@ -612,11 +738,10 @@ def main():
     dt = p.dt if p.dt else 0.9 * g.stability_dt()
     g.set_dt(dt)
     g.set_tuning(args.depth, args.variant)
-    if args.depth or args.variant:
-        depth = args.depth or (1 if args.variant in (-1, 3) else 2)
-        variant = args.variant or (3 if depth == 1 else 1)
-    else:   # autotune: time the compiled configurations on this grid, keep the fastest
-        depth, variant = g.autotune()
+    g.set_zchunk(args.zchunk)
+    if not (args.depth or args.variant or args.zchunk):
+        g.autotune()   # time the compiled configurations on this grid, keep the fastest
+    depth, variant, zchunk = g.tuning()
     passes_per_step = math.ceil(p.steps / depth)
 
     for _ in range(args.warmup):
@@ -626,9 +751,7 @@ def main():
     sampler = ClockSampler(local)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     # the dominant kernel's own launches are bracketed by events inside the
-    # library, on the grid's stream: every 16th pass (two event records per
-    # sampled pass are noise next to a pass, even a 64^3 one), at most about
-    # 4000 samples
+    # library, on the grid's stream: every 16th pass, at most about 4000 samples
     g.set_kernel_timing(max(16, math.ceil(args.steps * passes_per_step / 4000)))
     launches0 = g.launch_count()
     if dist:
@@ -654,9 +777,15 @@ def main():
 
     # roofline of the dominant kernel (the main sweep): algorithmic bytes per
     # launch (read T, read k, write T once per pass) over its mean duration,
-    # from the event pairs the library recorded around its sampled launches
+    # from the event pairs the library recorded around its sampled launches.
+    # When the main kernel is the pass's only kernel, the pass mean (no event
+    # records inside) bounds its duration from above and is the tighter figure.
     pass_s = total_s / (args.steps * passes_per_step)
     launch_s = kernel_ms / 1e3 / kernel_launches if kernel_launches else pass_s
+    launches_per_pass = gpu_launches / max(1, args.steps * passes_per_step)
+    event_s = launch_s
+    if launches_per_pass <= 1.0 + 1e-9:
+        launch_s = min(launch_s, pass_s)
     bpc = bytes_per_cell(storage == wfa.BF16, kvar)
     achieved = bpc * cells / launch_s / 1e9
     peaks = {}
@@ -670,26 +799,29 @@ def main():
     try:
         with open(TRAFFIC_FILE) as f:
             tr = json.load(f)
-        key = f"{'bf16' if storage else 'f32'}:{'k' if kvar else 'u'}:{'adv' if any(p.u) else 'noadv'}:v{variant}:d{depth}"
+        key = (f"{'bf16' if storage else 'f32'}:{'k' if kvar else 'u'}:{'adv' if any(p.u) else 'noadv'}"
+               f":v{variant}:d{depth}:{p.shape[0]}x{p.shape[1]}x{p.shape[2]}")
         ent = tr.get(key)
-        if ent and ent.get("kernel_hash") == kernel_hash():
+        if ent and ent.get("kernel_hash") == kernel_hash() and ent.get("zchunk", 0) == zchunk:
             traffic = ent["bytes_per_launch"]
     except (OSError, ValueError):
         pass
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "bytes_per_cell_per_launch": bpc, "steps_per_launch": depth,
-                "kernel_ms_mean": launch_s * 1e3, "kernel_launches_timed": kernel_launches,
+                "kernel_ms_mean": launch_s * 1e3, "kernel_ms_mean_event_pairs": event_s * 1e3,
+                "kernel_launches_timed": kernel_launches, "launches_per_pass": launches_per_pass,
                 # DRAM bytes per launch from ncu over this run's mean launch time
                 "ncu_dram_GBps": traffic / launch_s / 1e9 if traffic else None,
                 "ncu_dram_frac": traffic / launch_s / 1e9 / peak if traffic else None,
+                "traffic_over_algorithmic": traffic / (bpc * cells) if traffic else None,
                 "pass_ms_mean": pass_s * 1e3, "pass_GBps": bpc * cells / pass_s / 1e9,
                 "effective_GBps_paper_Teff": bpc * depth * cells / pass_s / 1e9,
                 "frac_of_nominal_8TBps": achieved / 8000.0}
 
     # end to end through the C ABI from pinned host buffers
-    e2e = None
-    if not args.no_e2e:
+    e2e_line = None
+    if e2e:
         T0h = torch.from_numpy(np.ascontiguousarray(p.T0)).pin_memory()
         kh = torch.from_numpy(np.ascontiguousarray(p.k)).pin_memory() if kvar else None
         outh = torch.empty(tuple(p.T0.shape), dtype=torch.float32).pin_memory()
@@ -707,34 +839,22 @@ def main():
                 e2e_t.append(time.perf_counter() - t0)
         e2e_s = sum(e2e_t) / len(e2e_t)
         e2e_s = max_over_ranks(e2e_s, dist, "cuda")
-        e2e = {"value": job_rate(world, cells * p.steps, e2e_s), "unit": "GLUPS",
-               "h2d_bytes_per_step": cells * 4 * (2 if kvar else 1), "d2h_bytes_per_step": cells * 4,
-               "ms_per_step": 1e3 * e2e_s}
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_rate(p, args.cpu_seconds)
-    serving = None
-    if rank == 0 and world == 1 and args.serve_requests and args.workload == "lognormal" and not args.shape:
-        serving = serving_sample(args.serve_requests)
-
+        e2e_line = {"value": job_rate(world, cells * p.steps, e2e_s), "unit": "GLUPS",
+                    "h2d_bytes_per_step": cells * 4 * (2 if kvar else 1), "d2h_bytes_per_step": cells * 4,
+                    "ms_per_step": 1e3 * e2e_s}
+    acc = None
+    if accuracy and rank == 0:
+        acc = accuracy_sample(g, p, dt, storage, min(100, p.steps))
     g.close()
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": p.name, "cells": cells, "time_steps_per_step": p.steps, "depth": depth,
-                           "kernel": {3: "sweep_col", 4: "sweep_col2 (two steps per pass)", 5: "sweep_col (boundaries in place)",
-                                      -1: "sweep_simple"}.get(variant, f"sweep_tb variant {variant}"),
-                           "dt": dt, "storage": "bf16" if storage else "f32",
-                           "conductivity": "per-cell lognormal(0,0.5)" if kvar else f"uniform {p.k}",
-                           "l2": "inputs larger than L2 (%.0f MiB field)" % (cells * (2 if storage else 4) / 2**20),
-                           "parallelism": f"replicas x{world}"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serving": serving,
-                "gpu_launches": gpu_launches, "clocks": clocks}
-        print(json.dumps(line), flush=True)
-    if dist:
-        dist.destroy_process_group()
+    config = {"workload": p.name, "cells": cells, "time_steps_per_step": p.steps, "depth": depth,
+              "kernel": KERNEL_NAMES.get(variant, f"sweep_tb variant {variant}"), "variant": variant,
+              "zchunk": zchunk or "automatic", "dt": dt, "storage": "bf16" if storage else "f32",
+              "conductivity": "per-cell lognormal(0,0.5)" if kvar else f"uniform {p.k}",
+              "l2": "inputs larger than L2 (%.0f MiB field)" % (cells * (2 if storage else 4) / 2**20),
+              "parallelism": f"replicas x{world}"}
+    return {"value": value, "unit": "GLUPS", "ms_per_step": 1e3 * total_s / args.steps, "steps": args.steps,
+            "warmup": args.warmup, "config": config, "roofline": roofline, "accuracy": acc, "e2e": e2e_line,
+            "gpu_launches": gpu_launches, "clocks": clocks}
 
 
 if __name__ == "__main__":
