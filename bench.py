@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--no-solo", action="store_true", help="batch: skip the one-grid-per-launch comparison")
     ap.add_argument("--zchunk", type=int, default=0, help="planes per z chunk of the column kernels (0: tuned)")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the oracle comparison of the bench line")
+    ap.add_argument("--split", choices=["none", "z"], default="none",
+                    help="z: one grid split into slabs along z, one slab per rank (NCCL plane exchange "
+                         "before every step), or --slabs slabs on one GPU")
+    ap.add_argument("--slabs", type=int, default=0, help="--split z on one GPU: number of slabs (default 2)")
     ap.add_argument("--no-extras", action="store_true",
                     help="default line: skip the advection-diffusion and batch configurations")
     return ap.parse_args()
@@ -629,6 +633,9 @@ def main():
     if args.workload == "dsl_heat":
         dsl_bench(args, rank, world, dist)
         return
+    if args.split == "z":
+        split_bench(args, rank, world, dist, local)
+        return
 
     p = workload(args.workload, args.solve_steps, args.shape)
     storage = wfa.BF16 if args.workload == "advdiff_bf16" else wfa.F32
@@ -664,6 +671,73 @@ def main():
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def split_bench(args, rank, world, dist, local):
+    """One grid split into slabs along z (Sec. 1 Fig. 1b domain
+    decomposition): with N ranks each GPU holds one slab and the boundary
+    planes move by NCCL send / receive before every step (strong scaling: the
+    grid stays the same); on one GPU, --slabs slabs step through
+    wfa_slabs_step (plane copies between slabs on the device)."""
+    import numpy as np
+    import torch
+
+    import paper_2209_13768_gb300 as wfa
+    from paper_2209_13768_gb300 import slabs
+    p = workload(args.workload, args.solve_steps, args.shape)
+    storage = wfa.BF16 if args.workload == "advdiff_bf16" else wfa.F32
+    cells = p.shape[0] * p.shape[1] * p.shape[2]
+    kvar = not np.isscalar(p.k)
+    stream = torch.cuda.current_stream()
+    if world > 1:
+        s = slabs.DistSlab(dist, p.shape, rank, world, h=p.h, storage=storage, bc=p.bc)
+        z0, z1 = s.z0, s.z1
+        s.set_field(np.ascontiguousarray(p.T0[z0:z1]))
+        s.set_coeffs(np.ascontiguousarray(p.k[z0:z1]) if kvar else p.k, p.u)
+        nslabs = world
+        interfaces = world if s.wrap else world - 1
+    else:
+        nslabs = args.slabs or 2
+        s = slabs.SlabGrid(p.shape, nslabs, h=p.h, storage=storage,
+                           stream=stream.cuda_stream or None, bc=p.bc)
+        s.set_field(p.T0)
+        s.set_coeffs(p.k, p.u)
+        interfaces = nslabs if p.bc[4][0] == "periodic" else nslabs - 1
+    dt = p.dt if p.dt else 0.9 * s.stability_dt()
+    s.set_dt(dt)
+    for _ in range(args.warmup):
+        s.step(p.steps)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        s.step(p.steps)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_s = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / 1e3, dist, "cuda")
+    value = cells * p.steps * args.steps / total_s / 1e9     # the whole grid, once (strong scaling)
+    esize = 2 if storage == wfa.BF16 else 4
+    plane = (p.shape[0] + 16 + 31) // 32 * 32 * (p.shape[1] + 16) * esize
+    s.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "bf16" if storage == wfa.BF16 else "f32",
+            "data": "synthetic",
+            "config": {"workload": p.name, "cells": cells, "time_steps_per_step": p.steps, "dt": dt,
+                       "decomposition": f"{nslabs} z slabs" + (" (one per GPU)" if world > 1 else " on one GPU"),
+                       "exchange": ("NCCL send/recv of whole padded planes before every time step" if world > 1
+                                    else "device copies of whole padded planes before every time step (wfa_slabs_step)"),
+                       "exchange_bytes_per_time_step": 2 * interfaces * plane,
+                       "parallelism": f"z slabs x{nslabs}"},
+            "roofline": None, "gpu_launches": None, "clocks": clocks}), flush=True)
 
 
 KERNEL_NAMES = {3: "sweep_col", 4: "sweep_col2 (two steps per pass)", 5: "sweep_col (boundaries in place)",

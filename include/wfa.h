@@ -57,7 +57,10 @@ enum wfa_bc_kind {
     WFA_BC_DIRICHLET = 0,      /* value on the boundary face, half a cell from the centre */
     WFA_BC_ZEROFLUX = 1,       /* no diffusive and no advective flux through the face     */
     WFA_BC_PERIODIC = 2,       /* must be set on both faces of an axis                    */
-    WFA_BC_DIRICHLET_CELL = 3  /* outer cell layer held at the value (Eq. expl_form, C in bc) */
+    WFA_BC_DIRICHLET_CELL = 3, /* outer cell layer held at the value (Eq. expl_form, C in bc) */
+    WFA_BC_EXCHANGE = 4        /* z faces only: the face between two slabs of one grid split
+                                  along z; the neighbour slab's cells are copied into the halo
+                                  plane beyond the face before every step (wfa_exchange) */
 };
 
 enum wfa_face { WFA_XLO = 0, WFA_XHI = 1, WFA_YLO = 2, WFA_YHI = 3, WFA_ZLO = 4, WFA_ZHI = 5 };
@@ -193,7 +196,9 @@ int wfa_total_heat(wfa_grid g, double* e);
  * overlap on the GPU (on different streams without ordering) race. The first
  * call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture begins. Bit-reproducible for a given n.
+ * before any stream capture begins. The address is kept per device and
+ * context: after a cudaDeviceReset the next call looks it up again (so make
+ * that call, too, outside a capture). Bit-reproducible for a given n.
  * Errors: WFA_ERR_ARG (null pointer, negative or too large n), WFA_ERR_CUDA. */
 int wfa_sum_f32_noalloc(const float* d_x, long long n, double scale, double* d_out, void* stream);
 
@@ -303,6 +308,62 @@ const char* wfa_last_error(void);
  * first device allocation, arms the same failure for the n-th allocation of
  * the process. Returns WFA_OK. */
 int wfa_inject_alloc_failure(int n);
+
+/* ------------------------------------------------ slabs (z decomposition) -- */
+/* One grid split along z into slabs, each an ordinary grid (Sec. 1, Fig. 1b:
+ * domain decomposition; Sec. 3: each WSE tile owns a 1 x 1 x Z column and
+ * exchanges neighbour values every step; Eq. iteration_time_model: a step's
+ * time is its computation or its halo exchange, whichever is longer, plus the
+ * boundary work). A slab holds planes [z0, z1) of the whole grid: nx, ny, the
+ * cell size, storage, x / y faces, conductivity (its planes), velocity and dt
+ * as the whole grid; its z faces towards neighbouring slabs are
+ * WFA_BC_EXCHANGE faces, its other z faces the whole grid's (a periodic z
+ * axis: exchange faces at both ends, the last slab's +z face meeting the
+ * first slab's -z face). Before every step the outermost plane of each slab
+ * is copied into the halo plane beyond the neighbour's exchange face; each
+ * cell then sees the operands it has in the whole grid, so the slabs' fields
+ * are bitwise the whole grid's. Slabs step with the column-march kernels
+ * (variants 3 and 5) or the one-column kernel, one step per pass; batched and
+ * implicit steps reject exchange faces (WFA_ERR_BC). The stability limit of a
+ * slab counts its exchange faces as interior faces and needs the
+ * neighbours' conductivity planes (wfa_exchange with WFA_PLANES_K) first: the
+ * whole grid's limit is the minimum over its slabs. Total heat: the sum over
+ * slabs. */
+enum { WFA_PLANES_FIELD = 0, WFA_PLANES_K = 1, WFA_PLANES_RECIP_K = 2 };
+
+/* Device addresses of the planes an exchange face moves, for callers that
+ * move them themselves (slabs on several GPUs or processes, e.g. NCCL send /
+ * receive into the receiving GPU's own memory). face: WFA_ZLO or WFA_ZHI,
+ * which must be an exchange face. what: WFA_PLANES_FIELD (the buffer that
+ * holds the current field: the addresses change with every step),
+ * WFA_PLANES_K or WFA_PLANES_RECIP_K (per-cell k and 1/k; both must be moved
+ * after every wfa_set_coeffs). *send: the slab's own outermost plane next to
+ * the face (z = 0 or nz - 1); *recv: the halo plane beyond the face (z = -1
+ * or nz), where the neighbour's outermost plane goes; *plane_bytes: the size
+ * of one such plane (whole padded planes, contiguous). Any output may be NULL.
+ * Queued halo and coefficient set-up work of the grid is issued first (on its
+ * stream), so that nothing overwrites a received plane later. Errors:
+ * WFA_ERR_ARG, WFA_ERR_BC (not an exchange face), WFA_ERR_STATE (k planes of
+ * a grid with uniform k). */
+int wfa_exchange_planes(wfa_grid g, int face, int what, void** send, void** recv, size_t* plane_bytes);
+
+/* Exchange planes between two slabs on one device: lower's +z exchange face
+ * meets upper's -z exchange face (lower == upper: one slab whose z axis wraps
+ * around). what: WFA_PLANES_FIELD (the current fields) or WFA_PLANES_K
+ * (per-cell k and 1/k; nothing for uniform k). Copies are queued on lower's
+ * stream after upper's queued work, and upper's later work waits for them.
+ * Errors: WFA_ERR_ARG (different nx, ny or storage, different devices),
+ * WFA_ERR_BC (not exchange faces), WFA_ERR_CUDA. */
+int wfa_exchange(wfa_grid lower, wfa_grid upper, int what);
+
+/* Advance the slabs gs[0 .. count-1] (in z order, one device) by n steps:
+ * the conductivity planes are exchanged once, then before every step the
+ * field planes of each pair of neighbouring slabs (and of the last and the
+ * first, when the z axis wraps), then every slab takes one step. The slabs
+ * need one dt. Errors: WFA_ERR_ARG, WFA_ERR_STATE (a slab without field,
+ * coefficients or dt), WFA_ERR_BC (neighbours that do not meet at exchange
+ * faces), WFA_ERR_CUDA. */
+int wfa_slabs_step(wfa_grid* gs, int count, long long n);
 
 /* ----------------------------------------------------------- batching -- */
 

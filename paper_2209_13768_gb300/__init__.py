@@ -23,9 +23,11 @@ LIB_PATH = os.path.join(_HERE, "libwfa.so")
 
 F32, BF16 = 0, 1
 CG_CLASSIC, CG_PIPELINED = 0, 1
-DIRICHLET, ZEROFLUX, PERIODIC, DIRICHLET_CELL = 0, 1, 2, 3
+DIRICHLET, ZEROFLUX, PERIODIC, DIRICHLET_CELL, EXCHANGE = 0, 1, 2, 3, 4
 BC_KINDS = {"dirichlet": DIRICHLET, "zeroflux": ZEROFLUX, "periodic": PERIODIC,
-            "dirichlet_cell": DIRICHLET_CELL}
+            "dirichlet_cell": DIRICHLET_CELL, "exchange": EXCHANGE}
+PLANES_FIELD, PLANES_K, PLANES_RECIP_K = 0, 1, 2
+ZLO, ZHI = 4, 5
 STATUS = {0: "WFA_OK", -1: "WFA_ERR_ARG", -2: "WFA_ERR_OOM", -3: "WFA_ERR_BC", -4: "WFA_ERR_UNSTABLE",
           -5: "WFA_ERR_CUDA", -6: "WFA_ERR_TIMEOUT", -7: "WFA_ERR_STATE", -8: "WFA_ERR_BUDGET"}
 
@@ -80,6 +82,9 @@ SIGNATURES = {
     "wfa_implicit_step": (_i, [_vp, _d, _ll, _d, _i, _llp, _dp]),
     "wfa_set_cg_method": (_i, [_vp, _i]),
     "wfa_batch_run": (_i, [ctypes.POINTER(_vp), _llp, _i]),
+    "wfa_exchange_planes": (_i, [_vp, _i, _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_sz)]),
+    "wfa_exchange": (_i, [_vp, _vp, _i]),
+    "wfa_slabs_step": (_i, [ctypes.POINTER(_vp), _i, _ll]),
     "wfa_server_create": (_i, [_sz, _i, _ll, ctypes.POINTER(_vp)]),
     "wfa_server_submit": (_i, [_vp, ctypes.POINTER(Request), _llp]),
     "wfa_server_poll": (_i, [_vp, _ll, _ip]),
@@ -288,6 +293,15 @@ class Grid:
                                       ctypes.byref(it), ctypes.byref(res)), "wfa_implicit_step")
         return it.value, res.value
 
+    def exchange_planes(self, face, what=PLANES_FIELD):
+        """(send, recv, plane_bytes): device addresses of this slab's outermost
+        plane next to an exchange face and of the halo plane beyond it (see
+        wfa_exchange_planes)."""
+        s, r, b = _vp(), _vp(), _sz()
+        check(lib().wfa_exchange_planes(self.handle, int(face), int(what), ctypes.byref(s), ctypes.byref(r),
+                                        ctypes.byref(b)), "wfa_exchange_planes")
+        return s.value, r.value, b.value
+
     def kernel_time(self):
         """(summed milliseconds, launches) of the sampled kernels since the last call."""
         ms, n = ctypes.c_double(), ctypes.c_longlong()
@@ -300,6 +314,18 @@ def sum_f32_noalloc(d_x, n, scale, d_out, stream=None):
     double at d_out, without allocating (see wfa_sum_f32_noalloc)."""
     check(lib().wfa_sum_f32_noalloc(_vp(d_x), int(n), float(scale), _vp(d_out), _vp(stream) if stream else None),
           "wfa_sum_f32_noalloc")
+
+
+def exchange(lower, upper, what=PLANES_FIELD):
+    """Copy planes across lower's +z and upper's -z exchange faces (see wfa_exchange)."""
+    check(lib().wfa_exchange(lower.handle, upper.handle, int(what)), "wfa_exchange")
+
+
+def slabs_step(slabs, n):
+    """Advance slabs of one grid (z order, one device) by n steps, exchanging
+    planes before every step (see wfa_slabs_step)."""
+    arr = (_vp * len(slabs))(*[g.handle for g in slabs])
+    check(lib().wfa_slabs_step(arr, len(slabs), int(n)), "wfa_slabs_step")
 
 
 def batch_run(grids, steps):

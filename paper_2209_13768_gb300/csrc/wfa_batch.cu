@@ -357,14 +357,30 @@ __global__ void __launch_bounds__(MG_THREADS, PersistOcc<CLS>::blocks)
 }
 
 // Launch (or query the occupancy of) the persistent kernel of class cls
-// (-1: every class).
+// (-1: every class). The launch is cooperative: the runtime starts it only
+// with all its blocks resident at once (or refuses it), which the kernel's
+// grid-wide barrier needs even while other streams keep SMs busy.
 cudaError_t persistent_kernel(int cls, bool launch, int* occ, int blocks, const unsigned char* dev, const PLayout& lay,
                               unsigned* count, cudaStream_t st) {
     int* status = reinterpret_cast<int*>(count + 1);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks > 0 ? blocks : 1);
+    cfg.blockDim = dim3(MG_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
 #define WFA_PERSIST_CASE(K)                                                                                   \
     case K:                                                                                                   \
-        if (launch) batch_persistent<K><<<blocks, MG_THREADS, 0, st>>>(dev, lay, count, status);              \
-        else return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, batch_persistent<K>, MG_THREADS, 0);   \
+        if (launch) {                                                                                         \
+            const cudaError_t e = cudaLaunchKernelEx(&cfg, batch_persistent<K>, dev, lay, count, status);     \
+            if (e != cudaSuccess) return e;                                                                   \
+        } else {                                                                                              \
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, batch_persistent<K>, MG_THREADS, 0);    \
+        }                                                                                                     \
         break;
     switch (cls) {
         WFA_PERSIST_CASE(-1)
@@ -502,6 +518,10 @@ extern "C" int wfa_batch_run(wfa_grid* gs, const long long* steps, int count) {
         if (g->stream != st) {
             set_error("wfa_batch_run: grid %d is on another stream than grid 0", i);
             return WFA_ERR_ARG;
+        }
+        if (has_exchange_face(g)) {
+            set_error("wfa_batch_run: grid %d has an exchange face (step slabs with wfa_slabs_step)", i);
+            return WFA_ERR_BC;
         }
         for (int j = 0; j < i; ++j)
             if (gs[j] == g) {

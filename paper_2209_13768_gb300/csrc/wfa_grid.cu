@@ -101,6 +101,17 @@ void dev_free(void* p, cudaStream_t st) {
     if (p) cudaFreeAsync(p, st);
 }
 
+cudaError_t padded_alloc(void** p, size_t bytes, int esize, cudaStream_t st) {
+    void* raw = nullptr;
+    const cudaError_t e = dev_alloc(&raw, bytes + LEAD_SLACK, st);
+    *p = e == cudaSuccess ? (char*)raw + lead_bytes(esize) : nullptr;
+    return e;
+}
+
+void padded_free(void* p, int esize, cudaStream_t st) {
+    if (p) dev_free((char*)p - lead_bytes(esize), st);
+}
+
 // Pinned host words (reduction results, status) carved from shared slabs of
 // 1024 slots of 64 bytes, so a grid costs no pinned allocation of its own.
 static std::mutex g_pin_mu;
@@ -140,6 +151,8 @@ int build_coef(const wfa_grid_s* g, SweepCoef* c) {
         const int lo = g->bc_kind[2 * a], hi = g->bc_kind[2 * a + 1];
         if ((lo == WFA_BC_PERIODIC) != (hi == WFA_BC_PERIODIC))
             return fail(WFA_ERR_BC, "axis %d: a periodic face needs a periodic opposite face", a);
+        if ((lo == WFA_BC_EXCHANGE || hi == WFA_BC_EXCHANGE) && a != 2)
+            return fail(WFA_ERR_BC, "axis %d: exchange faces are z faces", a);
         if ((lo == WFA_BC_DIRICHLET_CELL || hi == WFA_BC_DIRICHLET_CELL) && g->n[a] < 3)
             return fail(WFA_ERR_BC, "axis %d: held boundary cells need an edge >= 3", a);
         c->periodic[a] = lo == WFA_BC_PERIODIC;
@@ -158,8 +171,9 @@ int build_coef(const wfa_grid_s* g, SweepCoef* c) {
             c->bkind[f] = g->bc_kind[f];
             c->tb[f] = (float)g->bc_value[f];
             c->held[f] = g->bc_kind[f] == WFA_BC_DIRICHLET_CELL;
+            c->ext[f] = g->bc_kind[f] == WFA_BC_EXCHANGE;
             if (g->bc_kind[f] == WFA_BC_DIRICHLET) c->w_bd[f] = (float)(2.0 * g->k_uniform * cd + A);
-            else if (g->bc_kind[f] == WFA_BC_PERIODIC) c->w_bd[f] = c->w_in[f];
+            else if (g->bc_kind[f] == WFA_BC_PERIODIC || c->ext[f]) c->w_bd[f] = c->w_in[f];
             else c->w_bd[f] = 0.0f;
         }
         // a zero-flux face stops the advective flux: the cell keeps (or loses)
@@ -252,7 +266,14 @@ struct HaloSpec {
     int held[6];
     int dirichlet[6];   // face value on the face (ghost cells hold it)
     float gam[6];       // held-layer or Dirichlet value
+    int ext[6];         // exchange face: its halo planes hold the neighbour slab's values (left alone)
 };
+
+// Row (y, z) of the padded box lies in the halo planes beyond an exchange
+// face, which an exchange with the neighbouring slab fills (whole planes).
+__device__ __forceinline__ bool exchange_row(const HaloSpec& h, int z) {
+    return (h.ext[4] && z < 0) || (h.ext[5] && z >= h.n[2]);
+}
 
 // Dirichlet face whose ghost layer holds the halo cell c (outside the domain
 // on exactly one axis, and that axis not periodic), or -1.
@@ -344,6 +365,7 @@ __global__ void halo_kernel(S* __restrict__ base, const __grid_constant__ HaloSp
     for (long long r = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
         const int z = (int)(r / ey) - HALO;
         const int y = (int)(r - (long long)(z + HALO) * ey) - HALO;
+        if (exchange_row(h, z)) continue;
         const bool full = full_row(h, y, z);
         const int count = full ? h.n[0] + 2 * HALO : 2 * HALO + 2;
         for (int t = lane; t < count; t += 32) halo_cell<S>(base, h, row_x(h, full, t), y, z);
@@ -369,6 +391,7 @@ static HaloSpec halo_spec(const wfa_grid_s* g) {
         h.held[f] = g->bc_kind[f] == WFA_BC_DIRICHLET_CELL;
         h.dirichlet[f] = g->bc_kind[f] == WFA_BC_DIRICHLET;
         h.gam[f] = (float)g->bc_value[f];
+        h.ext[f] = g->bc_kind[f] == WFA_BC_EXCHANGE;
     }
     return h;
 }
@@ -523,7 +546,7 @@ __device__ __forceinline__ double rate64(const float* __restrict__ korigin, cons
             const int f = 2 * a + side;
             const bool edge = side == 0 ? c[a] == 0 : c[a] == r.n[a] - 1;
             bool active = true;
-            if (edge && r.kind[f] != WFA_BC_PERIODIC) {
+            if (edge && r.kind[f] != WFA_BC_PERIODIC && r.kind[f] != WFA_BC_EXCHANGE) {
                 if (r.kind[f] == WFA_BC_DIRICHLET) D += 2.0 * kC * r.inv_h2[a];
                 else active = false;
             } else {
@@ -554,7 +577,7 @@ __device__ __forceinline__ float rate32(const float* __restrict__ korigin, const
             const int f = 2 * a + side;
             const bool edge = side == 0 ? c[a] == 0 : c[a] == r.n[a] - 1;
             bool active = true;
-            if (edge && r.kind[f] != WFA_BC_PERIODIC) {
+            if (edge && r.kind[f] != WFA_BC_PERIODIC && r.kind[f] != WFA_BC_EXCHANGE) {
                 if (r.kind[f] == WFA_BC_DIRICHLET) D = __fadd_rn(D, __fmul_rn(__fmul_rn(2.0f, kC), r.inv_h2f[a]));
                 else active = false;
             } else {
@@ -674,6 +697,7 @@ __global__ void k_halo_kernel(float* __restrict__ base, const __grid_constant__ 
     for (long long r = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
         const int cz = (int)(r / ey) - HALO;
         const int cy = (int)(r - (long long)(cz + HALO) * ey) - HALO;
+        if (exchange_row(h, cz)) continue;
         const bool full = cy < 0 || cy >= h.n[1] || cz < 0 || cz >= h.n[2];
         const int count = full ? h.n[0] + 2 * HALO : 2 * HALO;
         for (int t = lane; t < count; t += 32) {
@@ -772,7 +796,7 @@ int wfa_create_grid(int nx, int ny, int nz, double hx, double hy, double hz, int
     cudaError_t e = cudaSuccess;
     g->own_T = true;
     g->own_k = true;
-    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = dev_alloc(&g->T[b], bytes, g->stream);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = padded_alloc(&g->T[b], bytes, g->esize, g->stream);
     if (e == cudaSuccess) e = dev_alloc((void**)&g->d_partials, 4096 * sizeof(double), g->stream);
     if (e == cudaSuccess) e = dev_alloc((void**)&g->d_status, 8 * sizeof(int), g->stream);
     if (e == cudaSuccess) {
@@ -797,10 +821,10 @@ int wfa_destroy_grid(wfa_grid g) {
     if (!g) return WFA_OK;
     cudaStreamSynchronize(g->stream);   // nothing of this grid is in flight below
     if (g->own_T)
-        for (int b = 0; b < 2; ++b) dev_free(g->T[b], g->stream);
+        for (int b = 0; b < 2; ++b) padded_free(g->T[b], g->esize, g->stream);
     if (g->own_k) {
-        dev_free(g->k, g->stream);
-        dev_free(g->r, g->stream);
+        padded_free(g->k, 4, g->stream);
+        padded_free(g->r, 4, g->stream);
     }
     dev_free(g->d_partials, g->stream);
     dev_free(g->d_stage, g->stream);
@@ -811,6 +835,7 @@ int wfa_destroy_grid(wfa_grid g) {
     free_timing(g);
     free_graphs(g);
     free_cg(g);
+    if (g->xev) cudaEventDestroy(g->xev);
     delete g;
     return WFA_OK;
 }
@@ -892,10 +917,10 @@ int wfa_set_coeffs(wfa_grid g, const float* k_host, double k_uniform, double ux,
             } else {
                 // both or neither: a grid never holds k without 1/k
                 float *kb = nullptr, *rb = nullptr;
-                WFA_CUDA(dev_alloc((void**)&kb, field_elems(g) * sizeof(float), g->stream));
-                const cudaError_t e = dev_alloc((void**)&rb, field_elems(g) * sizeof(float), g->stream);
+                WFA_CUDA(padded_alloc((void**)&kb, field_elems(g) * sizeof(float), 4, g->stream));
+                const cudaError_t e = padded_alloc((void**)&rb, field_elems(g) * sizeof(float), 4, g->stream);
                 if (e != cudaSuccess) {
-                    dev_free(kb, g->stream);
+                    padded_free(kb, 4, g->stream);
                     return cuda_fail(e, "conductivity allocation");
                 }
                 g->k = kb;
@@ -915,8 +940,8 @@ int wfa_set_coeffs(wfa_grid g, const float* k_host, double k_uniform, double ux,
         if (g->k) {
             cudaStreamSynchronize(g->stream);
             if (g->own_k) {
-                dev_free(g->k, g->stream);
-                dev_free(g->r, g->stream);
+                padded_free(g->k, 4, g->stream);
+                padded_free(g->r, 4, g->stream);
             }
             g->k = nullptr;
             g->r = nullptr;
@@ -935,7 +960,9 @@ int wfa_set_coeffs(wfa_grid g, const float* k_host, double k_uniform, double ux,
 int wfa_set_bc(wfa_grid g, int face, int kind, double value) {
     if (!g) return fail(WFA_ERR_ARG, "NULL grid");
     if (face < 0 || face > 5) return fail(WFA_ERR_ARG, "face %d out of range", face);
-    if (kind < 0 || kind > 3) return fail(WFA_ERR_ARG, "boundary kind %d out of range", kind);
+    if (kind < 0 || kind > WFA_BC_EXCHANGE) return fail(WFA_ERR_ARG, "boundary kind %d out of range", kind);
+    if (kind == WFA_BC_EXCHANGE && face < WFA_ZLO)
+        return fail(WFA_ERR_BC, "exchange faces are z faces (the grid is split into slabs along z)");
     if (!std::isfinite(value)) return fail(WFA_ERR_ARG, "boundary value must be finite");
     if (kind == WFA_BC_DIRICHLET_CELL && g->n[face / 2] < 3)
         return fail(WFA_ERR_BC, "held boundary cells need an edge >= 3");
@@ -1011,7 +1038,7 @@ static double uniform_rate_max(const RateSpec& r) {
                         const int f = 2 * a + side;
                         const bool edge = side == 0 ? c[a] == 0 : c[a] == r.n[a] - 1;
                         bool active = true;
-                        if (edge && r.kind[f] != WFA_BC_PERIODIC) {
+                        if (edge && r.kind[f] != WFA_BC_PERIODIC && r.kind[f] != WFA_BC_EXCHANGE) {
                             if (r.kind[f] == WFA_BC_DIRICHLET) D += 2.0 * kC * r.inv_h2[a];
                             else active = false;
                         } else {
@@ -1262,8 +1289,8 @@ int wfa_boundary_flux(wfa_grid g, double* flux) {
 
 int wfa_grid_buffer_bytes(wfa_grid g, size_t* field_bytes, size_t* k_bytes) {
     if (!g || !field_bytes || !k_bytes) return fail(WFA_ERR_ARG, "NULL argument");
-    *field_bytes = field_elems(g) * g->esize;
-    *k_bytes = field_elems(g) * sizeof(float);
+    *field_bytes = field_elems(g) * g->esize + LEAD_SLACK;
+    *k_bytes = field_elems(g) * sizeof(float) + LEAD_SLACK;
     return WFA_OK;
 }
 
@@ -1280,31 +1307,36 @@ int wfa_grid_attach_buffers(wfa_grid g, void* d_Ta, void* d_Tb, float* d_k, floa
         }
     }
     const size_t fb = field_elems(g) * g->esize, kb = field_elems(g) * sizeof(float);
+    // the padded arrays start lead_bytes() into the caller's buffers, as in the grid's own
+    char* ta = (char*)d_Ta + lead_bytes(g->esize);
+    char* tb = (char*)d_Tb + lead_bytes(g->esize);
+    float* ka = d_k ? (float*)((char*)d_k + lead_bytes(4)) : nullptr;
+    float* ra = d_r ? (float*)((char*)d_r + lead_bytes(4)) : nullptr;
     // the grid's current contents move into the caller's buffers
-    WFA_CUDA(cudaMemcpyAsync(d_Ta, g->T[0], fb, cudaMemcpyDeviceToDevice, g->stream));
-    WFA_CUDA(cudaMemcpyAsync(d_Tb, g->T[1], fb, cudaMemcpyDeviceToDevice, g->stream));
+    WFA_CUDA(cudaMemcpyAsync(ta, g->T[0], fb, cudaMemcpyDeviceToDevice, g->stream));
+    WFA_CUDA(cudaMemcpyAsync(tb, g->T[1], fb, cudaMemcpyDeviceToDevice, g->stream));
     if (d_k && g->k) {
-        WFA_CUDA(cudaMemcpyAsync(d_k, g->k, kb, cudaMemcpyDeviceToDevice, g->stream));
-        WFA_CUDA(cudaMemcpyAsync(d_r, g->r, kb, cudaMemcpyDeviceToDevice, g->stream));
+        WFA_CUDA(cudaMemcpyAsync(ka, g->k, kb, cudaMemcpyDeviceToDevice, g->stream));
+        WFA_CUDA(cudaMemcpyAsync(ra, g->r, kb, cudaMemcpyDeviceToDevice, g->stream));
     }
     WFA_CUDA(cudaStreamSynchronize(g->stream));
     if (g->own_T)
-        for (int b = 0; b < 2; ++b) dev_free(g->T[b], g->stream);
-    g->T[0] = d_Ta;
-    g->T[1] = d_Tb;
+        for (int b = 0; b < 2; ++b) padded_free(g->T[b], g->esize, g->stream);
+    g->T[0] = ta;
+    g->T[1] = tb;
     g->own_T = false;
     if (d_k) {
         if (g->k) {
             if (g->own_k) {
-                dev_free(g->k, g->stream);
-                dev_free(g->r, g->stream);
+                padded_free(g->k, 4, g->stream);
+                padded_free(g->r, 4, g->stream);
             }
-            g->k = d_k;
-            g->r = d_r;
+            g->k = ka;
+            g->r = ra;
             g->own_k = false;
         }
-        g->ext_k = d_k;
-        g->ext_r = d_r;
+        g->ext_k = ka;
+        g->ext_r = ra;
     }
     free_tmaps(g);   // descriptors name the old buffers
     return WFA_OK;

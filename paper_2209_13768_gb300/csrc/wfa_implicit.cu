@@ -1063,13 +1063,13 @@ void free_cg(wfa_grid_s* g) {
     for (int b = 0; b < 2; ++b) {
         if (w->ev[b]) cudaEventDestroy(w->ev[b]);
         pinned_release(w->h[b]);
-        dev_free(w->p[b], g->stream);
+        padded_free(w->p[b], 4, g->stream);
     }
     if (w->loop_exec) cudaGraphExecDestroy(w->loop_exec);
     dev_free(w->loop, g->stream);
-    for (float* e : w->extra) dev_free(e, g->stream);
-    dev_free(w->r, g->stream);
-    dev_free(w->q, g->stream);
+    for (float* e : w->extra) padded_free(e, 4, g->stream);
+    padded_free(w->r, 4, g->stream);
+    padded_free(w->q, 4, g->stream);
     dev_free(w->part, g->stream);
     dev_free(w->s, g->stream);
     delete w;
@@ -1088,9 +1088,10 @@ static int cg_workspace(wfa_grid_s* g, CgWork** out) {
     }
     g->cg = w;
     const size_t fb = field_elems(g) * sizeof(float);
-    cudaError_t e = dev_alloc((void**)&w->r, fb, g->stream);
-    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = dev_alloc((void**)&w->p[b], fb, g->stream);
-    if (e == cudaSuccess) e = dev_alloc((void**)&w->q, fb, g->stream);
+    // padded arrays in the field's layout (see lead_bytes)
+    cudaError_t e = padded_alloc((void**)&w->r, fb, 4, g->stream);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = padded_alloc((void**)&w->p[b], fb, 4, g->stream);
+    if (e == cudaSuccess) e = padded_alloc((void**)&w->q, fb, 4, g->stream);
     if (e == cudaSuccess) e = dev_alloc((void**)&w->part, 2 * CG_MAX_PART * sizeof(double), g->stream);
     if (e == cudaSuccess) e = dev_alloc((void**)&w->s, sizeof(CgState), g->stream);
     // the halos and held cells of the work vectors stay 0 (finite) for good
@@ -1304,6 +1305,10 @@ int wfa_implicit_step(wfa_grid g, double dt, long long n, double rtol, int max_i
             set_error("axis %d: a periodic face needs a periodic opposite face", a);
             return WFA_ERR_BC;
         }
+    if (has_exchange_face(g)) {   // a slab's CG would need the other slabs' inner products
+        set_error("wfa_implicit_step: exchange faces are for the explicit step only");
+        return WFA_ERR_BC;
+    }
     if (iters) *iters = 0;
     if (rel_res) *rel_res = 0.0;
     if (n == 0) return WFA_OK;
@@ -1363,7 +1368,7 @@ int wfa_implicit_step(wfa_grid g, double dt, long long n, double rtol, int max_i
         const size_t fb = field_elems(g) * sizeof(float);
         for (float*& e : w->extra)
             if (!e) {
-                WFA_CUDA(dev_alloc((void**)&e, fb, g->stream));
+                WFA_CUDA(padded_alloc((void**)&e, fb, 4, g->stream));
                 WFA_CUDA(cudaMemsetAsync(e, 0, fb, g->stream));
             }
         base.r2 = w->extra[0] + off;

@@ -13,6 +13,9 @@
 //   outside neighbour from the boundary condition.
 //   Per-cell conductivity k (fp32) uses the same layout (its periodic twins are
 //   written once by wfa_set_coeffs).
+//   Each padded array starts lead_bytes() into its allocation, so that domain
+//   column x = 0 (HALO elements into a row) falls on a 128-byte line: a row's
+//   4-cell vectors then fill whole lines (fewer L1 wavefronts per load).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -70,6 +73,8 @@ struct SweepCoef {
     float adv[6];          // A_f: upwind coefficient of face f: -face dt*max(u,0)/h, +face dt*max(-u,0)/h
     float s_lo[3], s_hi[3];  // self term of a cell on a zero-flux face with advection
     int held[6];           // face holds its outer cell layer (Dirichlet cell)
+    int ext[6];            // exchange face (z only): the neighbour values are in the halo layer,
+                           // written there by an exchange with the next slab; interior formula
     int any_self;          // some zero-flux face carries a self term
     int halo_bc;           // the halo encodes every boundary face (see build_coef): the
                            // interior formula is exact on boundary cells too
@@ -137,6 +142,7 @@ struct wfa_grid_s {
     void* graphs;         // wfa::StepGraphs (captured runs of passes for small grids)
     void* cg;             // wfa::CgWork (work vectors and graph of the implicit solver)
     int cg_method;        // WFA_CG_CLASSIC / WFA_CG_PIPELINED (wfa_set_cg_method)
+    cudaEvent_t xev;      // orders plane exchanges against this grid's stream (wfa_exchange)
 };
 
 namespace wfa {
@@ -145,6 +151,12 @@ inline long long domain_offset(const wfa_grid_s* g) {
     return ((long long)HALO * g->py + HALO) * g->px + HALO;
 }
 inline size_t field_elems(const wfa_grid_s* g) { return (size_t)g->px * g->py * g->pz; }
+// Bytes between an allocation and element 0 of the padded array it holds.
+inline size_t lead_bytes(int esize) { return (size_t)((128 - (HALO * esize) % 128) % 128); }
+constexpr size_t LEAD_SLACK = 128;   // an allocation holds the array plus this much
+inline bool has_exchange_face(const wfa_grid_s* g) {
+    return g->bc_kind[4] == WFA_BC_EXCHANGE || g->bc_kind[5] == WFA_BC_EXCHANGE;
+}
 
 int build_coef(const wfa_grid_s* g, SweepCoef* c);       // host: fp64 -> fp32 coefficients
 int refresh_halo(wfa_grid_s* g, int buf);                 // twins + held layers of one buffer
@@ -160,6 +172,9 @@ void free_timing(wfa_grid_s* g);
 void free_graphs(wfa_grid_s* g);
 cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st);   // grid memory pool, stream-ordered
 void dev_free(void* p, cudaStream_t st);
+// a padded array of `bytes` with elements of esize bytes (see lead_bytes)
+cudaError_t padded_alloc(void** p, size_t bytes, int esize, cudaStream_t st);
+void padded_free(void* p, int esize, cudaStream_t st);
 int grid_rebind_stream(wfa_grid_s* g, cudaStream_t st);          // move a quiet grid to another stream
 
 // ----------------------------------------------------------- device math --

@@ -239,6 +239,10 @@ static Choice choose(const wfa_grid_s* g) {
         ch = Choice{v, d};
     }
     if (g->force_zchunk) ch.zc = g->force_zchunk;
+    // exchange faces: the column kernels (one step a pass, the neighbour
+    // slab's plane read from the halo) or the one-column kernel
+    if (has_exchange_face(g) && ch.variant != COL_VARIANT && ch.variant != INPLACE_VARIANT && ch.variant >= 0)
+        ch = Choice{COL_VARIANT, 1, ch.zc};
     if (ch.variant < 0 || ch.variant == COL_VARIANT || ch.variant == INPLACE_VARIANT) ch.depth = 1;
     if (ch.variant == FUSED_VARIANT) ch.depth = g->k ? 1 : 2;   // per-cell k: the one-step column kernel
     return ch;
@@ -504,6 +508,7 @@ int autotune(wfa_grid_s* g, int* depth_out, int* variant_out) {
     for (const Choice& ch : cands) {
         if (e != cudaSuccess) break;
         if (ch.variant == FUSED_VARIANT && g->k) continue;   // uniform k only
+        if (has_exchange_face(g) && ch.variant != COL_VARIANT && ch.variant != INPLACE_VARIANT) continue;
         // one warm-up pass, then the timed passes
         rc = one_pass(g, c, ch.depth, ch.variant, ch.zc);
         if (rc) break;

@@ -64,9 +64,28 @@ __global__ void __launch_bounds__(1024) na_finish(const double* __restrict__ par
 
 // Device address of g_na_partials, looked up once per device with that
 // device current. In host code the array's name is only a host-side stand-in.
+// The address belongs to the device's current context: it is looked up again
+// when the context changes (after cudaDeviceReset the library's device image
+// is loaded afresh, possibly elsewhere).
 constexpr int NA_MAX_DEVICES = 64;
 std::mutex g_na_mu;
 double* g_na_addr[NA_MAX_DEVICES] = {};
+CUcontext g_na_ctx[NA_MAX_DEVICES] = {};
+
+using CtxGetCurrent = CUresult (*)(CUcontext*);
+
+CtxGetCurrent ctx_get_current() {
+    static CtxGetCurrent fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (CtxGetCurrent)p;
+    });
+    return fn;
+}
 
 int partials_address(double** out) {
     int dev = 0;
@@ -75,11 +94,18 @@ int partials_address(double** out) {
         wfa::set_error("wfa_sum_f32_noalloc: device ordinal %d out of range", dev);
         return WFA_ERR_ARG;
     }
+    // the current context (null on a thread the runtime has not bound to the
+    // device yet: the lookup below binds it, and the context is read again)
+    const CtxGetCurrent get = ctx_get_current();
+    CUcontext ctx = nullptr;
+    if (get && get(&ctx) != CUDA_SUCCESS) ctx = nullptr;
     std::lock_guard<std::mutex> lk(g_na_mu);
-    if (!g_na_addr[dev]) {
+    if (!g_na_addr[dev] || !ctx || ctx != g_na_ctx[dev]) {
         void* p = nullptr;
         WFA_CUDA(cudaGetSymbolAddress(&p, g_na_partials));
+        if (get && get(&ctx) != CUDA_SUCCESS) ctx = nullptr;
         g_na_addr[dev] = static_cast<double*>(p);
+        g_na_ctx[dev] = ctx;
     }
     *out = g_na_addr[dev];
     return WFA_OK;

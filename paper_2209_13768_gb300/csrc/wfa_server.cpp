@@ -198,7 +198,10 @@ void wfa_server_s::run() {
                 return stop || !pending.empty() || !resident.empty() || !ready.empty();
             });
             // admission: first come, first served, while memory and slots allow
-            while (!pending.empty() && (int)(resident.size() + ready.size() + to_setup.size()) < max_resident) {
+            // (a slot is held from admission on: queued for set-up, in set-up,
+            // ready or resident)
+            while (!pending.empty() &&
+                   (int)(resident.size() + ready.size() + to_setup.size()) + in_setup < max_resident) {
                 Req* r = pending.front();
                 if (used + r->bytes > budget) break;
                 pending.pop_front();

@@ -132,7 +132,7 @@ __device__ __forceinline__ float general_cell(const SweepCoef& c, const S* __res
         const bool edge = side ? pos[ax] == c.n[ax] - 1 : pos[ax] == 0;
         tn[f] = 0.0f;
         w[f] = 0.0f;
-        if (edge && !c.periodic[ax]) {
+        if (edge && !c.periodic[ax] && !c.ext[f]) {
             const bool dir = c.bkind[f] == WFA_BC_DIRICHLET;
             tn[f] = dir ? c.tb[f] : 0.0f;
             if (KVAR) w[f] = dir ? __fadd_rn(dirichlet_r(rc, c.tcd[ax]), c.adv[f]) : 0.0f;
@@ -222,7 +222,7 @@ __device__ __noinline__ float boundary_update(const SweepCoef* cp, float tc, flo
     for (int f = 0; f < 6; ++f) {
         const int ax = f >> 1;
         const bool edge = (f & 1) ? pos[ax] == c.n[ax] - 1 : pos[ax] == 0;
-        if (edge && !c.periodic[ax]) {
+        if (edge && !c.periodic[ax] && !c.ext[f]) {
             const bool dir = c.bkind[f] == WFA_BC_DIRICHLET;
             t[f] = dir ? c.tb[f] : 0.0f;
             if (KVAR) w[f] = dir ? __fadd_rn(dirichlet_r(rc, c.tcd[ax]), c.adv[f]) : 0.0f;

@@ -78,7 +78,7 @@ __device__ __forceinline__ float uniform_cell(const SweepCoef& c, float tc, floa
                                               float typ, float tzm, float tzp, int x, int y, int z) {
     const bool e0 = !c.periodic[0] && x == 0, e1 = !c.periodic[0] && x == c.n[0] - 1;
     const bool e2 = !c.periodic[1] && y == 0, e3 = !c.periodic[1] && y == c.n[1] - 1;
-    const bool e4 = !c.periodic[2] && z == 0, e5 = !c.periodic[2] && z == c.n[2] - 1;
+    const bool e4 = !c.periodic[2] && !c.ext[4] && z == 0, e5 = !c.periodic[2] && !c.ext[5] && z == c.n[2] - 1;
     auto tface = [&](int f) { return c.bkind[f] == WFA_BC_DIRICHLET ? c.tb[f] : 0.0f; };
     const float t0 = e0 ? tface(0) : txm, t1 = e1 ? tface(1) : txp;
     const float t2 = e2 ? tface(2) : tym, t3 = e3 ? tface(3) : typ;
@@ -213,7 +213,7 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
         ColNb<S, KVAR, COH> nb;                          // x / y neighbours, plane z
         nb.load(tp, rp, sy);
 
-        const bool bzm = !perz && z == 0, bzp = !perz && z == c.n[2] - 1;
+        const bool bzm = !perz && !c.ext[4] && z == 0, bzp = !perz && !c.ext[5] && z == c.n[2] - 1;
         // GHOST (c.halo_bc known at compile time) or c.halo_bc: the ghost layers hold the faces
         const bool fast = GHOST || c.halo_bc || (inner_xy && !bzm && !bzp);
         float xf[5], gzp[4];
@@ -337,7 +337,7 @@ template <typename S, bool KVAR>
 __global__ void __launch_bounds__(256) boundary_fix(const __grid_constant__ SweepArgs a) {
     const SweepCoef& c = a.c;
     const int f = blockIdx.y, ax = f >> 1;
-    if (c.periodic[ax]) return;
+    if (c.periodic[ax] || c.ext[f]) return;   // no boundary cells on this face
     const int b = ax == 0 ? 1 : 0, d = ax == 2 ? 1 : 2;
     const unsigned nb = (unsigned)c.n[b], plane = nb * (unsigned)c.n[d];
     int pos[3];

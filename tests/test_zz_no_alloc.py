@@ -1,7 +1,12 @@
 """The allocation-free field sum (wfa_sum_f32_noalloc), for callers that cannot
 allocate device memory: through the C ABI it must agree with the total-heat
 reduction of a grid holding the same field (which sums with scratch the grid
-allocated), on two calls in a row. This file is collected last on purpose."""
+allocated), on two calls in a row.
+
+The tests here depend on no other test and pass alone in a fresh process as
+well as after the rest of the suite. The file name only makes pytest collect
+it last, so that a run stopping at the first failure (-x) has run every other
+test before it reaches this one."""
 import ctypes
 
 import numpy as np
