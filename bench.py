@@ -698,8 +698,11 @@ def split_bench(args, rank, world, dist, local):
         interfaces = world if s.wrap else world - 1
     else:
         nslabs = args.slabs or 2
-        s = slabs.SlabGrid(p.shape, nslabs, h=p.h, storage=storage,
-                           stream=stream.cuda_stream or None, bc=p.bc)
+        # one stream per slab (their kernels overlap), timed on the first one:
+        # wfa_slabs_step makes every slab's step wait for its neighbours' planes
+        streams = [stream] + [torch.cuda.Stream() for _ in range(nslabs - 1)]
+        s = slabs.SlabGrid(p.shape, nslabs, h=p.h, storage=storage, bc=p.bc,
+                           streams=[st.cuda_stream or None for st in streams])
         s.set_field(p.T0)
         s.set_coeffs(p.k, p.u)
         interfaces = nslabs if p.bc[4][0] == "periodic" else nslabs - 1
@@ -714,9 +717,12 @@ def split_bench(args, rank, world, dist, local):
         dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
+    others = streams[1:] if world == 1 else []
     for i in range(args.steps):
         ev[i][0].record(stream)
         s.step(p.steps)
+        for st in others:   # the other slabs' last steps end inside the timed step
+            stream.wait_stream(st)
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()

@@ -51,14 +51,19 @@ class SlabGrid:
     """A grid of shape (nx, ny, nz) held as `parts` slabs on one device.
 
     Arrays are [z, y, x] as for ``Grid``; results are bitwise those of one
-    ``Grid`` of the same shape (the slabs see the same operands)."""
+    ``Grid`` of the same shape (the slabs see the same operands).
+    stream: one CUDA stream for every slab, or `streams`: one per slab (the
+    slabs' kernels then overlap; the plane copies wait for both sides)."""
 
-    def __init__(self, shape, parts, h=(1.0, 1.0, 1.0), storage=F32, stream=None, bc=None):
+    def __init__(self, shape, parts, h=(1.0, 1.0, 1.0), storage=F32, stream=None, bc=None, streams=None):
         self.shape = tuple(int(s) for s in shape)
         self.ranges = split_z(self.shape[2], parts)
         self.bc = list(bc) if bc else [("zeroflux", 0.0)] * 6
-        self.slabs = [Grid((self.shape[0], self.shape[1], z1 - z0), h=h, storage=storage, stream=stream)
-                      for z0, z1 in self.ranges]
+        streams = list(streams) if streams else [stream] * parts
+        if len(streams) != parts:
+            raise ValueError("one stream per slab")
+        self.slabs = [Grid((self.shape[0], self.shape[1], z1 - z0), h=h, storage=storage, stream=st)
+                      for (z0, z1), st in zip(self.ranges, streams)]
         self.set_bcs(self.bc)
 
     def close(self):

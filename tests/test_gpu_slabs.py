@@ -73,6 +73,24 @@ def test_slabs_bitwise_equal_whole_grid(mix, kvar, adv):
             assert s.total_heat() == pytest.approx(heat, rel=1e-12, abs=1e-9)
 
 
+@pytest.mark.parametrize("mix", [0, 3, 5])
+def test_slabs_on_their_own_streams(mix):
+    """Each slab on its own stream: the exchanges order the streams."""
+    torch = pytest.importorskip("torch")
+    p = _problem(mix, kvar=mix != 3, adv=True, seed=20 + mix)
+    dt = 0.9 * _dt(p)
+    ref, _ = _whole(p, wfa.F32, dt)
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    with slabs.SlabGrid(p.shape, 3, h=p.h, bc=p.bc, streams=[s.cuda_stream for s in streams]) as s:
+        s.set_coeffs(p.k, p.u)
+        s.set_field(p.T0)
+        s.set_dt(dt)
+        s.set_tuning(1, 3)
+        s.step(p.steps)
+        s.sync()
+        np.testing.assert_array_equal(s.read_field(), ref)
+
+
 @pytest.mark.parametrize("mix", [0, 2, 4, 6])
 def test_slabs_bf16(mix):
     p = _problem(mix, kvar=True, adv=True, seed=10 + mix)
