@@ -49,8 +49,8 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-6, help="implicit: CG tolerance ||r|| <= rtol ||b||")
     ap.add_argument("--cg", choices=["classic", "pipelined"], default="classic",
                     help="implicit: classic CG or Chronopoulos-Gear (one reduction an iteration)")
-    ap.add_argument("--serve-requests", type=int, default=400,
-                    help="requests in the serving sample added to the line (0: none)")
+    ap.add_argument("--serve-requests", type=int, default=10000,
+                    help="requests of the serving stream added to the line (0: none; 10^4 at 200/s is 50 s)")
     ap.add_argument("--solve-steps", type=int, default=0, help="time steps per benchmark step (0: workload default)")
     ap.add_argument("--shape", type=str, default="", help="NX,NY,NZ: same physics on another grid (profiling)")
     ap.add_argument("--depth", type=int, default=0, help="fused steps per pass (0: tuned)")
@@ -259,66 +259,122 @@ def reference_arm(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def serving_sample(n_requests, rate=200.0, seed=5, pool=24, quantum=64):
-    """Poisson arrivals (rate per second) of heat / advection-diffusion solves,
-    edges log-uniform in [32, 256], steps U{50..2000}, fp32 or bf16.
-    Inputs come from a pool of `pool` request shapes (generated once); each
-    arrival keeps its own time, step count and storage. Runs the stream through
-    the continuous-batching server and through the plain form (one grid at a
-    time, first come first served, wfa_step), and reports both."""
-    import numpy as np
+def _pct(v, q):
+    v = sorted(v)
+    return v[min(len(v) - 1, int(q * (len(v) - 1) + 0.5))] if v else None
+
+
+def serving_sample(n_requests, rate=200.0, seed=5, quantum=64, fifo_requests=1000, lookahead=192):
+    """The serving configuration: Poisson arrivals (rate per second) of heat /
+    advection-diffusion solves, each with its own shape (edges log-uniform in
+    [32, 256]) and its own fields, steps U{50..2000}, fp32 or bf16, through the
+    continuous-batching server (HBM budget 120 GB); then the first
+    fifo_requests arrivals of the same stream through the plain form (one grid
+    at a time, first come first served, wfa_step). Worker threads generate each
+    request's fields ahead of its arrival (at most `lookahead` in host memory).
+    Latency: from the scheduled arrival to the result on the host (the
+    server's submit-to-result time plus how late the submit was)."""
+    import concurrent.futures as cf
+    import threading
 
     import paper_2209_13768_gb300 as wfa
     from paper_2209_13768_gb300 import workloads as W
-    arrivals = W.request_stream(rate=rate, count=n_requests, seed=seed, pool=pool)
-    reqs = [(a.t, a.problem, a.problem.steps, a.storage) for a in arrivals]
-    updates = sum(p.shape[0] * p.shape[1] * p.shape[2] * n for _, p, n, _ in reqs)
+    specs = W.request_specs(rate=rate, count=n_requests, seed=seed)
+    cells = [s.shape[0] * s.shape[1] * s.shape[2] for s in specs]
+    updates = [c * s.steps for c, s in zip(cells, specs)]
+
+    def stream(count):
+        """(spec, problem) in arrival order, generated ahead by a thread pool."""
+        with cf.ThreadPoolExecutor(8) as ex:
+            futs = {}
+            for i in range(min(lookahead, count)):
+                futs[i] = ex.submit(W.make_request, specs[i])
+            for i in range(count):
+                p = futs.pop(i).result()
+                if i + lookahead < count:
+                    futs[i + lookahead] = ex.submit(W.make_request, specs[i + lookahead])
+                yield specs[i], p
 
     def run_server():
-        lat = []
+        late, lat = [], [None] * n_requests
+        pending = []                  # (index, ticket, lateness) not yet collected
+        lock = threading.Lock()
+        stop = threading.Event()
         with wfa.Server(budget_bytes=120 << 30, quantum=quantum) as srv:
-            t0 = time.perf_counter()
-            tickets = []
-            for t, p, n, st in reqs:
-                dt = t - (time.perf_counter() - t0)
-                if dt > 0:
-                    time.sleep(dt)
-                tickets.append((srv.submit(p.shape, p.T0, n, h=p.h, storage=st, k=p.k, u=p.u, bc=p.bc, dt=p.dt), t))
-            for tk, t in tickets:
-                srv.wait(tk, timeout=600)
-            wall = time.perf_counter() - t0
-            stats = srv.stats()
-        return wall, stats
 
-    def run_fifo():
+            def collect():            # latencies of finished tickets, freeing their arrays
+                while True:
+                    with lock:
+                        items = list(pending)
+                    left = []
+                    for i, tk, lt in items:
+                        if srv.poll(tk) == 1:
+                            lat[i] = srv.latency(tk) + lt
+                            srv.wait(tk, timeout=1.0)
+                        else:
+                            left.append((i, tk, lt))
+                    with lock:
+                        done = {i for i, _, _ in items} - {i for i, _, _ in left}
+                        pending[:] = [e for e in pending if e[0] not in done]
+                        empty = not pending
+                    if stop.is_set() and empty:
+                        return
+                    time.sleep(0.002)
+
+            th = threading.Thread(target=collect)
+            th.start()
+            t0 = time.perf_counter()
+            for i, (spec, p) in enumerate(stream(n_requests)):
+                wait = spec.t - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(wait)
+                lateness = max(0.0, time.perf_counter() - t0 - spec.t)
+                tk = srv.submit(p.shape, p.T0, spec.steps, h=p.h, storage=spec.storage, k=p.k, u=p.u, bc=p.bc,
+                                dt=p.dt)
+                late.append(lateness)
+                with lock:
+                    pending.append((i, tk, lateness))
+            stop.set()
+            th.join()
+            wall = time.perf_counter() - t0
+            st = srv.stats()
+        return wall, lat, late, st
+
+    def run_fifo(count):
         lat = []
         t0 = time.perf_counter()
-        for t, p, n, st in reqs:
-            dt = t - (time.perf_counter() - t0)
-            if dt > 0:
-                time.sleep(dt)
-            with wfa.Grid(p.shape, h=p.h, storage=st) as g:
+        for spec, p in stream(count):
+            wait = spec.t - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            with wfa.Grid(p.shape, h=p.h, storage=spec.storage) as g:
                 g.set_bcs(p.bc)
                 g.set_coeffs(p.k, p.u)
                 g.set_field(p.T0)
                 g.set_dt(p.dt if p.dt else 0.9 * g.stability_dt())
-                g.step(n)
+                g.step(spec.steps)
                 g.read_field()
-            lat.append(time.perf_counter() - t0 - t)
-        wall = time.perf_counter() - t0
-        lat.sort()
-        return wall, lat
+            lat.append(time.perf_counter() - t0 - spec.t)
+        return time.perf_counter() - t0, lat
 
-    wall_s, st = run_server()
-    wall_f, lat_f = run_fifo()
-    pct = lambda v, q: v[min(len(v) - 1, int(q * (len(v) - 1) + 0.5))]
-    return {"requests": len(reqs), "rate_per_s": rate, "offered_GLUPS": updates / reqs[-1][0] / 1e9,
-            "continuous_batching": {"GLUPS": updates / wall_s / 1e9, "p50_s": st["p50_latency_s"],
-                                    "p99_s": st["p99_latency_s"], "wall_s": wall_s, "ticks": st["ticks"],
-                                    "gpu_busy_s": st["busy_seconds"]},
-            "one_grid_per_launch_fifo": {"GLUPS": updates / wall_f / 1e9, "p50_s": pct(lat_f, 0.5),
-                                         "p99_s": pct(lat_f, 0.99), "wall_s": wall_f},
-            "inputs": f"pool of {pool} request shapes from the serving request stream"}
+    wall_s, lat_s, late, st = run_server()
+    nf = min(fifo_requests, n_requests)
+    wall_f, lat_f = run_fifo(nf)
+    thirds = [lat_s[i * n_requests // 3:(i + 1) * n_requests // 3] for i in range(3)]
+    span = specs[-1].t
+    return {"requests": n_requests, "rate_per_s": rate, "arrival_span_s": span,
+            "offered_GLUPS": sum(updates) / span / 1e9,
+            "inputs": "every request its own shape and fields (seeded), generated ahead of its arrival",
+            "continuous_batching": {
+                "GLUPS": sum(updates) / wall_s / 1e9, "wall_s": wall_s, "p50_s": _pct(lat_s, 0.5),
+                "p99_s": _pct(lat_s, 0.99), "p99_s_by_third_of_stream": [_pct(t, 0.99) for t in thirds],
+                "p50_s_by_third_of_stream": [_pct(t, 0.5) for t in thirds], "ticks": st["ticks"],
+                "gpu_busy_s": st["busy_seconds"], "peak_resident_GB": st["peak_resident_bytes"] / 1e9,
+                "max_submit_lateness_s": max(late) if late else 0.0},
+            "one_grid_per_launch_fifo": {
+                "requests": nf, "GLUPS": sum(updates[:nf]) / wall_f / 1e9, "wall_s": wall_f,
+                "p50_s": _pct(lat_f, 0.5), "p99_s": _pct(lat_f, 0.99),
+                "stream": f"the first {nf} arrivals of the same stream"}}
 
 
 def batch_bench(args, emit=True):

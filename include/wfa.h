@@ -455,6 +455,12 @@ int wfa_server_poll(wfa_server s, long long ticket, int* done);
  * Serving (see the note above); no counterpart call in the paper. */
 int wfa_server_wait(wfa_server s, long long ticket, double timeout_s);
 
+/* Latency of a finished request: seconds from its wfa_server_submit to its
+ * result in out_host. WFA_ERR_STATE while it is not done (or if it failed),
+ * WFA_ERR_ARG for an unknown ticket. Serving metrics (see the note above); no
+ * counterpart call in the paper. */
+int wfa_server_latency(wfa_server s, long long ticket, double* seconds);
+
 /* Counters and latency percentiles of the server so far (see
  * wfa_server_stats). Serving (see the note above); the iteration-rate and
  * latency figures the paper reports for single solves (Sec. 4) become

@@ -89,6 +89,7 @@ SIGNATURES = {
     "wfa_server_submit": (_i, [_vp, ctypes.POINTER(Request), _llp]),
     "wfa_server_poll": (_i, [_vp, _ll, _ip]),
     "wfa_server_wait": (_i, [_vp, _ll, _d]),
+    "wfa_server_latency": (_i, [_vp, _ll, _dp]),
     "wfa_server_stats_get": (_i, [_vp, ctypes.POINTER(ServerStats)]),
     "wfa_server_destroy": (_i, [_vp]),
 }
@@ -387,6 +388,12 @@ class Server:
         check(lib().wfa_server_wait(self.handle, int(ticket), float(timeout)), "wfa_server_wait")
         kept = self._keep.pop(ticket, None)
         return kept[0] if kept else None
+
+    def latency(self, ticket):
+        """Seconds from submit to result on the host of a finished ticket."""
+        v = ctypes.c_double()
+        check(lib().wfa_server_latency(self.handle, int(ticket), ctypes.byref(v)), "wfa_server_latency")
+        return v.value
 
     def stats(self):
         st = ServerStats()

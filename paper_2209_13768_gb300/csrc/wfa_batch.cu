@@ -84,7 +84,7 @@ __device__ __forceinline__ void mg_unit(const MgGrid& sg, int u, long long step,
     const int gx = 4 * (col % sg.ncx), gy = col / sg.ncx;
     const int z0 = chunk * sg.zchunk;
     const int z1 = min(z0 + sg.zchunk, sg.c.n[2]);
-    col_run<S, KVAR, ADV, COH, 1, false, true, GHOST>(sg.c, (const S*)sg.tb[step & 1], (S*)sg.tb[(step + 1) & 1],
+    col_run<S, KVAR, ADV, COH, 1, COL_INPLACE, true, GHOST>(sg.c, (const S*)sg.tb[step & 1], (S*)sg.tb[(step + 1) & 1],
                                                         sg.rk, status, gx, gy, z0, z1);
 }
 
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(MG_THREADS, (ColOcc<false, false, sizeof(S)>::
     const int gx = 4 * (col % sg.ncx), gy = col / sg.ncx;
     const int z0 = chunk * sg.zchunk;
     const int z1 = min(z0 + sg.zchunk, sg.c.n[2]);
-    col_run<S, false, false, false, ColOcc<false, false, sizeof(S)>::unroll, true, true>(
+    col_run<S, false, false, false, ColOcc<false, false, sizeof(S)>::unroll, COL_MAIN, true>(
         sg.c, (const S*)sg.tb[step & 1], (S*)sg.tb[(step + 1) & 1], nullptr, nullptr, gx, gy, z0, z1);
 }
 
@@ -799,6 +799,9 @@ extern "C" int wfa_batch_run(wfa_grid* gs, const long long* steps, int count) {
     for (int k = 0; k < ng; ++k) {
         wfa_grid g = gs[order[k]];
         g->cur = (int)((g->cur + mg[k].steps) & 1);
+        // the batched passes write every periodic copy (corners included)
+        g->thin[g->cur] = false;
+        if (mg[k].steps >= 2) g->thin[1 - g->cur] = false;
         g->steps_done += mg[k].steps;
     }
     return WFA_OK;

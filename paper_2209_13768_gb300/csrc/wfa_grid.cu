@@ -410,6 +410,7 @@ int refresh_halo(wfa_grid_s* g, int buf) {
             halo_kernel<float><<<grid_blocks(rows * 32, thr), thr, 0, g->stream>>>((float*)g->T[b], h);
         WFA_CUDA(cudaGetLastError());
     }
+    g->thin[0] = g->thin[1] = false;   // every periodic copy, corners included
     return WFA_OK;
 }
 
@@ -1123,7 +1124,7 @@ int wfa_set_dt(wfa_grid g, double dt) {
 int wfa_set_tuning(wfa_grid g, int depth, int variant) {
     if (!g) return fail(WFA_ERR_ARG, "NULL grid");
     if (depth < 0 || depth > MAX_DEPTH) return fail(WFA_ERR_ARG, "depth must be 0..%d", MAX_DEPTH);
-    if (variant < -1 || variant > INPLACE_VARIANT) return fail(WFA_ERR_ARG, "variant must be -1..%d", INPLACE_VARIANT);
+    if (variant < -1 || variant > T2_VARIANT) return fail(WFA_ERR_ARG, "variant must be -1..%d", T2_VARIANT);
     g->force_depth = depth;
     g->force_variant = variant;
     return WFA_OK;

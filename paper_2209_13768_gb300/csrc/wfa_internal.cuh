@@ -37,6 +37,8 @@ constexpr int NUM_TILE_VARIANTS = 2;  // tile shapes compiled per (storage, k mo
 constexpr int COL_VARIANT = 3;        // the one-step column-march kernel
 constexpr int FUSED_VARIANT = 4;      // the two-step column-march kernel (uniform k)
 constexpr int INPLACE_VARIANT = 5;    // the one-step column-march kernel, boundaries in place
+constexpr int WIDE_VARIANT = 6;       // the one-step column-march kernel, 8 cells a thread
+constexpr int T2_VARIANT = 7;         // two steps per pass, TMA-staged planes (uniform k)
 
 // NVTX range over one API call: a named span on a profiler's timeline
 // (nothing happens unless a tool is attached).
@@ -143,6 +145,8 @@ struct wfa_grid_s {
     void* cg;             // wfa::CgWork (work vectors and graph of the implicit solver)
     int cg_method;        // WFA_CG_CLASSIC / WFA_CG_PIPELINED (wfa_set_cg_method)
     cudaEvent_t xev;      // orders plane exchanges against this grid's stream (wfa_exchange)
+    bool thin[2];         // buffer's periodic copies hold one layer without corners (a thin column
+                          // pass wrote it): enough for one-step kernels, not for the tiled ones
 };
 
 namespace wfa {

@@ -241,10 +241,12 @@ static Choice choose(const wfa_grid_s* g) {
     if (g->force_zchunk) ch.zc = g->force_zchunk;
     // exchange faces: the column kernels (one step a pass, the neighbour
     // slab's plane read from the halo) or the one-column kernel
-    if (has_exchange_face(g) && ch.variant != COL_VARIANT && ch.variant != INPLACE_VARIANT && ch.variant >= 0)
+    if (has_exchange_face(g) && ch.variant != COL_VARIANT && ch.variant != INPLACE_VARIANT &&
+        ch.variant != WIDE_VARIANT && ch.variant >= 0)
         ch = Choice{COL_VARIANT, 1, ch.zc};
-    if (ch.variant < 0 || ch.variant == COL_VARIANT || ch.variant == INPLACE_VARIANT) ch.depth = 1;
-    if (ch.variant == FUSED_VARIANT) ch.depth = g->k ? 1 : 2;   // per-cell k: the one-step column kernel
+    if (ch.variant < 0 || ch.variant == COL_VARIANT || ch.variant == INPLACE_VARIANT || ch.variant == WIDE_VARIANT)
+        ch.depth = 1;
+    if (ch.variant == FUSED_VARIANT || ch.variant == T2_VARIANT) ch.depth = g->k ? 1 : 2;   // per-cell k: one step
     return ch;
 }
 
@@ -294,14 +296,35 @@ static SweepArgs base_args(wfa_grid_s* g, const SweepCoef& c, int in_buf, int zc
 static int pass_launches(const wfa_grid_s* g, const SweepCoef& c, int depth, int variant) {
     const int periodic = c.periodic[0] + c.periodic[1] + c.periodic[2];
     if (variant == FUSED_VARIANT && depth == 2 && !g->r) return 1 + periodic;
-    if (variant == COL_VARIANT || variant == FUSED_VARIANT)
-        return 1 + (periodic < 3 && !c.halo_bc ? 1 : 0) + periodic;
+    if (variant == COL_VARIANT || variant == WIDE_VARIANT || variant == FUSED_VARIANT || variant == T2_VARIANT) {   // thin pass
+        bool faces = false;   // boundary cells the ghost layers do not hold: one boundary_fix launch
+        for (int ax = 0; ax < 3; ++ax) faces = faces || (!c.periodic[ax] && !(c.ext[2 * ax] && c.ext[2 * ax + 1]));
+        return 1 + (faces && !c.halo_bc ? 1 : 0);
+    }
     return 1;
+}
+
+// The pass reads periodic copies beyond the first layer (or corner copies):
+// the tiled kernels and the two-step column kernel.
+static bool needs_full_twins(const wfa_grid_s* g, int depth, int variant) {
+    if (variant == FUSED_VARIANT || variant == T2_VARIANT) return depth == 2 && !g->r;
+    return variant >= 1 && variant <= NUM_TILE_VARIANTS;
+}
+// The pass writes one layer of periodic copies only (the thin column pass).
+static bool writes_thin_twins(const wfa_grid_s* g, const SweepCoef& c, int depth, int variant) {
+    if (!c.periodic[0] && !c.periodic[1] && !c.periodic[2]) return false;
+    const bool two = (variant == FUSED_VARIANT || variant == T2_VARIANT) && depth == 2 && !g->r;
+    return !two && (variant == COL_VARIANT || variant == WIDE_VARIANT || variant == FUSED_VARIANT || variant == T2_VARIANT);
 }
 
 // One pass of `depth` fused steps from buffer g->cur into the other buffer
 // (zc: planes per z chunk of the column kernels, 0 = automatic).
 static int one_pass(wfa_grid_s* g, const SweepCoef& c, int depth, int variant, int zc = 0) {
+    if (needs_full_twins(g, depth, variant) && g->thin[g->cur]) {   // complete the copies first
+        const int rc = refresh_halo(g, g->cur);
+        if (rc) return rc;
+    }
+    g->thin[1 - g->cur] = writes_thin_twins(g, c, depth, variant);
     g->launches += pass_launches(g, c, depth, variant);
     SweepArgs a = base_args(g, c, g->cur, zc);
     const cudaEvent_t* ev = timing_slot(g);
@@ -317,6 +340,16 @@ static int one_pass(wfa_grid_s* g, const SweepCoef& c, int depth, int variant, i
         g->cur = 1 - g->cur;
         return WFA_OK;
     }
+    if (variant == T2_VARIANT && depth == 2 && !g->r) {   // two steps, TMA-staged planes (uniform k)
+        TmapCache* tm = nullptr;
+        int rc = get_tmaps(g, 80, 20, &tm);
+        if (rc) return rc;
+        cudaError_t e = g->storage == WFA_BF16 ? launch_t2_bf16_u(&tm->t[g->cur], a, g->stream, num_sms(), ev)
+                                               : launch_t2_f32_u(&tm->t[g->cur], a, g->stream, num_sms(), ev);
+        if (e != cudaSuccess) return cuda_fail(e, "sweep_t2 launch");
+        g->cur = 1 - g->cur;
+        return WFA_OK;
+    }
     if (variant == FUSED_VARIANT && depth == 2 && !g->r) {   // two-step column march (uniform k)
         cudaError_t e = g->storage == WFA_BF16 ? launch_col2_bf16_u(a, g->stream, num_sms(), ev)
                                                : launch_col2_f32_u(a, g->stream, num_sms(), ev);
@@ -324,15 +357,16 @@ static int one_pass(wfa_grid_s* g, const SweepCoef& c, int depth, int variant, i
         g->cur = 1 - g->cur;
         return WFA_OK;
     }
-    if (variant == COL_VARIANT || variant == FUSED_VARIANT || variant == INPLACE_VARIANT) {   // column march, one step
-        const bool inl = variant == INPLACE_VARIANT;
+    if (variant == COL_VARIANT || variant == FUSED_VARIANT || variant == INPLACE_VARIANT || variant == T2_VARIANT ||
+        variant == WIDE_VARIANT) {   // column march, one step
+        const bool inl = variant == INPLACE_VARIANT, wide = variant == WIDE_VARIANT;
         cudaError_t e;
         if (g->storage == WFA_BF16)
-            e = g->r ? launch_col_bf16_k(a, g->stream, num_sms(), ev, inl)
-                     : launch_col_bf16_u(a, g->stream, num_sms(), ev, inl);
+            e = g->r ? launch_col_bf16_k(a, g->stream, num_sms(), ev, inl, wide)
+                     : launch_col_bf16_u(a, g->stream, num_sms(), ev, inl, wide);
         else
-            e = g->r ? launch_col_f32_k(a, g->stream, num_sms(), ev, inl)
-                     : launch_col_f32_u(a, g->stream, num_sms(), ev, inl);
+            e = g->r ? launch_col_f32_k(a, g->stream, num_sms(), ev, inl, wide)
+                     : launch_col_f32_u(a, g->stream, num_sms(), ev, inl, wide);
         if (e != cudaSuccess) return cuda_fail(e, "sweep_col launch");
         g->cur = 1 - g->cur;
         return WFA_OK;
@@ -411,6 +445,7 @@ static int run_graph(wfa_grid_s* g, const SweepCoef& c, const Choice& ch, cudaGr
         const cudaStream_t user = g->stream;
         const int cur0 = g->cur;
         const long long launches0 = g->launches;
+        const bool thin0[2] = {g->thin[0], g->thin[1]};
         g->stream = gs->stream;
         cudaError_t e = cudaStreamBeginCapture(gs->stream, cudaStreamCaptureModeThreadLocal);
         int rc = WFA_OK;
@@ -421,6 +456,8 @@ static int run_graph(wfa_grid_s* g, const SweepCoef& c, const Choice& ch, cudaGr
         g->stream = user;
         g->cur = cur0;
         g->launches = launches0;
+        g->thin[0] = thin0[0];
+        g->thin[1] = thin0[1];
         if (e == cudaSuccess) e = e2;
         if (e == cudaSuccess && !rc) e = cudaGraphInstantiate(&sl.exec, graph, 0);
         if (graph) cudaGraphDestroy(graph);
@@ -447,6 +484,10 @@ int launch_sweep(wfa_grid_s* g, long long nsteps) {
     const long long runs = nsteps / ((long long)ch.depth * GRAPH_PASSES);
     if (cells <= GRAPH_MAX_CELLS && runs >= 2) {
         cudaGraphExec_t exec = nullptr;
+        if (needs_full_twins(g, ch.depth, ch.variant) && g->thin[g->cur]) {   // not inside the graph
+            rc = refresh_halo(g, g->cur);
+            if (rc) return rc;
+        }
         const int every = g->timing_every;
         g->timing_every = 0;   // no event records inside the captured passes
         rc = run_graph(g, c, ch, &exec);
@@ -461,6 +502,7 @@ int launch_sweep(wfa_grid_s* g, long long nsteps) {
         }
         g->launches += runs * GRAPH_PASSES * pass_launches(g, c, ch.depth, ch.variant);
         nsteps -= runs * GRAPH_PASSES * ch.depth;
+        g->thin[0] = g->thin[1] = writes_thin_twins(g, c, ch.depth, ch.variant);   // both written by the run
     }
     while (nsteps > 0) {
         const int d = (int)std::min<long long>(ch.depth, nsteps);
@@ -484,7 +526,7 @@ int autotune(wfa_grid_s* g, int* depth_out, int* variant_out) {
         ~Pause() { g->timing_every = every; }
     } pause{g, g->timing_every};
     g->timing_every = 0;
-    std::vector<Choice> cands = {{COL_VARIANT, 1}, {INPLACE_VARIANT, 1}, {FUSED_VARIANT, 2}, {1, 1}, {2, 1},
+    std::vector<Choice> cands = {{COL_VARIANT, 1}, {WIDE_VARIANT, 1}, {INPLACE_VARIANT, 1}, {T2_VARIANT, 2}, {FUSED_VARIANT, 2}, {1, 1}, {2, 1},
                                  {1, 2}, {2, 2}, {1, 3}, {2, 3}, {1, 4}, {2, 4}, {1, 6}, {1, 8}};
     // the column kernel with longer z chunks: fewer boundary planes read
     // twice, fewer and longer-lived blocks; down to two chunks (one wave on
@@ -507,8 +549,10 @@ int autotune(wfa_grid_s* g, int* depth_out, int* variant_out) {
     float best_ms = 1e30f;
     for (const Choice& ch : cands) {
         if (e != cudaSuccess) break;
-        if (ch.variant == FUSED_VARIANT && g->k) continue;   // uniform k only
-        if (has_exchange_face(g) && ch.variant != COL_VARIANT && ch.variant != INPLACE_VARIANT) continue;
+        if ((ch.variant == FUSED_VARIANT || ch.variant == T2_VARIANT) && g->k) continue;   // uniform k only
+        if (has_exchange_face(g) && ch.variant != COL_VARIANT && ch.variant != INPLACE_VARIANT &&
+            ch.variant != WIDE_VARIANT)
+            continue;
         // one warm-up pass, then the timed passes
         rc = one_pass(g, c, ch.depth, ch.variant, ch.zc);
         if (rc) break;

@@ -351,6 +351,23 @@ int wfa_server_poll(wfa_server s, long long ticket, int* done) {
     return WFA_OK;
 }
 
+int wfa_server_latency(wfa_server s, long long ticket, double* seconds) {
+    if (!s || !seconds) return WFA_ERR_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) {
+        wfa::set_error("unknown ticket %lld", ticket);
+        return WFA_ERR_ARG;
+    }
+    const Req* r = it->second;
+    if (r->state != 2) {
+        wfa::set_error("ticket %lld is not done", ticket);
+        return WFA_ERR_STATE;
+    }
+    *seconds = std::chrono::duration<double>(r->t_done - r->t_submit).count();
+    return WFA_OK;
+}
+
 int wfa_server_wait(wfa_server s, long long ticket, double timeout_s) {
     if (!s) return WFA_ERR_ARG;
     std::unique_lock<std::mutex> lk(s->mu);

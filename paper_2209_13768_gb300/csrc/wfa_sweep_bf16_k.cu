@@ -56,8 +56,8 @@ cudaError_t launch_simple_bf16_k(const SweepArgs& a, cudaStream_t st) {
     return simple_launch<S, KVAR>(a, st);
 }
 
-cudaError_t launch_col_bf16_k(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev, bool inl) {
-    return col_launch<S, KVAR>(a, st, nsm, ev, inl);
+cudaError_t launch_col_bf16_k(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev, bool inl, bool wide) {
+    return col_launch<S, KVAR>(a, st, nsm, ev, inl, wide);
 }
 
 }  // namespace wfa

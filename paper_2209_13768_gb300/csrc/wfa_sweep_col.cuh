@@ -112,49 +112,91 @@ __device__ __forceinline__ bool outside_np(const SweepCoef& c, int x, int y, int
            (!c.periodic[2] && (z < 0 || z >= c.n[2]));
 }
 
-// x / y neighbours of one plane for one thread: the 4 cells below and above in
+// V consecutive stored values <-> V floats (V = 4 or 8; 8 fp32 values are two
+// 128-bit accesses, 8 bf16 values one).
+template <typename S, bool COH, int V>
+__device__ __forceinline__ void ldgv(const S* p, float v[V]) {
+    ldg4<S, COH>(p, v);
+    if (V == 8) ldg4<S, COH>(p + 4, v + 4);
+}
+template <>
+__device__ __forceinline__ void ldgv<__nv_bfloat16, false, 8>(const __nv_bfloat16* p, float v[8]) {
+    const uint4 q = __ldg(reinterpret_cast<const uint4*>(p));
+    unpack_bf16x4(make_uint2(q.x, q.y), v);
+    unpack_bf16x4(make_uint2(q.z, q.w), v + 4);
+}
+template <>
+__device__ __forceinline__ void ldgv<__nv_bfloat16, true, 8>(const __nv_bfloat16* p, float v[8]) {
+    const uint4 q = __ldcg(reinterpret_cast<const uint4*>(p));
+    unpack_bf16x4(make_uint2(q.x, q.y), v);
+    unpack_bf16x4(make_uint2(q.z, q.w), v + 4);
+}
+template <typename S, int V>
+__device__ __forceinline__ void stv(S* p, const float v[V]) {
+    Vec4<S>::store(p, v);
+    if (V == 8) Vec4<S>::store(p + 4, v + 4);
+}
+template <>
+__device__ __forceinline__ void stv<__nv_bfloat16, 8>(__nv_bfloat16* p, const float v[8]) {
+    uint4 q;
+    __nv_bfloat162 h[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    q.x = *reinterpret_cast<uint32_t*>(&h[0]);
+    q.y = *reinterpret_cast<uint32_t*>(&h[1]);
+    q.z = *reinterpret_cast<uint32_t*>(&h[2]);
+    q.w = *reinterpret_cast<uint32_t*>(&h[3]);
+    *reinterpret_cast<uint4*>(p) = q;
+}
+
+// x / y neighbours of one plane for one thread: the V cells below and above in
 // y and the x neighbours of the row ends; same for 1/k. They belong to other
 // threads' columns, so they come from L1 (or L2).
-template <typename S, bool KVAR, bool COH>
+template <typename S, bool KVAR, bool COH, int V = 4>
 struct ColNb {
-    float ty_m[4], ty_p[4], tx_m, tx_p;
-    float ry_m[4], ry_p[4], rx_m, rx_p;
+    float ty_m[V], ty_p[V], tx_m, tx_p;
+    float ry_m[V], ry_p[V], rx_m, rx_p;
     __device__ __forceinline__ void load(const S* tp, const float* rp, long long sy) {
-        ldg4<S, COH>(tp - sy, ty_m);
-        ldg4<S, COH>(tp + sy, ty_p);
+        ldgv<S, COH, V>(tp - sy, ty_m);
+        ldgv<S, COH, V>(tp + sy, ty_p);
         tx_m = ldg1<S, COH>(tp - 1);
-        tx_p = ldg1<S, COH>(tp + 4);
+        tx_p = ldg1<S, COH>(tp + V);
         if (KVAR) {   // 1/k never changes during a launch: read-only path
-            ldg4<float, false>(rp - sy, ry_m);
-            ldg4<float, false>(rp + sy, ry_p);
+            ldgv<float, false, V>(rp - sy, ry_m);
+            ldgv<float, false, V>(rp + sy, ry_p);
             rx_m = __ldg(rp - 1);
-            rx_p = __ldg(rp + 4);
+            rx_p = __ldg(rp + V);
         }
     }
 };
 
-// Latency hiding: the kernel keeps few live values so that four (per-cell k)
-// or six (uniform k) blocks fit on an SM, the z extent is cut into short
-// chunks so that thousands of blocks stream the grid at once, and each thread
-// asks L2 for plane z + 3 (prefetch.global.L2, no register cost) while it
-// loads plane z + 1, so most plane loads hit L2 (measured at 512^3: +11% with
-// per-cell k, +7% with uniform k). Register-level prefetch was slower: it
-// costs the occupancy.
-template <bool KVAR, bool INL = false, int ES = 4> struct ColOcc {
-    static constexpr int blocks = INL ? (KVAR ? 3 : 4) : (KVAR ? 4 : 6);
+// Latency hiding: the kernel keeps few live values so that several blocks fit
+// on an SM, the z extent is cut into short chunks so that thousands of blocks
+// stream the grid at once, and each thread asks L2 for plane z + 3
+// (prefetch.global.L2, no register cost) while it loads plane z + 1, so most
+// plane loads hit L2 (measured at 512^3: +11% with per-cell k, +7% with
+// uniform k). Register-level prefetch was slower: it costs the occupancy.
+template <bool KVAR, bool INL = false, int ES = 4, int V = 4> struct ColOcc {
+    static constexpr int blocks = V == 8 ? (KVAR ? 2 : 4) : INL ? (KVAR ? 3 : 4) : (KVAR ? 4 : 6);
     // measured: fp32 uniform k prefers the z loop unrolled twice, bf16 not
-    static constexpr int unroll = (KVAR || ES == 2) ? 1 : 2;
+    static constexpr int unroll = (KVAR || ES == 2 || V == 8) ? 1 : 2;
 };
 
-// One thread's work: cells (gx .. gx+3, gy) of planes [z0, z1), one step,
+// How a column pass treats boundary cells and periodic copies.
+enum ColMode {
+    COL_MAIN = 0,    // every cell takes the interior formula; boundary cells and periodic copies
+                     // are rewritten afterwards (the batched sweep's boundary and copy launches)
+    COL_INPLACE = 1, // boundary cells in place, every periodic copy of a written cell stored (full halo)
+    COL_THIN = 2     // every cell takes the interior formula, and one layer of periodic copies
+                     // (no corners: all that a one-step pass reads) is stored in the pass; the
+                     // boundary cells, if the ghost layers do not hold the faces, follow in a
+                     // short launch (boundary_fix) that stores their copies too
+};
+
+// One thread's work: cells (gx .. gx+V-1, gy) of planes [z0, z1), one step,
 // from tin into tout. Shared by the single-grid kernel and the batched one.
-// FIX = true: every cell takes the interior formula and stores go out as
-// 4-cell vectors (masked at the x end only); boundary cells and periodic halo
-// copies are rewritten afterwards by boundary_fix (unless the halo encodes
-// the boundary conditions) and twin_copy (single-grid passes).
-// FIX = false: boundary cells (unless the ghost layers encode the boundary
-// conditions) and halo copies are handled in place. GHOST: the caller
-// guarantees c.halo_bc, so the boundary path is not compiled at all.
+// MODE: see ColMode. GHOST: the caller guarantees c.halo_bc (the ghost layers
+// encode every boundary face), so the boundary path is not compiled at all.
 // DIR = +1 marches planes z0 .. z1-1 upwards, DIR = -1 marches z1-1 .. z0
 // downwards. The single-grid kernel alternates the direction between
 // neighbouring z chunks, so that the two chunks that share a boundary plane
@@ -162,10 +204,11 @@ template <bool KVAR, bool INL = false, int ES = 4> struct ColOcc {
 // and the second read hits L2 instead of DRAM. The march direction does not
 // change a cell's value: the z faces are symmetric bit for bit and every
 // cell takes the same operands in the same order.
-template <typename S, bool KVAR, bool ADV, bool COH, int UNROLL, bool FIX, bool PF = false, bool GHOST = false,
-          int DIR = 1>
+template <typename S, bool KVAR, bool ADV, bool COH, int UNROLL, ColMode MODE, bool PF = false, bool GHOST = false,
+          int DIR = 1, int V = 4, bool TW = true>
 __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict__ tin, S* __restrict__ tout,
                                         const float* __restrict__ rk, int* status, int gx, int gy, int z0, int z1) {
+    static_assert(V == 4 || V == 8, "cells per thread");
     const long long sy = c.sy, sz = c.sz;
     const long long col = (long long)gy * sy + gx;
     // plane p of T is tcol + p * sz (-1 <= p <= nz, inside the halo)
@@ -174,25 +217,28 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
 
     const bool perx = c.periodic[0], pery = c.periodic[1], perz = c.periodic[2];
     const bool bym = !pery && gy == 0, byp = !pery && gy == c.n[1] - 1;
-    const bool edge_x = !perx && (gx == 0 || gx + 3 >= c.n[0] - 1);
-    const bool inner_xy = !edge_x && !bym && !byp && gx + 3 < c.n[0];
-    const bool plain_xy = gx + 3 < c.n[0] && !(perx && (gx < HALO || gx + 3 >= c.n[0] - HALO)) &&
+    const bool full_x = gx + V - 1 < c.n[0];   // every cell of the group lies in the domain
+    const bool edge_x = !perx && (gx == 0 || gx + V - 1 >= c.n[0] - 1);
+    const bool inner_xy = !edge_x && !bym && !byp && full_x;
+    const bool plain_xy = full_x && !(perx && (gx < HALO || gx + V - 1 >= c.n[0] - HALO)) &&
                           !(pery && (gy < HALO || gy >= c.n[1] - HALO));
+    // threads per 128-byte line: one of them asks L2 for the line ahead
+    constexpr int LINE_T = 128 / (V * (int)sizeof(S)) > 0 ? 128 / (V * (int)sizeof(S)) : 1;
 
     // register queue: tm = the plane already passed (z - DIR), tc = plane z,
     // tz = the plane ahead (z + DIR), loaded at plane z; gzm = the face
     // between the passed plane and plane z (per-cell k)
     const int zs = DIR > 0 ? z0 : z1 - 1;          // first plane of the march
     const long long dsz = DIR > 0 ? sz : -sz;      // one plane ahead
-    float tm[4], tc[4], rc[4], gzm[4];
-    ldg4<S, COH>(tcol + (long long)(zs - DIR) * sz, tm);
-    ldg4<S, COH>(tcol + (long long)zs * sz, tc);
+    float tm[V], tc[V], rc[V], gzm[V];
+    ldgv<S, COH, V>(tcol + (long long)(zs - DIR) * sz, tm);
+    ldgv<S, COH, V>(tcol + (long long)zs * sz, tc);
     if (KVAR) {
-        float rb[4];
-        ldg4<float, false>(rcol + (long long)(zs - DIR) * sz, rb);
-        ldg4<float, false>(rcol + (long long)zs * sz, rc);
+        float rb[V];
+        ldgv<float, false, V>(rcol + (long long)(zs - DIR) * sz, rb);
+        ldgv<float, false, V>(rcol + (long long)zs * sz, rc);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) gzm[i] = face_r(rb[i], rc[i], c.tcd[2]);
+        for (int i = 0; i < V; ++i) gzm[i] = face_r(rb[i], rc[i], c.tcd[2]);
     }
 
 #pragma unroll(UNROLL)
@@ -200,35 +246,35 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
         const int z = DIR > 0 ? z0 + s : z1 - 1 - s;
         const S* tp = tcol + (long long)z * sz;
         const float* rp = KVAR ? rcol + (long long)z * sz : nullptr;
-        float tz[4], rz[4];
-        ldg4<S, COH>(tp + dsz, tz);                      // own cells, plane z + DIR
+        float tz[V], rz[V];
+        ldgv<S, COH, V>(tp + dsz, tz);                   // own cells, plane z + DIR
         // one thread per 128-byte line asks L2 for plane z + 3 DIR, as long as
         // the chunk still needs it (the last plane read is z1 going up, z0 - 1
         // going down); the plane after that belongs to the next chunk
-        if (PF && (threadIdx.x & 7) == 0 && s + 3 <= z1 - z0) {
+        if (PF && (threadIdx.x & (LINE_T - 1)) == 0 && s + 3 <= z1 - z0) {
             prefetch_l2(tp + 3 * dsz);
             if (KVAR) prefetch_l2(rp + 3 * dsz);
         }
-        if (KVAR) ldg4<float, false>(rp + dsz, rz);
-        ColNb<S, KVAR, COH> nb;                          // x / y neighbours, plane z
+        if (KVAR) ldgv<float, false, V>(rp + dsz, rz);
+        ColNb<S, KVAR, COH, V> nb;                       // x / y neighbours, plane z
         nb.load(tp, rp, sy);
 
         const bool bzm = !perz && !c.ext[4] && z == 0, bzp = !perz && !c.ext[5] && z == c.n[2] - 1;
         // GHOST (c.halo_bc known at compile time) or c.halo_bc: the ghost layers hold the faces
         const bool fast = GHOST || c.halo_bc || (inner_xy && !bzm && !bzp);
-        float xf[5], gzp[4];
+        float xf[V + 1], gzp[V];
         if (KVAR) {
             xf[0] = face_r(nb.rx_m, rc[0], c.tcd[0]);
 #pragma unroll
-            for (int i = 0; i < 3; ++i) xf[i + 1] = face_r(rc[i], rc[i + 1], c.tcd[0]);
-            xf[4] = face_r(rc[3], nb.rx_p, c.tcd[0]);
+            for (int i = 0; i < V - 1; ++i) xf[i + 1] = face_r(rc[i], rc[i + 1], c.tcd[0]);
+            xf[V] = face_r(rc[V - 1], nb.rx_p, c.tcd[0]);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) gzp[i] = face_r(rc[i], rz[i], c.tcd[2]);
+            for (int i = 0; i < V; ++i) gzp[i] = face_r(rc[i], rz[i], c.tcd[2]);
         }
-        // face weights of the 4 cells (same values on both paths below)
-        float w[4][6];
+        // face weights of the V cells (same values on every path below)
+        float w[V][6];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < V; ++i) {
             if (KVAR) {
                 w[i][0] = xf[i];
                 w[i][1] = xf[i + 1];
@@ -245,12 +291,12 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
                 for (int f = 0; f < 6; ++f) w[i][f] = c.w_in[f];
             }
         }
-        float out[4];
-        if (FIX || fast) {   // no cell of this thread touches a boundary at this plane
+        float out[V];
+        if (MODE == COL_MAIN || MODE == COL_THIN || fast) {   // interior formula (see ColMode)
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < V; ++i) {
                 const float txm = i == 0 ? nb.tx_m : tc[i - 1];
-                const float txp = i == 3 ? nb.tx_p : tc[i + 1];
+                const float txp = i == V - 1 ? nb.tx_p : tc[i + 1];
                 out[i] = storage_round<S>(__fadd_rn(tc[i], flux_sum(tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i],
                                                                     DIR > 0 ? tm[i] : tz[i], DIR > 0 ? tz[i] : tm[i],
                                                                     w[i][0], w[i][1], w[i][2], w[i][3], w[i][4],
@@ -258,9 +304,9 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
             }
         } else {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < V; ++i) {
                 const float txm = i == 0 ? nb.tx_m : tc[i - 1];
-                const float txp = i == 3 ? nb.tx_p : tc[i + 1];
+                const float txp = i == V - 1 ? nb.tx_p : tc[i + 1];
                 const float tzm = DIR > 0 ? tm[i] : tz[i], tzp = DIR > 0 ? tz[i] : tm[i];
                 const bool edge_cell = bym || byp || bzm || bzp || (!perx && (gx + i == 0 || gx + i == c.n[0] - 1));
                 float v;
@@ -277,22 +323,60 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
                 out[i] = storage_round<S>(v);
             }
         }
-        const bool plain = plain_xy && !(perz && (z < HALO || z >= c.n[2] - HALO));
-        // partial vector at the x end with per-cell k: the halo keeps its ghost
-        // values (uniform k never reads them, and the unmasked store is faster)
-        if (FIX && KVAR && gx + 3 >= c.n[0]) {
+        S* const orow = tout + (long long)z * sz + col;   // this thread's cells at plane z
+        if (MODE == COL_THIN) {
+            // the cells (masked at the x end: the halo there holds the x copies),
+            // then one layer of periodic copies for the next one-step pass
+            if (full_x) {
+                stv<S, V>(orow, out);
+            } else {
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (gx + i < c.n[0]) tout[(long long)z * sz + col + i] = from_f32<S>(out[i]);
-        } else if (FIX || plain) {
-            Vec4<S>::store(tout + (long long)z * sz + col, out);
+                for (int i = 0; i < V; ++i)
+                    if (gx + i < c.n[0]) orow[i] = from_f32<S>(out[i]);
+            }
+            if (TW && perx) {
+                if (gx == 0) orow[c.n[0]] = from_f32<S>(out[0]);
+                const int last = c.n[0] - 1 - gx;
+                if (last >= 0 && last < V) {
+#pragma unroll
+                    for (int i = 0; i < V; ++i)
+                        if (i == last) orow[i - c.n[0]] = from_f32<S>(out[i]);   // cell n - 1 at x = -1
+                }
+            }
+            const long long yoff = TW && pery ? (gy == 0 ? c.n[1] * sy : gy == c.n[1] - 1 ? -c.n[1] * sy : 0) : 0;
+            const long long zoff = TW && perz ? (z == 0 ? c.n[2] * sz : z == c.n[2] - 1 ? -c.n[2] * sz : 0) : 0;
+            for (long long off : {yoff, zoff}) {
+                if (!TW || off == 0) continue;
+                if (full_x) {
+                    stv<S, V>(orow + off, out);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < V; ++i)
+                        if (gx + i < c.n[0]) orow[off + i] = from_f32<S>(out[i]);
+                }
+            }
         } else {
+            const bool plain = plain_xy && !(perz && (z < HALO || z >= c.n[2] - HALO));
+            // partial vector at the x end with per-cell k: the halo keeps its ghost
+            // values (uniform k never reads them, and the unmasked store is faster)
+            if (MODE == COL_MAIN && KVAR && !full_x) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (gx + i < c.n[0]) store_twins_out_of_line<S>(tout, &c, gx + i, gy, z, out[i], status);
+                for (int i = 0; i < V; ++i)
+                    if (gx + i < c.n[0]) orow[i] = from_f32<S>(out[i]);
+            } else if (MODE == COL_MAIN || plain) {
+                stv<S, V>(orow, out);
+            } else if (!perx && !pery && !perz) {   // the x end of a row, no copies to store
+#pragma unroll
+                for (int i = 0; i < V; ++i)
+                    if (gx + i < c.n[0]) orow[i] = from_f32<S>(out[i]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < V; ++i)
+                    if (gx + i < c.n[0]) store_twins_out_of_line<S>(tout, &c, gx + i, gy, z, out[i], status);
+            }
         }
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < V; ++i) {
             tm[i] = tc[i];
             tc[i] = tz[i];
             if (KVAR) {
@@ -305,25 +389,29 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
 
 // ADV: per-cell k with a nonzero upwind weight on some face (uniform k folds
 // the upwind weights into its constants and never needs it).
-// INL: boundary cells and periodic copies in place, one launch per pass
-// (fastest for small grids, where launches dominate); otherwise the
-// branch-free main pass, followed by boundary_fix (unless the ghost layers
-// hold the faces) and twin_copy (fastest for large grids).
-template <typename S, bool KVAR, bool ADV, bool INL>
-__global__ void __launch_bounds__(256, (ColOcc<KVAR, INL, sizeof(S)>::blocks)) sweep_col(const __grid_constant__ SweepArgs a) {
+// INL: boundary cells and every periodic copy in place (variant 5, one
+// launch per pass); otherwise the thin pass (variant 3 with V = 4, variant 6
+// with V = 8): interior formula and one layer of periodic copies, then
+// boundary_fix where the ghost layers do not hold the faces.
+// TW: some axis is periodic (the thin pass stores its one layer of copies;
+// without a periodic axis that code is not compiled).
+template <typename S, bool KVAR, bool ADV, bool INL, int V = 4, bool TW = true>
+__global__ void __launch_bounds__(256, (ColOcc<KVAR, INL, sizeof(S), V>::blocks))
+    sweep_col(const __grid_constant__ SweepArgs a) {
     const SweepCoef& c = a.c;
-    const int gx = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    const int gx = (blockIdx.x * blockDim.x + threadIdx.x) * V;
     const int gy = blockIdx.y * blockDim.y + threadIdx.y;
     if (gx >= c.n[0] || gy >= c.n[1]) return;
     const int z0 = blockIdx.z * a.zchunk;
     const int z1 = min(z0 + a.zchunk, c.n[2]);
-    constexpr int U = ColOcc<KVAR, INL, sizeof(S)>::unroll;
+    constexpr int U = ColOcc<KVAR, INL, sizeof(S), V>::unroll;
+    constexpr ColMode MODE = INL ? COL_INPLACE : COL_THIN;
     if (blockIdx.z & 1)   // odd chunks march down: see col_run
-        col_run<S, KVAR, ADV, false, U, !INL, true, false, -1>(c, (const S*)a.tin, (S*)a.tout, a.rk, a.status, gx,
-                                                              gy, z0, z1);
+        col_run<S, KVAR, ADV, false, U, MODE, true, false, -1, V, TW>(c, (const S*)a.tin, (S*)a.tout, a.rk,
+                                                                     a.status, gx, gy, z0, z1);
     else
-        col_run<S, KVAR, ADV, false, U, !INL, true, false, 1>(c, (const S*)a.tin, (S*)a.tout, a.rk, a.status, gx,
-                                                             gy, z0, z1);
+        col_run<S, KVAR, ADV, false, U, MODE, true, false, 1, V, TW>(c, (const S*)a.tin, (S*)a.tout, a.rk,
+                                                                    a.status, gx, gy, z0, z1);
 }
 
 // Boundary cells (the outer layer on every non-periodic face): recomputed
@@ -347,7 +435,10 @@ __global__ void __launch_bounds__(256) boundary_fix(const __grid_constant__ Swee
         pos[d] = (int)(t / nb);
         const long long i = (long long)pos[2] * c.sz + (long long)pos[1] * c.sy + pos[0];
         const float v = general_cell<S, KVAR>(c, (const S*)a.tin, a.rk, i, pos[0], pos[1], pos[2], a.status);
-        ((S*)a.tout)[i] = from_f32<S>(v);
+        if (c.periodic[0] || c.periodic[1] || c.periodic[2])   // with its periodic copies
+            store_with_twins<S>((S*)a.tout, c, pos[0], pos[1], pos[2], from_f32<S>(v), a.status);
+        else
+            ((S*)a.tout)[i] = from_f32<S>(v);
     }
 }
 
@@ -417,14 +508,16 @@ cudaError_t fix_and_twins(const SweepArgs& a, cudaStream_t st, int nsm) {
     return cudaSuccess;
 }
 
-template <typename S, bool KVAR>
-cudaError_t col_launch(const SweepArgs& a_in, cudaStream_t st, int nsm, const cudaEvent_t* ev, bool inl) {
+// One column pass (variant 3: V = 4, variant 6: V = 8, both thin; variant 5:
+// in place, V = 4): one launch.
+template <typename S, bool KVAR, int V>
+cudaError_t col_launch_v(const SweepArgs& a_in, cudaStream_t st, int nsm, const cudaEvent_t* ev, bool inl) {
     SweepArgs a = a_in;
     dim3 block(16, 16);
-    const int gxb = (a.c.n[0] + 63) / 64, gyb = (a.c.n[1] + 15) / 16;
+    const int gxb = (a.c.n[0] + 16 * V - 1) / (16 * V), gyb = (a.c.n[1] + 15) / 16;
     // z chunks of about 16 planes: many short columns stream the grid at once
     const long long cols = (long long)gxb * gyb,
-                    resident = (long long)nsm * (inl ? ColOcc<KVAR, true>::blocks : ColOcc<KVAR>::blocks);
+                    resident = (long long)nsm * (inl ? ColOcc<KVAR, true>::blocks : ColOcc<KVAR, false, 4, V>::blocks);
     long long want = resident * 16;
     int nch = (int)std::max<long long>(1, want / cols);
     // chunks of at least 16 planes, unless that leaves SMs idle (small grids,
@@ -443,14 +536,31 @@ cudaError_t col_launch(const SweepArgs& a_in, cudaStream_t st, int nsm, const cu
     if (inl) {
         if (adv) sweep_col<S, KVAR, true, true><<<grid, block, 0, st>>>(a);
         else sweep_col<S, KVAR, false, true><<<grid, block, 0, st>>>(a);
-    } else {
-        if (adv) sweep_col<S, KVAR, true, false><<<grid, block, 0, st>>>(a);
-        else sweep_col<S, KVAR, false, false><<<grid, block, 0, st>>>(a);
+    } else if (a.c.periodic[0] || a.c.periodic[1] || a.c.periodic[2]) {
+        if (adv) sweep_col<S, KVAR, true, false, V, true><<<grid, block, 0, st>>>(a);
+        else sweep_col<S, KVAR, false, false, V, true><<<grid, block, 0, st>>>(a);
+    } else {   // no periodic axis: no copies to store
+        if (adv) sweep_col<S, KVAR, true, false, V, false><<<grid, block, 0, st>>>(a);
+        else sweep_col<S, KVAR, false, false, V, false><<<grid, block, 0, st>>>(a);
     }
     if (ev) cudaEventRecord(ev[1], st);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || inl) return e;   // in place: nothing after the pass
-    return fix_and_twins<S, KVAR>(a, st, nsm);
+    if (e != cudaSuccess || inl || a.c.halo_bc) return e;
+    long long plane = 0;   // the largest face with boundary cells
+    for (int ax = 0; ax < 3; ++ax) {
+        const int b = ax == 0 ? 1 : 0, d = ax == 2 ? 1 : 2;
+        if (!a.c.periodic[ax] && !(a.c.ext[2 * ax] && a.c.ext[2 * ax + 1]))
+            plane = std::max(plane, (long long)a.c.n[b] * a.c.n[d]);
+    }
+    if (plane == 0) return cudaSuccess;
+    const int nb = (int)std::min<long long>((plane + 255) / 256, (long long)nsm * 2);
+    boundary_fix<S, KVAR><<<dim3(nb, 6), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename S, bool KVAR>
+cudaError_t col_launch(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev, bool inl, bool wide) {
+    return wide && !inl ? col_launch_v<S, KVAR, 8>(a, st, nsm, ev, false) : col_launch_v<S, KVAR, 4>(a, st, nsm, ev, inl);
 }
 
 }  // namespace wfa

@@ -1,6 +1,7 @@
 // Compiled sweep kernels: f32 storage, uniform conductivity, depths 1..8.
 #include "wfa_sweep_col.cuh"
 #include "wfa_sweep_fused.cuh"
+#include "wfa_sweep_t2.cuh"
 #include "wfa_sweep_impl.cuh"
 
 namespace wfa {
@@ -57,12 +58,16 @@ cudaError_t launch_simple_f32_u(const SweepArgs& a, cudaStream_t st) {
     return simple_launch<S, KVAR>(a, st);
 }
 
-cudaError_t launch_col_f32_u(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev, bool inl) {
-    return col_launch<S, KVAR>(a, st, nsm, ev, inl);
+cudaError_t launch_col_f32_u(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev, bool inl, bool wide) {
+    return col_launch<S, KVAR>(a, st, nsm, ev, inl, wide);
 }
 
 cudaError_t launch_col2_f32_u(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev) {
     return col2_launch<S>(a, st, nsm, ev);
+}
+
+cudaError_t launch_t2_f32_u(const CUtensorMap* tmT, const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev) {
+    return t2_launch<S>(tmT, a, st, nsm, ev);
 }
 
 }  // namespace wfa

@@ -33,10 +33,14 @@ cudaError_t launch_simple_bf16_k(const SweepArgs& a, cudaStream_t st);
 // one-step column-march kernel (variant 3; inl: variant 5, boundaries and
 // periodic copies in the same launch); ev (may be null): events recorded just
 // before and just after the main kernel, outside its fix-up kernels
-cudaError_t launch_col_f32_u(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev, bool inl);
-cudaError_t launch_col_f32_k(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev, bool inl);
-cudaError_t launch_col_bf16_u(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev, bool inl);
-cudaError_t launch_col_bf16_k(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev, bool inl);
+cudaError_t launch_col_f32_u(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev, bool inl, bool wide);
+cudaError_t launch_col_f32_k(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev, bool inl, bool wide);
+cudaError_t launch_col_bf16_u(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev, bool inl, bool wide);
+cudaError_t launch_col_bf16_k(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev, bool inl, bool wide);
+// two steps per pass with TMA-staged input planes (variant 7, uniform k only);
+// tmT: the input buffer's tensor map with an 80 x 20 box
+cudaError_t launch_t2_f32_u(const CUtensorMap* tmT, const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev);
+cudaError_t launch_t2_bf16_u(const CUtensorMap* tmT, const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev);
 // two-step column-march kernel (variant 4, uniform k only)
 cudaError_t launch_col2_f32_u(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev);
 cudaError_t launch_col2_bf16_u(const SweepArgs& a, cudaStream_t st, int nsm, const cudaEvent_t* ev);

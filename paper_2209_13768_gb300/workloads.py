@@ -115,15 +115,23 @@ class Arrival:
     storage: int       # 0 fp32, 1 bf16
 
 
-def request_stream(rate=200.0, count=10000, lo=32, hi=256, steps=(50, 2000), seed=5, duration=None, pool=None):
-    """Poisson arrivals (mean `rate` per second) of heat or advection-diffusion
-    solves (probability 1/2 each), edges log-uniform in [lo, hi], steps uniform
-    in [steps[0], steps[1]], fp32 or bf16 storage (probability 1/2 each).
-    pool: only the first `pool` arrivals get their own fields; arrival i
-    reuses the shape and fields of arrival i % pool (its time, step count and
-    storage stay its own), so long streams need little host memory."""
-    from dataclasses import replace
+@dataclass
+class RequestSpec:
+    """One arrival of the request stream before its fields exist (they are
+    drawn from their own seed when the request is made)."""
+    t: float
+    shape: tuple
+    steps: int
+    seed: int
+    heat: bool
+    storage: int
 
+
+def request_specs(rate=200.0, count=10000, lo=32, hi=256, steps=(50, 2000), seed=5, duration=None):
+    """The arrivals of request_stream without their fields: Poisson arrival
+    times (mean `rate` per second), edges log-uniform in [lo, hi], steps
+    uniform in [steps[0], steps[1]], heat or advection-diffusion and fp32 or
+    bf16 with probability 1/2 each. Cheap for long streams (10^4 requests)."""
     rng = np.random.default_rng(seed)
     t = 0.0
     out = []
@@ -135,17 +143,40 @@ def request_stream(rate=200.0, count=10000, lo=32, hi=256, steps=(50, 2000), see
         shape = tuple(int(e) for e in edges)
         n = int(rng.integers(steps[0], steps[1] + 1))
         s = int(rng.integers(0, 2**31))
-        heat = rng.random() < 0.5
+        heat = bool(rng.random() < 0.5)
         storage = int(rng.random() < 0.5)
+        out.append(RequestSpec(t=t, shape=shape, steps=n, seed=s, heat=heat, storage=storage))
+    return out
+
+
+def make_request(spec):
+    """The Problem of one request: heat (lognormal k, T = 0 on every face,
+    T0 ~ U[0,1)) or advection-diffusion (k = 0.05, u = (0.3, 0.1, 0.05),
+    periodic x, zero-flux y / z, a Gaussian blob), fields from its seed."""
+    shape, s = spec.shape, spec.seed
+    if spec.heat:
+        return Problem(shape=shape, T0=uniform01(shape, s), k=lognormal_k(shape, s + 1), bc=[(D, 0.0)] * 6,
+                       steps=spec.steps, name="heat")
+    nx, ny, nz = shape
+    return Problem(shape=shape, T0=gaussian_blob(shape, (nx / 2, ny / 2, nz / 2), max(2.0, min(shape) / 16)),
+                   k=0.05, u=(0.3, 0.1, 0.05), bc=[(P, 0.0)] * 2 + [(ZF, 0.0)] * 4, dt=1.0, steps=spec.steps,
+                   name="advection-diffusion")
+
+
+def request_stream(rate=200.0, count=10000, lo=32, hi=256, steps=(50, 2000), seed=5, duration=None, pool=None):
+    """Poisson arrivals (mean `rate` per second) of heat or advection-diffusion
+    solves (probability 1/2 each), edges log-uniform in [lo, hi], steps uniform
+    in [steps[0], steps[1]], fp32 or bf16 storage (probability 1/2 each).
+    pool: only the first `pool` arrivals get their own fields; arrival i
+    reuses the shape and fields of arrival i % pool (its time, step count and
+    storage stay its own), so long streams need little host memory."""
+    from dataclasses import replace
+
+    out = []
+    for spec in request_specs(rate, count, lo, hi, steps, seed, duration):
         if pool is not None and len(out) >= pool:
-            prob = replace(out[len(out) % pool].problem, steps=n)
-        elif heat:
-            prob = Problem(shape=shape, T0=uniform01(shape, s), k=lognormal_k(shape, s + 1),
-                           bc=[(D, 0.0)] * 6, steps=n, name="heat")
+            prob = replace(out[len(out) % pool].problem, steps=spec.steps)
         else:
-            nx, ny, nz = shape
-            prob = Problem(shape=shape, T0=gaussian_blob(shape, (nx / 2, ny / 2, nz / 2), max(2.0, min(shape) / 16)),
-                           k=0.05, u=(0.3, 0.1, 0.05), bc=[(P, 0.0)] * 2 + [(ZF, 0.0)] * 4, dt=1.0,
-                           steps=n, name="advection-diffusion")
-        out.append(Arrival(t=t, problem=prob, storage=storage))
+            prob = make_request(spec)
+        out.append(Arrival(t=spec.t, problem=prob, storage=spec.storage))
     return out

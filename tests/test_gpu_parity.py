@@ -95,9 +95,13 @@ def test_boundary_mixes_all_kernels(mix, kvar, adv):
     np.testing.assert_array_equal(run_gpu(p, variant=3), base, err_msg="column kernel")
     # two-step column kernel (uniform k; per-cell k falls back to one step)
     np.testing.assert_array_equal(run_gpu(p, depth=2, variant=4), base, err_msg="two-step column kernel")
+    np.testing.assert_array_equal(run_gpu(p, depth=2, variant=7), base, err_msg="two-step TMA kernel")
     np.testing.assert_array_equal(run_gpu(p, variant=5), base, err_msg="column kernel, boundaries in place")
+    np.testing.assert_array_equal(run_gpu(p, variant=6), base, err_msg="column kernel, 8 cells a thread")
     np.testing.assert_array_equal(run_gpu(p, steps=p.steps - 1, depth=2, variant=4),
                                   run_gpu(p, steps=p.steps - 1, variant=-1), err_msg="two-step, odd count")
+    np.testing.assert_array_equal(run_gpu(p, steps=p.steps - 1, depth=2, variant=7),
+                                  run_gpu(p, steps=p.steps - 1, variant=-1), err_msg="two-step TMA, odd count")
 
 
 @pytest.mark.parametrize("kvar,adv", [(True, True), (False, True), (True, False)])
@@ -111,11 +115,31 @@ def test_column_kernel_z_chunks(mix, kvar, adv):
     for zc in (1, 2, 3, 5, 8, 12, 22, 23, 64):
         np.testing.assert_array_equal(run_gpu(p, variant=3, zchunk=zc), base, err_msg=f"variant 3, zchunk {zc}")
         np.testing.assert_array_equal(run_gpu(p, variant=5, zchunk=zc), base, err_msg=f"variant 5, zchunk {zc}")
+        np.testing.assert_array_equal(run_gpu(p, depth=2, variant=7, zchunk=zc), base, err_msg=f"variant 7, zchunk {zc}")
+        np.testing.assert_array_equal(run_gpu(p, variant=6, zchunk=zc), base, err_msg=f"variant 6, zchunk {zc}")
     for storage in (wfa.BF16,):
         ref = run_gpu(p, storage=storage, variant=-1)
         for zc in (3, 8, 12):
             np.testing.assert_array_equal(run_gpu(p, storage=storage, variant=3, zchunk=zc), ref,
                                           err_msg=f"bf16 zchunk {zc}")
+
+
+@pytest.mark.parametrize("kvar", [True, False])
+@pytest.mark.parametrize("mix", [2, 4, 5, 6])
+def test_kernel_switches_between_thin_and_full_periodic_copies(mix, kvar):
+    """The one-step column passes write one layer of periodic copies; a tiled
+    or two-step pass after them needs every layer (and the corners): the
+    switch completes the copies first, so any sequence of kernels gives the
+    field of one kernel throughout."""
+    p = _mixed_problem(mix, kvar=kvar, seed=70 + mix)
+    plan = [(1, 3, 3), (2, 7, 4), (2, 1, 2), (1, 6, 2), (2, 7, 3), (3, 2, 3), (1, 5, 1), (2, 4, 2), (1, 3, 1),
+            (2, 7, 2)]   # (depth, variant, steps)
+    ref = run_gpu(p, steps=sum(n for _, _, n in plan), variant=-1)
+    with make_grid(p) as g:
+        for depth, variant, steps in plan:
+            g.set_tuning(depth, variant)
+            g.step(steps)
+        np.testing.assert_array_equal(g.read_field(), ref)
 
 
 @pytest.mark.parametrize("shape", [(2, 2, 2), (3, 2, 5), (5, 7, 3), (64, 3, 9), (131, 67, 4), (70, 35, 40)])
@@ -132,9 +156,11 @@ def test_small_and_ragged_shapes(shape):
             np.testing.assert_array_equal(run_gpu(p, depth=depth, variant=1), base)
         np.testing.assert_array_equal(run_gpu(p, variant=3), base)
         np.testing.assert_array_equal(run_gpu(p, variant=5), base)
+        np.testing.assert_array_equal(run_gpu(p, variant=6), base)
         pu = _mixed_problem(mix, shape=shape, kvar=False, seed=7)
         pu.steps = 9
         np.testing.assert_array_equal(run_gpu(pu, depth=2, variant=4), run_gpu(pu, variant=-1), err_msg=str(shape))
+        np.testing.assert_array_equal(run_gpu(pu, depth=2, variant=7), run_gpu(pu, variant=-1), err_msg=str(shape))
 
 
 
@@ -206,6 +232,8 @@ def test_bf16_storage(mix):
     np.testing.assert_array_equal(run_gpu(p, storage=wfa.BF16, variant=5), base)
     pu = _mixed_problem(mix, kvar=False, seed=3)
     pu.steps = 30
+    np.testing.assert_array_equal(run_gpu(pu, storage=wfa.BF16, depth=2, variant=7),
+                                  run_gpu(pu, storage=wfa.BF16, variant=-1))
     np.testing.assert_array_equal(run_gpu(pu, storage=wfa.BF16, depth=2, variant=4),
                                   run_gpu(pu, storage=wfa.BF16, variant=-1))
 
@@ -312,7 +340,7 @@ def test_argument_limits():
     with wfa.Grid((8, 8, 8)) as g:
         for call, code in [(lambda: g.set_bc(6, ZF, 0.0), -1), (lambda: g.set_bc(0, 9, 0.0), -1),
                            (lambda: g.set_bc(0, D, float("inf")), -1), (lambda: g.set_coeffs(-1.0), -1),
-                           (lambda: g.set_tuning(9, 0), -1), (lambda: g.set_tuning(1, 6), -1)]:
+                           (lambda: g.set_tuning(9, 0), -1), (lambda: g.set_tuning(1, 8), -1)]:
             with pytest.raises(wfa.WfaError) as e:
                 call()
             assert e.value.code == code
@@ -433,6 +461,7 @@ def test_advection_diffusion_reduced(storage):
     err = rel_linf(T, ref)
     assert err <= (F32_TOL if storage == wfa.F32 else bf16_bound(p.steps)), err
     np.testing.assert_array_equal(run_gpu(p, storage=storage, depth=2, variant=4), run_gpu(p, storage=storage, variant=3))
+    np.testing.assert_array_equal(run_gpu(p, storage=storage, depth=2, variant=7), run_gpu(p, storage=storage, variant=3))
 
 
 def test_autotune_keeps_state_and_results():
@@ -442,7 +471,7 @@ def test_autotune_keeps_state_and_results():
         g.step(5)
         before = g.read_field()
         d, v = g.autotune()
-        assert 1 <= d <= 8 and v in (1, 2, 3)
+        assert 1 <= d <= 8 and v in (1, 2, 3, 4, 5, 6, 7)
         np.testing.assert_array_equal(g.read_field(), before)
         assert g.steps_done() == 5
         g.step(12)
