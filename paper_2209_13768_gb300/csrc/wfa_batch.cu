@@ -64,10 +64,9 @@ struct MgGrid {
     int nblocks;          // units: ceil(ncols * nch / MG_THREADS)
     int block0;           // first unit of the grid in a per-round launch of its class
     int unit0;            // first unit of the grid in the persistent kernel's table
-    // uniform k, per-round launches: a branch-free main pass, then the
-    // boundary cells and the periodic copies in launches of their own
+    // uniform k, per-round launches: a branch-free main pass that stores one
+    // layer of periodic copies, then the boundary cells in a launch of its own
     int nbu, bu0;         // boundary-cell units (256 cells) and the first in its class
-    int ntw[3], tw0[3];   // periodic-copy units per axis and the first in its class
     int pad;
     long long steps;
 };
@@ -108,7 +107,8 @@ __global__ void __launch_bounds__(MG_THREADS, MgOcc<KVAR, GHOST>::blocks)
 }
 
 // Uniform k, per-round launches: every cell takes the interior formula
-// (branch-free, the occupancy of the single-grid main pass) ...
+// (branch-free, the occupancy of the single-grid main pass) and stores one
+// layer of periodic copies, all that the next one-step pass reads ...
 template <typename S>
 __global__ void __launch_bounds__(MG_THREADS, (ColOcc<false, false, sizeof(S)>::blocks))
     mg_sweep_main(const MgGrid* __restrict__ grids, const int* __restrict__ block_grid, long long step) {
@@ -121,12 +121,13 @@ __global__ void __launch_bounds__(MG_THREADS, (ColOcc<false, false, sizeof(S)>::
     const int gx = 4 * (col % sg.ncx), gy = col / sg.ncx;
     const int z0 = chunk * sg.zchunk;
     const int z1 = min(z0 + sg.zchunk, sg.c.n[2]);
-    col_run<S, false, false, false, ColOcc<false, false, sizeof(S)>::unroll, COL_MAIN, true>(
+    col_run<S, false, false, false, ColOcc<false, false, sizeof(S)>::unroll, COL_THIN, true>(
         sg.c, (const S*)sg.tb[step & 1], (S*)sg.tb[(step + 1) & 1], nullptr, nullptr, gx, gy, z0, z1);
 }
 
 // ... then the outer cell layer of every non-periodic face recomputed with
-// the boundary conditions (the cells of a face in 256-cell units) ...
+// the boundary conditions (the cells of a face in 256-cell units), with its
+// periodic copies where another axis is periodic.
 template <typename S>
 __global__ void __launch_bounds__(MG_THREADS)
     mg_boundary(const MgGrid* __restrict__ grids, const int* __restrict__ unit_grid, long long step, int* status) {
@@ -154,32 +155,12 @@ __global__ void __launch_bounds__(MG_THREADS)
     if (!found) return;   // past the last face
     const S* tin = (const S*)sg.tb[step & 1];
     const long long i = (long long)pos[2] * c.sz + (long long)pos[1] * c.sy + pos[0];
-    ((S*)sg.tb[(step + 1) & 1])[i] = from_f32<S>(general_cell<S, false>(c, tin, nullptr, i, pos[0], pos[1], pos[2], status));
-}
-
-// ... then the periodic copies of one axis (x, y, z in turn: corners come
-// out right), over the full extent of the other two axes.
-template <typename S>
-__global__ void __launch_bounds__(MG_THREADS)
-    mg_twins(const MgGrid* __restrict__ grids, const int* __restrict__ unit_grid, long long step, int ax) {
-    __shared__ MgGrid sg;
-    load_desc(&sg, &grids[unit_grid[blockIdx.x]]);
-    __syncthreads();
-    const SweepCoef& c = sg.c;
-    const int b = ax == 0 ? 1 : 0, d = ax == 2 ? 1 : 2;
-    const long long eb = c.n[b] + 2 * HALO, ed = c.n[d] + 2 * HALO;
-    const long long t = (long long)((int)blockIdx.x - sg.tw0[ax]) * MG_THREADS + threadIdx.x;
-    if (t >= 2LL * HALO * eb * ed) return;
-    const long long st[3] = {1, c.sy, c.sz};
-    const int k = (int)(t % (2 * HALO));
-    const long long rest = t / (2 * HALO);
-    const int pb = (int)(rest % eb) - HALO, pd = (int)(rest / eb) - HALO;
-    const int dst = k < HALO ? k - HALO : c.n[ax] + (k - HALO);
-    int src = dst % c.n[ax];
-    if (src < 0) src += c.n[ax];
-    S* origin = (S*)sg.tb[(step + 1) & 1];
-    const long long other = pb * st[b] + pd * st[d];
-    origin[other + dst * st[ax]] = origin[other + src * st[ax]];
+    const S v = from_f32<S>(general_cell<S, false>(c, tin, nullptr, i, pos[0], pos[1], pos[2], status));
+    S* tout = (S*)sg.tb[(step + 1) & 1];
+    if (c.periodic[0] || c.periodic[1] || c.periodic[2])
+        store_with_twins<S>(tout, c, pos[0], pos[1], pos[2], v, status);
+    else
+        tout[i] = v;
 }
 
 template <typename S>
@@ -201,15 +182,13 @@ cudaError_t launch_class(int cls, int blocks, const MgGrid* grids, const int* bl
                        : launch_kind<__nv_bfloat16>(cls - NKIND, blocks, grids, block_grid, step, status, st);
 }
 
-// One round of a uniform-k class: main pass, boundary cells, periodic copies
-// (block counts 0 skip a launch).
+// One round of a uniform-k class: main pass, then boundary cells (a block
+// count of 0 skips that launch).
 template <typename S>
-cudaError_t uniform_round(int blocks, int bblocks, const int tblocks[3], const MgGrid* grids, const int* map,
-                          const int* bmap, const int* const tmap[3], long long step, int* status, cudaStream_t st) {
+cudaError_t uniform_round(int blocks, int bblocks, const MgGrid* grids, const int* map, const int* bmap,
+                          long long step, int* status, cudaStream_t st) {
     mg_sweep_main<S><<<blocks, MG_THREADS, 0, st>>>(grids, map, step);
     if (bblocks > 0) mg_boundary<S><<<bblocks, MG_THREADS, 0, st>>>(grids, bmap, step, status);
-    for (int ax = 0; ax < 3; ++ax)
-        if (tblocks[ax] > 0) mg_twins<S><<<tblocks[ax], MG_THREADS, 0, st>>>(grids, tmap[ax], step, ax);
     return cudaGetLastError();
 }
 
@@ -674,45 +653,39 @@ extern "C" int wfa_batch_run(wfa_grid* gs, const long long* steps, int count) {
         long long total_blocks = 0;
         auto uniform_class = [](int t) { return (t / NGROUP) % NKIND == 0; };   // t: a branch
         for (int t = 0; t < NBRANCH; ++t) {
-            long long b0 = 0, bu = 0, tw[3] = {0, 0, 0};
+            long long b0 = 0, bu = 0;
             for (int j = cls_first[t]; j < cls_first[t + 1]; ++j) {
                 MgGrid& m = sorted[j];
                 m = mg[idx[j]];
                 m.cls = t / NGROUP;
                 m.block0 = (int)b0;
                 b0 += m.nblocks;
-                if (uniform_class(t)) {   // boundary-cell and periodic-copy units
+                if (uniform_class(t)) {   // boundary-cell units
                     long long bcells = 0;
                     for (int ax = 0; ax < 3; ++ax) {
                         const int b = ax == 0 ? 1 : 0, d = ax == 2 ? 1 : 2;
                         if (!m.c.periodic[ax]) bcells += 2LL * m.c.n[b] * m.c.n[d];
-                        const long long twins =
-                            m.c.periodic[ax] ? 2LL * HALO * (m.c.n[b] + 2 * HALO) * (m.c.n[d] + 2 * HALO) : 0;
-                        m.ntw[ax] = (int)((twins + MG_THREADS - 1) / MG_THREADS);
-                        m.tw0[ax] = (int)tw[ax];
-                        tw[ax] += m.ntw[ax];
                     }
                     m.nbu = (int)((bcells + MG_THREADS - 1) / MG_THREADS);
                     m.bu0 = (int)bu;
                     bu += m.nbu;
                 }
             }
-            if (b0 > (1LL << 30) || bu > (1LL << 30) || tw[0] > (1LL << 30) || tw[1] > (1LL << 30) ||
-                tw[2] > (1LL << 30)) {
+            if (b0 > (1LL << 30) || bu > (1LL << 30)) {
                 set_error("wfa_batch_run: too many blocks in one launch");
                 return WFA_ERR_ARG;
             }
-            total_blocks += b0 + bu + tw[0] + tw[1] + tw[2];
+            total_blocks += b0 + bu;
         }
         // device tables: the descriptors, then per class the block -> grid
-        // maps (main units; for uniform k also boundary and copy units)
+        // maps (main units; for uniform k also boundary units)
         const size_t grid_bytes = ((size_t)ng * sizeof(MgGrid) + 255) / 256 * 256;
         const size_t bytes = grid_bytes + (size_t)total_blocks * sizeof(int);
         rc = reserve(c, bytes, 0, 0);
         if (rc) return rc;
         memcpy(c->host, sorted.data(), (size_t)ng * sizeof(MgGrid));
         int* bmap = reinterpret_cast<int*>(c->host + grid_bytes);
-        long long cls_map[NBRANCH], cls_bmap[NBRANCH], cls_tmap[NBRANCH][3];   // offsets (ints)
+        long long cls_map[NBRANCH], cls_bmap[NBRANCH];   // offsets (ints)
         {
             long long o = 0;
             for (int t = 0; t < NBRANCH; ++t) {
@@ -723,12 +696,6 @@ extern "C" int wfa_batch_run(wfa_grid* gs, const long long* steps, int count) {
                 if (uniform_class(t))
                     for (int j = cls_first[t]; j < cls_first[t + 1]; ++j)
                         for (int b = 0; b < sorted[j].nbu; ++b) bmap[o++] = j;
-                for (int ax = 0; ax < 3; ++ax) {
-                    cls_tmap[t][ax] = o;
-                    if (uniform_class(t))
-                        for (int j = cls_first[t]; j < cls_first[t + 1]; ++j)
-                            for (int b = 0; b < sorted[j].ntw[ax]; ++b) bmap[o++] = j;
-                }
             }
         }
         // mode "rounds": captured on a private stream into one graph, launched
@@ -760,21 +727,17 @@ extern "C" int wfa_batch_run(wfa_grid* gs, const long long* steps, int count) {
             cudaStream_t cs = mode == 1 ? c->cls_stream[t] : ls;
             if (mode == 1) e = cudaStreamWaitEvent(cs, c->fork, 0);
             int active = cls_first[t + 1];
-            const int* tmaps[3] = {dmap + cls_tmap[t][0], dmap + cls_tmap[t][1], dmap + cls_tmap[t][2]};
             for (long long s = 0; s < max_steps && e == cudaSuccess; ++s) {
                 while (active > cls_first[t] && sorted[active - 1].steps <= s) --active;
                 if (active == cls_first[t]) break;
                 const MgGrid& last = sorted[active - 1];
                 const int type = t / NGROUP;
                 if (uniform_class(t)) {
-                    const int tblocks[3] = {last.tw0[0] + last.ntw[0], last.tw0[1] + last.ntw[1],
-                                            last.tw0[2] + last.ntw[2]};
-                    e = type < NKIND ? uniform_round<float>(last.block0 + last.nblocks, last.bu0 + last.nbu, tblocks,
-                                                         dgrids, dmap + cls_map[t], dmap + cls_bmap[t], tmaps, s,
-                                                         status, cs)
-                                  : uniform_round<__nv_bfloat16>(last.block0 + last.nblocks, last.bu0 + last.nbu,
-                                                                 tblocks, dgrids, dmap + cls_map[t],
-                                                                 dmap + cls_bmap[t], tmaps, s, status, cs);
+                    e = type < NKIND ? uniform_round<float>(last.block0 + last.nblocks, last.bu0 + last.nbu, dgrids,
+                                                         dmap + cls_map[t], dmap + cls_bmap[t], s, status, cs)
+                                     : uniform_round<__nv_bfloat16>(last.block0 + last.nblocks, last.bu0 + last.nbu,
+                                                                    dgrids, dmap + cls_map[t], dmap + cls_bmap[t], s,
+                                                                    status, cs);
                 } else {
                     e = launch_class(type, last.block0 + last.nblocks, dgrids, dmap + cls_map[t], s, status, cs);
                 }
@@ -799,9 +762,12 @@ extern "C" int wfa_batch_run(wfa_grid* gs, const long long* steps, int count) {
     for (int k = 0; k < ng; ++k) {
         wfa_grid g = gs[order[k]];
         g->cur = (int)((g->cur + mg[k].steps) & 1);
-        // the batched passes write every periodic copy (corners included)
-        g->thin[g->cur] = false;
-        if (mg[k].steps >= 2) g->thin[1 - g->cur] = false;
+        // the persistent kernel and the per-cell-k passes write every periodic
+        // copy (corners included); the per-round uniform-k passes one layer
+        const bool one_layer = mode != 0 && cls[k] % NKIND == 0 &&
+                               (mg[k].c.periodic[0] || mg[k].c.periodic[1] || mg[k].c.periodic[2]);
+        if (mg[k].steps >= 1) g->thin[g->cur] = one_layer;
+        if (mg[k].steps >= 2) g->thin[1 - g->cur] = one_layer;
         g->steps_done += mg[k].steps;
     }
     return WFA_OK;
