@@ -32,6 +32,7 @@
 
 #include <algorithm>
 #include <map>
+#include <tuple>
 #include <type_traits>
 #include <mutex>
 #include <vector>
@@ -379,9 +380,10 @@ cudaError_t persistent_kernel(int cls, bool launch, int* occ, int blocks, const 
     return cudaGetLastError();
 }
 
-// Per (device, stream) context: descriptor buffers, counters and, per class
-// of persistent kernel, the graph of its launch (copy descriptors in, clear
-// the counters, run).
+// Per (device, stream, slot) context: descriptor buffers, counters and, per
+// class of persistent kernel, the graph of its launch (copy descriptors in,
+// clear the counters, run). Two slots let a caller issue the next batch while
+// the previous one runs (batch_launch without waiting, then batch_wait).
 struct BatchCtx {
     unsigned char* host = nullptr;     // pinned descriptors
     unsigned char* dev = nullptr;      // device descriptors
@@ -394,16 +396,22 @@ struct BatchCtx {
     cudaEvent_t fork = nullptr, join[NBRANCH] = {};
     int blocks[NCLASS + 1] = {};       // launch size per persistent kernel (index cls + 1)
     cudaGraphExec_t exec[NCLASS + 1] = {};
+    // a launch not waited for: its graph, an event behind it and its status word read back
+    bool pending = false;
+    cudaGraphExec_t pending_exec = nullptr;
+    cudaEvent_t done = nullptr;
+    int* h_status = nullptr;           // pinned, 8 words
+    int* pending_status = nullptr;     // the device status word it copied
 };
 
 std::mutex g_batch_mu;
-std::map<std::pair<int, cudaStream_t>, BatchCtx*> g_batch;
+std::map<std::tuple<int, cudaStream_t, int>, BatchCtx*> g_batch;
 
-BatchCtx* context_for(cudaStream_t st) {
+BatchCtx* context_for(cudaStream_t st, int slot) {
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(g_batch_mu);
-    BatchCtx*& c = g_batch[{dev, st}];
+    BatchCtx*& c = g_batch[std::make_tuple(dev, st, slot)];
     if (!c) c = new BatchCtx();
     return c;
 }
@@ -470,12 +478,37 @@ int graph_for(BatchCtx* c, int cls) {
 
 }  // namespace
 
-}  // namespace wfa
+// Waits for the launch that batch_launch(..., slot, false) left running on
+// stream st, frees its graph and reports its status word (WFA_OK when none is
+// pending).
+int batch_wait(cudaStream_t st, int slot) {
+    BatchCtx* c = context_for(st, slot);
+    if (!c->pending) return WFA_OK;
+    c->pending = false;
+    const cudaError_t e = cudaEventSynchronize(c->done);
+    if (c->pending_exec) cudaGraphExecDestroy(c->pending_exec);
+    c->pending_exec = nullptr;
+    if (e != cudaSuccess) return cuda_fail(e, "wfa_batch_run wait");
+    const int code = c->h_status[0];
+    if (code != 0) {
+        cudaMemsetAsync(c->pending_status, 0, 8 * sizeof(int), st);
+        cudaStreamSynchronize(st);
+        if (code >= 10) {
+            set_error("checked build: bad access, code %d at (%d, %d, %d) extra %d", code, c->h_status[1],
+                      c->h_status[2], c->h_status[3], c->h_status[4]);
+            return WFA_ERR_CUDA;
+        }
+        set_error("a device-side wait gave up after its time limit (code %d)", code);
+        return WFA_ERR_TIMEOUT;
+    }
+    return WFA_OK;
+}
 
-using namespace wfa;
-
-extern "C" int wfa_batch_run(wfa_grid* gs, const long long* steps, int count) {
-    NvtxRange nvtx_("wfa_batch_run");
+// The batched sweep. wait = false (per-round modes only; the persistent mode
+// always waits) returns once the work is queued on the grids' stream, with
+// the grids' state already advanced; batch_wait(stream, slot) must follow
+// before the slot is used again, and the grids must stay alive until then.
+int batch_launch(wfa_grid* gs, const long long* steps, int count, int slot, bool wait) {
     if (count < 0 || (count > 0 && (!gs || !steps))) {
         set_error("wfa_batch_run: bad arguments");
         return WFA_ERR_ARG;
@@ -564,8 +597,13 @@ extern "C" int wfa_batch_run(wfa_grid* gs, const long long* steps, int count) {
     // on the stream)
     const char* mode_env = getenv("WFA_BATCH_MODE");
     const int mode = !mode_env ? 1 : !strcmp(mode_env, "persistent") ? 0 : !strcmp(mode_env, "stream") ? 2 : 1;
-    BatchCtx* c = context_for(st);
-    int rc;
+    BatchCtx* c = context_for(st, slot);
+    int rc = batch_wait(st, slot);   // a launch of this slot still in flight
+    if (rc) return rc;
+    if (!wait && !c->done) {
+        WFA_CUDA(cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming));
+        WFA_CUDA(cudaMallocHost(&c->h_status, 8 * sizeof(int)));
+    }
     if (mode == 0) {
         // persistent launch: grids by step count (descending), units in that order
         std::vector<int> idx(ng);
@@ -753,10 +791,22 @@ extern "C" int wfa_batch_run(wfa_grid* gs, const long long* steps, int count) {
             if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, gr, 0);
             if (e == cudaSuccess) e = cudaGraphLaunch(ex, st);
         }
-        rc = e == cudaSuccess ? check_status(gs[order[0]]) : cuda_fail(e, "wfa_batch_run launch");   // synchronises
+        if (gr) cudaGraphDestroy(gr);   // the executable graph holds what it runs
+        if (e == cudaSuccess && !wait) {
+            // read back the status word behind the work, then an event for batch_wait
+            e = cudaMemcpyAsync(c->h_status, status, 8 * sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaEventRecord(c->done, st);
+            if (e == cudaSuccess) {
+                c->pending = true;
+                c->pending_exec = ex;
+                c->pending_status = status;
+                ex = nullptr;
+            }
+        }
+        rc = e != cudaSuccess ? cuda_fail(e, "wfa_batch_run launch")
+                              : wait ? check_status(gs[order[0]]) : WFA_OK;   // check_status synchronises
         if (e != cudaSuccess) cudaStreamSynchronize(st);
         if (ex) cudaGraphExecDestroy(ex);
-        if (gr) cudaGraphDestroy(gr);
         if (rc) return rc;
     }
     for (int k = 0; k < ng; ++k) {
@@ -771,4 +821,13 @@ extern "C" int wfa_batch_run(wfa_grid* gs, const long long* steps, int count) {
         g->steps_done += mg[k].steps;
     }
     return WFA_OK;
+}
+
+}  // namespace wfa
+
+using namespace wfa;
+
+extern "C" int wfa_batch_run(wfa_grid* gs, const long long* steps, int count) {
+    NvtxRange nvtx_("wfa_batch_run");
+    return batch_launch(gs, steps, count, 0, true);
 }

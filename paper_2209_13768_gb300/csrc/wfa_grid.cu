@@ -1361,4 +1361,11 @@ int grid_rebind_stream(wfa_grid_s* g, cudaStream_t st) {
     g->stream = st;
     return WFA_OK;
 }
+
+// As grid_rebind_stream, for a caller that knows no work of g is pending on
+// its stream (it has waited for an event behind the last of it).
+int grid_move_stream(wfa_grid_s* g, cudaStream_t st) {
+    g->stream = st;
+    return WFA_OK;
+}
 }  // namespace wfa

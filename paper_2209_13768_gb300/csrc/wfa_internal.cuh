@@ -180,6 +180,7 @@ void dev_free(void* p, cudaStream_t st);
 cudaError_t padded_alloc(void** p, size_t bytes, int esize, cudaStream_t st);
 void padded_free(void* p, int esize, cudaStream_t st);
 int grid_rebind_stream(wfa_grid_s* g, cudaStream_t st);          // move a quiet grid to another stream
+int grid_move_stream(wfa_grid_s* g, cudaStream_t st);            // the same, the caller has waited already
 
 // ----------------------------------------------------------- device math --
 // The fixed per-cell arithmetic. Every kernel that updates a cell calls these

@@ -5,9 +5,11 @@
 // (shortest remaining work first, with no resident passed over more than 8
 // ticks in a row) and moves each by up to `quantum` steps (all of its steps
 // when fewer than two quanta are left), all of them together in one batched
-// launch (wfa_batch_run; measured faster than stepping the large ones alone,
-// which serialises them). Requests that arrive while others run join at the next
-// tick. Four more threads move inputs to the device and results back, each
+// launch (the batched sweep; measured faster than stepping the large ones
+// alone, which serialises them). A tick is launched without waiting: the host
+// builds the next one while it runs, then waits for it and hands its finished
+// requests to read-back. Requests that arrive while others run join at the
+// next tick. Four more threads move inputs to the device and results back, each
 // on its own stream, while the ticks run; a finished request's memory is
 // released as soon as its result is on the host.
 #include <cuda_runtime.h>
@@ -32,6 +34,9 @@
 namespace wfa {
 void set_error(const char* fmt, ...);
 int grid_rebind_stream(wfa_grid g, cudaStream_t st);
+int grid_move_stream(wfa_grid g, cudaStream_t st);
+int batch_launch(wfa_grid* gs, const long long* steps, int count, int slot, bool wait);
+int batch_wait(cudaStream_t st, int slot);
 }
 
 namespace {
@@ -70,6 +75,17 @@ size_t device_bytes(const wfa_request& r) {
 
 }  // namespace
 
+// One tick: the residents it advances, by how many steps, and those it
+// finishes. Ticks are launched without waiting, so the host builds the next
+// tick (selection, descriptors, graph) while this one runs on the GPU.
+struct Tick {
+    bool live = false;   // launched, not yet waited for
+    int slot = 0;        // batch context (two alternate)
+    std::vector<Req*> work, finished;
+    double upd = 0.0;    // cell updates
+    clk::time_point t0;
+};
+
 struct wfa_server_s {
     size_t budget = 0;
     int max_resident = 1024;
@@ -97,7 +113,10 @@ struct wfa_server_s {
     size_t used = 0, peak_used = 0;
     std::vector<double> latencies;
 
+    clk::time_point busy_end{};     // when the last waited tick ended
+
     void run();
+    void settle(Tick& t, int rc, const std::string& why);
     void prep_loop(int w);
     int setup(Req* r, cudaStream_t st);
     int setup_grid(Req* r, cudaStream_t st);
@@ -171,7 +190,8 @@ void wfa_server_s::prep_loop(int w) {
             }
         }
         if (retire) {
-            int rc = r->err.empty() ? wfa::grid_rebind_stream(r->g, prep[w]) : WFA_ERR_STATE;
+            // its last tick has been waited for: nothing of it is pending on the tick stream
+            int rc = r->err.empty() ? wfa::grid_move_stream(r->g, prep[w]) : WFA_ERR_STATE;
             if (!rc) rc = wfa_read_field(r->g, r->spec.out_host);
             finish(r, rc == 0, rc ? (r->err.empty() ? std::string(wfa_last_error()) : r->err) : std::string());
             continue;
@@ -186,17 +206,54 @@ void wfa_server_s::prep_loop(int w) {
     }
 }
 
+// Waits for a launched tick; its finished requests go to read-back. On
+// failure every request of the tick fails and leaves the resident set
+// (the caller has waited for any later tick that still used them).
+void wfa_server_s::settle(Tick& t, int rc, const std::string& why) {
+    const auto t1 = clk::now();
+    std::lock_guard<std::mutex> lk(mu);
+    ++ticks;
+    busy_s += std::chrono::duration<double>(t1 - std::max(t.t0, busy_end)).count();
+    busy_end = t1;
+    if (!rc) {
+        cell_updates += t.upd;
+    } else {
+        for (Req* r : t.work) {
+            if (r->err.empty()) r->err = why.empty() ? "tick failed" : why;
+            auto it = std::find(resident.begin(), resident.end(), r);
+            if (it != resident.end()) {
+                resident.erase(it);
+                t.finished.push_back(r);
+            }
+        }
+    }
+    for (Req* r : t.finished) to_retire.push_back(r);
+    t.live = false;
+    t.work.clear();
+    t.finished.clear();
+    cv_prep.notify_all();
+}
+
 void wfa_server_s::run() {
     cudaSetDevice(device);
     std::vector<wfa_grid> gs;
     std::vector<long long> steps;
+    Tick ticks_[2];
+    int cur = 0;   // ticks_[cur] is the next to launch, ticks_[1 - cur] may be in flight
+    auto wait_tick = [&](Tick& t) {
+        const int rc = wfa::batch_wait(stream, t.slot);
+        settle(t, rc, rc ? std::string(wfa_last_error()) : std::string());
+        return rc;
+    };
     for (;;) {
+        Tick& prev = ticks_[1 - cur];
         std::vector<Req*> work;
         {
             std::unique_lock<std::mutex> lk(mu);
-            cv_work.wait(lk, [&] {
-                return stop || !pending.empty() || !resident.empty() || !ready.empty();
-            });
+            if (!prev.live)
+                cv_work.wait(lk, [&] {
+                    return stop || !pending.empty() || !resident.empty() || !ready.empty();
+                });
             // admission: first come, first served, while memory and slots allow
             // (a slot is held from admission on: queued for set-up, in set-up,
             // ready or resident)
@@ -215,6 +272,11 @@ void wfa_server_s::run() {
             for (Req* r : ready) resident.push_back(r);
             ready.clear();
             if (resident.empty()) {
+                if (prev.live) {   // finish the tick in flight first: it frees memory and slots
+                    lk.unlock();
+                    wait_tick(prev);
+                    continue;
+                }
                 if (stop && pending.empty() && to_setup.empty() && in_setup == 0) {
                     sched_done = true;
                     cv_prep.notify_all();
@@ -229,55 +291,65 @@ void wfa_server_s::run() {
         // this tick: the residents with the least remaining work first, up to
         // about TICK_CELLS cells (enough to fill the GPU), plus any resident
         // passed over MAX_SKIP ticks in a row; one that is nearly done gets
-        // all its remaining steps
+        // all its remaining steps (remaining work already counts the tick in
+        // flight)
         auto cells = [](const Req* r) { return (double)r->spec.nx * r->spec.ny * r->spec.nz; };
         std::stable_sort(work.begin(), work.end(),
                          [&](const Req* a, const Req* b) { return cells(a) * a->remaining < cells(b) * b->remaining; });
-        std::vector<Req*> sel;
+        Tick& t = ticks_[cur];
+        t.work.clear();
+        t.finished.clear();
+        t.upd = 0.0;
         double sel_cells = 0.0;
         for (Req* r : work) {
             if (sel_cells < TICK_CELLS || r->skipped >= MAX_SKIP) {
-                sel.push_back(r);
+                t.work.push_back(r);
                 sel_cells += cells(r);
                 r->skipped = 0;
             } else {
                 ++r->skipped;
             }
         }
-        work.swap(sel);
         gs.clear();
         steps.clear();
-        std::vector<long long> q_of(work.size());
-        double upd = 0.0;
-        int rc = 0;
-        const auto t0 = clk::now();
-        for (size_t i = 0; i < work.size(); ++i) {
-            Req* r = work[i];
+        std::vector<long long> q_of(t.work.size());
+        for (size_t i = 0; i < t.work.size(); ++i) {
+            Req* r = t.work[i];
             const long long q = r->remaining <= 2 * quantum ? r->remaining : quantum;
             q_of[i] = q;
-            upd += (double)q * cells(r);
+            t.upd += (double)q * cells(r);
             gs.push_back(r->g);
             steps.push_back(q);
         }
+        t.t0 = clk::now();
+        t.slot = cur;
         nvtxRangePushA("wfa_server_tick");
-        if (!rc && !gs.empty()) rc = wfa_batch_run(gs.data(), steps.data(), (int)gs.size());
-        if (!rc) rc = cudaStreamSynchronize(stream) == cudaSuccess ? 0 : WFA_ERR_CUDA;
+        const int rc = wfa::batch_launch(gs.data(), steps.data(), (int)gs.size(), t.slot, false);
         nvtxRangePop();
-        const auto t1 = clk::now();
         const std::string why = rc ? std::string(wfa_last_error()) : std::string();
-        std::lock_guard<std::mutex> lk(mu);
-        ++ticks;
-        busy_s += std::chrono::duration<double>(t1 - t0).count();
-        if (!rc) cell_updates += upd;
-        for (size_t i = 0; i < work.size(); ++i) {
-            Req* r = work[i];
-            if (rc || (r->remaining -= q_of[i]) <= 0) {
-                if (rc) r->err = why.empty() ? "tick failed" : why;
-                resident.erase(std::find(resident.begin(), resident.end(), r));
-                to_retire.push_back(r);
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            for (size_t i = 0; i < t.work.size(); ++i) {
+                Req* r = t.work[i];
+                if (!rc && (r->remaining -= q_of[i]) <= 0) {
+                    resident.erase(std::find(resident.begin(), resident.end(), r));
+                    t.finished.push_back(r);
+                }
             }
         }
-        cv_prep.notify_all();
+        t.live = !rc;
+        // the previous tick has run meanwhile: retire what it finished
+        int rc_prev = prev.live ? wait_tick(prev) : 0;
+        if (rc_prev && t.live) {   // its requests may be in this tick too: fail both
+            wfa::batch_wait(stream, t.slot);
+            settle(t, rc_prev, "an earlier tick failed");
+        }
+        if (rc) {   // nothing of this tick runs: its requests fail
+            t.live = true;
+            t.t0 = clk::now();
+            settle(t, rc, why);
+        }
+        cur = 1 - cur;
     }
 }
 
