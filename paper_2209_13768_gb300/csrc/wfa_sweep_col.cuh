@@ -12,6 +12,7 @@
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
 
 #include "wfa_sweep.cuh"
 
@@ -20,6 +21,12 @@ namespace wfa {
 // Ask L2 for the line holding p (no register, no completion to wait for).
 __device__ __forceinline__ void prefetch_l2(const void* p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+// The same under a predicate: no branch, so the warps that do not ask pay one
+// instruction and no reconvergence.
+__device__ __forceinline__ void prefetch_l2_if(const void* p, bool pred) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %1, 0;\n\t@q prefetch.global.L2 [%0];\n\t}" ::"l"(p),
+                 "r"((int)pred));
 }
 
 // 4 consecutive stored values -> 4 floats, and one value. COH = false reads
@@ -149,6 +156,54 @@ __device__ __forceinline__ void stv<__nv_bfloat16, 8>(__nv_bfloat16* p, const fl
     *reinterpret_cast<uint4*>(p) = q;
 }
 
+// V new values rounded to S once (bf16: packed in pairs), then stored at one
+// or more places; store_if is a predicated vector store (no branch). Every
+// address is aligned to V elements.
+__device__ __forceinline__ void st4_if(float* p, float a, float b, float c, float d, bool pred) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %5, 0;\n\t@q st.global.v4.f32 [%0], {%1, %2, %3, %4};\n\t}" ::"l"(p),
+                 "f"(a), "f"(b), "f"(c), "f"(d), "r"((int)pred));
+}
+__device__ __forceinline__ void st4_if(void* p, unsigned a, unsigned b, unsigned c, unsigned d, bool pred) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %5, 0;\n\t@q st.global.v4.b32 [%0], {%1, %2, %3, %4};\n\t}" ::"l"(p),
+                 "r"(a), "r"(b), "r"(c), "r"(d), "r"((int)pred));
+}
+__device__ __forceinline__ void st2_if(void* p, unsigned a, unsigned b, bool pred) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\t@q st.global.v2.b32 [%0], {%1, %2};\n\t}" ::"l"(p),
+                 "r"(a), "r"(b), "r"((int)pred));
+}
+__device__ __forceinline__ unsigned pack_bf16x2(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const unsigned*>(&h);
+}
+template <typename S, int V> struct StoreVec;
+template <int V> struct StoreVec<float, V> {
+    float v[V];
+    __device__ __forceinline__ explicit StoreVec(const float* o) {
+#pragma unroll
+        for (int i = 0; i < V; ++i) v[i] = o[i];
+    }
+    __device__ __forceinline__ void store(float* p) const { stv<float, V>(p, v); }
+    __device__ __forceinline__ void store_if(float* p, bool pred) const {
+        st4_if(p, v[0], v[1], v[2], v[3], pred);
+        if (V == 8) st4_if(p + 4, v[4], v[5], v[6], v[7], pred);
+    }
+};
+template <int V> struct StoreVec<__nv_bfloat16, V> {
+    unsigned u[V / 2];
+    __device__ __forceinline__ explicit StoreVec(const float* o) {
+#pragma unroll
+        for (int i = 0; i < V / 2; ++i) u[i] = pack_bf16x2(o[2 * i], o[2 * i + 1]);
+    }
+    __device__ __forceinline__ void store(__nv_bfloat16* p) const {
+        if (V == 8) *reinterpret_cast<uint4*>(p) = make_uint4(u[0], u[1], u[2], u[3]);
+        else *reinterpret_cast<uint2*>(p) = make_uint2(u[0], u[1]);
+    }
+    __device__ __forceinline__ void store_if(__nv_bfloat16* p, bool pred) const {
+        if (V == 8) st4_if(p, u[0], u[1], u[2], u[V == 8 ? 3 : 1], pred);
+        else st2_if(p, u[0], u[1], pred);
+    }
+};
+
 // x / y neighbours of one plane for one thread: the V cells below and above in
 // y and the x neighbours of the row ends; same for 1/k. They belong to other
 // threads' columns, so they come from L1 (or L2).
@@ -156,16 +211,18 @@ template <typename S, bool KVAR, bool COH, int V = 4>
 struct ColNb {
     float ty_m[V], ty_p[V], tx_m, tx_p;
     float ry_m[V], ry_p[V], rx_m, rx_p;
-    __device__ __forceinline__ void load(const S* tp, const float* rp, long long sy) {
-        ldgv<S, COH, V>(tp - sy, ty_m);
-        ldgv<S, COH, V>(tp + sy, ty_p);
-        tx_m = ldg1<S, COH>(tp - 1);
-        tx_p = ldg1<S, COH>(tp + V);
+    // plane at byte offset to of base tB (1/k: ro of rB); syt / syr: one row in bytes
+    template <typename OT>
+    __device__ __forceinline__ void load(const char* tB, OT to, const char* rB, OT ro, OT syt, OT syr) {
+        ldgv<S, COH, V>(reinterpret_cast<const S*>(tB + (OT)(to - syt)), ty_m);
+        ldgv<S, COH, V>(reinterpret_cast<const S*>(tB + (OT)(to + syt)), ty_p);
+        tx_m = ldg1<S, COH>(reinterpret_cast<const S*>(tB + (OT)(to - (OT)sizeof(S))));
+        tx_p = ldg1<S, COH>(reinterpret_cast<const S*>(tB + (OT)(to + (OT)(V * sizeof(S)))));
         if (KVAR) {   // 1/k never changes during a launch: read-only path
-            ldgv<float, false, V>(rp - sy, ry_m);
-            ldgv<float, false, V>(rp + sy, ry_p);
-            rx_m = __ldg(rp - 1);
-            rx_p = __ldg(rp + V);
+            ldgv<float, false, V>(reinterpret_cast<const float*>(rB + (OT)(ro - syr)), ry_m);
+            ldgv<float, false, V>(reinterpret_cast<const float*>(rB + (OT)(ro + syr)), ry_p);
+            rx_m = __ldg(reinterpret_cast<const float*>(rB + (OT)(ro - 4u)));
+            rx_p = __ldg(reinterpret_cast<const float*>(rB + (OT)(ro + 4u * V)));
         }
     }
 };
@@ -178,8 +235,9 @@ struct ColNb {
 // uniform k). Register-level prefetch was slower: it costs the occupancy.
 template <bool KVAR, bool INL = false, int ES = 4, int V = 4> struct ColOcc {
     static constexpr int blocks = V == 8 ? (KVAR ? 2 : 4) : INL ? (KVAR ? 3 : 4) : (KVAR ? 4 : 6);
-    // measured: fp32 uniform k prefers the z loop unrolled twice, bf16 not
-    static constexpr int unroll = (KVAR || ES == 2 || V == 8) ? 1 : 2;
+    // measured: uniform k prefers the z loop unrolled twice (fp32 with 4
+    // cells a thread, bf16 with 8), per-cell k not
+    static constexpr int unroll = KVAR ? 1 : (V == 4 && ES == 4) || (V == 8 && ES == 2) ? 2 : 1;
 };
 
 // How a column pass treats boundary cells and periodic copies.
@@ -205,7 +263,7 @@ enum ColMode {
 // change a cell's value: the z faces are symmetric bit for bit and every
 // cell takes the same operands in the same order.
 template <typename S, bool KVAR, bool ADV, bool COH, int UNROLL, ColMode MODE, bool PF = false, bool GHOST = false,
-          int DIR = 1, int V = 4, bool TW = true>
+          int DIR = 1, int V = 4, bool TW = true, bool O32 = false>
 __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict__ tin, S* __restrict__ tout,
                                         const float* __restrict__ rk, int* status, int gx, int gy, int z0, int z1) {
     static_assert(V == 4 || V == 8, "cells per thread");
@@ -241,23 +299,49 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
         for (int i = 0; i < V; ++i) gzm[i] = face_r(rb[i], rc[i], c.tcd[2]);
     }
 
+    // Addresses in the loop: a base at the start of the padded array and a
+    // byte offset. O32 (the caller has checked that every array is under
+    // 4 GiB): 32-bit offsets, one integer add per address; otherwise 64-bit.
+    // T and the new field share the layout, so one offset serves both.
+    using OT = typename std::conditional<O32, unsigned, unsigned long long>::type;
+    const long long org = HALO * sz + HALO * sy + HALO;   // elements before the domain origin
+    const char* const tB = reinterpret_cast<const char*>(tin - org);
+    char* const oB = reinterpret_cast<char*>(tout - org);
+    const char* const rB = KVAR ? reinterpret_cast<const char*>(rk - org) : nullptr;
+    const long long cell0 = org + col + (long long)zs * sz;   // this thread's first cell, plane zs
+    OT to = (OT)(cell0 * (long long)sizeof(S));
+    OT ro = KVAR ? (OT)(cell0 * 4) : (OT)0;
+    const OT dzt = (OT)(dsz * (long long)sizeof(S)), dzr = (OT)(dsz * 4);
+    const OT syt = (OT)(sy * (long long)sizeof(S)), syr = (OT)(sy * 4);
+    const int len = z1 - z0;
+    const bool pf_lead = PF && (threadIdx.x & (LINE_T - 1)) == 0;
+    // THIN: the periodic copies this thread stores at every plane. With
+    // n_x a multiple of V the row's first and last vectors are stored whole
+    // (shifted by -+n_x into the halo: every shifted cell is a copy);
+    // otherwise cell by cell.
+    const bool xvec = c.n[0] % V == 0;
+    const bool xt_first = MODE == COL_THIN && TW && perx && gx == 0;
+    const int xlast = c.n[0] - 1 - gx;   // index of cell n_x - 1 in this thread's vector (if 0 <= xlast < V)
+    const bool xt_last = MODE == COL_THIN && TW && perx && xlast >= 0 && xlast < V;
+    const long long yoff = MODE == COL_THIN && TW && pery ? (gy == 0 ? c.n[1] * sy : gy == c.n[1] - 1 ? -c.n[1] * sy : 0) : 0;
+    const OT yoffb = (OT)(yoff * (long long)sizeof(S)), xoffb = (OT)((long long)c.n[0] * (long long)sizeof(S));
+
 #pragma unroll(UNROLL)
-    for (int s = 0; s < z1 - z0; ++s) {
+    for (int s = 0; s < len; ++s) {
         const int z = DIR > 0 ? z0 + s : z1 - 1 - s;
-        const S* tp = tcol + (long long)z * sz;
-        const float* rp = KVAR ? rcol + (long long)z * sz : nullptr;
         float tz[V], rz[V];
-        ldgv<S, COH, V>(tp + dsz, tz);                   // own cells, plane z + DIR
+        ldgv<S, COH, V>(reinterpret_cast<const S*>(tB + (OT)(to + dzt)), tz);   // own cells, plane z + DIR
         // one thread per 128-byte line asks L2 for plane z + 3 DIR, as long as
         // the chunk still needs it (the last plane read is z1 going up, z0 - 1
         // going down); the plane after that belongs to the next chunk
-        if (PF && (threadIdx.x & (LINE_T - 1)) == 0 && s + 3 <= z1 - z0) {
-            prefetch_l2(tp + 3 * dsz);
-            if (KVAR) prefetch_l2(rp + 3 * dsz);
+        if (PF) {
+            prefetch_l2_if(tB + (OT)(to + 3 * dzt), pf_lead && s + 3 <= len);
+            if (KVAR) prefetch_l2_if(rB + (OT)(ro + 3 * dzr), pf_lead && s + 3 <= len);
         }
-        if (KVAR) ldgv<float, false, V>(rp + dsz, rz);
+        if (KVAR) ldgv<float, false, V>(reinterpret_cast<const float*>(rB + (OT)(ro + dzr)), rz);
         ColNb<S, KVAR, COH, V> nb;                       // x / y neighbours, plane z
-        nb.load(tp, rp, sy);
+        nb.load(tB, to, rB, ro, syt, syr);
+        S* const op = reinterpret_cast<S*>(oB + to);     // this thread's cells at plane z
 
         const bool bzm = !perz && !c.ext[4] && z == 0, bzp = !perz && !c.ext[5] && z == c.n[2] - 1;
         // GHOST (c.halo_bc known at compile time) or c.halo_bc: the ghost layers hold the faces
@@ -291,16 +375,16 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
                 for (int f = 0; f < 6; ++f) w[i][f] = c.w_in[f];
             }
         }
+        // the new values in fp32; every store rounds them to S once
         float out[V];
         if (MODE == COL_MAIN || MODE == COL_THIN || fast) {   // interior formula (see ColMode)
 #pragma unroll
             for (int i = 0; i < V; ++i) {
                 const float txm = i == 0 ? nb.tx_m : tc[i - 1];
                 const float txp = i == V - 1 ? nb.tx_p : tc[i + 1];
-                out[i] = storage_round<S>(__fadd_rn(tc[i], flux_sum(tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i],
-                                                                    DIR > 0 ? tm[i] : tz[i], DIR > 0 ? tz[i] : tm[i],
-                                                                    w[i][0], w[i][1], w[i][2], w[i][3], w[i][4],
-                                                                    w[i][5])));
+                out[i] = __fadd_rn(tc[i], flux_sum(tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i], DIR > 0 ? tm[i] : tz[i],
+                                                   DIR > 0 ? tz[i] : tm[i], w[i][0], w[i][1], w[i][2], w[i][3],
+                                                   w[i][4], w[i][5]));
             }
         } else {
 #pragma unroll
@@ -309,50 +393,49 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
                 const float txp = i == V - 1 ? nb.tx_p : tc[i + 1];
                 const float tzm = DIR > 0 ? tm[i] : tz[i], tzp = DIR > 0 ? tz[i] : tm[i];
                 const bool edge_cell = bym || byp || bzm || bzp || (!perx && (gx + i == 0 || gx + i == c.n[0] - 1));
-                float v;
                 if (!KVAR) {   // uniform k: the boundary formula by select, inline
-                    v = uniform_cell(c, tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i], tzm, tzp, gx + i, gy, z);
+                    out[i] = uniform_cell(c, tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i], tzm, tzp, gx + i, gy, z);
                 } else if (!edge_cell) {
-                    v = __fadd_rn(tc[i], flux_sum(tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i], tzm, tzp, w[i][0],
-                                                  w[i][1], w[i][2], w[i][3], w[i][4], w[i][5]));
+                    out[i] = __fadd_rn(tc[i], flux_sum(tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i], tzm, tzp, w[i][0],
+                                                       w[i][1], w[i][2], w[i][3], w[i][4], w[i][5]));
                 } else {
-                    v = boundary_update<KVAR>(&c, tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i], tzm, tzp, w[i][0],
-                                              w[i][1], w[i][2], w[i][3], w[i][4], w[i][5], KVAR ? rc[i] : 0.0f,
-                                              gx + i, gy, z);
+                    out[i] = boundary_update<KVAR>(&c, tc[i], txm, txp, nb.ty_m[i], nb.ty_p[i], tzm, tzp, w[i][0],
+                                                   w[i][1], w[i][2], w[i][3], w[i][4], w[i][5], KVAR ? rc[i] : 0.0f,
+                                                   gx + i, gy, z);
                 }
-                out[i] = storage_round<S>(v);
             }
         }
-        S* const orow = tout + (long long)z * sz + col;   // this thread's cells at plane z
         if (MODE == COL_THIN) {
             // the cells (masked at the x end: the halo there holds the x copies),
             // then one layer of periodic copies for the next one-step pass
+            const StoreVec<S, V> sv(out);
+            const long long zoff = TW && perz ? (z == 0 ? c.n[2] * sz : z == c.n[2] - 1 ? -c.n[2] * sz : 0) : 0;
             if (full_x) {
-                stv<S, V>(orow, out);
+                sv.store(op);
+                // pery / perz are the same for every thread: uniform branches
+                if (TW && pery) sv.store_if(reinterpret_cast<S*>(oB + (OT)(to + yoffb)), yoff != 0);
+                if (TW && perz)
+                    sv.store_if(reinterpret_cast<S*>(oB + (OT)(to + (OT)(zoff * (long long)sizeof(S)))), zoff != 0);
             } else {
 #pragma unroll
                 for (int i = 0; i < V; ++i)
-                    if (gx + i < c.n[0]) orow[i] = from_f32<S>(out[i]);
+                    if (gx + i < c.n[0]) {
+                        op[i] = from_f32<S>(out[i]);
+                        if (TW && yoff != 0) op[yoff + i] = from_f32<S>(out[i]);
+                        if (TW && zoff != 0) op[zoff + i] = from_f32<S>(out[i]);
+                    }
             }
             if (TW && perx) {
-                if (gx == 0) orow[c.n[0]] = from_f32<S>(out[0]);
-                const int last = c.n[0] - 1 - gx;
-                if (last >= 0 && last < V) {
-#pragma unroll
-                    for (int i = 0; i < V; ++i)
-                        if (i == last) orow[i - c.n[0]] = from_f32<S>(out[i]);   // cell n - 1 at x = -1
-                }
-            }
-            const long long yoff = TW && pery ? (gy == 0 ? c.n[1] * sy : gy == c.n[1] - 1 ? -c.n[1] * sy : 0) : 0;
-            const long long zoff = TW && perz ? (z == 0 ? c.n[2] * sz : z == c.n[2] - 1 ? -c.n[2] * sz : 0) : 0;
-            for (long long off : {yoff, zoff}) {
-                if (!TW || off == 0) continue;
-                if (full_x) {
-                    stv<S, V>(orow + off, out);
+                if (xvec) {
+                    sv.store_if(reinterpret_cast<S*>(oB + (OT)(to + xoffb)), xt_first);
+                    sv.store_if(reinterpret_cast<S*>(oB + (OT)(to - xoffb)), xt_last);
                 } else {
+                    if (xt_first) op[c.n[0]] = from_f32<S>(out[0]);
+                    if (xt_last) {
 #pragma unroll
-                    for (int i = 0; i < V; ++i)
-                        if (gx + i < c.n[0]) orow[off + i] = from_f32<S>(out[i]);
+                        for (int i = 0; i < V; ++i)
+                            if (i == xlast) op[i - c.n[0]] = from_f32<S>(out[i]);   // cell n - 1 at x = -1
+                    }
                 }
             }
         } else {
@@ -362,13 +445,13 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
             if (MODE == COL_MAIN && KVAR && !full_x) {
 #pragma unroll
                 for (int i = 0; i < V; ++i)
-                    if (gx + i < c.n[0]) orow[i] = from_f32<S>(out[i]);
+                    if (gx + i < c.n[0]) op[i] = from_f32<S>(out[i]);
             } else if (MODE == COL_MAIN || plain) {
-                stv<S, V>(orow, out);
+                stv<S, V>(op, out);
             } else if (!perx && !pery && !perz) {   // the x end of a row, no copies to store
 #pragma unroll
                 for (int i = 0; i < V; ++i)
-                    if (gx + i < c.n[0]) orow[i] = from_f32<S>(out[i]);
+                    if (gx + i < c.n[0]) op[i] = from_f32<S>(out[i]);
             } else {
 #pragma unroll
                 for (int i = 0; i < V; ++i)
@@ -384,6 +467,8 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
                 gzm[i] = gzp[i];
             }
         }
+        to += dzt;
+        if (KVAR) ro += dzr;
     }
 }
 
@@ -395,7 +480,8 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
 // boundary_fix where the ghost layers do not hold the faces.
 // TW: some axis is periodic (the thin pass stores its one layer of copies;
 // without a periodic axis that code is not compiled).
-template <typename S, bool KVAR, bool ADV, bool INL, int V = 4, bool TW = true>
+// O32: every array of the grid is under 4 GiB (32-bit byte offsets).
+template <typename S, bool KVAR, bool ADV, bool INL, int V = 4, bool TW = true, bool O32 = true>
 __global__ void __launch_bounds__(256, (ColOcc<KVAR, INL, sizeof(S), V>::blocks))
     sweep_col(const __grid_constant__ SweepArgs a) {
     const SweepCoef& c = a.c;
@@ -407,11 +493,11 @@ __global__ void __launch_bounds__(256, (ColOcc<KVAR, INL, sizeof(S), V>::blocks)
     constexpr int U = ColOcc<KVAR, INL, sizeof(S), V>::unroll;
     constexpr ColMode MODE = INL ? COL_INPLACE : COL_THIN;
     if (blockIdx.z & 1)   // odd chunks march down: see col_run
-        col_run<S, KVAR, ADV, false, U, MODE, true, false, -1, V, TW>(c, (const S*)a.tin, (S*)a.tout, a.rk,
-                                                                     a.status, gx, gy, z0, z1);
+        col_run<S, KVAR, ADV, false, U, MODE, true, false, -1, V, TW, O32>(c, (const S*)a.tin, (S*)a.tout, a.rk,
+                                                                          a.status, gx, gy, z0, z1);
     else
-        col_run<S, KVAR, ADV, false, U, MODE, true, false, 1, V, TW>(c, (const S*)a.tin, (S*)a.tout, a.rk,
-                                                                    a.status, gx, gy, z0, z1);
+        col_run<S, KVAR, ADV, false, U, MODE, true, false, 1, V, TW, O32>(c, (const S*)a.tin, (S*)a.tout, a.rk,
+                                                                         a.status, gx, gy, z0, z1);
 }
 
 // Boundary cells (the outer layer on every non-periodic face): recomputed
@@ -532,16 +618,28 @@ cudaError_t col_launch_v(const SweepArgs& a_in, cudaStream_t st, int nsm, const 
     dim3 grid(gxb, gyb, nch);
     const bool adv = KVAR && (a.c.adv[0] != 0.0f || a.c.adv[1] != 0.0f || a.c.adv[2] != 0.0f ||
                               a.c.adv[3] != 0.0f || a.c.adv[4] != 0.0f || a.c.adv[5] != 0.0f);
+    // 32-bit byte offsets when the largest array (1/k, or T) is under 4 GiB
+    const bool o32 = (double)a.c.pz * (double)a.c.sz * 4.0 < 4294967296.0;
     if (ev) cudaEventRecord(ev[0], st);
     if (inl) {
-        if (adv) sweep_col<S, KVAR, true, true><<<grid, block, 0, st>>>(a);
-        else sweep_col<S, KVAR, false, true><<<grid, block, 0, st>>>(a);
+        if (adv) sweep_col<S, KVAR, true, true, 4, true, false><<<grid, block, 0, st>>>(a);
+        else sweep_col<S, KVAR, false, true, 4, true, false><<<grid, block, 0, st>>>(a);
     } else if (a.c.periodic[0] || a.c.periodic[1] || a.c.periodic[2]) {
-        if (adv) sweep_col<S, KVAR, true, false, V, true><<<grid, block, 0, st>>>(a);
-        else sweep_col<S, KVAR, false, false, V, true><<<grid, block, 0, st>>>(a);
+        if (adv) {
+            if (o32) sweep_col<S, KVAR, true, false, V, true, true><<<grid, block, 0, st>>>(a);
+            else sweep_col<S, KVAR, true, false, V, true, false><<<grid, block, 0, st>>>(a);
+        } else {
+            if (o32) sweep_col<S, KVAR, false, false, V, true, true><<<grid, block, 0, st>>>(a);
+            else sweep_col<S, KVAR, false, false, V, true, false><<<grid, block, 0, st>>>(a);
+        }
     } else {   // no periodic axis: no copies to store
-        if (adv) sweep_col<S, KVAR, true, false, V, false><<<grid, block, 0, st>>>(a);
-        else sweep_col<S, KVAR, false, false, V, false><<<grid, block, 0, st>>>(a);
+        if (adv) {
+            if (o32) sweep_col<S, KVAR, true, false, V, false, true><<<grid, block, 0, st>>>(a);
+            else sweep_col<S, KVAR, true, false, V, false, false><<<grid, block, 0, st>>>(a);
+        } else {
+            if (o32) sweep_col<S, KVAR, false, false, V, false, true><<<grid, block, 0, st>>>(a);
+            else sweep_col<S, KVAR, false, false, V, false, false><<<grid, block, 0, st>>>(a);
+        }
     }
     if (ev) cudaEventRecord(ev[1], st);
     cudaError_t e = cudaGetLastError();
