@@ -39,6 +39,7 @@
 // a thread's planes, fp64 above that (the block, the fixed-order sum over
 // blocks); the GPU's fp64 rate is low, so no fp64 arithmetic sits in the
 // hot loops.
+#include <type_traits>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -108,6 +109,14 @@ __device__ __forceinline__ long long cg_at(const CgCoef& c, int x, int y, int z)
 __device__ __forceinline__ bool cg_held(const CgCoef& c, int x, int y, int z) {
     return (c.held[0] && x == 0) || (c.held[1] && x == c.n[0] - 1) || (c.held[2] && y == 0) ||
            (c.held[3] && y == c.n[1] - 1) || (c.held[4] && z == 0) || (c.held[5] && z == c.n[2] - 1);
+}
+// The same over the faces of mask FM (bit f: face f); the caller knows that
+// the cell is on no face outside FM.
+template <int FM>
+__device__ __forceinline__ bool cg_held_m(const CgCoef& c, int x, int y, int z) {
+    return ((FM & 1) && c.held[0] && x == 0) || ((FM & 2) && c.held[1] && x == c.n[0] - 1) ||
+           ((FM & 4) && c.held[2] && y == 0) || ((FM & 8) && c.held[3] && y == c.n[1] - 1) ||
+           ((FM & 16) && c.held[4] && z == 0) || ((FM & 32) && c.held[5] && z == c.n[2] - 1);
 }
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
@@ -239,15 +248,19 @@ __device__ __forceinline__ float ghost(const CgCoef& c, int f, float v) { return
 // Dirichlet face, T_C across a zero-flux face, the cell's own 1/k), adds the
 // known values to b (Dirichlet faces: d_f Tb; held neighbours: c_f T_D) and
 // masks held cells and cells beyond the x end; without it every neighbour
-// is a free cell inside the domain or across a periodic face.
-template <bool KVAR, bool EDGE>
+// is a free cell inside the domain or across a periodic face. FM: the faces
+// (bit f: face f) whose boundary or held layer may be near the warp's cells
+// (x faces only for warps away from the y and z faces); the others are not
+// looked at.
+template <bool KVAR, bool EDGE, int FM = 63>
 __device__ __forceinline__ void cg_r4(const CgCoef& c, const CgEdge& e, int gx, int gy, int z, const float tc[4],
                                       const float tm[4], const float tp[4], const float ym[4], const float yp[4],
                                       float xm, float xp, const float kc[4], const float km[4], const float kp[4],
                                       const float kym[4], const float kyp[4], float kxm, float kxp, float rv[4],
                                       float& sr, float& sb) {
     const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
-    const bool zlo = EDGE && !c.periodic[2] && z == 0, zhi = EDGE && !c.periodic[2] && z == nz - 1;
+    const bool zlo = EDGE && (FM & 16) && !c.periodic[2] && z == 0,
+               zhi = EDGE && (FM & 32) && !c.periodic[2] && z == nz - 1;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         float t[6] = {i == 0 ? xm : tc[i - 1], i == 3 ? xp : tc[i + 1], ym[i], yp[i], tm[i], tp[i]};
@@ -263,12 +276,15 @@ __device__ __forceinline__ void cg_r4(const CgCoef& c, const CgEdge& e, int gx, 
         float bs = tc[i];
         if (EDGE) {
             const int xi = gx + i;
-            const bool bd[6] = {i == 0 && (e.bits & 1u) != 0, i == e.ih, (e.bits & 2u) != 0, (e.bits & 4u) != 0, zlo, zhi};
+            const bool bd[6] = {(FM & 1) && i == 0 && (e.bits & 1u) != 0, (FM & 2) && i == e.ih,
+                                (FM & 4) && (e.bits & 2u) != 0, (FM & 8) && (e.bits & 4u) != 0, zlo, zhi};
             // a neighbour inside the domain is held only through its own axis's face
-            const bool hn[6] = {c.held[0] && xi == 1, c.held[1] && xi == nx - 2, c.held[2] && gy == 1,
-                                c.held[3] && gy == ny - 2, c.held[4] && z == 1, c.held[5] && z == nz - 2};
+            const bool hn[6] = {(FM & 1) && c.held[0] && xi == 1, (FM & 2) && c.held[1] && xi == nx - 2,
+                                (FM & 4) && c.held[2] && gy == 1, (FM & 8) && c.held[3] && gy == ny - 2,
+                                (FM & 16) && c.held[4] && z == 1, (FM & 32) && c.held[5] && z == nz - 2};
 #pragma unroll
             for (int f = 0; f < 6; ++f) {
+                if (!((FM >> f) & 1)) continue;
                 const float cf = KVAR ? face_r(kc[i], bd[f] ? kc[i] : k[f], c.tcd[f >> 1]) : c.cu[f >> 1];
                 if (hn[f]) bs = __fmaf_rn(cf, t[f], bs);
                 if (bd[f]) {
@@ -292,7 +308,7 @@ __device__ __forceinline__ void cg_r4(const CgCoef& c, const CgEdge& e, int gx, 
             acc = __fmaf_rn(c.cu[2], __fadd_rn(__fsub_rn(t[4], tc[i]), __fsub_rn(t[5], tc[i])), acc);
         }
         if (EDGE) {
-            const bool isfree = gx + i < nx && gy < ny && !cg_held(c, gx + i, gy, z);
+            const bool isfree = gx + i < nx && gy < ny && !cg_held_m<FM>(c, gx + i, gy, z);
             rv[i] = isfree ? acc : 0.0f;
             sr = __fmaf_rn(rv[i], rv[i], sr);
             if (isfree) sb = __fmaf_rn(bs, bs, sb);
@@ -309,8 +325,10 @@ __device__ __forceinline__ void cg_r4(const CgCoef& c, const CgEdge& e, int gx, 
 // the column-march layout of cg_spmv (4 x cells a thread, z queue). The
 // field's periodic twins are current (refresh_halo before the first step,
 // cg_update after every iteration). b adds to T the known values: Dirichlet
-// faces and held neighbours.
-template <bool KVAR>
+// faces and held neighbours. O32: every array is under 4 GiB, so the loop
+// addresses its planes by a 32-bit byte offset from the array's start (one
+// integer add an address); otherwise by a 64-bit one.
+template <bool KVAR, bool O32>
 __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_init(const __grid_constant__ CgArgs a, double tol2,
                                                                          int max_iter) {
     __shared__ double red[CG_TX * CG_TY / 32];
@@ -328,8 +346,9 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_init(co
         const long long sy = c.sy, sz = c.sz;
         const long long row = cg_at(c, gx, gy, 0);
         // fast cells: no boundary face and no held neighbour (two cells from
-        // every non-periodic face)
-        const bool inner_xy = gx + 3 < nx && (perx || (gx > 1 && gx + 5 < nx)) && (pery || (gy > 1 && gy < ny - 2));
+        // every non-periodic face); inner_y: the same along y only
+        const bool inner_y = pery || (gy > 1 && gy < ny - 2);
+        const bool inner_xy = gx + 3 < nx && (perx || (gx > 1 && gx + 5 < nx)) && inner_y;
         const CgEdge edge = cg_edge(c, gx, gy);
         float tm[4], tc[4], km[4], kc[4];
         ld4(xv + row + (long long)(z0 - 1) * sz, tm);
@@ -338,32 +357,48 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_init(co
             ld4(rk + row + (long long)(z0 - 1) * sz, km);
             ld4(rk + row + (long long)z0 * sz, kc);
         }
+        using OT = typename std::conditional<O32, unsigned, unsigned long long>::type;
+        const long long org = HALO * sz + HALO * sy + HALO;   // elements before the domain origin
+        const char* const xB = reinterpret_cast<const char*>(xv - org);
+        const char* const kB = KVAR ? reinterpret_cast<const char*>(rk - org) : nullptr;
+        char* const rB = reinterpret_cast<char*>(a.r - org);
+        auto F = [](const char* b, OT o) { return reinterpret_cast<const float*>(b + o); };
+        OT o = (OT)((org + row + (long long)z0 * sz) * 4);   // plane z, this thread's first cell
+        const OT dz = (OT)(sz * 4), dy = (OT)(sy * 4);
+        const bool twins = perx || pery || perz;
         for (int z = z0; z < z1; ++z) {
-            const long long o = row + (long long)z * sz;
-            if ((tx & 7) == 0) prefetch_l2(xv + o + 3 * sz);
+            if ((tx & 7) == 0) prefetch_l2(F(xB, o + 3 * dz));
             float tp[4], ym[4], yp[4];
-            ld4(xv + o + sz, tp);
-            ld4(xv + o - sy, ym);
-            ld4(xv + o + sy, yp);
-            const float xm = __ldg(xv + o - 1), xp = __ldg(xv + o + 4);
+            ld4(F(xB, o + dz), tp);
+            ld4(F(xB, o - dy), ym);
+            ld4(F(xB, o + dy), yp);
+            const float xm = __ldg(F(xB, o - 4u)), xp = __ldg(F(xB, o + 16u));
             float kp[4], kym[4], kyp[4], kxm = 0.0f, kxp = 0.0f;
             if (KVAR) {
-                ld4(rk + o + sz, kp);
-                ld4(rk + o - sy, kym);
-                ld4(rk + o + sy, kyp);
-                kxm = __ldg(rk + o - 1);
-                kxp = __ldg(rk + o + 4);
+                ld4(F(kB, o + dz), kp);
+                ld4(F(kB, o - dy), kym);
+                ld4(F(kB, o + dy), kyp);
+                kxm = __ldg(F(kB, o - 4u));
+                kxp = __ldg(F(kB, o + 16u));
             }
             float rv[4];
             float sr = 0.0f, sb = 0.0f;
-            const bool fast = inner_xy && (perz || (z > 1 && z < nz - 2));
-            if (__all_sync(__activemask(), fast))   // warp-uniform choice, as in cg_spmv
+            const bool inner_z = perz || (z > 1 && z < nz - 2);
+            const bool fast = inner_xy && inner_z;
+            const unsigned am = __activemask();
+            if (__all_sync(am, fast))   // warp-uniform choice, as in cg_spmv
                 cg_r4<KVAR, false>(c, edge, gx, gy, z, tc, tm, tp, ym, yp, xm, xp, kc, km, kp, kym, kyp, kxm, kxp, rv,
                                    sr, sb);
+            else if (__all_sync(am, inner_y && inner_z))   // near an x face only
+                cg_r4<KVAR, true, 3>(c, edge, gx, gy, z, tc, tm, tp, ym, yp, xm, xp, kc, km, kp, kym, kyp, kxm, kxp,
+                                     rv, sr, sb);
             else
                 cg_r4<KVAR, true>(c, edge, gx, gy, z, tc, tm, tp, ym, yp, xm, xp, kc, km, kp, kym, kyp, kxm, kxp, rv,
                                   sr, sb);
-            st4_twins(a.r, c, gx, gy, z, rv);
+            if (twins)   // the same for every thread
+                st4_twins(a.r, c, gx, gy, z, rv);
+            else
+                st4_row(reinterpret_cast<float*>(rB + o), gx, nx, rv);
             rr.add(sr);
             bb.add(sb);
 #pragma unroll
@@ -375,6 +410,7 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_init(co
                     kc[i] = kp[i];
                 }
             }
+            o += dz;
         }
     }
     const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
@@ -427,14 +463,15 @@ __device__ __forceinline__ float pnew1(const PNew& P, long long o) {
 // boundary faces and masks held cells and cells beyond the x end; without
 // it every neighbour is inside the domain or across a periodic face. Both
 // evaluate the same expression, so an interior cell gets the same bits
-// either way.
-template <bool KVAR, bool EDGE>
+// either way. FM: the faces that may be near the warp's cells (see cg_r4).
+template <bool KVAR, bool EDGE, int FM = 63>
 __device__ __forceinline__ float cg_q4(const CgCoef& c, const CgEdge& e, int gx, int gy, int z, const float pc[4],
                                        const float pm[4], const float pp[4], const float ym[4], const float yp[4],
                                        float xm, float xp, const float kc[4], const float km[4], const float kp[4],
                                        const float kym[4], const float kyp[4], float kxm, float kxp, float q[4]) {
     float psum = 0.0f;
-    const bool zlo = EDGE && !c.periodic[2] && z == 0, zhi = EDGE && !c.periodic[2] && z == c.n[2] - 1;
+    const bool zlo = EDGE && (FM & 16) && !c.periodic[2] && z == 0,
+               zhi = EDGE && (FM & 32) && !c.periodic[2] && z == c.n[2] - 1;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         float pw = i == 0 ? xm : pc[i - 1], pe = i == 3 ? xp : pc[i + 1];
@@ -449,10 +486,10 @@ __device__ __forceinline__ float cg_q4(const CgCoef& c, const CgEdge& e, int gx,
             kz1 = kp[i];
         }
         if (EDGE) {
-            if (i == 0 && (e.bits & 1u)) { pw = ghost(c, 0, pc[i]); kw = kc[i]; }
-            if (i == e.ih) { pe = ghost(c, 1, pc[i]); ke = kc[i]; }
-            if (e.bits & 2u) { y0 = ghost(c, 2, pc[i]); ky0 = kc[i]; }
-            if (e.bits & 4u) { y1 = ghost(c, 3, pc[i]); ky1 = kc[i]; }
+            if ((FM & 1) && i == 0 && (e.bits & 1u)) { pw = ghost(c, 0, pc[i]); kw = kc[i]; }
+            if ((FM & 2) && i == e.ih) { pe = ghost(c, 1, pc[i]); ke = kc[i]; }
+            if ((FM & 4) && (e.bits & 2u)) { y0 = ghost(c, 2, pc[i]); ky0 = kc[i]; }
+            if ((FM & 8) && (e.bits & 4u)) { y1 = ghost(c, 3, pc[i]); ky1 = kc[i]; }
             if (zlo) { z0 = ghost(c, 4, pc[i]); kz0 = kc[i]; }
             if (zhi) { z1 = ghost(c, 5, pc[i]); kz1 = kc[i]; }
         }
@@ -473,7 +510,7 @@ __device__ __forceinline__ float cg_q4(const CgCoef& c, const CgEdge& e, int gx,
             qi = __fmaf_rn(-c.cu[2], __fadd_rn(z0, z1), acc);
         }
         if (EDGE) {
-            const bool isfree = gx + i < c.n[0] && gy < c.n[1] && !cg_held(c, gx + i, gy, z);
+            const bool isfree = gx + i < c.n[0] && gy < c.n[1] && !cg_held_m<FM>(c, gx + i, gy, z);
             qi = isfree ? qi : 0.0f;
             psum = isfree ? __fmaf_rn(pc[i], qi, psum) : psum;
         } else {
@@ -508,7 +545,8 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv(co
     if (gx < nx && gy < ny) {
         const long long sy = c.sy, sz = c.sz;
         const long long row = cg_at(c, gx, gy, 0);
-        const bool inner_xy = gx + 3 < nx && (perx || (gx > 0 && gx + 4 < nx)) && (pery || (gy > 0 && gy < ny - 1));
+        const bool inner_y = pery || (gy > 0 && gy < ny - 1);
+        const bool inner_xy = gx + 3 < nx && (perx || (gx > 0 && gx + 4 < nx)) && inner_y;
         const CgEdge edge = cg_edge(c, gx, gy);
         float pm[4], pc[4], km[4], kc[4];
         pnew4(P, row + (long long)(z0 - 1) * sz, pm);
@@ -537,12 +575,18 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv(co
                 kxp = __ldg(rk + o + 4);
             }
             float q[4];
-            const bool fast = inner_xy && (perz || (z > 0 && z < nz - 1));
-            const float psum = __all_sync(__activemask(), fast)
-                                   ? cg_q4<KVAR, false>(c, edge, gx, gy, z, pc, pm, pp, ym, yp, xm, xp, kc, km, kp, kym,
-                                                        kyp, kxm, kxp, q)
-                                   : cg_q4<KVAR, true>(c, edge, gx, gy, z, pc, pm, pp, ym, yp, xm, xp, kc, km, kp, kym,
-                                                       kyp, kxm, kxp, q);
+            const bool inner_z = perz || (z > 0 && z < nz - 1);
+            const bool fast = inner_xy && inner_z;
+            const unsigned am = __activemask();
+            const float psum =
+                __all_sync(am, fast)
+                    ? cg_q4<KVAR, false>(c, edge, gx, gy, z, pc, pm, pp, ym, yp, xm, xp, kc, km, kp, kym, kyp, kxm, kxp,
+                                         q)
+                : __all_sync(am, inner_y && inner_z)   // near an x face only
+                    ? cg_q4<KVAR, true, 3>(c, edge, gx, gy, z, pc, pm, pp, ym, yp, xm, xp, kc, km, kp, kym, kyp, kxm,
+                                           kxp, q)
+                    : cg_q4<KVAR, true>(c, edge, gx, gy, z, pc, pm, pp, ym, yp, xm, xp, kc, km, kp, kym, kyp, kxm, kxp,
+                                        q);
             dot.add(psum);
             st4_twins(pn, c, gx, gy, z, pc);
             if (a.q_twins) {
@@ -1051,6 +1095,7 @@ struct CgWork {
     int spmv_grid[3] = {0, 0, 0};
     int upd_blocks = 0;
     long long prev_iters = 0;   // iterations the last step needed (sizes the first run of the next)
+    bool o32 = false;           // every array under 4 GiB: cg_init takes 32-bit byte offsets
 };
 
 void free_cg(wfa_grid_s* g) {
@@ -1088,6 +1133,7 @@ static int cg_workspace(wfa_grid_s* g, CgWork** out) {
     }
     g->cg = w;
     const size_t fb = field_elems(g) * sizeof(float);
+    w->o32 = fb < ((size_t)1 << 32);
     // padded arrays in the field's layout (see lead_bytes)
     cudaError_t e = padded_alloc((void**)&w->r, fb, 4, g->stream);
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = padded_alloc((void**)&w->p[b], fb, 4, g->stream);
@@ -1241,7 +1287,10 @@ static cudaError_t build_loop_graph(CgWork* w, const CgArgs& base, bool kvar, in
     e = cudaGraphConditionalHandleCreate(&ho, top, 1, cudaGraphCondAssignDefault);
     if (e == cudaSuccess) e = add_while(top, &n_outer, nullptr, ho, &outer);
     if (e == cudaSuccess)
-        e = add_kernel(outer, &n, nullptr, kvar ? (const void*)cg_init<true> : (const void*)cg_init<false>, sgrid,
+        e = add_kernel(outer, &n, nullptr,
+                       kvar ? (w->o32 ? (const void*)cg_init<true, true> : (const void*)cg_init<true, false>)
+                            : (w->o32 ? (const void*)cg_init<false, true> : (const void*)cg_init<false, false>),
+                       sgrid,
                        sblock, a_init);
     prev = n;
     if (e == cudaSuccess && method == WFA_CG_PIPELINED) {
@@ -1441,9 +1490,11 @@ int wfa_implicit_step(wfa_grid g, double dt, long long n, double rtol, int max_i
     double last_rel = 0.0;
     for (long long step = 0; step < n; ++step) {
         if (kvar)
-            cg_init<true><<<sgrid, sblock, 0, g->stream>>>(ia, rtol * rtol, max_iter);
+            if (w->o32) cg_init<true, true><<<sgrid, sblock, 0, g->stream>>>(ia, rtol * rtol, max_iter);
+            else cg_init<true, false><<<sgrid, sblock, 0, g->stream>>>(ia, rtol * rtol, max_iter);
         else
-            cg_init<false><<<sgrid, sblock, 0, g->stream>>>(ia, rtol * rtol, max_iter);
+            if (w->o32) cg_init<false, true><<<sgrid, sblock, 0, g->stream>>>(ia, rtol * rtol, max_iter);
+            else cg_init<false, false><<<sgrid, sblock, 0, g->stream>>>(ia, rtol * rtol, max_iter);
         WFA_CUDA(cudaGetLastError());
         g->launches += 1;
         if (method == WFA_CG_PIPELINED) {
