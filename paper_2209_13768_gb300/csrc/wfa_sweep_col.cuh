@@ -410,26 +410,33 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
             // then one layer of periodic copies for the next one-step pass
             const StoreVec<S, V> sv(out);
             const long long zoff = TW && perz ? (z == 0 ? c.n[2] * sz : z == c.n[2] - 1 ? -c.n[2] * sz : 0) : 0;
-            if (full_x) {
+            S* const oy = reinterpret_cast<S*>(oB + (OT)(to + yoffb));
+            S* const oz = reinterpret_cast<S*>(oB + (OT)(to + (OT)(zoff * (long long)sizeof(S))));
+            if (xvec) {
+                // n_x a multiple of V (the same for every thread): every vector
+                // lies in the domain, and the row ends store theirs shifted
                 sv.store(op);
-                // pery / perz are the same for every thread: uniform branches
-                if (TW && pery) sv.store_if(reinterpret_cast<S*>(oB + (OT)(to + yoffb)), yoff != 0);
-                if (TW && perz)
-                    sv.store_if(reinterpret_cast<S*>(oB + (OT)(to + (OT)(zoff * (long long)sizeof(S)))), zoff != 0);
-            } else {
-#pragma unroll
-                for (int i = 0; i < V; ++i)
-                    if (gx + i < c.n[0]) {
-                        op[i] = from_f32<S>(out[i]);
-                        if (TW && yoff != 0) op[yoff + i] = from_f32<S>(out[i]);
-                        if (TW && zoff != 0) op[zoff + i] = from_f32<S>(out[i]);
-                    }
-            }
-            if (TW && perx) {
-                if (xvec) {
+                if (TW && pery) sv.store_if(oy, yoff != 0);
+                if (TW && perz) sv.store_if(oz, zoff != 0);
+                if (TW && perx) {
                     sv.store_if(reinterpret_cast<S*>(oB + (OT)(to + xoffb)), xt_first);
                     sv.store_if(reinterpret_cast<S*>(oB + (OT)(to - xoffb)), xt_last);
+                }
+            } else {
+                if (full_x) {
+                    sv.store(op);
+                    if (TW && pery) sv.store_if(oy, yoff != 0);
+                    if (TW && perz) sv.store_if(oz, zoff != 0);
                 } else {
+#pragma unroll
+                    for (int i = 0; i < V; ++i)
+                        if (gx + i < c.n[0]) {
+                            op[i] = from_f32<S>(out[i]);
+                            if (TW && yoff != 0) oy[i] = from_f32<S>(out[i]);
+                            if (TW && zoff != 0) oz[i] = from_f32<S>(out[i]);
+                        }
+                }
+                if (TW && perx) {
                     if (xt_first) op[c.n[0]] = from_f32<S>(out[0]);
                     if (xt_last) {
 #pragma unroll
