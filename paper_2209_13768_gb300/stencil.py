@@ -37,6 +37,7 @@ import threading
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "_dsl_cache")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-shared", "-Xcompiler", "-fPIC", "-cudart", "static"]
 MAX_RADIUS = 4
 _lock = threading.Lock()
 
@@ -278,23 +279,46 @@ def _nvcc():
     raise RuntimeError("nvcc not found: the stencil front end compiles its kernels with nvcc")
 
 
+_toolchain = None
+
+
+def _toolchain_key() -> str:
+    """Hash of the compiler (its path and `--version`), the target and the
+    flags: a cached kernel built by another toolchain or with other flags is
+    not reused."""
+    global _toolchain
+    if _toolchain is None:
+        nv = _nvcc()
+        ver = subprocess.run([nv, "--version"], capture_output=True, text=True).stdout
+        _toolchain = hashlib.sha256("\n".join([nv, ver] + ARCH + FLAGS).encode()).hexdigest()[:12]
+    return _toolchain
+
+
 def build(program: Program) -> str:
-    """Compile the program's kernel into _dsl_cache/ (once per source)."""
+    """Compile the program's kernel into _dsl_cache/ (once per source,
+    toolchain and host architecture). The source and the library are
+    written under per-process names and the library renamed into place, so
+    processes compiling the same program at once do not clobber each
+    other's files."""
     with _lock:
         os.makedirs(CACHE, exist_ok=True)
-        so = os.path.join(CACHE, f"stencil_{program.key}_{platform.machine()}.so")   # per host architecture
+        so = os.path.join(CACHE, f"stencil_{program.key}_{_toolchain_key()}_{platform.machine()}.so")
         if os.path.exists(so):
             return so
-        src = os.path.join(CACHE, f"stencil_{program.key}.cu")
+        src = os.path.join(CACHE, f"stencil_{program.key}.{os.getpid()}.cu")
         with open(src, "w") as f:
             f.write(program.source)
         tmp = so + f".{os.getpid()}.tmp"
-        cmd = [_nvcc()] + ARCH + ["-O3", "-std=c++17", "-lineinfo", "-shared", "-Xcompiler", "-fPIC",
-                                  "-cudart", "static", src, "-o", tmp]
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError(f"nvcc failed for the generated stencil:\n{r.stderr[-4000:]}")
-        os.replace(tmp, so)
+        cmd = [_nvcc()] + ARCH + FLAGS + [src, "-o", tmp]
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True)
+            if r.returncode != 0:
+                raise RuntimeError(f"nvcc failed for the generated stencil:\n{r.stderr[-4000:]}")
+            os.replace(tmp, so)
+        finally:
+            for leftover in (src, tmp):
+                if os.path.exists(leftover):
+                    os.remove(leftover)
         return so
 
 
