@@ -964,21 +964,31 @@ def grid_bench(args, p, storage, world, rank, dist, local, e2e=True, accuracy=Tr
         outh = torch.empty(tuple(p.T0.shape), dtype=torch.float32).pin_memory()
         nrep = max(1, min(args.steps, 3))
         e2e_t = []
+        parts = {"set_field": [], "set_coeffs": [], "set_dt": [], "step": [], "read_field": []}
         for i in range(nrep + 1):
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            g.set_field(T0h)
-            g.set_coeffs(kh if kvar else p.k, p.u)
-            g.set_dt(dt)
+            t = [time.perf_counter()]
+            g.set_field(T0h)                          # returns once the host buffer was read
+            t.append(time.perf_counter())
+            g.set_coeffs(kh if kvar else p.k, p.u)    # validates k on the device: synchronous
+            t.append(time.perf_counter())
+            g.set_dt(dt)                              # checks dt against the fp64 limit: synchronous
+            t.append(time.perf_counter())
             g.step(p.steps)
+            g.sync()                                  # only to time the pieces; read_field waits anyway
+            t.append(time.perf_counter())
             g.read_field(outh)
+            t.append(time.perf_counter())
             if i:   # first one is a warm-up
-                e2e_t.append(time.perf_counter() - t0)
+                e2e_t.append(t[-1] - t[0])
+                for k, (a, b) in zip(parts, zip(t, t[1:])):
+                    parts[k].append(1e3 * (b - a))
         e2e_s = sum(e2e_t) / len(e2e_t)
         e2e_s = max_over_ranks(e2e_s, dist, "cuda")
         e2e_line = {"value": job_rate(world, cells * p.steps, e2e_s), "unit": "GLUPS",
                     "h2d_bytes_per_step": cells * 4 * (2 if kvar else 1), "d2h_bytes_per_step": cells * 4,
-                    "ms_per_step": 1e3 * e2e_s}
+                    "ms_per_step": 1e3 * e2e_s,
+                    "ms_by_call": {k: sum(v) / len(v) for k, v in parts.items()}}
     acc = None
     if accuracy and rank == 0:
         acc = accuracy_sample(g, p, dt, storage, min(100, p.steps))

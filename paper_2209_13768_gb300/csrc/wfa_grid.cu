@@ -421,7 +421,9 @@ constexpr int RED_BLOCKS = 304;
 // word kept for the k check (index 4095)
 constexpr int RATE_BLOCKS = 152 * 8;
 constexpr int RATE_P2 = 1280;
-static_assert(RATE_P2 > RATE_BLOCKS + 1 && RATE_P2 + RATE_BLOCKS < 4095, "scratch layout");
+constexpr int RATE_RISKY = 2560;   // pass 1's per-block flags: the block met a risky cell
+static_assert(RATE_P2 > RATE_BLOCKS + 1 && RATE_P2 + RATE_BLOCKS <= RATE_RISKY && RATE_RISKY + RATE_BLOCKS < 4095,
+              "scratch layout");
 constexpr int RED_THREADS = 256;
 
 template <typename S>
@@ -561,12 +563,14 @@ __device__ __forceinline__ double rate64(const float* __restrict__ korigin, cons
     return D;
 }
 
-// The same sum in fp32: every operation is correctly rounded and every term
-// is >= 0, so for a cell whose k values lie in [1e-15, 1e15] (or are 0) no
-// product leaves the normal range and the result is within 18 units of
-// 2^-24, relative, of the fp64 one (3 roundings per harmonic mean, 2 per
-// product with 1/h^2 and its conversion, at most 12 additions). A cell with
-// other k values is `risky`.
+// The same sum in fp32 (only to find the candidates of the fp64 pass):
+// every term is >= 0 and every operation is correctly rounded except the
+// division of the harmonic mean, a fast division within 2 ulp for a
+// denominator in (2^-126, 2^126). For a cell whose k values lie in
+// [1e-15, 1e15] (or are 0) no operand leaves the normal range and the result
+// is within 24 units of 2^-24, relative, of the fp64 one (2 roundings and
+// the division per harmonic mean, 2 per product with 1/h^2 and its
+// conversion, at most 12 additions). A cell with other k values is `risky`.
 __device__ __forceinline__ float rate32(const float* __restrict__ korigin, const RateSpec& r, const int c[3],
                                         long long idx, bool* risky) {
     const long long st[3] = {1, r.px, r.px * r.py};
@@ -585,7 +589,7 @@ __device__ __forceinline__ float rate32(const float* __restrict__ korigin, const
                 const float kD = korigin[idx + (side ? st[a] : -st[a])];
                 bad = bad || (kD != 0.0f && !(kD >= 1e-15f && kD <= 1e15f));
                 const float s2 = __fadd_rn(kC, kD);
-                const float h = s2 > 0.0f ? __fdiv_rn(__fmul_rn(__fmul_rn(2.0f, kC), kD), s2) : 0.0f;
+                const float h = s2 > 0.0f ? __fdividef(__fmul_rn(__fmul_rn(2.0f, kC), kD), s2) : 0.0f;
                 D = __fadd_rn(D, __fmul_rn(h, r.inv_h2f[a]));
             }
             if (active) D = __fadd_rn(D, side ? r.upf[a] : r.umf[a]);
@@ -637,39 +641,100 @@ __global__ void __launch_bounds__(RED_THREADS) rate_partial_kernel(const float* 
 }
 
 // Per-cell k, pass 1: block maxima of the fp32 D_C over the cells that are
-// neither held nor risky.
+// neither held nor risky, and per block whether it met a risky cell.
 __global__ void __launch_bounds__(RED_THREADS) rate32_partial_kernel(const float* __restrict__ korigin,
                                                                      const __grid_constant__ RateSpec r,
-                                                                     double* __restrict__ partials) {
+                                                                     double* __restrict__ partials,
+                                                                     double* __restrict__ risky_out) {
     float best = 0.0f;
+    int any_risky = 0;
     for_each_cell(r, [&](const int c[3], long long idx) {
         if (rate_held(r, c)) return;
         bool risky;
         const float d = rate32(korigin, r, c, idx, &risky);
         if (!risky) best = fmaxf(best, d);
+        else any_risky = 1;
     });
     block_max_out((double)best, &partials[blockIdx.x]);
+    any_risky = __syncthreads_or(any_risky);
+    if (threadIdx.x == 0) risky_out[blockIdx.x] = any_risky ? 1.0 : 0.0;
 }
 
 // Per-cell k, pass 2: fp64 D_C of the candidates only, the cells whose fp32
 // value reaches M (1 - 2^-12), M the pass-1 maximum, and the risky cells. The
 // cell with the largest fp64 value is always a candidate: its fp32 value is
-// at least M (1 - 2 * 18 * 2^-24) > M (1 - 2^-12). So the maximum over the
+// at least M (1 - 2 * 24 * 2^-24) > M (1 - 2^-12). So the maximum over the
 // candidates is the fp64 maximum over all cells, the same number as the
-// one-pass reduction gives.
+// one-pass reduction gives. Candidates lie only in the rows that pass-1
+// blocks with a maximum at the threshold (or a risky cell) visited; with
+// at most RATE_ACTIVE such blocks, every block of this launch takes a share
+// of those rows (so the few that hold candidates do not serialise on one
+// block), otherwise each block takes its pass-1 rows again.
+constexpr int RATE_ACTIVE = 64;
 __global__ void __launch_bounds__(RED_THREADS) rate_cand_kernel(const float* __restrict__ korigin,
                                                                 const __grid_constant__ RateSpec r,
+                                                                const double* __restrict__ pass1,
+                                                                const double* __restrict__ risky,
                                                                 const double* __restrict__ m32,
                                                                 double* __restrict__ partials) {
+    __shared__ int s_act[RATE_ACTIVE];
+    __shared__ int s_nact;
     const float m = (float)*m32;
     const float thr = __fsub_rn(m, __fmul_rn(m, 0x1p-12f));
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {   // the pass-1 blocks that may hold candidates, in order
+        int n = 0;
+        for (int base = 0; base < RATE_BLOCKS; base += 32) {
+            const int b = base + lane;
+            const bool act = b < RATE_BLOCKS && ((float)pass1[b] >= thr || risky[b] != 0.0);
+            unsigned bits = __ballot_sync(0xffffffffu, act);
+            while (bits) {
+                const int i = __ffs(bits) - 1;
+                bits &= bits - 1;
+                if (lane == 0 && n < RATE_ACTIVE) s_act[n] = base + i;
+                ++n;
+            }
+        }
+        if (lane == 0) s_nact = n;
+    }
+    __syncthreads();
+    const int nact = s_nact;
     double best = 0.0;
-    for_each_cell(r, [&](const int c[3], long long idx) {
+    auto cell = [&](const int c[3], long long idx) {
         if (rate_held(r, c)) return;
-        bool risky;
-        const float d = rate32(korigin, r, c, idx, &risky);
-        if (risky || d >= thr) best = fmax(best, rate64(korigin, r, c, idx));
-    });
+        bool rk;
+        const float d = rate32(korigin, r, c, idx, &rk);
+        if (rk || d >= thr) best = fmax(best, rate64(korigin, r, c, idx));
+    };
+    if (nact > RATE_ACTIVE) {
+        for_each_cell(r, cell);
+    } else {
+        // pass-1 block b took rows 8b + w + k W (w < 8 warps, W = all warps of
+        // the launch); here warp g of the launch takes the j-th of those
+        // rows for j = g, g + W, ..., over the active blocks in turn
+        const int wpb = RED_THREADS / 32;
+        const long long W = (long long)RATE_BLOCKS * wpb;
+        const long long rows = (long long)r.n[1] * r.n[2];
+        const long long gw = (long long)blockIdx.x * wpb + (threadIdx.x >> 5);
+        for (int t = 0; t < nact; ++t) {
+            const int b = s_act[t];
+            const long long first = (long long)b * wpb;
+            if (first >= rows) continue;
+            const long long per = wpb * ((rows - first + W - 1) / W);   // an upper bound of b's rows
+            for (long long j = gw; j < per; j += W) {
+                const long long row = first + (j % wpb) + (j / wpb) * W;
+                if (row >= rows) continue;
+                int c[3];
+                c[2] = (int)(row / r.n[1]);
+                c[1] = (int)(row - (long long)c[2] * r.n[1]);
+                const long long base = (long long)c[2] * r.px * r.py + (long long)c[1] * r.px;
+                for (int x = lane; x < r.n[0]; x += 32) {
+                    c[0] = x;
+                    cell(c, base + x);
+                }
+            }
+        }
+    }
     block_max_out(best, &partials[blockIdx.x]);
 }
 
@@ -1088,9 +1153,10 @@ int wfa_stability_dt(wfa_grid g, double* dt_max) {
             if (rate32_applies(r)) {
                 // partials of pass 1 at [0, RATE_BLOCKS), its maximum at RATE_BLOCKS,
                 // partials of pass 2 at [RATE_P2, RATE_P2 + RATE_BLOCKS), the result at RATE_BLOCKS + 1
-                rate32_partial_kernel<<<RATE_BLOCKS, RED_THREADS, 0, g->stream>>>(ko, r, part);
+                rate32_partial_kernel<<<RATE_BLOCKS, RED_THREADS, 0, g->stream>>>(ko, r, part, part + RATE_RISKY);
                 finish_max_kernel<<<1, 512, 0, g->stream>>>(part, RATE_BLOCKS, part + RATE_BLOCKS);
-                rate_cand_kernel<<<RATE_BLOCKS, RED_THREADS, 0, g->stream>>>(ko, r, part + RATE_BLOCKS, part + RATE_P2);
+                rate_cand_kernel<<<RATE_BLOCKS, RED_THREADS, 0, g->stream>>>(ko, r, part, part + RATE_RISKY,
+                                                                             part + RATE_BLOCKS, part + RATE_P2);
                 finish_max_kernel<<<1, 512, 0, g->stream>>>(part + RATE_P2, RATE_BLOCKS, part + RATE_BLOCKS + 1);
             } else {
                 rate_partial_kernel<<<RATE_BLOCKS, RED_THREADS, 0, g->stream>>>(ko, r, part + RATE_P2);
