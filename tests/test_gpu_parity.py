@@ -281,6 +281,31 @@ def test_stability_dt_two_pass_cases(case):
         assert abs(got - ref) <= 1e-13 * ref, (case, mix, got, ref)
 
 
+@pytest.mark.parametrize("case", ["all_tied", "one_far_row"])
+def test_stability_dt_candidate_blocks(case):
+    # the fp64 pass visits only the rows of the fp32 pass's blocks that can
+    # hold the maximum, spread over the whole launch; with too many such
+    # blocks every block takes its own rows again. all_tied: periodic faces
+    # and one k value in every cell, so every block holds the maximum (more
+    # than the spread path takes); one_far_row: one cell with the largest k
+    # in a row past the first period of the fp32 pass's rows
+    rng = np.random.default_rng(31)
+    if case == "all_tied":
+        shape = (20, 32, 32)
+        k = np.full(shape[::-1], 1.3, np.float32)
+        bc = [(P, 0.0)] * 6
+    else:
+        shape = (8, 128, 100)
+        k = rng.uniform(0.5, 1.0, shape[::-1]).astype(np.float32)
+        k[97, 101, 3] = 2.5        # row 97 * 128 + 101 = 12517, beyond 9728 warps
+        bc = [(D, 0.0), (D, 1.0), (ZF, 0.0), (ZF, 0.0), (P, 0.0), (P, 0.0)]
+    p = W.Problem(shape=shape, T0=np.zeros(shape[::-1], np.float32), k=k, bc=bc, steps=1)
+    ref = oracle.dt_max(shape=shape, h=p.h, k=np.asarray(k, np.float64), u=p.u, bc=bc)
+    with make_grid(p, dt=1e-30) as g:
+        got = g.stability_dt()
+    assert abs(got - ref) <= 1e-13 * ref, (case, got, ref)
+
+
 def test_unstable_dt_rejected():
     p = _mixed_problem(0)
     with make_grid(p) as g:
