@@ -37,7 +37,7 @@ constexpr int NUM_TILE_VARIANTS = 2;  // tile shapes compiled per (storage, k mo
 constexpr int COL_VARIANT = 3;        // the one-step column-march kernel
 constexpr int FUSED_VARIANT = 4;      // the two-step column-march kernel (uniform k)
 constexpr int INPLACE_VARIANT = 5;    // the one-step column-march kernel, boundaries in place
-constexpr int WIDE_VARIANT = 6;       // the one-step column-march kernel, 8 cells a thread
+constexpr int WIDE_VARIANT = 6;       // the one-step column-march kernel, 8 cells a thread (16 for bf16, uniform k)
 constexpr int T2_VARIANT = 7;         // two steps per pass, TMA-staged planes (uniform k)
 
 // NVTX range over one API call: a named span on a profiler's timeline
