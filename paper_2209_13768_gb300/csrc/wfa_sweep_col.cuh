@@ -1,14 +1,18 @@
 // sweep_col<S, KVAR>: one explicit step per pass (Sec. 1.1.1,
 // Eq. expl_form in face-flux form) without shared memory or barriers.
 //
-// Every thread owns 4 consecutive x cells of one row and marches along z over
-// a chunk of planes. Its own values at planes z-1, z, z+1 live in a register
-// queue; at plane z it loads plane z + 1 (own cells, 128-bit along x) and
-// the x / y neighbours at plane z, and asks L2 for plane z + 3, so the loads
-// mostly hit L2 by the time they are issued. x / y neighbours of a thread are
-// other threads' cells of the same plane, so they come from L1; every value
-// is read from DRAM about once per pass. The per-cell arithmetic is the same
-// fixed expression as the tiled kernels (bit-identical results).
+// Every thread owns V consecutive x cells of one row (4; 8 for the wide
+// variant, 16 for bf16 with uniform k) and marches along z over a chunk of
+// planes. Its own values at planes z-1, z, z+1 live in a register queue; at
+// plane z it loads plane z + 1 (own cells, 128-bit along x) and the x / y
+// neighbours at plane z, and asks L2 for plane z + 3, so the loads mostly
+// hit L2 by the time they are issued. x / y neighbours of a thread are other
+// threads' cells of the same plane, so they come from L1; every value is read
+// from DRAM about once per pass. Addresses are byte offsets from the start of
+// each padded array (32-bit when every array is under 4 GiB). The per-cell
+// arithmetic is the same fixed expression as the tiled kernels (bit-identical
+// results); the new values are rounded to the storage type once, at the
+// store.
 #pragma once
 
 #include <algorithm>
