@@ -239,7 +239,7 @@ template <typename S, bool KVAR, bool COH, int V = 4>
 struct ColNb {
     float ty_m[V], ty_p[V], tx_m, tx_p;
     float ry_m[V], ry_p[V], rx_m, rx_p;
-    // plane at byte offset to of base tB (1/k: ro of rB); syt / syr: one row in bytes
+    // plane at byte offset to from tB (1/k: ro from rB); syt / syr: one row in bytes
     template <typename OT>
     __device__ __forceinline__ void load(const char* tB, OT to, const char* rB, OT ro, OT syt, OT syr) {
         ldgv<S, COH, V>(reinterpret_cast<const S*>(tB + (OT)(to - syt)), ty_m);
@@ -357,19 +357,26 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
 #pragma unroll(UNROLL)
     for (int s = 0; s < len; ++s) {
         const int z = DIR > 0 ? z0 + s : z1 - 1 - s;
+        // this plane's bases: with O32 the array's base and the 32-bit offset
+        // (one integer add an address); otherwise a 64-bit pointer to this
+        // thread's cells and offsets from it
+        const char* const tP = O32 ? tB : tB + to;
+        const char* const rP = KVAR ? (O32 ? rB : rB + ro) : nullptr;
+        char* const oP = O32 ? oB : oB + to;
+        const OT tO = O32 ? to : (OT)0, rO = O32 ? ro : (OT)0;
         float tz[V], rz[V];
-        ldgv<S, COH, V>(reinterpret_cast<const S*>(tB + (OT)(to + dzt)), tz);   // own cells, plane z + DIR
+        ldgv<S, COH, V>(reinterpret_cast<const S*>(tP + (OT)(tO + dzt)), tz);   // own cells, plane z + DIR
         // one thread per 128-byte line asks L2 for plane z + 3 DIR, as long as
         // the chunk still needs it (the last plane read is z1 going up, z0 - 1
         // going down); the plane after that belongs to the next chunk
         if (PF) {
-            prefetch_l2_if(tB + (OT)(to + 3 * dzt), pf_lead && s + 3 <= len);
-            if (KVAR) prefetch_l2_if(rB + (OT)(ro + 3 * dzr), pf_lead && s + 3 <= len);
+            prefetch_l2_if(tP + (OT)(tO + 3 * dzt), pf_lead && s + 3 <= len);
+            if (KVAR) prefetch_l2_if(rP + (OT)(rO + 3 * dzr), pf_lead && s + 3 <= len);
         }
-        if (KVAR) ldgv<float, false, V>(reinterpret_cast<const float*>(rB + (OT)(ro + dzr)), rz);
+        if (KVAR) ldgv<float, false, V>(reinterpret_cast<const float*>(rP + (OT)(rO + dzr)), rz);
         ColNb<S, KVAR, COH, V> nb;                       // x / y neighbours, plane z
-        nb.load(tB, to, rB, ro, syt, syr);
-        S* const op = reinterpret_cast<S*>(oB + to);     // this thread's cells at plane z
+        nb.load(tP, tO, rP, rO, syt, syr);
+        S* const op = reinterpret_cast<S*>(oP + tO);     // this thread's cells at plane z
 
         const bool bzm = !perz && !c.ext[4] && z == 0, bzp = !perz && !c.ext[5] && z == c.n[2] - 1;
         // GHOST (c.halo_bc known at compile time) or c.halo_bc: the ghost layers hold the faces
@@ -438,8 +445,8 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
             // then one layer of periodic copies for the next one-step pass
             const StoreVec<S, V> sv(out);
             const long long zoff = TW && perz ? (z == 0 ? c.n[2] * sz : z == c.n[2] - 1 ? -c.n[2] * sz : 0) : 0;
-            S* const oy = reinterpret_cast<S*>(oB + (OT)(to + yoffb));
-            S* const oz = reinterpret_cast<S*>(oB + (OT)(to + (OT)(zoff * (long long)sizeof(S))));
+            S* const oy = reinterpret_cast<S*>(oP + (OT)(tO + yoffb));
+            S* const oz = reinterpret_cast<S*>(oP + (OT)(tO + (OT)(zoff * (long long)sizeof(S))));
             if (xvec) {
                 // n_x a multiple of V (the same for every thread): every vector
                 // lies in the domain, and the row ends store theirs shifted
@@ -447,8 +454,8 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
                 if (TW && pery) sv.store_if(oy, yoff != 0);
                 if (TW && perz) sv.store_if(oz, zoff != 0);
                 if (TW && perx) {
-                    sv.store_if(reinterpret_cast<S*>(oB + (OT)(to + xoffb)), xt_first);
-                    sv.store_if(reinterpret_cast<S*>(oB + (OT)(to - xoffb)), xt_last);
+                    sv.store_if(reinterpret_cast<S*>(oP + (OT)(tO + xoffb)), xt_first);
+                    sv.store_if(reinterpret_cast<S*>(oP + (OT)(tO - xoffb)), xt_last);
                 }
             } else {
                 if (full_x) {
