@@ -788,10 +788,13 @@ __global__ void k_halo_kernel(float* __restrict__ base, const __grid_constant__ 
 }
 
 // Smallest index of a negative or non-finite k (bad stays at its initial
-// value when every k is valid).
-__global__ void check_k_kernel(const float* __restrict__ k, long long n, unsigned long long* bad) {
+// value when every k is valid). copy: also write every k to `out` (src is
+// then pinned host memory the GPU reads over the host link).
+__global__ void check_k_kernel(const float* __restrict__ k, long long n, unsigned long long* bad,
+                               float* __restrict__ out = nullptr) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float v = k[i];
+        if (out) out[i] = v;
         if (!(v >= 0.0f && v <= 3.402823466e38f)) atomicMin(bad, (unsigned long long)i);
     }
 }
@@ -963,11 +966,19 @@ int wfa_set_coeffs(wfa_grid g, const float* k_host, double k_uniform, double ux,
     if (k_host) {
         int rc = ensure_stage(g);
         if (rc) return rc;
-        WFA_CUDA(cudaMemcpyAsync(g->d_stage, k_host, N * sizeof(float), cudaMemcpyHostToDevice, g->stream));
-        // validate on the device before anything of the grid changes
+        // validate on the device before anything of the grid changes. Pinned
+        // host memory is read by the checking kernel itself, which also
+        // copies it into the staging buffer (as wfa_set_field reads its
+        // input); pageable memory goes through a copy into the staging buffer
         unsigned long long* bad = reinterpret_cast<unsigned long long*>(g->d_partials + 4095);
         WFA_CUDA(cudaMemsetAsync(bad, 0xFF, sizeof(unsigned long long), g->stream));
-        check_k_kernel<<<grid_blocks(N, 256), 256, 0, g->stream>>>(g->d_stage, N, bad);
+        const float* kv = static_cast<const float*>(host_device_view(k_host));
+        if (kv) {
+            check_k_kernel<<<grid_blocks(N, 256), 256, 0, g->stream>>>(kv, N, bad, g->d_stage);
+        } else {
+            WFA_CUDA(cudaMemcpyAsync(g->d_stage, k_host, N * sizeof(float), cudaMemcpyHostToDevice, g->stream));
+            check_k_kernel<<<grid_blocks(N, 256), 256, 0, g->stream>>>(g->d_stage, N, bad);
+        }
         WFA_CUDA(cudaGetLastError());
         WFA_CUDA(cudaMemcpyAsync(g->h_result, bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, g->stream));
         WFA_CUDA(cudaStreamSynchronize(g->stream));
