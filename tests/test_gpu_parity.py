@@ -570,6 +570,31 @@ def test_pinned_host_buffers_go_direct(storage):
         np.testing.assert_array_equal(g.read_field(), pageable)
 
 
+def test_pinned_conductivity_goes_direct():
+    # pinned k is read by the checking kernel itself, pageable k through the
+    # staging buffer: the same fields, and an invalid pinned k is rejected
+    # with the grid left as it was
+    torch = pytest.importorskip("torch")
+    p = _mixed_problem(6, shape=(37, 29, 23), kvar=True, adv=True, seed=9)
+    ref = run_gpu(p, steps=6)
+    with make_grid(p) as g:
+        kp = torch.from_numpy(np.ascontiguousarray(p.k, dtype=np.float32)).pin_memory()
+        g.set_field(p.T0)
+        g.set_coeffs(kp, p.u)
+        g.set_dt(p.dt if p.dt else p.dt_factor * g.stability_dt())
+        g.step(6)
+        np.testing.assert_array_equal(g.read_field(), ref)
+        bad = kp.clone().pin_memory()
+        bad.view(-1)[1234] = float("nan")
+        with pytest.raises(wfa.WfaError) as e:
+            g.set_coeffs(bad, p.u)
+        assert "1234" in str(e.value)
+        g.set_field(p.T0)
+        g.set_dt(p.dt if p.dt else p.dt_factor * g.stability_dt())
+        g.step(6)
+        np.testing.assert_array_equal(g.read_field(), ref)
+
+
 def test_caller_owned_buffers():
     # fields and k in caller-owned device memory (torch tensors): the same
     # results, before and after set_coeffs, and the caller's memory is used
