@@ -149,9 +149,21 @@ def _check_name(name):
         raise ValueError(f"bad name {name!r}: an identifier not starting with '_'")
 
 
-def _wname(field, dz):
-    """Register of a z window: field value at plane z + dz of the own column."""
-    return f"zw_{field}_{'m' if dz < 0 else 'p'}{abs(dz)}"
+V = 4   # x cells a thread
+
+
+def _sn(v):
+    return ("m%d" % -v) if v < 0 else ("p%d" % v)
+
+
+def _sname(field, dy, dz, k):
+    """Register of row (field, dy, dz) at x0 + k in the generated kernel."""
+    return f"s_{field}_{_sn(dy)}_{_sn(dz)}_{_sn(k)}"
+
+
+def _rname(dy, dz):
+    """Element offset of row (dy, dz) from the thread's cell."""
+    return f"ro_{_sn(dy)}_{_sn(dz)}"
 
 
 def _walk(e):
@@ -191,70 +203,154 @@ class Program:
             raise ValueError("a field is updated twice")
         self.params = sorted(params)
         self.radius = radius   # 0: a pointwise update of every cell
-        # z windows: a field read at several dz of the cell's own column keeps
-        # those values in registers while the thread marches z (one new load
-        # a plane instead of one a reference)
-        col = {}
+        # rows: every (field, dy, dz) referenced, with the x offsets it is
+        # read at; a thread loads each such row's segment once a plane
+        rows = {}
         for _, e in self.updates:
             for n in _walk(e):
-                if isinstance(n, Ref) and n.offset[0] == 0 and n.offset[1] == 0:
-                    col.setdefault(n.field.name, set()).add(n.offset[2])
+                if isinstance(n, Ref):
+                    dx, dy, dz = n.offset
+                    lo, hi = rows.get((n.field.name, dy, dz), (dx, dx))
+                    rows[(n.field.name, dy, dz)] = (min(lo, dx), max(hi, dx))
+        # z windows: a field read in its own row (dy = 0) at several dz keeps
+        # those segments in registers while the thread marches z (one new
+        # segment a plane); a window's segments share the union of the x ranges
+        col = {}
+        for (f, dy, dz) in rows:
+            if dy == 0:
+                col.setdefault(f, set()).add(dz)
         self.windows = {f: (min(d), max(d)) for f, d in col.items() if len(d) >= 2}
+        self.rows = {k: v for k, v in rows.items() if not (k[1] == 0 and k[0] in self.windows)}
+        for f, (zlo, zhi) in self.windows.items():   # every plane of the window, one x range
+            wl = min(v[0] for (g, dy, _), v in rows.items() if g == f and dy == 0)
+            wh = max(v[1] for (g, dy, _), v in rows.items() if g == f and dy == 0)
+            for dz in range(zlo, zhi + 1):
+                self.rows[(f, 0, dz)] = (wl, wh)
         self.source = self._source()
         self.key = hashlib.sha256(self.source.encode()).hexdigest()[:16]
 
-    def _expr(self, e):
+    def _expr(self, e, i):
+        """fp32 expression of cell i (0..V-1) of the thread's group."""
         if isinstance(e, Const):
             return f"{e.value!r}f" if "e" in repr(e.value) or "." in repr(e.value) else f"{e.value!r}.0f"
         if isinstance(e, Param):
             return f"p_{e.name}"
         if isinstance(e, Ref):
             dx, dy, dz = e.offset
-            if dx == 0 and dy == 0 and e.field.name in getattr(self, "windows", {}):
-                return _wname(e.field.name, dz)
-            return f"__ldg(in_{e.field.name} + o + ({dx}) + ({dy}) * sy + ({dz}) * sz)"
+            return _sname(e.field.name, dy, dz, i + dx)
         if isinstance(e, Neg):
-            return f"(-{self._expr(e.a)})"
+            return f"(-{self._expr(e.a, i)})"
         if isinstance(e, BinOp):
             fn = {"+": "__fadd_rn", "-": "__fsub_rn", "*": "__fmul_rn", "/": "__fdiv_rn"}[e.op]
-            return f"{fn}({self._expr(e.a)}, {self._expr(e.b)})"
+            return f"{fn}({self._expr(e.a, i)}, {self._expr(e.b, i)})"
         raise TypeError(type(e).__name__)
+
+    def _load_row(self, f, dy, dz, plane, indent, decl=True):
+        """Statements loading row (f, dy, dz) of plane z + `plane` into its
+        segment: the V cells by one 128-bit load when VEC, the x halo (and,
+        without VEC, every element) cell by cell, masked to the row."""
+        lo, hi = self.rows[(f, dy, dz)]
+        base = f"(q_{f} + {_rname(dy, plane)})"
+        out = []
+        out.append(f"{indent}{{")
+        out.append(f"{indent}    const float* r_ = {base};")
+        out.append(f"{indent}    if (VEC) {{")
+        out.append(f"{indent}        const float4 c_ = __ldg(reinterpret_cast<const float4*>(r_));")
+        for k, comp in zip(range(V), "xyzw"):
+            out.append(f"{indent}        {_sname(f, dy, dz, k)} = c_.{comp};")
+        out.append(f"{indent}    }} else {{")
+        for k in range(V):
+            out.append(f"{indent}        {_sname(f, dy, dz, k)} = x0 + {k} < nx ? __ldg(r_ + {k}) : 0.0f;")
+        out.append(f"{indent}    }}")
+        for k in list(range(lo, 0)) + list(range(V, V + hi)):
+            out.append(f"{indent}    {_sname(f, dy, dz, k)} = (unsigned)(x0 + ({k})) < (unsigned)nx ? "
+                       f"__ldg(r_ + ({k})) : 0.0f;")
+        out.append(f"{indent}}}")
+        decls = [f"{indent}float {_sname(f, dy, dz, k)};" for k in range(lo, V + hi)] if decl else []
+        return decls + out
 
     def _source(self):
         ins = ", ".join(f"const float* __restrict__ in_{f}" for f in self.fields)
         outs = ", ".join(f"float* __restrict__ out_{f}" for f in self.written)
         prm = ", ".join(f"float p_{p}" for p in self.params)
         sig = ", ".join(x for x in (ins, outs, prm) if x)
-        body = "\n".join(f"        out_{f.name}[o] = {self._expr(e)};" for f, e in self.updates)
         call_in = ", ".join(f"in[{i}]" for i in range(len(self.fields)))
         call_out = ", ".join(f"out[{i}]" for i in range(len(self.written)))
         call_p = ", ".join(f"params[{i}]" for i in range(len(self.params)))
         call = ", ".join(x for x in (call_in, call_out, call_p) if x)
         R = self.radius
         pre, top, shift = [], [], []
+        # per-thread pointers to the group's first cell at plane z (advanced
+        # a plane an iteration); row offsets dy sy + dz sz are loop invariants
+        for f in self.fields:
+            pre.append(f"    const float* __restrict__ q_{f} = in_{f} + o0;")
+        for f in self.written:
+            pre.append(f"    float* __restrict__ w_{f} = out_{f} + o0;")
+        offs = sorted({(dy, dz) for (_, dy, dz) in self.rows} |
+                      {(0, d) for f, (lo, hi) in self.windows.items() for d in range(lo, hi + 1)})
+        for dy, dz in offs:
+            pre.append(f"    const long long {_rname(dy, dz)} = ({dy}) * sy + ({dz}) * sz;")
+        # window segments below the top one, loaded before the march
         for f, (lo, hi) in sorted(self.windows.items()):
             for dz in range(lo, hi):
-                pre.append(f"    float {_wname(f, dz)} = __ldg(in_{f} + o0 + ({dz}) * sz);")
-            top.append(f"        const float {_wname(f, hi)} = __ldg(in_{f} + o + ({hi}) * sz);")
-            shift.extend(f"        {_wname(f, dz)} = {_wname(f, dz + 1)};" for dz in range(lo, hi))
-        pre_s, top_s, shift_s = "\n".join(pre), "\n".join(top), "\n".join(shift)
+                pre.extend(self._load_row(f, 0, dz, dz, "    "))
+        # every plane: the windows' top segments and the other rows
+        for (f, dy, dz) in sorted(self.rows):
+            if dy == 0 and f in self.windows:
+                if dz == self.windows[f][1]:
+                    top.extend(self._load_row(f, 0, dz, dz, "        ", decl=False))
+            else:
+                top.extend(self._load_row(f, dy, dz, dz, "        ", decl=False))
+        # one thread per 128-byte line asks L2 for the plane three ahead of
+        # the furthest one read
+        zmax = max([dz for (_, _, dz) in self.rows] + [0])
+        for f in self.fields:
+            top.append(f"        if ((threadIdx.x & 7) == 0 && z + {zmax + 3} < nz) "
+                       f"asm volatile(\"prefetch.global.L2 [%0];\" :: \"l\"(q_{f} + ({zmax + 3}) * sz));")
+        body = []
+        for f, e in self.updates:
+            for i in range(V):
+                body.append(f"        const float v_{f.name}_{i} = {self._expr(e, i)};")
+        for f, _ in self.updates:
+            body.append(f"        if (full) {{")
+            body.append(f"            *reinterpret_cast<float4*>(w_{f.name}) = make_float4("
+                        + ", ".join(f"v_{f.name}_{i}" for i in range(V)) + ");")
+            body.append(f"        }} else {{")
+            for i in range(V):
+                body.append(f"            if (x0 + {i} >= {R} && x0 + {i} < nx - {R}) w_{f.name}[{i}] = v_{f.name}_{i};")
+            body.append(f"        }}")
+        for f, (lo, hi) in sorted(self.windows.items()):
+            wl, wh = self.rows[(f, 0, lo)]
+            for dz in range(lo, hi):
+                for k in range(wl, V + wh):
+                    shift.append(f"        {_sname(f, 0, dz, k)} = {_sname(f, 0, dz + 1, k)};")
+        shift.extend([f"        q_{f} += sz;" for f in self.fields] + [f"        w_{f} += sz;" for f in self.written])
+        top_decl = []
+        for (f, dy, dz), (lo, hi) in sorted(self.rows.items()):
+            if dy == 0 and f in self.windows and dz < self.windows[f][1]:
+                continue   # declared before the march
+            top_decl.extend(f"        float {_sname(f, dy, dz, k)};" for k in range(lo, V + hi))
+        pre_s, top_s, body_s, shift_s = "\n".join(pre), "\n".join(top_decl + top), "\n".join(body), "\n".join(shift)
         return f"""// generated by paper_2209_13768_gb300.stencil: one explicit step, every update fused
 #include <cuda_runtime.h>
-// one thread per (x, y) column of interior cells and z chunk, marching z;
-// x fastest (coalesced); neighbours through the read-only cache
+// each thread takes {V} consecutive x cells (a 16-byte aligned group) of one
+// row of a z chunk and marches z; every row it reads is loaded once a plane
+// (the {V} cells by one 128-bit load when VEC, the x halo cell by cell, masked
+// to the row), and updated cells that lie in the interior are stored
+template <bool VEC>
 __global__ void __launch_bounds__(256) step_kernel({sig}, int nx, int ny, int nz, int zchunk) {{
-    const int x = {R} + blockIdx.x * 32 + threadIdx.x;
+    const int x0 = {V} * (blockIdx.x * 32 + threadIdx.x);
     const int y = {R} + blockIdx.y * 8 + threadIdx.y;
-    if (x >= nx - {R} || y >= ny - {R}) return;
+    if (x0 + {V - 1} < {R} || x0 >= nx - {R} || y >= ny - {R}) return;
     const int z0 = {R} + blockIdx.z * zchunk;
     const int z1 = min(z0 + zchunk, nz - {R});
     const long long sy = nx, sz = (long long)nx * ny;
-    const long long o0 = x + y * sy + z0 * sz;
+    const long long o0 = x0 + y * sy + z0 * sz;
+    const bool full = VEC && x0 >= {R} && x0 + {V - 1} < nx - {R};   // every cell of the group is updated
 {pre_s}
     for (int z = z0; z < z1; ++z) {{
-        const long long o = x + y * sy + z * sz;
 {top_s}
-{body}
+{body_s}
 {shift_s}
     }}
 }}
@@ -264,9 +360,14 @@ extern "C" int stencil_launch(float** in, float** out, const float* params, int 
     (void)params;
     const int ix = nx - 2 * {R}, iy = ny - 2 * {R}, iz = nz - 2 * {R};
     if (ix <= 0 || iy <= 0 || iz <= 0) return 0;
+    // 128-bit loads and stores when every row starts on a 16-byte boundary
+    bool vec = nx % {V} == 0;
+    for (int i = 0; i < {len(self.fields)}; ++i) vec = vec && ((size_t)in[i] % 16 == 0);
+    for (int i = 0; i < {len(self.written)}; ++i) vec = vec && ((size_t)out[i] % 16 == 0);
     const dim3 block(32, 8);
-    const dim3 grid((ix + 31) / 32, (iy + 7) / 8, (iz + zchunk - 1) / zchunk);
-    step_kernel<<<grid, block, 0, (cudaStream_t)stream>>>({call}, nx, ny, nz, zchunk);
+    const dim3 grid(((nx + {V - 1}) / {V} + 31) / 32, (iy + 7) / 8, (iz + zchunk - 1) / zchunk);
+    if (vec) step_kernel<true><<<grid, block, 0, (cudaStream_t)stream>>>({call}, nx, ny, nz, zchunk);
+    else step_kernel<false><<<grid, block, 0, (cudaStream_t)stream>>>({call}, nx, ny, nz, zchunk);
     return (int)cudaGetLastError();
 }}
 """

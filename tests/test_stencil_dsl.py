@@ -22,9 +22,16 @@ def test_program_analysis():
     q = S.Program({T: T + K[0, 0, 2] * (T[0, 0, 1] - T)})
     assert q.fields == ["K", "T"] and q.written == ["T"] and q.params == [] and q.radius == 2
     assert S.Program({T: 2 * T}).radius == 0
-    # the own column's z neighbours ride in a register window; x / y ones load
+    # the own row's z neighbours ride in a register window (its segments,
+    # x halo included, shift down a plane); other rows load once a plane
     assert p.windows == {"T": (-1, 1)} and q.windows == {"T": (0, 1)}
-    assert "zw_T_m1 = zw_T_p0;" in p.source and "__ldg(in_T + o + (1) + (0) * sy + (0) * sz)" in p.source
+    assert p.rows[("T", 0, 0)] == (-1, 1) and p.rows[("T", 1, 0)] == (0, 0)
+    assert "s_T_p0_m1_p0 = s_T_p0_p0_p0;" in p.source and "s_T_p0_p0_m1 = s_T_p0_p1_m1;" in p.source
+    # other rows: a loop-invariant offset from the per-plane pointer, the
+    # 4 cells by one 128-bit load, the x halo masked to the row
+    assert "const long long ro_m1_p0 = (-1) * sy + (0) * sz;" in p.source
+    assert "__ldg(reinterpret_cast<const float4*>(r_))" in p.source and "q_T += sz;" in p.source
+    assert "(unsigned)(x0 + (-1)) < (unsigned)nx ? __ldg(r_ + (-1)) : 0.0f" in p.source
     assert p.key != q.key
 
 
@@ -164,5 +171,5 @@ def test_more_programs_cross_compile(case):
         prog = S.Program({A: A + a * (A[3, 0, 0] - A[-3, 0, 0]) / 6.0 - (-A[0, 0, -3] + A[0, 0, 3]) * b
                           + A[0, 2, 1] * A[0, -2, -1]})
         assert prog.radius == 3 and prog.windows == {"A": (-3, 3)}
-        assert "zw_A_m3" in prog.source and "zw_A_p3" in prog.source
+        assert "s_A_p0_m3_p0" in prog.source and "s_A_p0_p3_p0" in prog.source and ("A", 0, -2) in prog.rows
     assert S.build(prog).endswith(".so")
