@@ -297,8 +297,12 @@ static int pass_launches(const wfa_grid_s* g, const SweepCoef& c, int depth, int
     const int periodic = c.periodic[0] + c.periodic[1] + c.periodic[2];
     if (variant == FUSED_VARIANT && depth == 2 && !g->r) return 1 + periodic;
     if (variant == COL_VARIANT || variant == WIDE_VARIANT || variant == FUSED_VARIANT || variant == T2_VARIANT) {   // thin pass
-        bool faces = false;   // boundary cells the ghost layers do not hold: one boundary_fix launch
-        for (int ax = 0; ax < 3; ++ax) faces = faces || (!c.periodic[ax] && !(c.ext[2 * ax] && c.ext[2 * ax + 1]));
+        // boundary cells the ghost layers do not hold: one boundary_fix launch
+        // (the one-step column pass keeps held faces itself)
+        const bool col = variant == COL_VARIANT || variant == WIDE_VARIANT ||
+                         ((variant == FUSED_VARIANT || variant == T2_VARIANT) && !(depth == 2 && !g->r));
+        bool faces = false;
+        for (int f = 0; f < 6; ++f) faces = faces || (!c.periodic[f >> 1] && !c.ext[f] && !(col && c.held[f]));
         return 1 + (faces && !c.halo_bc ? 1 : 0);
     }
     return 1;

@@ -290,7 +290,7 @@ enum ColMode {
 // change a cell's value: the z faces are symmetric bit for bit and every
 // cell takes the same operands in the same order.
 template <typename S, bool KVAR, bool ADV, bool COH, int UNROLL, ColMode MODE, bool PF = false, bool GHOST = false,
-          int DIR = 1, int V = 4, bool TW = true>
+          int DIR = 1, int V = 4, bool TW = true, bool HELD = false>
 __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict__ tin, S* __restrict__ tout,
                                         const float* __restrict__ rk, int* status, int gx, int gy, int z0, int z1) {
     static_assert(V == 4 || V == 8 || V == 16, "cells per thread");
@@ -353,6 +353,9 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
     const int xlast = c.n[0] - 1 - gx;   // index of cell n_x - 1 in this thread's vector (if 0 <= xlast < V)
     const bool xt_last = MODE == COL_THIN && TW && perx && xlast >= 0 && xlast < V;
     const long long yoff = MODE == COL_THIN && TW && pery ? (gy == 0 ? c.n[1] * sy : gy == c.n[1] - 1 ? -c.n[1] * sy : 0) : 0;
+    // THIN with HELD (some face holds its cell layer): those cells keep
+    // their value in the pass itself, so those faces need no boundary launch
+    const bool held_y = HELD && ((c.held[2] && gy == 0) || (c.held[3] && gy == c.n[1] - 1));
     const OT yoffb = (OT)(yoff * (long long)sizeof(S)), xoffb = (OT)((long long)c.n[0] * (long long)sizeof(S));
 
 #pragma unroll(UNROLL)
@@ -439,6 +442,12 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
             }
         }
         if (MODE == COL_THIN) {
+            if (HELD) {
+                const bool held_yz = held_y || (c.held[4] && z == 0) || (c.held[5] && z == c.n[2] - 1);
+#pragma unroll
+                for (int i = 0; i < V; ++i)
+                    if (held_yz || (c.held[0] && gx + i == 0) || (c.held[1] && gx + i == c.n[0] - 1)) out[i] = tc[i];
+            }
             // the cells (masked at the x end: the halo there holds the x copies),
             // then one layer of periodic copies for the next one-step pass
             const StoreVec<S, V> sv(out);
@@ -521,7 +530,7 @@ __device__ __forceinline__ void col_run(const SweepCoef& c, const S* __restrict_
 // boundary_fix where the ghost layers do not hold the faces.
 // TW: some axis is periodic (the thin pass stores its one layer of copies;
 // without a periodic axis that code is not compiled).
-template <typename S, bool KVAR, bool ADV, bool INL, int V = 4, bool TW = true>
+template <typename S, bool KVAR, bool ADV, bool INL, int V = 4, bool TW = true, bool HELD = false>
 __global__ void __launch_bounds__(256, (ColOcc<KVAR, INL, sizeof(S), V>::blocks))
     sweep_col(const __grid_constant__ SweepArgs a) {
     const SweepCoef& c = a.c;
@@ -533,11 +542,11 @@ __global__ void __launch_bounds__(256, (ColOcc<KVAR, INL, sizeof(S), V>::blocks)
     constexpr int U = ColOcc<KVAR, INL, sizeof(S), V>::unroll;
     constexpr ColMode MODE = INL ? COL_INPLACE : COL_THIN;
     if (blockIdx.z & 1)   // odd chunks march down: see col_run
-        col_run<S, KVAR, ADV, false, U, MODE, true, false, -1, V, TW>(c, (const S*)a.tin, (S*)a.tout, a.rk,
-                                                                     a.status, gx, gy, z0, z1);
+        col_run<S, KVAR, ADV, false, U, MODE, true, false, -1, V, TW, HELD>(c, (const S*)a.tin, (S*)a.tout, a.rk,
+                                                                           a.status, gx, gy, z0, z1);
     else
-        col_run<S, KVAR, ADV, false, U, MODE, true, false, 1, V, TW>(c, (const S*)a.tin, (S*)a.tout, a.rk,
-                                                                    a.status, gx, gy, z0, z1);
+        col_run<S, KVAR, ADV, false, U, MODE, true, false, 1, V, TW, HELD>(c, (const S*)a.tin, (S*)a.tout, a.rk,
+                                                                          a.status, gx, gy, z0, z1);
 }
 
 // Boundary cells (the outer layer on every non-periodic face): recomputed
@@ -547,11 +556,12 @@ __global__ void __launch_bounds__(256, (ColOcc<KVAR, INL, sizeof(S), V>::blocks)
 // faces are read and written in whole rows (cells on an edge are visited once
 // per face and get the same value). Plane sizes fit 32-bit arithmetic (the
 // caller checks).
-template <typename S, bool KVAR>
+// SKIPHELD: the main pass kept the cells of held faces (the thin column pass).
+template <typename S, bool KVAR, bool SKIPHELD = false>
 __global__ void __launch_bounds__(256) boundary_fix(const __grid_constant__ SweepArgs a) {
     const SweepCoef& c = a.c;
     const int f = blockIdx.y, ax = f >> 1;
-    if (c.periodic[ax] || c.ext[f]) return;   // no boundary cells on this face
+    if (c.periodic[ax] || c.ext[f] || (SKIPHELD && c.held[f])) return;   // no boundary cells to fix on this face
     const int b = ax == 0 ? 1 : 0, d = ax == 2 ? 1 : 2;
     const unsigned nb = (unsigned)c.n[b], plane = nb * (unsigned)c.n[d];
     int pos[3];
@@ -662,6 +672,10 @@ cudaError_t col_launch_v(const SweepArgs& a_in, cudaStream_t st, int nsm, const 
     if (inl) {
         if (adv) sweep_col<S, KVAR, true, true><<<grid, block, 0, st>>>(a);
         else sweep_col<S, KVAR, false, true><<<grid, block, 0, st>>>(a);
+    } else if (a.c.held[0] || a.c.held[1] || a.c.held[2] || a.c.held[3] || a.c.held[4] || a.c.held[5]) {
+        // held cell layers: kept in the pass (copies for any periodic axis too)
+        if (adv) sweep_col<S, KVAR, true, false, V, true, true><<<grid, block, 0, st>>>(a);
+        else sweep_col<S, KVAR, false, false, V, true, true><<<grid, block, 0, st>>>(a);
     } else if (a.c.periodic[0] || a.c.periodic[1] || a.c.periodic[2]) {
         if (adv) sweep_col<S, KVAR, true, false, V, true><<<grid, block, 0, st>>>(a);
         else sweep_col<S, KVAR, false, false, V, true><<<grid, block, 0, st>>>(a);
@@ -672,15 +686,15 @@ cudaError_t col_launch_v(const SweepArgs& a_in, cudaStream_t st, int nsm, const 
     if (ev) cudaEventRecord(ev[1], st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || inl || a.c.halo_bc) return e;
-    long long plane = 0;   // the largest face with boundary cells
+    long long plane = 0;   // the largest face with boundary cells to fix (held faces are done)
     for (int ax = 0; ax < 3; ++ax) {
         const int b = ax == 0 ? 1 : 0, d = ax == 2 ? 1 : 2;
-        if (!a.c.periodic[ax] && !(a.c.ext[2 * ax] && a.c.ext[2 * ax + 1]))
+        if (!a.c.periodic[ax] && ((!a.c.ext[2 * ax] && !a.c.held[2 * ax]) || (!a.c.ext[2 * ax + 1] && !a.c.held[2 * ax + 1])))
             plane = std::max(plane, (long long)a.c.n[b] * a.c.n[d]);
     }
     if (plane == 0) return cudaSuccess;
     const int nb = (int)std::min<long long>((plane + 255) / 256, (long long)nsm * 2);
-    boundary_fix<S, KVAR><<<dim3(nb, 6), 256, 0, st>>>(a);
+    boundary_fix<S, KVAR, true><<<dim3(nb, 6), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
