@@ -16,7 +16,6 @@
 #pragma once
 
 #include <algorithm>
-#include <type_traits>
 
 #include "wfa_sweep.cuh"
 
