@@ -571,12 +571,44 @@ __device__ __forceinline__ double rate64(const float* __restrict__ korigin, cons
 // is within 24 units of 2^-24, relative, of the fp64 one (2 roundings and
 // the division per harmonic mean, 2 per product with 1/h^2 and its
 // conversion, at most 12 additions). A cell with other k values is `risky`.
+// A cell whose six neighbours are all cells (inside the domain, or across a
+// periodic or exchange face: their copies are in the halo); never held.
+__device__ __forceinline__ bool rate_inner(const RateSpec& r, const int c[3]) {
+    bool in = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const bool wlo = r.kind[2 * a] == WFA_BC_PERIODIC || r.kind[2 * a] == WFA_BC_EXCHANGE;
+        const bool whi = r.kind[2 * a + 1] == WFA_BC_PERIODIC || r.kind[2 * a + 1] == WFA_BC_EXCHANGE;
+        in = in & (wlo | (c[a] > 0)) & (whi | (c[a] < r.n[a] - 1));   // no short circuit: no branches
+    }
+    return in;
+}
+
+// inner (rate_inner): the same operations in the same order without the
+// face tests.
 __device__ __forceinline__ float rate32(const float* __restrict__ korigin, const RateSpec& r, const int c[3],
-                                        long long idx, bool* risky) {
+                                        long long idx, bool* risky, bool inner) {
     const long long st[3] = {1, r.px, r.px * r.py};
     const float kC = korigin[idx];
-    bool bad = kC != 0.0f && !(kC >= 1e-15f && kC <= 1e15f);
+    bool bad = (kC != 0.0f) & !((kC >= 1e-15f) & (kC <= 1e15f));   // bitwise: no branches
     float D = 0.0f;
+    if (inner) {
+        const float k2 = __fmul_rn(2.0f, kC);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const float kD = korigin[idx + (side ? st[a] : -st[a])];
+                bad = bad | ((kD != 0.0f) & !((kD >= 1e-15f) & (kD <= 1e15f)));
+                const float s2 = __fadd_rn(kC, kD);
+                const float h = s2 > 0.0f ? __fdividef(__fmul_rn(k2, kD), s2) : 0.0f;
+                D = __fadd_rn(D, __fmul_rn(h, r.inv_h2f[a]));
+                D = __fadd_rn(D, side ? r.upf[a] : r.umf[a]);
+            }
+        }
+        *risky = bad;
+        return D;
+    }
     for (int a = 0; a < 3; ++a) {
         for (int side = 0; side < 2; ++side) {
             const int f = 2 * a + side;
@@ -649,9 +681,10 @@ __global__ void __launch_bounds__(RED_THREADS) rate32_partial_kernel(const float
     float best = 0.0f;
     int any_risky = 0;
     for_each_cell(r, [&](const int c[3], long long idx) {
-        if (rate_held(r, c)) return;
+        const bool inner = rate_inner(r, c);
+        if (!inner && rate_held(r, c)) return;
         bool risky;
-        const float d = rate32(korigin, r, c, idx, &risky);
+        const float d = rate32(korigin, r, c, idx, &risky, inner);
         if (!risky) best = fmaxf(best, d);
         else any_risky = 1;
     });
@@ -701,9 +734,10 @@ __global__ void __launch_bounds__(RED_THREADS) rate_cand_kernel(const float* __r
     const int nact = s_nact;
     double best = 0.0;
     auto cell = [&](const int c[3], long long idx) {
-        if (rate_held(r, c)) return;
+        const bool inner = rate_inner(r, c);
+        if (!inner && rate_held(r, c)) return;
         bool rk;
-        const float d = rate32(korigin, r, c, idx, &rk);
+        const float d = rate32(korigin, r, c, idx, &rk, inner);
         if (rk || d >= thr) best = fmax(best, rate64(korigin, r, c, idx));
     };
     if (nact > RATE_ACTIVE) {
