@@ -1,5 +1,5 @@
 #!/usr/bin/env python
-"""Benchmark: explicit finite-volume sweep on GB300 (arXiv 2209.13768, Sec. 4.1).
+"""Benchmark: explicit finite-volume sweep on GB300 (arXiv 2209.13768, Sec. 3.1).
 
 Default workload: one 512^3 grid, fp32 field, per-cell conductivity
 k ~ lognormal(0, 0.5), x faces Dirichlet 1 / 0, y and z zero-flux,

@@ -79,7 +79,7 @@ int wfa_create_grid(int nx, int ny, int nz, double hx, double hy, double hz, int
                     void* cuda_stream, wfa_grid* out);
 
 /* Free the handle and its device memory (synchronises its stream). NULL is a
- * no-op. The handle is this library's counterpart of a WSE_Array (Sec. 3,
+ * no-op. The handle is this library's counterpart of a WSE_Array (Sec. 2.1,
  * Example Code): the field and its coefficients resident on the device for
  * the whole solve, released here. */
 int wfa_destroy_grid(wfa_grid g);
@@ -96,7 +96,10 @@ int wfa_set_field(wfa_grid g, const float* host_dense);
 int wfa_set_coeffs(wfa_grid g, const float* k_host, double k_uniform, double ux, double uy,
                    double uz);
 
-/* Boundary condition of one face (enum wfa_face). value: the face value for
+/* Boundary condition of one face (enum wfa_face; Sec. 1.1.1, Eq. expl_form
+ * holds the boundary cells at a constant: WFA_BC_DIRICHLET_CELL; the face
+ * Dirichlet, zero-flux, periodic and exchange kinds have no counterpart in
+ * the paper). value: the face value for
  * WFA_BC_DIRICHLET, the held cell value for WFA_BC_DIRICHLET_CELL (which needs
  * an edge >= 3 on that axis), ignored otherwise. A periodic face whose
  * opposite face is not periodic makes the next wfa_step fail with WFA_ERR_BC. */
@@ -111,10 +114,12 @@ int wfa_set_bc(wfa_grid g, int face, int kind, double value);
  * coefficients (WFA_ERR_STATE otherwise). */
 int wfa_stability_dt(wfa_grid g, double* dt_max);
 
-/* Set the time step. dt must be > 0 and <= dt_max (WFA_ERR_UNSTABLE otherwise). */
+/* Set the time step (Sec. 1.1.1: omega = alpha dt / dl^2 in Eq. expl_form).
+ * dt must be > 0 and <= dt_max (WFA_ERR_UNSTABLE otherwise). */
 int wfa_set_dt(wfa_grid g, double dt);
 
-/* Force a kernel configuration instead of the tuned one.
+/* Force a kernel configuration instead of the tuned one (no counterpart in
+ * the paper, whose step is one fused program per tile, Sec. 2.1).
  * depth: time steps fused per pass over the grid (1..8; 0 = automatic).
  * variant: 0 = automatic; 1..2 = one of the compiled tile shapes of the
  * tiled TMA kernel (depth steps per pass); 3 = the column-march kernel (one
@@ -137,13 +142,15 @@ int wfa_set_tuning(wfa_grid g, int depth, int variant);
  * Errors: WFA_ERR_ARG for a NULL grid or planes < 0. */
 int wfa_set_zchunk(wfa_grid g, int planes);
 
-/* The kernel configuration the next wfa_step of this grid uses (after
+/* No counterpart in the paper (a tuning aid, like wfa_set_tuning).
+ * The kernel configuration the next wfa_step of this grid uses (after
  * wfa_set_tuning, wfa_set_zchunk and wfa_autotune): fused depth, variant
  * (as in wfa_set_tuning) and planes per z chunk (0 = automatic). Any output
  * pointer may be NULL. Errors: WFA_ERR_ARG for a NULL grid. */
 int wfa_get_tuning(wfa_grid g, int* depth, int* variant, int* zchunk);
 
-/* Time the compiled kernel configurations (the column-march kernels 3, 4, 5,
+/* No counterpart in the paper (its step has one mapping, a column per tile,
+ * Sec. 2.1). Time the compiled kernel configurations (the column-march kernels 3, 4, 5,
  * kernel 3 also with z chunks of 32, 64, 128 planes and of half the z extent;
  * the tiled TMA kernel at depths 1..8 and two tile shapes) on this grid and
  * use the fastest from now
@@ -161,7 +168,7 @@ int wfa_autotune(wfa_grid g, int* depth, int* variant);
  * applications of Eq. expl_form (Sec. 1.1.1, the explicit time step, T^n ->
  * T^{n+1} for every cell from the values of step n), in the face-flux form
  * given at the top of this file. The paper's fused kernel runs one step per
- * RPC (Sec. 3, Example Code); here a step is one pass of a kernel over the
+ * RPC (Sec. 2.1, Example Code); here a step is one pass of a kernel over the
  * grid, or several steps per pass with temporal blocking.
  * Errors: WFA_ERR_STATE before the field, coefficients and dt are set,
  * WFA_ERR_BC for an unpaired periodic face, WFA_ERR_CUDA. */
@@ -173,7 +180,7 @@ int wfa_steps_done(wfa_grid g, long long* n);
 
 /* Copy the field out as dense fp32 (nx*ny*nz floats). Synchronises the
  * stream. The counterpart of reading a WSE_Array back into a NumPy array
- * (Sec. 3, Example Code), where the WFA's validation mode compares results. */
+ * (Sec. 2.1, Example Code), where the WFA's validation mode compares results. */
 int wfa_read_field(wfa_grid g, float* host_dense);
 
 /* Total heat E = sum_C T_C hx hy hz, summed on the device in fp64 in a fixed
@@ -231,7 +238,7 @@ int wfa_implicit_step(wfa_grid g, double dt, long long n, double rtol, int max_i
  *                     iteration (Sec. 1.1.2);
  *   WFA_CG_PIPELINED  Chronopoulos and Gear's CG, both inner products in one
  *                     reduction and one kernel an iteration (the
- *                     reduction-limited variant Sec. 4.2 points to); w = A r
+ *                     reduction-limited variant Sec. 3.2 points to); w = A r
  *                     and s = A p by recurrence, three more fp32 work fields.
  * Errors: WFA_ERR_ARG for a NULL grid or another value. */
 enum { WFA_CG_CLASSIC = 0, WFA_CG_PIPELINED = 1 };
@@ -249,10 +256,12 @@ int wfa_set_cg_method(wfa_grid g, int method);
 int wfa_boundary_flux(wfa_grid g, double* flux);
 
 /* Bytes of one padded field buffer and of one padded k (or 1/k) buffer of
- * this grid, for callers that own the device memory (below). */
+ * this grid, for callers that own the device memory (below). No counterpart
+ * in the paper (the WFA's arrays live in each tile's own memory, Sec. 1). */
 int wfa_grid_buffer_bytes(wfa_grid g, size_t* field_bytes, size_t* k_bytes);
 
-/* Let caller-owned device memory hold the grid's data (e.g. tensors of a
+/* No counterpart in the paper (the WFA's arrays live in each tile's own memory, Sec. 1).
+ * Let caller-owned device memory hold the grid's data (e.g. tensors of a
  * framework that manages all device memory): d_Ta and d_Tb, field_bytes
  * each, take the two field buffers; d_k and d_r, k_bytes each (both or both
  * NULL), take the per-cell conductivity and its reciprocal, now if the grid
@@ -289,7 +298,7 @@ int wfa_launch_count(wfa_grid g, long long* n);
 /* Synchronise the stream, then give the summed duration in milliseconds and
  * the number of the sampled kernel launches since the last call (0 and 0 when
  * timing is off), and start counting afresh. A profiling aid with no
- * counterpart in the paper (it feeds the bandwidth model of Sec. 4.1.3,
+ * counterpart in the paper (it feeds the bandwidth model of Sec. 3.1.3,
  * Eqs. A_eff and t_it_min, with measured kernel times). */
 int wfa_kernel_time(wfa_grid g, double* ms, long long* launches);
 
@@ -311,8 +320,8 @@ int wfa_inject_alloc_failure(int n);
 
 /* ------------------------------------------------ slabs (z decomposition) -- */
 /* One grid split along z into slabs, each an ordinary grid (Sec. 1, Fig. 1b:
- * domain decomposition; Sec. 3: each WSE tile owns a 1 x 1 x Z column and
- * exchanges neighbour values every step; Eq. iteration_time_model: a step's
+ * domain decomposition; Sec. 2.1: each WSE tile owns a column of cells;
+ * Sec. 3: neighbour values come over the fabric for every product; Eq. iteration_time_model: a step's
  * time is its computation or its halo exchange, whichever is longer, plus the
  * boundary work). A slab holds planes [z0, z1) of the whole grid: nx, ny, the
  * cell size, storage, x / y faces, conductivity (its planes), velocity and dt
@@ -331,7 +340,10 @@ int wfa_inject_alloc_failure(int n);
  * slabs. */
 enum { WFA_PLANES_FIELD = 0, WFA_PLANES_K = 1, WFA_PLANES_RECIP_K = 2 };
 
-/* Device addresses of the planes an exchange face moves, for callers that
+/* Sec. 3: a tile's column receives its neighbours' values for every
+ * product (Sec. 2.1: a column of cells per tile); here one
+ * slab's boundary plane with the next slab's (Sec. 1, Fig. 1b's partition).
+ * Device addresses of the planes an exchange face moves, for callers that
  * move them themselves (slabs on several GPUs or processes, e.g. NCCL send /
  * receive into the receiving GPU's own memory). face: WFA_ZLO or WFA_ZHI,
  * which must be an exchange face. what: WFA_PLANES_FIELD (the buffer that
@@ -347,7 +359,8 @@ enum { WFA_PLANES_FIELD = 0, WFA_PLANES_K = 1, WFA_PLANES_RECIP_K = 2 };
  * a grid with uniform k). */
 int wfa_exchange_planes(wfa_grid g, int face, int what, void** send, void** recv, size_t* plane_bytes);
 
-/* Exchange planes between two slabs on one device: lower's +z exchange face
+/* The neighbour exchange (Sec. 3) between two slabs on one device (Sec. 1,
+ * Fig. 1b's partition along z): lower's +z exchange face
  * meets upper's -z exchange face (lower == upper: one slab whose z axis wraps
  * around). what: WFA_PLANES_FIELD (the current fields) or WFA_PLANES_K
  * (per-cell k and 1/k; nothing for uniform k). Copies are queued on lower's
@@ -356,7 +369,9 @@ int wfa_exchange_planes(wfa_grid g, int face, int what, void** send, void** recv
  * WFA_ERR_BC (not exchange faces), WFA_ERR_CUDA. */
 int wfa_exchange(wfa_grid lower, wfa_grid upper, int what);
 
-/* Advance the slabs gs[0 .. count-1] (in z order, one device) by n steps:
+/* Eq. expl_form on a grid partitioned into z slabs (Sec. 1, Fig. 1b), with
+ * the neighbour exchange (Sec. 3) before every step.
+ * Advance the slabs gs[0 .. count-1] (in z order, one device) by n steps:
  * the conductivity planes are exchanged once, then before every step the
  * field planes of each pair of neighbouring slabs (and of the last and the
  * first, when the z axis wraps), then every slab takes one step. The slabs
@@ -367,7 +382,7 @@ int wfa_slabs_step(wfa_grid* gs, int count, long long n);
 
 /* ----------------------------------------------------------- batching -- */
 
-/* Advance many grids in one go (Sec. 4.1.2: iteration rate at small
+/* Advance many grids in one go (Sec. 3.1.2: iteration rate at small
  * workloads per processor). gs[i] advances steps[i] >= 0 steps; grids may mix
  * storage types and conductivity modes. All grids must share the stream of
  * gs[0], appear once, and have their field, coefficients and dt set. Round
@@ -386,7 +401,7 @@ int wfa_slabs_step(wfa_grid* gs, int count, long long n);
 int wfa_batch_run(wfa_grid* gs, const long long* steps, int count);
 
 /* ------------------------------------------------------------- serving -- */
-/* Serving has no counterpart call in the paper. It applies Sec. 4.1.2's
+/* Serving has no counterpart call in the paper. It applies Sec. 3.1.2's
  * point about small workloads per processor (the explicit step keeps its rate
  * down to about 50 cells per WSE tile, where a distributed code needs
  * thousands) to a stream of independent small solves: many grids resident on
@@ -426,7 +441,9 @@ typedef struct {
     size_t resident_bytes, peak_resident_bytes;
 } wfa_server_stats;
 
-/* Start a continuous-batching server on its own scheduler thread.
+/* Start a continuous-batching server on its own scheduler thread (many
+ * small workloads sharing one processor, Sec. 3.1.2; the paper has no
+ * server).
  * hbm_budget_bytes: admission limit on the device memory of resident
  * requests; max_resident: most requests on the device at once (0 = 1024);
  * quantum: steps a resident request advances per scheduler tick (0 = 64).
@@ -463,7 +480,7 @@ int wfa_server_latency(wfa_server s, long long ticket, double* seconds);
 
 /* Counters and latency percentiles of the server so far (see
  * wfa_server_stats). Serving (see the note above); the iteration-rate and
- * latency figures the paper reports for single solves (Sec. 4) become
+ * latency figures the paper reports for single solves (Sec. 3) become
  * throughput and p50 / p99 latency of a request stream here. */
 int wfa_server_stats_get(wfa_server s, wfa_server_stats* st);
 

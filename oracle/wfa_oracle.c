@@ -419,7 +419,7 @@ int wfa_oracle_implicit(const int64_t n[3], const double h[3], double k_uniform,
 /*
  * The same backward-Euler steps solved by Chronopoulos and Gear's CG: one
  * synchronisation per iteration, both inner products taken together (the
- * reduction-limited Krylov variants Sec. 1.1.2 and Sec. 4.2 point to). In
+ * reduction-limited Krylov variants Sec. 1.1.2 and Sec. 3.2 point to). In
  * exact arithmetic its iterates are those of classic CG; it carries w = A r
  * and s = A p by recurrence instead of applying A to p:
  *   x = T^n on free cells;  r = b - A x;  w = A r

@@ -1,5 +1,5 @@
 // wfa_batch_run: many grids of different sizes and step counts advanced
-// together (Sec. 4.1.2: iteration rate at small workloads per processor —
+// together (Sec. 3.1.2: iteration rate at small workloads per processor —
 // one launch per grid and step would leave most of the GPU idle for grids of
 // 16^3..128^3 cells, and every launch would pay its own latency).
 //

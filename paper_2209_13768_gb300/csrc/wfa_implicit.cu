@@ -794,7 +794,7 @@ __global__ void __launch_bounds__(CG_TX * CG_TY, CgOcc<KVAR>::blocks) cg_spmv_sm
 
 // ---------------------------------------------------------------- cg_pipe --
 // One iteration of Chronopoulos and Gear's CG in one kernel and one
-// reduction (the reduction-limited variant Sec. 4.2 points to): with alpha,
+// reduction (the reduction-limited variant Sec. 3.2 points to): with alpha,
 // beta of this iteration,
 //   s = w + beta s,  p = r + beta p,  x += alpha p,  r' = r - alpha s,
 //   w' = A r',  gamma' = r'.r',  delta' = w'.r'

@@ -1,5 +1,6 @@
 // One grid split into slabs along z (domain decomposition, Sec. 1, Fig. 1b;
-// Sec. 3's 1 x 1 x Z columns exchange neighbour values every step).
+// Sec. 2.1's 1 x 1 x Z columns, whose neighbour values come over the fabric
+// for every product, Sec. 3).
 //
 // A slab is an ordinary grid whose z faces towards its neighbours are
 // exchange faces (WFA_BC_EXCHANGE): the kernels read the neighbour's cells

@@ -1,6 +1,6 @@
 """One grid split into slabs along z (domain decomposition: Sec. 1, Fig. 1b;
-each WSE tile's 1 x 1 x Z column exchanges neighbour values every step,
-Sec. 3; the step time model of Eq. iteration_time_model).
+each WSE tile's 1 x 1 x Z column, Sec. 2.1, receives its neighbours' values
+for every product, Sec. 3; the step time model of Eq. iteration_time_model).
 
 Two forms, both over the C ABI's exchange faces (``WFA_BC_EXCHANGE``):
 

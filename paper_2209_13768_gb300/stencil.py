@@ -1,7 +1,7 @@
 """Expression front end: explicit field updates written as array expressions
 with relative offsets, compiled into one fused CUDA kernel for sm_103a.
 
-The WFA's Python front end (Sec. 3, Example Code) writes a time step as
+The WFA's Python front end (Sec. 2.1, Example Code) writes a time step as
 NumPy-like operations on arrays whose indices are relative to the cell
 (-1, 0, +1 for the neighbour on each side), and can fuse a whole step into one
 kernel. The same here: a `Field` indexed with an offset triple is the value of

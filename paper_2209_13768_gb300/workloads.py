@@ -1,5 +1,5 @@
 """Seeded synthetic inputs with the shapes and distributions of the paper's
-workloads (uniform Cartesian grids, omega = 1/10, Sec. 1.1.1 and Sec. 4.1) and
+workloads (uniform Cartesian grids, omega = 1/10, Sec. 1.1.1 and Sec. 3.1) and
 of the benchmark configurations built on them. The paper uses no dataset; these
 stand in for its heat-equation test problems.
 
