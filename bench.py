@@ -803,7 +803,7 @@ def split_bench(args, rank, world, dist, local):
 
 
 KERNEL_NAMES = {3: "sweep_col", 4: "sweep_col2 (two steps per pass)", 5: "sweep_col (boundaries in place)",
-                6: "sweep_col (8 cells a thread)", 7: "sweep_t2 (two steps per pass, TMA-staged planes)",
+                6: "sweep_col (8 cells a thread; 16 for bf16 with uniform k)", 7: "sweep_t2 (two steps per pass, TMA-staged planes)",
                 -1: "sweep_simple"}
 
 
