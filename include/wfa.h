@@ -128,7 +128,10 @@ int wfa_set_dt(wfa_grid g, double dt);
  * kernel (uniform k; two steps per pass, shared-memory stage plane; with
  * per-cell k it acts as 3); 5 = the column-march kernel with boundary cells
  * and periodic copies inside the pass (one launch per step; for small
- * grids); -1 = the plain one-thread-per-column kernel (one step per pass; a
+ * grids); 6 = the column-march kernel with 8 cells a thread (16 for bf16
+ * fields with uniform k); 7 = two steps per pass with TMA-staged input
+ * planes (uniform k; with per-cell k it acts as 3); -1 = the plain
+ * one-thread-per-column kernel (one step per pass; a
  * second, independent realisation of the same per-cell arithmetic).
  * Results do not depend on the choice: every kernel evaluates the same fixed
  * per-cell expression, so fields are bit-identical. */
@@ -150,11 +153,11 @@ int wfa_set_zchunk(wfa_grid g, int planes);
 int wfa_get_tuning(wfa_grid g, int* depth, int* variant, int* zchunk);
 
 /* No counterpart in the paper (its step has one mapping, a column per tile,
- * Sec. 2.1). Time the compiled kernel configurations (the column-march kernels 3, 4, 5,
- * kernel 3 also with z chunks of 32, 64, 128 planes and of half the z extent;
- * the tiled TMA kernel at depths 1..8 and two tile shapes) on this grid and
- * use the fastest from now
- * on. The trials run on a scratch copy of the field: the field and the step
+ * Sec. 2.1). Time the compiled kernel configurations (the column-march kernels 3 to 7,
+ * kernel 3 also with z chunks of 8, 12, 32, 64, 128 planes and of half the
+ * z extent, kernel 6 with chunks of 12 and 32; the tiled TMA kernel at
+ * depths 1..8 and two tile shapes) on this grid and use the fastest from
+ * now on. The trials run on a scratch copy of the field: the field and the step
  * count are left as they were, and results never depend on the choice. The
  * choice is also remembered for later grids of the same size class (device
  * compute capability and SM count, storage,
