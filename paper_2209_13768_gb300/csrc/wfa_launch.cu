@@ -155,7 +155,9 @@ static int num_sms() {
 // ------------------------------------------------------------ tuning ------
 // Kernel configuration of a pass: variant (COL_VARIANT = column march, one
 // step; INPLACE_VARIANT = the same with boundaries and periodic copies in the
-// pass itself; FUSED_VARIANT = column march, two steps, uniform k; 1..NUM_TILE_VARIANTS
+// pass itself; FUSED_VARIANT = column march, two steps, uniform k;
+// WIDE_VARIANT = column march, 8 cells a thread (16 for bf16 with uniform k);
+// T2_VARIANT = two steps, TMA-staged planes, uniform k; 1..NUM_TILE_VARIANTS
 // = tiled TMA kernel, `depth` fused steps; -1 = the plain one-column kernel)
 // and depth.
 struct Choice {
