@@ -26,7 +26,9 @@
 // block stops and the call returns WFA_ERR_TIMEOUT. WFA_BATCH_MODE=stream
 // issues the per-round launches directly on the stream. All three give the
 // same fields bit for bit; the per-round graph was the fastest measured
-// (256 grids of 16..128 cells per edge: 200 GLUPS against 168 persistent).
+// (256 grids of 16..128 cells per edge, side by side with an earlier column
+// march: 200 GLUPS against 168 persistent; the per-round graph now runs
+// about 305).
 #include <stdlib.h>
 #include <string.h>
 
