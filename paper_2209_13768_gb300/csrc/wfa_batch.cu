@@ -579,8 +579,8 @@ int batch_launch(wfa_grid* gs, const long long* steps, int count, int slot, bool
         b.ncx = (g->n[0] + 3) / 4;
         b.ncols = b.ncx * g->n[1];
         // z chunks of about 16 planes (the 256-grid batch: 1% faster than 12,
-        // 1.2% than 8), shorter (down to 4) while a grid has fewer pairs than
-        // a block has threads
+        // 1.2% than 8, 1.5% than 24), shorter (down to 4) while a grid has
+        // fewer pairs than a block has threads
         const int nz = g->n[2];
         int nch = std::max((nz + 15) / 16, (MG_THREADS + b.ncols - 1) / b.ncols);
         nch = std::max(1, std::min(nch, nz / 4));
